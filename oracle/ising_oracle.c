@@ -1,0 +1,480 @@
+/*
+ * ising_oracle.c -- the ORACLE for the replica-parallel Metropolis sweep with
+ * parallel tempering (Dickson, Karimi & Hamze, "Importance of Explicit
+ * Vectorization for CPU and GPU Software Performance", arXiv:1004.0024).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously correct CPU
+ * restatement of what the GPU path computes.  It shares no code, header,
+ * table or constant generator with the CUDA library; only the tests, the
+ * smoke check and bench.py's cpu_baseline / reference leg may call it.
+ *
+ * What it follows, step by step:
+ *   - Ising cost function (paper section 1):
+ *         f(s) = -sum_i h_i s_i - sum_{i,j} J_ij s_i s_j ,  s_i in {-1,+1}.
+ *     Reading: every undirected edge is counted once in the pair sum.  This
+ *     is the reading under which the field update of Figure 6,
+ *     h_eff[target] -= 2*S_mul*J, keeps h_eff_i = h_i + sum_j J_ij s_j.
+ *   - Metropolis sweep (Figure 1): visit spins i = 0..N-1 in index order;
+ *     draw one uniform; if it is below the flip probability, flip s_i and
+ *     update the data of every adjacent spin (Figure 6: f_j -= 2 s_i J_ij,
+ *     with s_i the value before the flip).
+ *     Readings: flip probability = min(1, exp(-beta dE)), dE = 2 s_i f_i.
+ *     The uniform is a uint32 word u and the probability is the integer
+ *     threshold T_beta(k) = floor(2^32 exp(-2 beta k)) built in FP64, so the
+ *     test "uniform < probability" is u < T_beta(k) (strict, as in Figure 1),
+ *     and k = s_i f_i <= 0 always flips.  One word is drawn per visit, also
+ *     when the flip is certain.
+ *   - MT19937 (paper ref [9], the generator of section 3 / Figure 8):
+ *     Matsumoto & Nishimura's recurrence and tempering, seeded with their
+ *     init_genrand.  One generator per replica, seeded with seed + r.
+ *   - Parallel tempering (section 1 and section 3.1 mention it; the rule is in
+ *     the paper's refs [16], [17], not in the paper).  Reading: standard
+ *     replica exchange between adjacent inverse temperatures, label swaps
+ *     (states stay in their slots), pass p tries the pairs (k, k+1) with
+ *     k = p mod 2, ascending k, accept if d = E_lo - E_hi <= 0 or
+ *     u < floor(2^32 exp(-(beta_{k+1} - beta_k) d)); one word per attempted
+ *     pair from a per-instance swap stream (MT19937 seeded with seed + R).
+ *   - Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) as the alternative
+ *     counter-based generator, with this counter map (spin i = t*S + q for a
+ *     declared slice size S):
+ *         sweep word  : key (seed, r),          ctr ((t>>2)*S + q, c, inst, 0), lane t&3
+ *         init word   : key (seed, r),          ctr ((t>>2)*S + q, 0, inst, 3), lane t&3
+ *         swap word   : key (seed, 0xFFFFFFFF), ctr (j>>2, p, inst, 1),       lane j&3
+ *     where c counts the sweeps the instance has done, p the PT passes, and
+ *     j = k>>1 is the ordinal of pair (k, k+1) within its pass.
+ *   - Initial state: s_i = +1 when bit 31 of the i-th init word is set, else
+ *     -1.  For MT19937 the init words are the first N outputs of the replica's
+ *     stream, and sweep c uses outputs N(1+c) .. N(2+c)-1.  Slot r starts at
+ *     temperature index r.
+ *
+ * Replicas are independent between PT passes, so sweeps of different
+ * replicas run on a pthread pool (one replica chunk per thread); the order of
+ * work inside a replica is exactly the sequential order above.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#include <pthread.h>
+#include <unistd.h>
+
+/* ---------------------------------------------------------------- MT19937 */
+/* Matsumoto & Nishimura (1998): degree n = 624, middle word m = 397,
+ * twist matrix a = 0x9908B0DF, upper/lower split at bit 31, tempering
+ * (u,d) = (11, 0xFFFFFFFF), (s,b) = (7, 0x9D2C5680), (t,c) = (15, 0xEFC60000),
+ * l = 18.  Paper Figure 8 shows the two twist lines restated in regenerate(). */
+typedef struct {
+    uint32_t x[624];
+    int next;
+} orc_mt;
+
+void orc_mt_seed(orc_mt* g, uint32_t seed)
+{
+    g->x[0] = seed;
+    for (int i = 1; i < 624; i++) {
+        uint32_t prev = g->x[i - 1];
+        g->x[i] = 1812433253u * (prev ^ (prev >> 30)) + (uint32_t)i;
+    }
+    g->next = 624;
+}
+
+static void orc_mt_regenerate(orc_mt* g)
+{
+    for (int k = 0; k < 624; k++) {
+        uint32_t y = (g->x[k] & 0x80000000u) | (g->x[(k + 1) % 624] & 0x7FFFFFFFu);
+        uint32_t v = g->x[(k + 397) % 624] ^ (y >> 1);
+        if (y & 1u)
+            v ^= 0x9908B0DFu;
+        g->x[k] = v;
+    }
+    g->next = 0;
+}
+
+uint32_t orc_mt_next(orc_mt* g)
+{
+    if (g->next >= 624)
+        orc_mt_regenerate(g);
+    uint32_t y = g->x[g->next++];
+    y ^= (y >> 11);
+    y ^= (y << 7) & 0x9D2C5680u;
+    y ^= (y << 15) & 0xEFC60000u;
+    y ^= (y >> 18);
+    return y;
+}
+
+void orc_mt_stream(uint32_t seed, int64_t n, uint32_t* out)
+{
+    orc_mt g;
+    orc_mt_seed(&g, seed);
+    for (int64_t i = 0; i < n; i++)
+        out[i] = orc_mt_next(&g);
+}
+
+/* ---------------------------------------------------------- Philox4x32-10 */
+/* Salmon et al. (SC'11): 10 rounds; each round multiplies counter words 0 and
+ * 2 by 0xD2511F53 and 0xCD9E8D57 (64-bit products split into hi/lo), then
+ * out = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); between rounds the key is
+ * bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85). */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* One Philox word under the counter map described in the file header. */
+static uint32_t philox_word(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                            uint32_t c2, uint32_t c3, int lane)
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {k0, k1};
+    uint32_t out[4];
+    orc_philox(ctr, key, out);
+    return out[lane];
+}
+
+/* ------------------------------------------------------------- thresholds */
+/* T_beta(k) = floor(2^32 exp(-2 beta k)) for k >= 1, in FP64. */
+uint32_t orc_flip_threshold(double beta, int64_t k)
+{
+    double p = exp(-2.0 * beta * (double)k);
+    return (uint32_t)floor(ldexp(p, 32));
+}
+
+/* S(d) = floor(2^32 exp(-dbeta d)) for d >= 1, dbeta = beta_{k+1} - beta_k. */
+uint32_t orc_swap_threshold(double dbeta, int64_t d)
+{
+    double p = exp(-dbeta * (double)d);
+    return (uint32_t)floor(ldexp(p, 32));
+}
+
+/* ----------------------------------------------------- energy and fields */
+/* f_i = h_i + sum_j J_ij s_j (the quantity Figure 6 keeps up to date). */
+void orc_fields(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                const int32_t* J, const int32_t* h, const int8_t* s, int64_t* f)
+{
+    for (int32_t i = 0; i < n; i++) {
+        int64_t acc = h[i];
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; e++)
+            acc += (int64_t)J[e] * (int64_t)s[col[e]];
+        f[i] = acc;
+    }
+}
+
+/* Cost function of section 1, each undirected edge once (CSR holds both
+ * directions, so the pair term takes j > i only). */
+int64_t orc_energy(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                   const int32_t* J, const int32_t* h, const int8_t* s)
+{
+    int64_t e = 0;
+    for (int32_t i = 0; i < n; i++) {
+        e -= (int64_t)h[i] * s[i];
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; k++)
+            if (col[k] > i)
+                e -= (int64_t)J[k] * s[i] * s[col[k]];
+    }
+    return e;
+}
+
+/* ------------------------------------------------------------- simulation */
+typedef struct {
+    /* graph */
+    int32_t n, slice;
+    int32_t *row_ptr, *col, *J, *h;
+    int64_t kmax; /* largest possible |f_i| */
+    /* ladder */
+    int32_t R;
+    double* beta;          /* [R] ascending */
+    uint32_t** thr;        /* [R][kmax+1], thr[k][0] unused */
+    /* rng */
+    uint32_t seed, inst;
+    int32_t mode;          /* 0 = MT19937, 1 = Philox4x32-10 */
+    orc_mt* mt;            /* [R] replica streams (mode 0) */
+    orc_mt swap_mt;        /* swap stream (mode 0) */
+    /* state */
+    int8_t* s;             /* [R][n] */
+    int64_t* f;            /* [R][n] */
+    int64_t* E;            /* [R] */
+    int32_t* temp_of_slot; /* [R] */
+    int32_t* slot_of_temp; /* [R] */
+    uint64_t* swap_acc;    /* [R-1] */
+    uint64_t sweeps, passes;
+    int32_t threads;
+} orc_sim;
+
+static uint32_t init_word(orc_sim* m, int32_t r, int32_t i)
+{
+    if (m->mode == 0)
+        return orc_mt_next(&m->mt[r]);
+    int32_t t = i / m->slice, q = i % m->slice;
+    return philox_word(m->seed, (uint32_t)r, (uint32_t)((t >> 2) * m->slice + q), 0u,
+                       m->inst, 3u, t & 3);
+}
+
+/* Figure 1 on one replica, with the Figure 6 neighbour update, repeated for
+ * `nsweeps` sweeps.  Philox words depend on the instance sweep counter, so
+ * the block starts from counter `c0` (replicas of one block run
+ * concurrently, each with its own copy of the counter). */
+static void sweep_replica_block(orc_sim* m, int32_t r, uint64_t c0, int64_t nsweeps)
+{
+    int8_t* s = m->s + (int64_t)r * m->n;
+    int64_t* f = m->f + (int64_t)r * m->n;
+    const uint32_t* T = m->thr[m->temp_of_slot[r]];
+    for (int64_t c = 0; c < nsweeps; c++) {
+        int64_t dE = 0;
+        uint32_t sweep_id = (uint32_t)(c0 + (uint64_t)c);
+        for (int32_t i = 0; i < m->n; i++) {
+            uint32_t u;
+            if (m->mode == 0) {
+                u = orc_mt_next(&m->mt[r]);
+            } else {
+                int32_t t = i / m->slice, q = i % m->slice;
+                u = philox_word(m->seed, (uint32_t)r, (uint32_t)((t >> 2) * m->slice + q),
+                                sweep_id, m->inst, 0u, t & 3);
+            }
+            int64_t k = (int64_t)s[i] * f[i];
+            int accept = (k <= 0) || (u < T[k]);
+            if (accept) {
+                int64_t two_s = 2 * (int64_t)s[i];
+                for (int32_t e = m->row_ptr[i]; e < m->row_ptr[i + 1]; e++)
+                    f[m->col[e]] -= two_s * m->J[e];
+                s[i] = (int8_t)(-s[i]);
+                dE += 2 * k;
+            }
+        }
+        m->E[r] += dE;
+    }
+}
+
+typedef struct {
+    orc_sim* m;
+    int32_t r0, r1;
+    uint64_t c0;
+    int64_t nsweeps;
+} block_job;
+
+static void* block_worker(void* arg)
+{
+    block_job* jb = (block_job*)arg;
+    for (int32_t r = jb->r0; r < jb->r1; r++)
+        sweep_replica_block(jb->m, r, jb->c0, jb->nsweeps);
+    return NULL;
+}
+
+/* n sweeps of every replica with no PT pass in between (replicas are
+ * independent, so they run on the thread pool). */
+void orc_sim_sweep(orc_sim* m, int64_t nsweeps)
+{
+    if (nsweeps <= 0)
+        return;
+    int32_t nt = m->threads < m->R ? m->threads : m->R;
+    if (nt <= 1) {
+        for (int32_t r = 0; r < m->R; r++)
+            sweep_replica_block(m, r, m->sweeps, nsweeps);
+    } else {
+        pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nt);
+        block_job* jobs = (block_job*)malloc(sizeof(block_job) * nt);
+        for (int32_t w = 0; w < nt; w++) {
+            jobs[w].m = m;
+            jobs[w].r0 = (int32_t)((int64_t)m->R * w / nt);
+            jobs[w].r1 = (int32_t)((int64_t)m->R * (w + 1) / nt);
+            jobs[w].c0 = m->sweeps;
+            jobs[w].nsweeps = nsweeps;
+            pthread_create(&th[w], NULL, block_worker, &jobs[w]);
+        }
+        for (int32_t w = 0; w < nt; w++)
+            pthread_join(th[w], NULL);
+        free(th);
+        free(jobs);
+    }
+    m->sweeps += (uint64_t)nsweeps;
+}
+
+/* One PT pass (parity = pass count mod 2). */
+void orc_sim_pt(orc_sim* m)
+{
+    uint32_t p = (uint32_t)m->passes;
+    for (int32_t k = (int32_t)(m->passes & 1u); k + 1 < m->R; k += 2) {
+        uint32_t u;
+        if (m->mode == 0) {
+            u = orc_mt_next(&m->swap_mt);
+        } else {
+            uint32_t j = (uint32_t)(k >> 1);
+            u = philox_word(m->seed, 0xFFFFFFFFu, j >> 2, p, m->inst, 1u, (int)(j & 3u));
+        }
+        int32_t a = m->slot_of_temp[k], b = m->slot_of_temp[k + 1];
+        int64_t d = m->E[a] - m->E[b];
+        int accept = (d <= 0) || (u < orc_swap_threshold(m->beta[k + 1] - m->beta[k], d));
+        if (accept) {
+            m->slot_of_temp[k] = b;
+            m->slot_of_temp[k + 1] = a;
+            m->temp_of_slot[a] = k + 1;
+            m->temp_of_slot[b] = k;
+            m->swap_acc[k]++;
+        }
+    }
+    m->passes++;
+}
+
+/* n sweeps; after every `swap_every`-th sweep of this call, one PT pass
+ * (swap_every <= 0: no PT). */
+void orc_sim_run(orc_sim* m, int64_t nsweeps, int32_t swap_every)
+{
+    if (swap_every <= 0) {
+        orc_sim_sweep(m, nsweeps);
+        return;
+    }
+    int64_t done = 0;
+    while (done < nsweeps) {
+        int64_t chunk = swap_every;
+        if (chunk > nsweeps - done)
+            chunk = nsweeps - done;
+        orc_sim_sweep(m, chunk);
+        done += chunk;
+        if (chunk == swap_every)
+            orc_sim_pt(m);
+    }
+}
+
+orc_sim* orc_sim_create(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                        const int32_t* J, const int32_t* h, int32_t slice, int32_t R,
+                        const double* beta, uint32_t seed, uint32_t inst, int32_t mode,
+                        int32_t threads)
+{
+    orc_sim* m = (orc_sim*)calloc(1, sizeof(orc_sim));
+    int32_t nnz = row_ptr[n];
+    m->n = n;
+    m->slice = slice > 0 ? slice : n;
+    m->row_ptr = (int32_t*)malloc(sizeof(int32_t) * (n + 1));
+    m->col = (int32_t*)malloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+    m->J = (int32_t*)malloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+    m->h = (int32_t*)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    memcpy(m->row_ptr, row_ptr, sizeof(int32_t) * (n + 1));
+    if (nnz > 0) {
+        memcpy(m->col, col, sizeof(int32_t) * nnz);
+        memcpy(m->J, J, sizeof(int32_t) * nnz);
+    }
+    if (n > 0)
+        memcpy(m->h, h, sizeof(int32_t) * n);
+    m->kmax = 0;
+    for (int32_t i = 0; i < n; i++) {
+        int64_t b = llabs((long long)h[i]);
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; e++)
+            b += llabs((long long)J[e]);
+        if (b > m->kmax)
+            m->kmax = b;
+    }
+    m->R = R;
+    m->beta = (double*)malloc(sizeof(double) * R);
+    memcpy(m->beta, beta, sizeof(double) * R);
+    m->thr = (uint32_t**)malloc(sizeof(uint32_t*) * R);
+    for (int32_t k = 0; k < R; k++) {
+        m->thr[k] = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m->kmax + 1));
+        m->thr[k][0] = 0; /* never read: k <= 0 flips unconditionally */
+        for (int64_t x = 1; x <= m->kmax; x++)
+            m->thr[k][x] = orc_flip_threshold(beta[k], x);
+    }
+    m->seed = seed;
+    m->inst = inst;
+    m->mode = mode;
+    m->s = (int8_t*)malloc((size_t)R * (n > 0 ? n : 1));
+    m->f = (int64_t*)malloc(sizeof(int64_t) * (size_t)R * (n > 0 ? n : 1));
+    m->E = (int64_t*)malloc(sizeof(int64_t) * R);
+    m->temp_of_slot = (int32_t*)malloc(sizeof(int32_t) * R);
+    m->slot_of_temp = (int32_t*)malloc(sizeof(int32_t) * R);
+    m->swap_acc = (uint64_t*)calloc(R > 1 ? R - 1 : 1, sizeof(uint64_t));
+    if (mode == 0) {
+        m->mt = (orc_mt*)malloc(sizeof(orc_mt) * R);
+        for (int32_t r = 0; r < R; r++)
+            orc_mt_seed(&m->mt[r], seed + (uint32_t)r);
+        orc_mt_seed(&m->swap_mt, seed + (uint32_t)R);
+    }
+    for (int32_t r = 0; r < R; r++) {
+        int8_t* s = m->s + (int64_t)r * n;
+        for (int32_t i = 0; i < n; i++)
+            s[i] = (init_word(m, r, i) >> 31) ? (int8_t)1 : (int8_t)-1;
+        orc_fields(n, m->row_ptr, m->col, m->J, m->h, s, m->f + (int64_t)r * n);
+        m->E[r] = orc_energy(n, m->row_ptr, m->col, m->J, m->h, s);
+        m->temp_of_slot[r] = r;
+        m->slot_of_temp[r] = r;
+    }
+    if (threads <= 0) {
+        long c = sysconf(_SC_NPROCESSORS_ONLN);
+        threads = c > 0 ? (int32_t)c : 1;
+    }
+    m->threads = threads;
+    return m;
+}
+
+void orc_sim_read(const orc_sim* m, int8_t* spins, int64_t* fields, int64_t* energy,
+                  int32_t* temp_of_slot, uint64_t* counters, uint64_t* swap_acc)
+{
+    size_t rn = (size_t)m->R * (size_t)m->n;
+    if (spins)
+        memcpy(spins, m->s, rn);
+    if (fields)
+        memcpy(fields, m->f, rn * sizeof(int64_t));
+    if (energy)
+        memcpy(energy, m->E, sizeof(int64_t) * m->R);
+    if (temp_of_slot)
+        memcpy(temp_of_slot, m->temp_of_slot, sizeof(int32_t) * m->R);
+    if (counters) {
+        counters[0] = m->sweeps;
+        counters[1] = m->passes;
+    }
+    if (swap_acc && m->R > 1)
+        memcpy(swap_acc, m->swap_acc, sizeof(uint64_t) * (m->R - 1));
+}
+
+int32_t orc_sim_threads(const orc_sim* m) { return m->threads; }
+
+void orc_sim_destroy(orc_sim* m)
+{
+    if (!m)
+        return;
+    for (int32_t k = 0; k < m->R; k++)
+        free(m->thr[k]);
+    free(m->thr);
+    free(m->beta);
+    free(m->row_ptr);
+    free(m->col);
+    free(m->J);
+    free(m->h);
+    free(m->s);
+    free(m->f);
+    free(m->E);
+    free(m->temp_of_slot);
+    free(m->slot_of_temp);
+    free(m->swap_acc);
+    free(m->mt);
+    free(m);
+}
+
+/* Overwrite the spins of slot r (tests start chains from chosen states);
+ * fields and energy are recomputed from scratch. */
+void orc_sim_set_spins(orc_sim* m, int32_t r, const int8_t* spins)
+{
+    int8_t* s = m->s + (int64_t)r * m->n;
+    memcpy(s, spins, (size_t)m->n);
+    orc_fields(m->n, m->row_ptr, m->col, m->J, m->h, s, m->f + (int64_t)r * m->n);
+    m->E[r] = orc_energy(m->n, m->row_ptr, m->col, m->J, m->h, s);
+}
