@@ -1,0 +1,194 @@
+/*
+ * ising_gb300.h -- C ABI of the GB300 (sm_103a) replica-parallel Metropolis
+ * sweep with parallel tempering.
+ *
+ * Method: Dickson, Karimi & Hamze, "Importance of Explicit Vectorization for
+ * CPU and GPU Software Performance" (arXiv:1004.0024).  The sampled model is
+ * the Ising cost function of section 1,
+ *     E(s) = -sum_i h_i s_i - sum_{edges (i,j)} J_ij s_i s_j ,   s_i = +-1,
+ * (each undirected edge counted once), swept in the fixed sequential order of
+ * Figure 1 with incrementally updated integer local fields
+ * f_i = h_i + sum_j J_ij s_j (Figure 6: f_j -= 2 s_i J_ij after s_i flips),
+ * under parallel tempering between adjacent inverse temperatures
+ * (section 1, "use Parallel Tempering"; section 3.1).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns int32_t: ISING_OK (0) or a negative ISING_ERR_*.
+ *     ising_last_error() returns a thread-local message for the last failure.
+ *   - The caller owns every array it passes; input arrays are copied before the
+ *     call returns and may be freed afterwards.  The library owns all device
+ *     state of a handle until ising_destroy().
+ *   - Unless stated otherwise, pointers are HOST pointers.
+ *   - Work is enqueued asynchronously on the handle's CUDA stream
+ *     (ising_set_stream; default: the legacy default stream).  Calls that
+ *     return data to host memory synchronise that stream.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - Spin index i = t*S + q for a graph declared as M identical slices of
+ *     S = n/M spins (t = slice, q = site in the slice); M = 1 means "no slice
+ *     structure declared".
+ */
+#ifndef ISING_GB300_H
+#define ISING_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define ISING_OK 0
+#define ISING_ERR_INVALID_ARG (-1)      /* bad size, pointer, ladder, mode   */
+#define ISING_ERR_ASYMMETRIC_J (-2)     /* J_ij != J_ji or (i,j) w/o (j,i)   */
+#define ISING_ERR_SELF_LOOP_OR_DUP (-3) /* i in row i, or a column repeated  */
+#define ISING_ERR_FIELD_OVERFLOW (-4)   /* max_i |h_i|+sum_j|J_ij| too wide  */
+#define ISING_ERR_NOT_INITIALISED (-5)  /* replicas_init not called yet      */
+#define ISING_ERR_OOM (-6)              /* device allocation failed          */
+#define ISING_ERR_CUDA (-7)             /* CUDA runtime error                */
+#define ISING_ERR_TIMEOUT (-8)          /* a bounded device wait gave up     */
+#define ISING_ERR_UNSUPPORTED (-9)      /* valid input outside kernel limits */
+
+/* ---- random number generators ---- */
+#define ISING_RNG_MT19937 0 /* one MT19937 per replica, init_genrand(seed + r);
+                               PT swap stream init_genrand(seed + R)          */
+#define ISING_RNG_PHILOX 1  /* Philox4x32-10, key (seed, r); see replicas_init */
+
+typedef struct ising_s* ising_t;
+
+/* Thread-local message describing the last non-OK status (never NULL). */
+const char* ising_last_error(void);
+
+/*
+ * ising_create -- validate a sparse Ising model and upload its tables.
+ *   n        number of spins (1 .. 2^24).
+ *   row_ptr  [n+1] CSR offsets, row_ptr[0] = 0, non-decreasing.
+ *   col      [row_ptr[n]] neighbour indices in [0, n); both directions of
+ *            every edge are listed; no self loops, no repeats in a row.
+ *   J        [row_ptr[n]] integer couplings, J of (i,j) equal to J of (j,i),
+ *            |J| <= 32767.
+ *   h        [n] integer biases.
+ *   n_slices M >= 1: the graph is M identical slices of S = n/M spins in a
+ *            Trotter ring (spin (q,t) coupled to (q,t+-1 mod M) with a
+ *            per-site coupling; h and spatial couplings identical in every
+ *            slice).  The declaration is verified; M = 1 accepts any graph.
+ *   flags    reserved, pass 0.
+ *   out      receives the handle.
+ * Errors: INVALID_ARG (sizes, ranges, declared slice structure not found),
+ * SELF_LOOP_OR_DUP, ASYMMETRIC_J, UNSUPPORTED (slice larger than the kernel's
+ * shared-memory limits), OOM, CUDA.
+ * Reference: the model of section 1; per-spin (target, J) records with the two
+ * Trotter ("tau") edges kept apart from the spatial ones, section 2.2 and
+ * Figure 6.
+ */
+int32_t ising_create(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* J,
+                     const int32_t* h, int32_t n_slices, uint32_t flags, ising_t* out);
+
+/* Use `cuda_stream` (a cudaStream_t, NULL = legacy default stream) for all
+ * later work of this handle. */
+int32_t ising_set_stream(ising_t h, void* cuda_stream);
+
+/*
+ * ising_replicas_init -- allocate R replicas and draw their initial states.
+ *   R          number of replicas = number of temperatures (1 .. 2^20).
+ *   betas      [R] inverse temperatures, strictly ascending, > 0.  Slot r
+ *              starts at temperature index r.
+ *   seed       base seed.
+ *   rng_mode   ISING_RNG_MT19937 or ISING_RNG_PHILOX.  MT19937: slot r owns
+ *              init_genrand(seed + r); its first n outputs are the initial
+ *              spins (s_i = +1 iff bit 31 is set) and sweep c consumes outputs
+ *              n(1+c) .. n(2+c)-1, one per visited spin in index order.
+ *              Philox4x32-10: key (seed, r), spin i = t*S + q of sweep c uses
+ *              lane t&3 of counter ((t>>2)*S + q, c, instance, 0) and the
+ *              initial spin lane t&3 of ((t>>2)*S + q, 0, instance, 3);
+ *              instance is 0 for a handle made by ising_create.
+ *   field_bits 16 or 32: width of the stored local fields.  16 requires
+ *              max_i |h_i| + sum_j |J_ij| <= 32767.
+ * Builds, in FP64 on the host, the flip thresholds
+ * T_beta(k) = floor(2^32 exp(-2 beta k)) (flip iff k = s_i f_i <= 0 or
+ * u < T_beta(k), Figure 1 with the Metropolis probability) and the swap
+ * thresholds floor(2^32 exp(-(beta_{k+1}-beta_k) d)).
+ * Re-initialising an initialised handle discards its replicas.
+ * Errors: INVALID_ARG, FIELD_OVERFLOW, UNSUPPORTED, OOM, CUDA.
+ */
+int32_t ising_replicas_init(ising_t h, int32_t R, const double* betas, uint32_t seed,
+                            int32_t rng_mode, int32_t field_bits);
+
+/*
+ * ising_sweep -- n sequential Metropolis sweeps (Figure 1) of every replica,
+ * no PT pass in between.  Each sweep visits spins 0..n-1 of each replica in
+ * index order (executed as a dependency-level wavefront that reproduces that
+ * order exactly).  Asynchronous.  Errors: NOT_INITIALISED, INVALID_ARG, CUDA.
+ */
+int32_t ising_sweep(ising_t h, int64_t n);
+
+/*
+ * ising_pt_swap -- one parallel-tempering pass.  Pass p (0-based count of
+ * passes so far) tries the pairs (k, k+1) with k = p mod 2 in ascending k and
+ * swaps their temperature labels iff d = E(slot at k) - E(slot at k+1) <= 0 or
+ * u < floor(2^32 exp(-(beta_{k+1}-beta_k) d)).  Words: MT19937 swap stream
+ * init_genrand(seed + R), one per attempted pair in order; Philox: key
+ * (seed, 0xFFFFFFFF), lane j&3 of counter (j>>2, p, instance, 1), j = k>>1.
+ * Asynchronous.  Errors: NOT_INITIALISED, CUDA.
+ */
+int32_t ising_pt_swap(ising_t h);
+
+/*
+ * ising_run -- n sweeps with one PT pass after every swap_every-th sweep of
+ * this call (swap_every <= 0: no PT).  The sequence is recorded once as a CUDA
+ * graph per (n, swap_every) and replayed.  When all replicas fit on the GPU at
+ * once the whole run is one persistent launch that keeps every replica in
+ * shared memory and exchanges energies through a bounded grid barrier.
+ * Asynchronous.  Errors: NOT_INITIALISED, INVALID_ARG, TIMEOUT (reported by a
+ * later synchronising call), CUDA.
+ */
+int32_t ising_run(ising_t h, int64_t n, int32_t swap_every);
+
+/*
+ * ising_read_state -- copy the state to host buffers and synchronise.
+ *   spins        [R*n] int8, slot-major (slot r, spin i at r*n + i), or NULL.
+ *   fields       [R*n] int32 local fields f_i, slot-major, or NULL.
+ *   energy       [R] int64 energies, by slot, or NULL.
+ *   temp_of_slot [R] int32 temperature index held by each slot, or NULL.
+ *   counters     [2] uint64 {sweeps done, PT passes done}, or NULL.
+ * Errors: NOT_INITIALISED, TIMEOUT (a bounded device wait of an earlier
+ * call gave up), CUDA.
+ */
+int32_t ising_read_state(ising_t h, int8_t* spins, int32_t* fields, int64_t* energy,
+                         int32_t* temp_of_slot, uint64_t* counters);
+
+/* accepted[R-1]: accepted swaps of pair (k, k+1) so far (host, synchronises). */
+int32_t ising_read_swap_stats(ising_t h, uint64_t* accepted);
+
+/*
+ * ising_save / ising_load -- checkpoint blob of the full replica state (spins,
+ * fields, energies, labels, RNG states and positions, counters).  save: pass
+ * buf = NULL to query the size in *size; otherwise cap >= *size.  load: the
+ * handle must be initialised with the same n, R and modes.  Running k sweeps,
+ * saving, loading into another handle and running m more gives the same
+ * result as k + m straight sweeps.  Errors: NOT_INITIALISED, INVALID_ARG.
+ */
+int32_t ising_save(ising_t h, void* buf, size_t cap, size_t* size);
+int32_t ising_load(ising_t h, const void* buf, size_t size);
+
+/* Layout facts of a handle (for tests and tuning reports). */
+typedef struct {
+    int32_t n, slices, slice_size, levels, slice_depth, replicas;
+    int32_t replicas_per_block, threads_per_block, blocks, smem_bytes;
+    int32_t persistent_ok; /* 1 if ising_run uses the single persistent launch */
+    int32_t field_bits, rng_mode, kmax;
+} ising_info_t;
+int32_t ising_get_info(ising_t h, ising_info_t* out);
+
+/* Override the launch shape (0 = automatic): replicas per block, threads per
+ * block, and whether ising_run may use the persistent launch. */
+int32_t ising_set_launch(ising_t h, int32_t replicas_per_block, int32_t threads_per_block,
+                         int32_t allow_persistent);
+
+/* Release all device memory of the handle (NULL is ignored). */
+int32_t ising_destroy(ising_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISING_GB300_H */

@@ -1,0 +1,193 @@
+// Random-number streams, state initialisation and the parallel-tempering pass.
+#include "ising_internal.cuh"
+
+namespace isg {
+namespace {
+
+// ---------------------------------------------------------------- MT19937
+// One block per stream.  x_w for w >= 624 follows x_w = x_{w-227} ^
+// twist(x_{w-624}, x_{w-623}); the 227 words w in [B, B+227) depend only on
+// words below B, so a block computes them in parallel.  The ring keeps the
+// last 1024 words, so slot w & 1023 (written) never aliases a slot read in the
+// same step (reads reach back 624 words at most).  Output j of the stream is
+// temper(x_{624+j}).
+__global__ void __launch_bounds__(256) mt_gen_kernel(const MtGenArgs a)
+{
+    __shared__ uint32_t ring[kMtRing];
+    const int stream = a.first_stream + blockIdx.x;
+    const bool swap = a.do_swap && stream == a.R;
+    uint32_t* gring = a.ring + size_t(stream) * kMtRing;
+    for (int i = threadIdx.x; i < kMtRing; i += blockDim.x)
+        ring[i] = gring[i];
+    const unsigned long long w0 = a.pos[stream];
+
+    long long nwords = a.nwords;
+    int par0 = 0, n_first = 0, n_pair = 0;
+    if (swap) {
+        // words of `swap_passes` passes starting at pass parity par0
+        const unsigned long long p0 = a.counters[1];
+        par0 = int(p0 & 1ull);
+        const int n_even = a.R / 2;        // pairs (0,1),(2,3),...  = floor(R/2)
+        const int n_odd = (a.R - 1) / 2;   // pairs (1,2),(3,4),...  = floor((R-1)/2)
+        n_first = par0 ? n_odd : n_even;
+        n_pair = n_even + n_odd;
+        const long long full = a.swap_passes / 2;
+        nwords = full * n_pair + ((a.swap_passes & 1) ? n_first : 0);
+    }
+    __syncthreads();
+
+    for (long long base = 0; base < nwords; base += kMtStep) {
+        const long long cnt = min((long long)kMtStep, nwords - base);
+        if (threadIdx.x < cnt) {
+            const long long k = base + threadIdx.x;
+            const unsigned long long w = w0 + (unsigned long long)k;
+            const uint32_t x = mt_recur(ring[(w - 624) & (kMtRing - 1)],
+                                        ring[(w - 623) & (kMtRing - 1)],
+                                        ring[(w - 227) & (kMtRing - 1)]);
+            ring[w & (kMtRing - 1)] = x;
+            const uint32_t out = mt_temper(x);
+            if (swap) {
+                const long long cyc = k / n_pair, rem = k - cyc * n_pair;
+                long long prel;
+                int j;
+                if (rem < n_first) {
+                    prel = 2 * cyc;
+                    j = int(rem);
+                } else {
+                    prel = 2 * cyc + 1;
+                    j = int(rem - n_first);
+                }
+                a.swbuf[size_t(prel) * a.maxpairs + j] = out;
+            } else if (a.mode == 1) {
+                a.spins[size_t(stream) * a.N + k] = (out >> 31) ? int8_t(1) : int8_t(-1);
+            } else {
+                const long long c = k / a.N;
+                const int i = int(k - c * a.N);
+                const int t = i / a.S, q = i - t * a.S;
+                a.wbuf[size_t(c) * a.wbuf_sweep_stride + (size_t(stream) * a.S + a.pos_of_site[q]) * a.Mp + t] = out;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < kMtRing; i += blockDim.x)
+        gring[i] = ring[i];
+    if (threadIdx.x == 0)
+        a.pos[stream] = w0 + (unsigned long long)nwords;
+}
+
+// ------------------------------------------------------------ Philox init
+__global__ void philox_init_kernel(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst)
+{
+    const long long total = (long long)R * N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int r = int(idx / N), i = int(idx - (long long)r * N);
+        const int t = i / S, q = i - t * S;
+        const uint4 ctr = make_uint4(uint32_t((t >> 2) * S + q), 0u, inst, 3u);
+        const uint32_t u = pick4(philox4x32_10(ctr, seed, uint32_t(r)), t & 3);
+        spins[idx] = (u >> 31) ? int8_t(1) : int8_t(-1);
+    }
+}
+
+// ---------------------------------------------------- fields and energies
+// f_i = h_i + sum_j J_ij s_j; E = -1/2 sum_i s_i (f_i + h_i) (each edge once).
+template <typename FT>
+__global__ void __launch_bounds__(256) state_init_kernel(const int8_t* spins, FT* fields, int* E,
+                                                         int N, const int* row_ptr, const int* col,
+                                                         const int* J, const int* h)
+{
+    __shared__ long long red[256];
+    const int r = blockIdx.x;
+    const int8_t* s = spins + size_t(r) * N;
+    long long acc = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        int f = h[i];
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            f += J[e] * int(s[col[e]]);
+        fields[size_t(r) * N + i] = FT(f);
+        acc += (long long)s[i] * (f + h[i]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        E[r] = int(-red[0] / 2);
+}
+
+// -------------------------------------------------------- PT pass
+// Pass p tries pairs (k, k+1), k = 2j + (p & 1).  Pairs of one pass are
+// disjoint, so each thread decides and applies its own pairs.
+__global__ void __launch_bounds__(1024) pt_kernel(const PtArgs a)
+{
+    const unsigned long long p = a.counters[1];
+    const int par = int(p & 1ull);
+    const int npairs = par ? (a.R - 1) / 2 : a.R / 2;
+    for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
+        const int k = 2 * j + par;
+        const int sa = a.slot_of_temp[k], sb = a.slot_of_temp[k + 1];
+        const long long d = (long long)a.E[sa] - (long long)a.E[sb];
+        uint32_t u;
+        if (a.rng == 0) {
+            u = a.swbuf[size_t(a.pass_rel) * a.maxpairs + j];
+        } else {
+            const uint4 ctr = make_uint4(uint32_t(j) >> 2, uint32_t(p), a.inst, 1u);
+            u = pick4(philox4x32_10(ctr, a.seed, 0xFFFFFFFFu), j & 3);
+        }
+        const bool acc = (d <= 0) || (d < a.swlen[k] && u < a.swthr[a.swoff[k] + d]);
+        if (acc) {
+            a.slot_of_temp[k] = sb;
+            a.slot_of_temp[k + 1] = sa;
+            a.temp_of_slot[sa] = k + 1;
+            a.temp_of_slot[sb] = k;
+            a.swap_acc[k] += 1ull;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        a.counters[1] = p + 1ull;
+}
+
+}  // namespace
+
+cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st)
+{
+    mt_gen_kernel<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst,
+                               cudaStream_t st)
+{
+    const long long total = (long long)R * N;
+    const int blocks = int(min((total + 255) / 256, 65535LL));
+    philox_init_kernel<<<blocks, 256, 0, st>>>(spins, R, N, S, seed, inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_init(const int8_t* spins, void* fields, int field_bits, int* E, int R,
+                              int N, const int* row_ptr, const int* col, const int* J,
+                              const int* h, cudaStream_t st)
+{
+    if (field_bits == 16)
+        state_init_kernel<int16_t><<<R, 256, 0, st>>>(spins, static_cast<int16_t*>(fields), E, N,
+                                                       row_ptr, col, J, h);
+    else
+        state_init_kernel<int32_t><<<R, 256, 0, st>>>(spins, static_cast<int32_t*>(fields), E, N,
+                                                       row_ptr, col, J, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pt(const PtArgs& a, cudaStream_t st)
+{
+    const int npairs = a.R / 2;
+    int threads = ((npairs + 31) / 32) * 32;
+    threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+    pt_kernel<<<1, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace isg

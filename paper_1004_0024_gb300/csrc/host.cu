@@ -1,0 +1,1038 @@
+// Host side of the C ABI declared in include/ising_gb300.h.
+//
+// ising_create validates the CSR model, verifies the declared slice
+// structure, computes the slice wavefront levels and packs the per-slice
+// tables.  ising_replicas_init builds the FP64 flip and swap thresholds and
+// draws the initial replicas.  ising_sweep / ising_pt_swap / ising_run plan a
+// sequence of launches (MT19937 word generation, wavefront sweeps, PT passes)
+// that reads every mutable quantity from device memory, so a recorded CUDA
+// graph can be replayed any number of times.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ising_gb300.h"
+#include "ising_internal.cuh"
+
+using namespace isg;
+
+namespace {
+
+thread_local std::string g_err = "";
+
+int32_t fail(int32_t code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int32_t cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? ISING_ERR_OOM : ISING_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess)                     \
+            return cuda_fail(e_, #call);           \
+    } while (0)
+
+template <typename T>
+int32_t dalloc(T** p, size_t count)
+{
+    size_t bytes = ((count * sizeof(T)) + 15) & ~size_t(15);
+    if (bytes == 0)
+        bytes = 16;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    e = cudaMemset(*p, 0, bytes);
+    if (e == cudaSuccess)  // allocations are rare: finish the fill before any stream uses it
+        e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMemset");
+    return ISING_OK;
+}
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p)
+        cudaFree(p);
+    p = nullptr;
+}
+
+template <typename T>
+int32_t upload(T** d, const std::vector<T>& h)
+{
+    int32_t rc = dalloc(d, h.size());
+    if (rc)
+        return rc;
+    if (!h.empty())
+        CK(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ISING_OK;
+}
+
+int g_num_sms = 0;
+std::once_flag g_once;
+cudaError_t g_init_err = cudaSuccess;
+
+cudaError_t device_setup()
+{
+    std::call_once(g_once, [] {
+        int dev = 0;
+        g_init_err = cudaGetDevice(&dev);
+        if (g_init_err == cudaSuccess)
+            g_init_err = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_init_err == cudaSuccess)
+            g_init_err = sweep_set_smem_limits();
+    });
+    return g_init_err;
+}
+
+// MT19937 init_genrand (Matsumoto & Nishimura): x_0 = seed,
+// x_i = 1812433253 (x_{i-1} ^ (x_{i-1} >> 30)) + i.
+void mt_seed_ring(uint32_t seed, uint32_t* ring)
+{
+    ring[0] = seed;
+    for (int i = 1; i < 624; ++i)
+        ring[i] = 1812433253u * (ring[i - 1] ^ (ring[i - 1] >> 30)) + uint32_t(i);
+    for (int i = 624; i < kMtRing; ++i)
+        ring[i] = 0u;
+}
+
+}  // namespace
+
+struct ising_s {
+    // graph
+    int n = 0, M = 1, S = 0, W = 1, Mp = 4, D0 = 0, D = 0;
+    long long kmax = 0, ebound = 0;
+    std::vector<int> row_ptr, col, J, h;
+    std::vector<int> site, pos, lev0p, jtau, nbr_off;
+    std::vector<uint32_t> nbr;
+    int *d_row_ptr = nullptr, *d_col = nullptr, *d_J = nullptr, *d_h = nullptr;
+    int *d_nbr_off = nullptr, *d_jtau = nullptr, *d_lev0 = nullptr, *d_site = nullptr,
+        *d_pos = nullptr;
+    uint32_t* d_nbr = nullptr;
+    // replicas
+    bool inited = false;
+    int R = 0, rng = 0, field_bits = 32, K = 1, maxpairs = 0;
+    uint32_t seed = 0, inst = 0;
+    std::vector<double> betas;
+    int8_t* d_spins = nullptr;
+    void* d_fields = nullptr;
+    int *d_E = nullptr, *d_temp = nullptr, *d_slot = nullptr, *d_err = nullptr;
+    unsigned long long *d_swap_acc = nullptr, *d_counters = nullptr, *d_mtpos = nullptr;
+    unsigned* d_done = nullptr;
+    uint32_t *d_thr = nullptr, *d_swthr = nullptr, *d_mtring = nullptr;
+    long long* d_swoff = nullptr;
+    int* d_swlen = nullptr;
+    uint32_t *d_wbuf = nullptr, *d_swbuf = nullptr;
+    long long wbuf_cap = 0, swbuf_cap = 0;  // sweeps / passes
+    // launch configuration
+    int G = 1, T = 32, cmax = 1, blocks = 1, tables_smem = 1, thr_smem = 1;
+    size_t smem = 0;
+    int G_req = 0, T_req = 0, allow_persistent = 1;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to record graphs
+    std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
+
+    void free_replicas();
+    void free_all();
+    void drop_graphs();
+};
+
+void ising_s::drop_graphs()
+{
+    for (auto& kv : graphs)
+        cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+}
+
+void ising_s::free_replicas()
+{
+    drop_graphs();
+    dfree(d_spins);
+    if (d_fields)
+        cudaFree(d_fields);
+    d_fields = nullptr;
+    dfree(d_E);
+    dfree(d_temp);
+    dfree(d_slot);
+    dfree(d_err);
+    dfree(d_swap_acc);
+    dfree(d_counters);
+    dfree(d_mtpos);
+    dfree(d_done);
+    dfree(d_thr);
+    dfree(d_swthr);
+    dfree(d_mtring);
+    dfree(d_swoff);
+    dfree(d_swlen);
+    dfree(d_wbuf);
+    dfree(d_swbuf);
+    wbuf_cap = swbuf_cap = 0;
+    inited = false;
+}
+
+void ising_s::free_all()
+{
+    free_replicas();
+    if (cap_stream)
+        cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
+    dfree(d_row_ptr);
+    dfree(d_col);
+    dfree(d_J);
+    dfree(d_h);
+    dfree(d_nbr_off);
+    dfree(d_jtau);
+    dfree(d_lev0);
+    dfree(d_site);
+    dfree(d_pos);
+    dfree(d_nbr);
+}
+
+namespace {
+
+// ---------------------------------------------------------- validation
+int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* J)
+{
+    if (row_ptr[0] != 0)
+        return fail(ISING_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+    for (int i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i])
+            return fail(ISING_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
+    const long long nnz = row_ptr[n];
+    std::vector<std::pair<int, int>> row;
+    for (int i = 0; i < n; ++i) {
+        row.clear();
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (col[e] < 0 || col[e] >= n)
+                return fail(ISING_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
+            if (col[e] == i)
+                return fail(ISING_ERR_SELF_LOOP_OR_DUP, "self loop at spin " + std::to_string(i));
+            if (J[e] > 32767 || J[e] < -32767)
+                return fail(ISING_ERR_INVALID_ARG, "|J| must be <= 32767");
+            row.emplace_back(col[e], J[e]);
+        }
+        std::sort(row.begin(), row.end());
+        for (size_t k = 1; k < row.size(); ++k)
+            if (row[k].first == row[k - 1].first)
+                return fail(ISING_ERR_SELF_LOOP_OR_DUP, "repeated neighbour in row " + std::to_string(i));
+    }
+    // symmetry: every (i, j, J) needs (j, i, J)
+    std::vector<std::vector<std::pair<int, int>>> rows(n);
+    for (int i = 0; i < n; ++i) {
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            rows[i].emplace_back(col[e], J[e]);
+        std::sort(rows[i].begin(), rows[i].end());
+    }
+    (void)nnz;
+    for (int i = 0; i < n; ++i)
+        for (auto& cj : rows[i]) {
+            auto& rj = rows[cj.first];
+            auto it = std::lower_bound(rj.begin(), rj.end(), std::make_pair(i, INT32_MIN));
+            if (it == rj.end() || it->first != i || it->second != cj.second)
+                return fail(ISING_ERR_ASYMMETRIC_J,
+                            "J(" + std::to_string(i) + "," + std::to_string(cj.first) + ") has no equal transpose");
+        }
+    return ISING_OK;
+}
+
+// Checks that spin i = t*S + q has the spatial row of site q shifted to slice
+// t plus the Trotter ring entries, with h and couplings identical in every
+// slice.  Fills the slice tables.
+int32_t extract_slices(ising_s* g)
+{
+    const int n = g->n, M = g->M, S = g->S;
+    std::vector<std::vector<std::pair<int, int>>> sp(S);
+    std::vector<int> jt(S, 0);
+    for (int t = 0; t < M; ++t) {
+        for (int q = 0; q < S; ++q) {
+            const int i = t * S + q;
+            if (g->h[i] != g->h[q])
+                return fail(ISING_ERR_INVALID_ARG, "declared slices differ in h at spin " + std::to_string(i));
+            std::vector<std::pair<int, int>> spat;
+            int ntrot = 0, jtrot = 0;
+            bool jt_ok = true;
+            const int tm = (t + M - 1) % M, tp = (t + 1) % M;
+            for (int e = g->row_ptr[i]; e < g->row_ptr[i + 1]; ++e) {
+                const int c = g->col[e];
+                const int tc = c / S, qc = c - tc * S;
+                if (tc == t) {
+                    spat.emplace_back(qc, g->J[e]);
+                } else if (qc == q && M >= 2 && (tc == tm || tc == tp)) {
+                    if (ntrot > 0 && g->J[e] != jtrot)
+                        jt_ok = false;
+                    jtrot = g->J[e];
+                    ++ntrot;
+                } else {
+                    return fail(ISING_ERR_INVALID_ARG,
+                                "spin " + std::to_string(i) + " has a coupling that is neither spatial nor Trotter");
+                }
+            }
+            const int want = (M >= 3) ? 2 : (M == 2 ? 1 : 0);
+            if (ntrot != want || !jt_ok)
+                return fail(ISING_ERR_INVALID_ARG,
+                            "spin " + std::to_string(i) + " lacks the Trotter ring couplings of the declared slices");
+            std::sort(spat.begin(), spat.end());
+            if (t == 0) {
+                sp[q] = spat;
+                jt[q] = jtrot;
+            } else if (spat != sp[q] || jtrot != jt[q]) {
+                return fail(ISING_ERR_INVALID_ARG, "declared slices are not identical at spin " + std::to_string(i));
+            }
+        }
+    }
+    (void)n;
+    // slice wavefront levels: lev0(q) = 1 + max lev0(q') over spatial q' < q
+    std::vector<int> lev(S, 0);
+    int D0 = 0;
+    for (int q = 0; q < S; ++q) {
+        int l = 0;
+        for (auto& e : sp[q])
+            if (e.first < q)
+                l = std::max(l, lev[e.first] + 1);
+        lev[q] = l;
+        D0 = std::max(D0, l + 1);
+    }
+    g->D0 = D0;
+    g->D = D0 + M - 1;
+    g->site.resize(S);
+    for (int q = 0; q < S; ++q)
+        g->site[q] = q;
+    std::stable_sort(g->site.begin(), g->site.end(), [&](int a, int b) { return lev[a] < lev[b]; });
+    g->pos.assign(S, 0);
+    for (int p = 0; p < S; ++p)
+        g->pos[g->site[p]] = p;
+    g->lev0p.resize(S);
+    g->jtau.resize(S);
+    g->nbr_off.assign(S + 1, 0);
+    g->nbr.clear();
+    for (int p = 0; p < S; ++p) {
+        const int q = g->site[p];
+        g->lev0p[p] = lev[q];
+        g->jtau[p] = jt[q];
+        for (auto& e : sp[q])
+            g->nbr.push_back((uint32_t(g->pos[e.first]) << 16) | (uint32_t(e.second) & 0xFFFFu));
+        g->nbr_off[p + 1] = int(g->nbr.size());
+    }
+    return ISING_OK;
+}
+
+// --------------------------------------------------- launch configuration
+SweepArgs base_args(ising_s* g)
+{
+    SweepArgs a{};
+    a.S = g->S;
+    a.M = g->M;
+    a.W = g->W;
+    a.N = g->n;
+    a.D0 = g->D0;
+    a.D = g->D;
+    a.Mp = g->Mp;
+    a.K = g->K;
+    a.G = g->G;
+    a.R = g->R;
+    a.tables_smem = g->tables_smem;
+    a.thr_smem = g->thr_smem;
+    a.nbr_count = int(g->nbr.size());
+    a.nbr_off = g->d_nbr_off;
+    a.nbr = g->d_nbr;
+    a.jtau = g->d_jtau;
+    a.lev0 = g->d_lev0;
+    a.site = g->d_site;
+    a.pos = g->d_pos;
+    a.spins = g->d_spins;
+    a.fields = g->d_fields;
+    a.E = g->d_E;
+    a.temp_of_slot = g->d_temp;
+    a.thr = g->d_thr;
+    a.rng = g->rng;
+    a.seed = g->seed;
+    a.inst = g->inst;
+    a.counters = g->d_counters;
+    a.done_blocks = g->d_done;
+    a.err = g->d_err;
+    a.wbuf_sweep_stride = (long long)g->R * g->S * g->Mp;
+    return a;
+}
+
+int32_t choose_launch(ising_s* g)
+{
+    const int sms = g_num_sms > 0 ? g_num_sms : 148;
+    const size_t kMaxSmem = sweep_max_dynamic_smem() ? sweep_max_dynamic_smem() : 200 * 1024;
+    const long long table_bytes = 4LL * (4 * g->S + 1) + 4LL * (long long)g->nbr.size();
+    std::vector<int> Gs;
+    if (g->G_req > 0) {
+        Gs.push_back(g->G_req);
+    } else {
+        for (int G : {8, 4, 2, 1})
+            if ((long long)((g->R + G - 1) / G) >= 2LL * sms || G == 1)
+                Gs.push_back(G);
+    }
+    for (int G : Gs) {
+        for (int tables_smem : {1, 0}) {
+            if (tables_smem && table_bytes > 96 * 1024)
+                continue;
+            SweepArgs a = base_args(g);
+            a.G = G;
+            a.tables_smem = tables_smem;
+            a.thr_smem = (4LL * G * g->K <= 16 * 1024) ? 1 : 0;
+            const size_t smem = sweep_smem_bytes(a, g->field_bits);
+            if (smem > kMaxSmem)
+                continue;
+            int T = g->T_req;
+            if (T <= 0) {
+                const long long want = ((long long)g->S * G + 3) / 4;
+                T = int(std::min<long long>(1024, std::max<long long>(32, ((want + 31) / 32) * 32)));
+            }
+            if (T % 32 != 0 || T > 1024 || T % G != 0)
+                return fail(ISING_ERR_INVALID_ARG, "threads per block must be a multiple of 32 and of G, <= 1024");
+            const long long C = ((long long)g->S * G + T - 1) / T;
+            const int cmax = sweep_cmax_for(int(std::min<long long>(C, 64)));
+            if (cmax == 0) {
+                if (g->T_req > 0)
+                    return fail(ISING_ERR_UNSUPPORTED, "more than 32 columns per thread");
+                continue;
+            }
+            g->G = G;
+            g->T = T;
+            g->cmax = cmax;
+            g->tables_smem = tables_smem;
+            g->thr_smem = a.thr_smem;
+            g->smem = smem;
+            g->blocks = (g->R + G - 1) / G;
+            return ISING_OK;
+        }
+    }
+    return fail(ISING_ERR_UNSUPPORTED, "replica state of one block does not fit in shared memory");
+}
+
+// ------------------------------------------------------- launch planning
+struct Op {
+    enum Kind { GEN, SWEEP, PT } kind;
+    int sweeps;   // GEN: sweeps of words; SWEEP: sweeps
+    int passes;   // GEN: passes of swap words
+    int offset;   // SWEEP: sweep offset into wbuf; PT: pass offset into swbuf
+};
+
+std::vector<Op> plan(ising_s* g, long long n, int swap_every, long long cap)
+{
+    std::vector<Op> ops;
+    const bool mt = g->rng == ISING_RNG_MT19937;
+    long long done = 0;
+    if (n <= 0 && swap_every == -1) {
+        // a lone PT pass
+        if (mt)
+            ops.push_back({Op::GEN, 0, 1, 0});
+        ops.push_back({Op::PT, 0, 0, 0});
+        return ops;
+    }
+    while (done < n) {
+        std::vector<Op> chunk;
+        long long cs = 0;
+        int cp = 0;
+        while (done < n && cs < cap) {
+            const long long to_pt = swap_every > 0 ? swap_every - (done % swap_every) : n - done;
+            const long long m = std::min({to_pt, n - done, cap - cs});
+            chunk.push_back({Op::SWEEP, int(m), 0, int(cs)});
+            cs += m;
+            done += m;
+            if (swap_every > 0 && done % swap_every == 0) {
+                chunk.push_back({Op::PT, 0, 0, cp});
+                ++cp;
+            }
+        }
+        if (mt)
+            ops.push_back({Op::GEN, int(cs), cp, 0});
+        ops.insert(ops.end(), chunk.begin(), chunk.end());
+    }
+    return ops;
+}
+
+long long words_cap(ising_s* g, long long n)
+{
+    if (g->rng != ISING_RNG_MT19937)
+        return std::max<long long>(n, 1);
+    const long long per_sweep = (long long)g->R * g->S * g->Mp * 4;
+    const long long budget = 1LL << 30;
+    return std::max<long long>(1, std::min<long long>(std::max<long long>(n, 1), budget / per_sweep));
+}
+
+int32_t ensure_buffers(ising_s* g, long long cap_sweeps, long long cap_passes)
+{
+    if (g->rng != ISING_RNG_MT19937)
+        return ISING_OK;
+    if (cap_sweeps > g->wbuf_cap) {
+        dfree(g->d_wbuf);
+        int32_t rc = dalloc(&g->d_wbuf, size_t(cap_sweeps) * g->R * g->S * g->Mp);
+        if (rc)
+            return rc;
+        g->wbuf_cap = cap_sweeps;
+    }
+    if (cap_passes > g->swbuf_cap) {
+        dfree(g->d_swbuf);
+        int32_t rc = dalloc(&g->d_swbuf, size_t(cap_passes) * std::max(g->maxpairs, 1));
+        if (rc)
+            return rc;
+        g->swbuf_cap = cap_passes;
+    }
+    return ISING_OK;
+}
+
+int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
+{
+    for (const Op& op : ops) {
+        cudaError_t e = cudaSuccess;
+        if (op.kind == Op::GEN) {
+            MtGenArgs a{};
+            a.ring = g->d_mtring;
+            a.pos = g->d_mtpos;
+            a.R = g->R;
+            a.mode = 0;
+            a.nwords = (long long)op.sweeps * g->n;
+            a.N = g->n;
+            a.S = g->S;
+            a.M = g->M;
+            a.Mp = g->Mp;
+            a.pos_of_site = g->d_pos;
+            a.wbuf = g->d_wbuf;
+            a.wbuf_sweep_stride = (long long)g->R * g->S * g->Mp;
+            a.do_swap = op.passes > 0;
+            a.swap_passes = op.passes;
+            a.swbuf = g->d_swbuf;
+            a.maxpairs = g->maxpairs;
+            a.counters = g->d_counters;
+            // blocks: the R replica streams (when sweep words are needed), then
+            // the swap stream (index R) when passes are needed
+            a.first_stream = op.sweeps > 0 ? 0 : g->R;
+            const int blocks = (op.sweeps > 0 ? g->R : 0) + (a.do_swap ? 1 : 0);
+            if (blocks > 0)
+                e = launch_mt_gen(a, blocks, st);
+        } else if (op.kind == Op::SWEEP) {
+            SweepArgs a = base_args(g);
+            a.nsweeps = op.sweeps;
+            a.wbuf = g->d_wbuf ? g->d_wbuf + size_t(op.offset) * a.wbuf_sweep_stride : nullptr;
+            e = launch_sweep(a, g->field_bits, g->cmax, g->T, g->blocks, g->smem, st);
+        } else {
+            PtArgs a{};
+            a.R = g->R;
+            a.E = g->d_E;
+            a.temp_of_slot = g->d_temp;
+            a.slot_of_temp = g->d_slot;
+            a.swap_acc = g->d_swap_acc;
+            a.counters = g->d_counters;
+            a.swthr = g->d_swthr;
+            a.swoff = g->d_swoff;
+            a.swlen = g->d_swlen;
+            a.rng = g->rng;
+            a.seed = g->seed;
+            a.inst = g->inst;
+            a.swbuf = g->d_swbuf;
+            a.maxpairs = g->maxpairs;
+            a.pass_rel = op.offset;
+            e = launch_pt(a, st);
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "kernel launch");
+    }
+    return ISING_OK;
+}
+
+int32_t check_device_error(ising_s* g)
+{
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (err == kErrTimeout)
+        return fail(ISING_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (err != 0)
+        return fail(ISING_ERR_CUDA, "device error flag " + std::to_string(err));
+    return ISING_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* ising_last_error(void) { return g_err.c_str(); }
+
+int32_t ising_create(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* J,
+                     const int32_t* h, int32_t n_slices, uint32_t flags, ising_t* out)
+{
+    if (!out)
+        return fail(ISING_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > (1 << 24))
+        return fail(ISING_ERR_INVALID_ARG, "n must be in [1, 2^24]");
+    if (!row_ptr || !h || (row_ptr[n] > 0 && (!col || !J)))
+        return fail(ISING_ERR_INVALID_ARG, "NULL array");
+    if (n_slices < 1 || n % n_slices != 0)
+        return fail(ISING_ERR_INVALID_ARG, "n_slices must be >= 1 and divide n");
+    if (flags != 0)
+        return fail(ISING_ERR_INVALID_ARG, "flags must be 0");
+    int32_t rc = validate_csr(n, row_ptr, col, J);
+    if (rc)
+        return rc;
+
+    ising_s* g = new ising_s();
+    g->n = n;
+    g->M = n_slices;
+    g->S = n / n_slices;
+    g->W = (g->M + 31) / 32;
+    g->Mp = ((g->M + 3) / 4) * 4;
+    const int nnz = row_ptr[n];
+    g->row_ptr.assign(row_ptr, row_ptr + n + 1);
+    g->col.assign(col, col + nnz);
+    g->J.assign(J, J + nnz);
+    g->h.assign(h, h + n);
+    if (g->S > 65536) {
+        delete g;
+        return fail(ISING_ERR_UNSUPPORTED, "slice larger than 65536 spins");
+    }
+    rc = extract_slices(g);
+    if (rc) {
+        delete g;
+        return rc;
+    }
+    long long eb = 0, km = 0;
+    for (int i = 0; i < n; ++i) {
+        long long b = std::llabs((long long)h[i]);
+        eb += std::llabs((long long)h[i]);
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            b += std::llabs((long long)J[e]);
+            if (col[e] > i)
+                eb += std::llabs((long long)J[e]);
+        }
+        km = std::max(km, b);
+    }
+    g->kmax = km;
+    g->ebound = eb;
+    if (eb > (1LL << 30)) {
+        delete g;
+        return fail(ISING_ERR_FIELD_OVERFLOW, "sum |h| + sum |J| exceeds 2^30");
+    }
+    cudaError_t ce = device_setup();
+    if (ce != cudaSuccess) {
+        delete g;
+        return cuda_fail(ce, "device setup");
+    }
+    if ((rc = upload(&g->d_row_ptr, g->row_ptr)) || (rc = upload(&g->d_col, g->col)) ||
+        (rc = upload(&g->d_J, g->J)) || (rc = upload(&g->d_h, g->h)) ||
+        (rc = upload(&g->d_nbr_off, g->nbr_off)) || (rc = upload(&g->d_nbr, g->nbr)) ||
+        (rc = upload(&g->d_jtau, g->jtau)) || (rc = upload(&g->d_lev0, g->lev0p)) ||
+        (rc = upload(&g->d_site, g->site)) || (rc = upload(&g->d_pos, g->pos))) {
+        g->free_all();
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return ISING_OK;
+}
+
+int32_t ising_set_stream(ising_t g, void* s)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (g->stream != static_cast<cudaStream_t>(s))
+        g->drop_graphs();
+    g->stream = static_cast<cudaStream_t>(s);
+    return ISING_OK;
+}
+
+int32_t ising_replicas_init(ising_t g, int32_t R, const double* betas, uint32_t seed,
+                            int32_t rng_mode, int32_t field_bits)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (R < 1 || R > (1 << 20) || !betas)
+        return fail(ISING_ERR_INVALID_ARG, "R must be in [1, 2^20] with betas given");
+    for (int k = 0; k < R; ++k) {
+        if (!(betas[k] > 0.0) || !std::isfinite(betas[k]))
+            return fail(ISING_ERR_INVALID_ARG, "betas must be finite and > 0");
+        if (k > 0 && !(betas[k] > betas[k - 1]))
+            return fail(ISING_ERR_INVALID_ARG, "betas must be strictly ascending");
+    }
+    if (rng_mode != ISING_RNG_MT19937 && rng_mode != ISING_RNG_PHILOX)
+        return fail(ISING_ERR_INVALID_ARG, "unknown rng_mode");
+    if (field_bits != 16 && field_bits != 32)
+        return fail(ISING_ERR_INVALID_ARG, "field_bits must be 16 or 32");
+    if (field_bits == 16 && g->kmax > 32767)
+        return fail(ISING_ERR_FIELD_OVERFLOW, "max |h_i| + sum_j |J_ij| exceeds int16");
+    if ((long long)R * g->n > (1LL << 36))
+        return fail(ISING_ERR_INVALID_ARG, "R * n too large");
+    g->free_replicas();
+    g->R = R;
+    g->rng = rng_mode;
+    g->field_bits = field_bits;
+    g->seed = seed;
+    g->betas.assign(betas, betas + R);
+    g->maxpairs = R / 2;
+
+    // flip thresholds T_beta(k) = floor(2^32 exp(-2 beta k)), FP64; k >= K -> 0
+    long long kz = g->kmax + 1;
+    for (long long k = 1; k <= g->kmax; ++k)
+        if (std::floor(std::ldexp(std::exp(-2.0 * betas[0] * double(k)), 32)) == 0.0) {
+            kz = k;
+            break;
+        }
+    g->K = int(std::max<long long>(1, std::min<long long>(g->kmax + 1, kz)));
+    std::vector<uint32_t> thr(size_t(R) * g->K, 0u);
+    for (int t = 0; t < R; ++t)
+        for (int k = 1; k < g->K; ++k)
+            thr[size_t(t) * g->K + k] =
+                uint32_t(std::floor(std::ldexp(std::exp(-2.0 * betas[t] * double(k)), 32)));
+    // swap thresholds S_k(d) = floor(2^32 exp(-(b_{k+1}-b_k) d)) for 1 <= d < len_k
+    std::vector<long long> swoff(std::max(R - 1, 1), 0);
+    std::vector<int> swlen(std::max(R - 1, 1), 1);
+    std::vector<uint32_t> swthr;
+    const long long dmax = 2 * g->ebound + 1;
+    for (int k = 0; k + 1 < R; ++k) {
+        const double db = betas[k + 1] - betas[k];
+        swoff[k] = (long long)swthr.size();
+        swthr.push_back(0u);
+        long long d = 1;
+        for (; d < dmax; ++d) {
+            const double v = std::floor(std::ldexp(std::exp(-db * double(d)), 32));
+            if (v == 0.0)
+                break;
+            swthr.push_back(uint32_t(v));
+            if (swthr.size() > (size_t(1) << 28))
+                return fail(ISING_ERR_UNSUPPORTED, "swap threshold tables exceed 2^28 entries");
+        }
+        swlen[k] = int(d);
+    }
+    int32_t rc;
+    const size_t RN = size_t(R) * g->n;
+    if ((rc = dalloc(&g->d_spins, RN)))
+        return rc;
+    {
+        cudaError_t e = cudaMalloc(&g->d_fields, ((RN * (field_bits / 8)) + 15) & ~size_t(15));
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc fields");
+    }
+    std::vector<int> ident(R);
+    for (int r = 0; r < R; ++r)
+        ident[r] = r;
+    if ((rc = dalloc(&g->d_E, R)) || (rc = upload(&g->d_temp, ident)) ||
+        (rc = upload(&g->d_slot, ident)) || (rc = dalloc(&g->d_err, 1)) ||
+        (rc = dalloc(&g->d_swap_acc, std::max(R - 1, 1))) || (rc = dalloc(&g->d_counters, 2)) ||
+        (rc = dalloc(&g->d_done, 1)) || (rc = upload(&g->d_thr, thr)) ||
+        (rc = upload(&g->d_swthr, swthr)) || (rc = upload(&g->d_swoff, swoff)) ||
+        (rc = upload(&g->d_swlen, swlen))) {
+        g->free_replicas();
+        return rc;
+    }
+    if (rng_mode == ISING_RNG_MT19937) {
+        std::vector<uint32_t> ring(size_t(R + 1) * kMtRing);
+        std::vector<unsigned long long> pos(R + 1, 624ull);
+        for (int r = 0; r <= R; ++r)
+            mt_seed_ring(seed + uint32_t(r), ring.data() + size_t(r) * kMtRing);
+        if ((rc = upload(&g->d_mtring, ring)) || (rc = upload(&g->d_mtpos, pos))) {
+            g->free_replicas();
+            return rc;
+        }
+    }
+    if ((rc = choose_launch(g))) {
+        g->free_replicas();
+        return rc;
+    }
+    // initial spins, fields, energies
+    if (rng_mode == ISING_RNG_MT19937) {
+        MtGenArgs a{};
+        a.ring = g->d_mtring;
+        a.pos = g->d_mtpos;
+        a.R = R;
+        a.mode = 1;
+        a.nwords = g->n;
+        a.N = g->n;
+        a.S = g->S;
+        a.M = g->M;
+        a.Mp = g->Mp;
+        a.spins = g->d_spins;
+        a.counters = g->d_counters;
+        CK(launch_mt_gen(a, R, g->stream));
+    } else {
+        CK(launch_philox_init(g->d_spins, R, g->n, g->S, seed, g->inst, g->stream));
+    }
+    CK(launch_state_init(g->d_spins, g->d_fields, field_bits, g->d_E, R, g->n, g->d_row_ptr,
+                         g->d_col, g->d_J, g->d_h, g->stream));
+    g->inited = true;
+    return ISING_OK;
+}
+
+static int32_t run_ops(ising_t g, long long n, int swap_every, bool use_graph)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    const long long cap = (n > 0) ? words_cap(g, n) : 1;
+    int32_t rc = ensure_buffers(g, cap, cap);
+    if (rc)
+        return rc;
+    std::vector<Op> ops = plan(g, n, swap_every, cap);
+    if (!use_graph)
+        return enqueue(g, ops, g->stream);
+    const auto key = std::make_pair(n, swap_every);
+    auto it = g->graphs.find(key);
+    if (it == g->graphs.end()) {
+        // record on a private stream (the legacy default stream cannot be
+        // captured); the graph is then launched on the handle's stream
+        if (!g->cap_stream)
+            CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue(g, ops, g->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (rc) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaGraphInstantiate");
+        it = g->graphs.emplace(key, exec).first;
+    }
+    CK(cudaGraphLaunch(it->second, g->stream));
+    return ISING_OK;
+}
+
+int32_t ising_sweep(ising_t g, int64_t n)
+{
+    if (n < 0)
+        return fail(ISING_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0)
+        return (g && g->inited) ? ISING_OK : fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    return run_ops(g, n, 0, false);
+}
+
+int32_t ising_pt_swap(ising_t g) { return run_ops(g, 0, -1, false); }
+
+int32_t ising_run(ising_t g, int64_t n, int32_t swap_every)
+{
+    if (n < 0)
+        return fail(ISING_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0)
+        return (g && g->inited) ? ISING_OK : fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    return run_ops(g, n, swap_every > 0 ? swap_every : 0, true);
+}
+
+int32_t ising_read_state(ising_t g, int8_t* spins, int32_t* fields, int64_t* energy,
+                         int32_t* temp_of_slot, uint64_t* counters)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    int32_t rc = check_device_error(g);
+    if (rc)
+        return rc;
+    const size_t RN = size_t(g->R) * g->n;
+    if (spins)
+        CK(cudaMemcpyAsync(spins, g->d_spins, RN, cudaMemcpyDeviceToHost, g->stream));
+    std::vector<int16_t> f16;
+    if (fields) {
+        if (g->field_bits == 32) {
+            CK(cudaMemcpyAsync(fields, g->d_fields, RN * 4, cudaMemcpyDeviceToHost, g->stream));
+        } else {
+            f16.resize(RN);
+            CK(cudaMemcpyAsync(f16.data(), g->d_fields, RN * 2, cudaMemcpyDeviceToHost, g->stream));
+        }
+    }
+    std::vector<int> e32(g->R);
+    CK(cudaMemcpyAsync(e32.data(), g->d_E, sizeof(int) * g->R, cudaMemcpyDeviceToHost, g->stream));
+    if (temp_of_slot)
+        CK(cudaMemcpyAsync(temp_of_slot, g->d_temp, sizeof(int) * g->R, cudaMemcpyDeviceToHost,
+                           g->stream));
+    unsigned long long cnt[2] = {0, 0};
+    CK(cudaMemcpyAsync(cnt, g->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (fields && g->field_bits == 16)
+        for (size_t i = 0; i < RN; ++i)
+            fields[i] = f16[i];
+    if (energy)
+        for (int r = 0; r < g->R; ++r)
+            energy[r] = e32[r];
+    if (counters) {
+        counters[0] = cnt[0];
+        counters[1] = cnt[1];
+    }
+    return ISING_OK;
+}
+
+int32_t ising_read_swap_stats(ising_t g, uint64_t* accepted)
+{
+    if (!g || !accepted)
+        return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    if (g->R < 2)
+        return ISING_OK;
+    CK(cudaMemcpyAsync(accepted, g->d_swap_acc, sizeof(uint64_t) * (g->R - 1),
+                       cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return ISING_OK;
+}
+
+namespace {
+struct BlobHeader {
+    uint32_t magic, version;
+    int32_t n, R, field_bits, rng, M, pad;
+};
+constexpr uint32_t kMagic = 0x31475349u;  // "ISG1"
+
+size_t blob_size(ising_s* g)
+{
+    const size_t RN = size_t(g->R) * g->n;
+    size_t s = sizeof(BlobHeader) + RN + RN * (g->field_bits / 8) + 4 * size_t(g->R) * 3 +
+               8 * size_t(std::max(g->R - 1, 1)) + 16;
+    if (g->rng == ISING_RNG_MT19937)
+        s += 4 * size_t(g->R + 1) * kMtRing + 8 * size_t(g->R + 1);
+    return s;
+}
+}  // namespace
+
+int32_t ising_save(ising_t g, void* buf, size_t cap, size_t* size)
+{
+    if (!g || !size)
+        return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    const size_t need = blob_size(g);
+    *size = need;
+    if (!buf)
+        return ISING_OK;
+    if (cap < need)
+        return fail(ISING_ERR_INVALID_ARG, "buffer too small");
+    int32_t rc = check_device_error(g);
+    if (rc)
+        return rc;
+    char* p = static_cast<char*>(buf);
+    BlobHeader hd{kMagic, 1u, g->n, g->R, g->field_bits, g->rng, g->M, 0};
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    const size_t RN = size_t(g->R) * g->n;
+    auto d2h = [&](const void* d, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(p, d, bytes, cudaMemcpyDeviceToHost, g->stream);
+        p += bytes;
+        return e;
+    };
+    CK(d2h(g->d_spins, RN));
+    CK(d2h(g->d_fields, RN * (g->field_bits / 8)));
+    CK(d2h(g->d_E, 4 * size_t(g->R)));
+    CK(d2h(g->d_temp, 4 * size_t(g->R)));
+    CK(d2h(g->d_slot, 4 * size_t(g->R)));
+    CK(d2h(g->d_swap_acc, 8 * size_t(std::max(g->R - 1, 1))));
+    CK(d2h(g->d_counters, 16));
+    if (g->rng == ISING_RNG_MT19937) {
+        CK(d2h(g->d_mtring, 4 * size_t(g->R + 1) * kMtRing));
+        CK(d2h(g->d_mtpos, 8 * size_t(g->R + 1)));
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return ISING_OK;
+}
+
+int32_t ising_load(ising_t g, const void* buf, size_t size)
+{
+    if (!g || !buf)
+        return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    if (size != blob_size(g))
+        return fail(ISING_ERR_INVALID_ARG, "blob size does not match this handle");
+    const char* p = static_cast<const char*>(buf);
+    BlobHeader hd;
+    std::memcpy(&hd, p, sizeof hd);
+    p += sizeof hd;
+    if (hd.magic != kMagic || hd.n != g->n || hd.R != g->R || hd.field_bits != g->field_bits ||
+        hd.rng != g->rng || hd.M != g->M)
+        return fail(ISING_ERR_INVALID_ARG, "blob was saved from a different configuration");
+    const size_t RN = size_t(g->R) * g->n;
+    auto h2d = [&](void* d, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, g->stream);
+        p += bytes;
+        return e;
+    };
+    CK(h2d(g->d_spins, RN));
+    CK(h2d(g->d_fields, RN * (g->field_bits / 8)));
+    CK(h2d(g->d_E, 4 * size_t(g->R)));
+    CK(h2d(g->d_temp, 4 * size_t(g->R)));
+    CK(h2d(g->d_slot, 4 * size_t(g->R)));
+    CK(h2d(g->d_swap_acc, 8 * size_t(std::max(g->R - 1, 1))));
+    CK(h2d(g->d_counters, 16));
+    if (g->rng == ISING_RNG_MT19937) {
+        CK(h2d(g->d_mtring, 4 * size_t(g->R + 1) * kMtRing));
+        CK(h2d(g->d_mtpos, 8 * size_t(g->R + 1)));
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return ISING_OK;
+}
+
+int32_t ising_get_info(ising_t g, ising_info_t* o)
+{
+    if (!g || !o)
+        return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    std::memset(o, 0, sizeof *o);
+    o->n = g->n;
+    o->slices = g->M;
+    o->slice_size = g->S;
+    o->levels = g->D;
+    o->slice_depth = g->D0;
+    o->replicas = g->R;
+    o->replicas_per_block = g->G;
+    o->threads_per_block = g->T;
+    o->blocks = g->blocks;
+    o->smem_bytes = int(g->smem);
+    o->persistent_ok = 0;
+    o->field_bits = g->field_bits;
+    o->rng_mode = g->rng;
+    o->kmax = int(std::min<long long>(g->kmax, INT32_MAX));
+    return ISING_OK;
+}
+
+int32_t ising_set_launch(ising_t g, int32_t replicas_per_block, int32_t threads_per_block,
+                         int32_t allow_persistent)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (replicas_per_block < 0 || (replicas_per_block & (replicas_per_block - 1)) ||
+        replicas_per_block > 32)
+        return fail(ISING_ERR_INVALID_ARG, "replicas_per_block must be 0 or a power of two <= 32");
+    g->G_req = replicas_per_block;
+    g->T_req = threads_per_block;
+    g->allow_persistent = allow_persistent;
+    g->drop_graphs();
+    if (g->inited)
+        return choose_launch(g);
+    return ISING_OK;
+}
+
+int32_t ising_destroy(ising_t g)
+{
+    if (!g)
+        return ISING_OK;
+    g->free_all();
+    delete g;
+    return ISING_OK;
+}
+
+}  // extern "C"

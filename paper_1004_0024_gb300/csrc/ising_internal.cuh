@@ -1,0 +1,202 @@
+// Internal declarations of the GB300 Ising library (not part of the C ABI).
+//
+// Data layout (HBM):
+//   spins   int8  [R][n]       slot-major, spin index order (API layout)
+//   fields  int16|int32 [R][n] total local field f_i = h_i + sum_j J_ij s_j
+//   E       int32 [R]          energy of each slot
+// Per-slice tables (sorted position p = rank of site q by (slice level, q)):
+//   nbr_off int32 [S+1], nbr uint32 [E] packed (pos(q') << 16 | (uint16)J),
+//   jtau int32 [S] Trotter coupling, lev0 int32 [S] slice wavefront level,
+//   site int32 [S] (site at position p), pos int32 [S] (position of site q).
+// Inside a sweep block (shared memory), per replica g of the block:
+//   colbits uint32 [S][G][W]  bit t of column (p, g) = spin (q, t) is +1
+//   fsp     FT     [S][M][G]  spatial field h_q + sum_{q'} J s_{q',t}
+//                             (int16 kept biased by +32768 inside 32-bit words)
+// The Trotter part of the field, Jtau_q (s_{q,t-1} + s_{q,t+1}), is read from
+// the column bits, so only the spatial part needs atomic updates.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace isg {
+
+constexpr int kMtRing = 1024;  // ring slots of an MT19937 stream (>= 624 + 227)
+constexpr int kMtStep = 227;   // words of one stream computable in parallel
+
+// Device error flag values (first error wins).
+constexpr int kErrTimeout = 1;
+constexpr int kErrBadConfig = 2;
+
+struct SweepArgs {
+    // slice structure
+    int S, M, W, N, D0, D, Mp;
+    int K;          // flip-threshold table length: k in [1, K) tabulated, k >= K -> 0
+    int G, R;       // replicas per block, replicas in total
+    int nsweeps;    // sweeps in this launch
+    int tables_smem;     // 1: stage tables in shared memory via bulk copies
+    int thr_smem;        // 1: thresholds staged in shared memory
+    int nbr_count;       // entries of nbr
+    const int* nbr_off;
+    const uint32_t* nbr;
+    const int* jtau;
+    const int* lev0;
+    const int* site;
+    const int* pos;
+    // state
+    int8_t* spins;
+    void* fields;
+    int* E;
+    const int* temp_of_slot;
+    const uint32_t* thr;  // [R temps][K]
+    // random numbers
+    int rng;              // 0 MT19937 (words from wbuf), 1 Philox
+    uint32_t seed, inst;
+    unsigned long long* counters;  // [0] sweeps done, [1] passes done
+    const uint32_t* wbuf;          // MT words: [sweep][R][S][Mp]
+    long long wbuf_sweep_stride;   // = R*S*Mp
+    unsigned int* done_blocks;     // block-completion counter for the counter update
+    int* err;
+};
+
+struct PtArgs {
+    int R;
+    int* E;
+    int* temp_of_slot;
+    int* slot_of_temp;
+    unsigned long long* swap_acc;
+    unsigned long long* counters;
+    const uint32_t* swthr;     // flattened swap thresholds
+    const long long* swoff;    // [R-1] start of pair k's table
+    const int* swlen;          // [R-1] table length (d in [1, len) tabulated)
+    int rng;
+    uint32_t seed, inst;
+    const uint32_t* swbuf;     // MT swap words [pass][maxpairs]
+    int maxpairs;
+    int pass_rel;              // pass index inside swbuf
+};
+
+struct MtGenArgs {
+    uint32_t* ring;            // [streams][kMtRing]
+    unsigned long long* pos;   // [streams] index w of the next x_w to generate
+    int R;                     // replica streams 0..R-1, swap stream R
+    int first_stream;          // block b generates stream first_stream + b
+    int mode;                  // 0 sweep words, 1 initial spins
+    long long nwords;          // words per replica stream
+    int N, S, M, Mp;
+    const int* pos_of_site;
+    uint32_t* wbuf;
+    long long wbuf_sweep_stride;
+    int8_t* spins;
+    // swap stream (block R when do_swap)
+    int do_swap;
+    int swap_passes;           // passes to cover
+    uint32_t* swbuf;
+    int maxpairs;
+    const unsigned long long* counters;
+};
+
+// ------------------------------------------------------------------ RNG
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t pick4(uint4 v, int lane)
+{
+    return (lane & 2) ? ((lane & 1) ? v.w : v.z) : ((lane & 1) ? v.y : v.x);
+}
+
+// MT19937 recurrence x_w = x_{w-227} ^ twist(x_{w-624}, x_{w-623}) and
+// tempering (Matsumoto & Nishimura 1998).
+__device__ __forceinline__ uint32_t mt_recur(uint32_t xa, uint32_t xb, uint32_t xm)
+{
+    const uint32_t y = (xa & 0x80000000u) | (xb & 0x7FFFFFFFu);
+    return xm ^ (y >> 1) ^ ((0u - (y & 1u)) & 0x9908B0DFu);
+}
+
+__device__ __forceinline__ uint32_t mt_temper(uint32_t y)
+{
+    y ^= y >> 11;
+    y ^= (y << 7) & 0x9D2C5680u;
+    y ^= (y << 15) & 0xEFC60000u;
+    y ^= y >> 18;
+    return y;
+}
+
+// ------------------------------------------------ bulk copy (TMA) + mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk global -> shared copy; dst, src 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long max_polls)
+{
+    for (long long i = 0; i < max_polls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void set_err(int* err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------- launchers
+cudaError_t launch_sweep(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
+                         size_t smem, cudaStream_t st);
+size_t sweep_smem_bytes(const SweepArgs& a, int field_bits);
+cudaError_t sweep_set_smem_limits();
+size_t sweep_max_dynamic_smem();
+int sweep_cmax_for(int c);
+cudaError_t sweep_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
+                                    int* out);
+cudaError_t launch_pt(const PtArgs& a, cudaStream_t st);
+cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst,
+                               cudaStream_t st);
+cudaError_t launch_state_init(const int8_t* spins, void* fields, int field_bits, int* E, int R,
+                              int N, const int* row_ptr, const int* col, const int* J,
+                              const int* h, cudaStream_t st);
+
+}  // namespace isg

@@ -1,0 +1,243 @@
+"""ctypes binding of the C ABI in ``include/ising_gb300.h``.
+
+Argument marshalling only: every step of the sampler runs in the CUDA library
+``libising_gb300.so`` built in-tree by ``paper_1004_0024_gb300/build.py``.
+Importing this module loads that library and raises ``ImportError`` when it
+has not been built; there is no CPU fallback.
+
+The functions keep the C names (``ising_create``, ``ising_replicas_init``,
+``ising_sweep``, ``ising_pt_swap``, ``ising_run``, ``ising_read_state`` ...);
+:class:`Ising` bundles one handle with numpy-friendly methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libising_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+ISING_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "ASYMMETRIC_J", -3: "SELF_LOOP_OR_DUP", -4: "FIELD_OVERFLOW",
+    -5: "NOT_INITIALISED", -6: "OOM", -7: "CUDA", -8: "TIMEOUT", -9: "UNSUPPORTED",
+}
+RNG = {"mt19937": 0, "philox": 1}
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class IsingInfo(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in (
+        "n", "slices", "slice_size", "levels", "slice_depth", "replicas",
+        "replicas_per_block", "threads_per_block", "blocks", "smem_bytes", "persistent_ok",
+        "field_bits", "rng_mode", "kmax")]
+
+
+_SIGS = {
+    "ising_last_error": ([], ctypes.c_char_p),
+    "ising_create": ([ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_uint32,
+                      ctypes.POINTER(_vp)], ctypes.c_int32),
+    "ising_set_stream": ([_vp, _vp], ctypes.c_int32),
+    "ising_replicas_init": ([_vp, ctypes.c_int32, _f64p, ctypes.c_uint32, ctypes.c_int32,
+                             ctypes.c_int32], ctypes.c_int32),
+    "ising_sweep": ([_vp, ctypes.c_int64], ctypes.c_int32),
+    "ising_pt_swap": ([_vp], ctypes.c_int32),
+    "ising_run": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int32),
+    "ising_read_state": ([_vp, _i8p, _i32p, _i64p, _i32p, _u64p], ctypes.c_int32),
+    "ising_read_swap_stats": ([_vp, _u64p], ctypes.c_int32),
+    "ising_save": ([_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
+    "ising_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int32),
+    "ising_get_info": ([_vp, ctypes.POINTER(IsingInfo)], ctypes.c_int32),
+    "ising_set_launch": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
+    "ising_destroy": ([_vp], ctypes.c_int32),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+def _check(rc: int):
+    if rc != ISING_OK:
+        raise IsingError(rc, _lib.ising_last_error().decode(errors="replace"))
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+# ------------------------------------------------------------ C-named calls
+def ising_last_error() -> str:
+    return _lib.ising_last_error().decode(errors="replace")
+
+
+def ising_create(n, row_ptr, col, J, h, n_slices=1, flags=0):
+    rp, c, j, hh = _arr(row_ptr, np.int32), _arr(col, np.int32), _arr(J, np.int32), _arr(h, np.int32)
+    if c.size == 0:
+        c = np.zeros(1, np.int32)
+        j = np.zeros(1, np.int32)
+    out = _vp()
+    _check(_lib.ising_create(int(n), _p(rp, _i32p), _p(c, _i32p), _p(j, _i32p), _p(hh, _i32p),
+                             int(n_slices), int(flags), ctypes.byref(out)))
+    return out
+
+
+def ising_set_stream(h, stream):
+    """`stream`: a cudaStream_t as int (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+    _check(_lib.ising_set_stream(h, _vp(int(stream) if stream else None)))
+
+
+def ising_replicas_init(h, R, betas, seed, rng_mode=0, field_bits=32):
+    b = _arr(betas, np.float64)
+    if isinstance(rng_mode, str):
+        rng_mode = RNG[rng_mode]
+    _check(_lib.ising_replicas_init(h, int(R), _p(b, _f64p), int(seed) & 0xFFFFFFFF, int(rng_mode),
+                                    int(field_bits)))
+
+
+def ising_sweep(h, n):
+    _check(_lib.ising_sweep(h, int(n)))
+
+
+def ising_pt_swap(h):
+    _check(_lib.ising_pt_swap(h))
+
+
+def ising_run(h, n, swap_every=1):
+    _check(_lib.ising_run(h, int(n), int(swap_every)))
+
+
+def ising_read_state(h, R, n):
+    spins = np.empty((R, n), dtype=np.int8)
+    fields = np.empty((R, n), dtype=np.int32)
+    E = np.empty(R, dtype=np.int64)
+    temp = np.empty(R, dtype=np.int32)
+    cnt = np.empty(2, dtype=np.uint64)
+    _check(_lib.ising_read_state(h, _p(spins, _i8p), _p(fields, _i32p), _p(E, _i64p),
+                                 _p(temp, _i32p), _p(cnt, _u64p)))
+    return dict(spins=spins, fields=fields, energy=E, temp_of_slot=temp, sweeps=int(cnt[0]),
+                passes=int(cnt[1]))
+
+
+def ising_read_swap_stats(h, R):
+    acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
+    _check(_lib.ising_read_swap_stats(h, _p(acc, _u64p)))
+    return acc[:max(R - 1, 0)]
+
+
+def ising_save(h) -> bytes:
+    size = ctypes.c_size_t(0)
+    _check(_lib.ising_save(h, None, 0, ctypes.byref(size)))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(_lib.ising_save(h, ctypes.cast(buf, _vp), size.value, ctypes.byref(size)))
+    return buf.raw[: size.value]
+
+
+def ising_load(h, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib.ising_load(h, ctypes.cast(buf, _vp), len(blob)))
+
+
+def ising_get_info(h) -> dict:
+    info = IsingInfo()
+    _check(_lib.ising_get_info(h, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in IsingInfo._fields_}
+
+
+def ising_set_launch(h, replicas_per_block=0, threads_per_block=0, allow_persistent=1):
+    _check(_lib.ising_set_launch(h, int(replicas_per_block), int(threads_per_block),
+                                 int(allow_persistent)))
+
+
+def ising_destroy(h):
+    if h:
+        _check(_lib.ising_destroy(h))
+
+
+# ------------------------------------------------------------------ wrapper
+class Ising:
+    """One model with its replicas: ``Ising(graph, betas, seed, rng, field_bits)``.
+
+    ``graph`` has ``n, row_ptr, col, J, h`` and ``n_slices`` (see
+    ``paper_1004_0024_gb300.workloads.Graph``).
+    """
+
+    def __init__(self, graph, betas=None, seed=5489, rng="mt19937", field_bits=32, stream=None):
+        self.n = int(graph.n)
+        self.h = ising_create(graph.n, graph.row_ptr, graph.col, graph.J, graph.h,
+                              getattr(graph, "n_slices", 1))
+        if stream is not None:
+            ising_set_stream(self.h, stream)
+        self.R = 0
+        if betas is not None:
+            self.replicas_init(betas, seed, rng, field_bits)
+
+    def replicas_init(self, betas, seed=5489, rng="mt19937", field_bits=32):
+        betas = np.asarray(betas, dtype=np.float64)
+        ising_replicas_init(self.h, betas.size, betas, seed, rng, field_bits)
+        self.R = int(betas.size)
+
+    def set_stream(self, stream):
+        ising_set_stream(self.h, stream)
+
+    def sweep(self, n=1):
+        ising_sweep(self.h, n)
+
+    def pt_swap(self):
+        ising_pt_swap(self.h)
+
+    def run(self, n, swap_every=1):
+        ising_run(self.h, n, swap_every)
+
+    def read_state(self):
+        return ising_read_state(self.h, self.R, self.n)
+
+    def swap_stats(self):
+        return ising_read_swap_stats(self.h, self.R)
+
+    def save(self) -> bytes:
+        return ising_save(self.h)
+
+    def load(self, blob: bytes):
+        ising_load(self.h, blob)
+
+    def info(self) -> dict:
+        return ising_get_info(self.h)
+
+    def set_launch(self, replicas_per_block=0, threads_per_block=0, allow_persistent=1):
+        ising_set_launch(self.h, replicas_per_block, threads_per_block, allow_persistent)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ising_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,189 @@
+"""Bit-exact parity of the CUDA path with the oracle (GPU).
+
+Every comparison is element by element on spins, local fields, energies,
+temperature labels, PT acceptance counts and sweep/pass counters.  Inputs come
+from ``paper_1004_0024_gb300.workloads`` (seeded, synthetic).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_0024_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1004_0024_gb300 import ising as mod
+    return mod
+
+
+def assert_same(dev, ref, what=""):
+    d, r = dev.read_state(), ref.read()
+    assert np.array_equal(d["spins"], r["spins"]), f"spins {what}"
+    assert np.array_equal(d["fields"], r["fields"]), f"fields {what}"
+    assert np.array_equal(d["energy"], r["energy"]), f"energy {what}"
+    assert np.array_equal(d["temp_of_slot"], r["temp_of_slot"]), f"labels {what}"
+    assert (d["sweeps"], d["passes"]) == (r["sweeps"], r["passes"]), f"counters {what}"
+    if dev.R > 1:
+        assert np.array_equal(dev.swap_stats(), r["swap_acc"]), f"swap counts {what}"
+
+
+def pair(ising, g, betas, seed, rng, field_bits, launch=None):
+    dev = ising.Ising(g, betas, seed=seed, rng=rng, field_bits=field_bits)
+    if launch is not None:
+        dev.set_launch(*launch)
+    ref = oracle.Sim(g, betas, seed=seed, rng=rng)
+    assert_same(dev, ref, "after init")
+    return dev, ref
+
+
+# ------------------------------------------------------------ named configs
+def test_config0_1000_sweeps_pt_every_sweep_mt19937(ising):
+    c = W.config0()
+    dev, ref = pair(ising, c["graph"], c["betas"], c["seed"], "mt19937", 32)
+    for chunk in range(4):
+        dev.run(250, 1)
+        ref.run(250, 1)
+        assert_same(dev, ref, f"after {250 * (chunk + 1)} sweeps")
+
+
+def test_config0_philox(ising):
+    c = W.config0()
+    dev, ref = pair(ising, c["graph"], c["betas"], c["seed"], "philox", 32)
+    dev.run(300, 1)
+    ref.run(300, 1)
+    assert_same(dev, ref)
+
+
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_config1_first_20_sweeps(ising, rng):
+    c = W.config1()
+    dev, ref = pair(ising, c["graph"], c["betas"], c["seed"], rng, 16)
+    for _ in range(4):
+        dev.run(5, 1)
+        ref.run(5, 1)
+        assert_same(dev, ref)
+
+
+def test_config1_full_200_sweeps_bit_exact(ising):
+    """The full 32768-spin x 256-replica run (200 sweeps + PT), as timed by bench.py."""
+    c = W.config1()
+    dev, ref = pair(ising, c["graph"], c["betas"], c["seed"], "mt19937", 16)
+    dev.run(200, 1)
+    ref.run(200, 1)
+    assert_same(dev, ref)
+    st = dev.read_state()
+    g = c["graph"]
+    for r in (0, 77, 255):  # fields and energy recomputed from scratch
+        assert np.array_equal(oracle.fields(g, st["spins"][r]), st["fields"][r])
+        assert oracle.energy(g, st["spins"][r]) == st["energy"][r]
+
+
+# --------------------------------------------------------- shapes and edges
+@pytest.mark.parametrize("n,edges,R", [(1, 0, 1), (2, 1, 2), (3, 3, 3), (5, 7, 7), (17, 40, 4),
+                                       (100, 300, 5), (1000, 2500, 6)])
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_unstructured_graphs(ising, n, edges, R, rng):
+    g = W.random_graph(n, edges, seed=n + edges)
+    betas = W.geometric_betas(R, 0.2, 1.5)
+    dev, ref = pair(ising, g, betas, 99 + n, rng, 32 if n % 2 else 16)
+    dev.run(7, 2)
+    ref.run(7, 2)
+    assert_same(dev, ref)
+
+
+@pytest.mark.parametrize("L,M", [(3, 2), (3, 3), (4, 4), (3, 5), (4, 33), (3, 64)])
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_slice_counts(ising, L, M, rng):
+    g = W.layered_graph(L, M, graph_seed=L * 100 + M, j_tau=3)
+    betas = W.geometric_betas(9, 0.1, 2.0)
+    dev, ref = pair(ising, g, betas, 4242, rng, 16)
+    dev.run(9, 1)
+    ref.run(9, 1)
+    assert_same(dev, ref)
+
+
+@pytest.mark.parametrize("G,T", [(1, 32), (2, 64), (4, 128), (8, 256), (1, 1024), (8, 64),
+                                 (2, 32)])
+def test_launch_shapes_give_identical_results(ising, G, T):
+    c = W.config0()
+    betas = W.geometric_betas(30, 0.1, 3.0)  # 30 replicas: ragged last block
+    dev, ref = pair(ising, c["graph"], betas, 7, "mt19937", 16, launch=(G, T, 0))
+    dev.run(25, 1)
+    ref.run(25, 1)
+    assert_same(dev, ref)
+
+
+def test_separate_sweep_and_pt_calls(ising):
+    c = W.config0()
+    dev, ref = pair(ising, c["graph"], c["betas"][:13], 31, "mt19937", 32)
+    for k in range(6):
+        dev.sweep(k + 1)
+        ref.sweep(k + 1)
+        dev.pt_swap()
+        ref.pt_swap()
+        dev.pt_swap()
+        ref.pt_swap()
+    assert_same(dev, ref)
+    dev.run(10, 3)
+    ref.run(10, 3)
+    assert_same(dev, ref)
+
+
+def test_zero_model_and_isolated_spins(ising):
+    g = W.graph_from_edges(64, {}, np.zeros(64))
+    dev, ref = pair(ising, g, [0.5, 1.0, 2.0], 3, "mt19937", 32)
+    s0 = dev.read_state()["spins"]
+    dev.sweep(1)
+    assert np.array_equal(dev.read_state()["spins"], -s0)
+    h = np.arange(-4, 4)
+    g2 = W.graph_from_edges(8, {}, h)
+    dev, ref = pair(ising, g2, [0.3, 0.9], 5, "philox", 16)
+    dev.run(5, 1)
+    ref.run(5, 1)
+    assert_same(dev, ref)
+    assert np.array_equal(dev.read_state()["fields"][0], h)
+
+
+def test_checkpoint_resume_is_bit_exact(ising):
+    c = W.config0()
+    a = ising.Ising(c["graph"], c["betas"], seed=11, rng="mt19937", field_bits=16)
+    a.run(10, 1)
+    blob = a.save()
+    b = ising.Ising(c["graph"], c["betas"], seed=999, rng="mt19937", field_bits=16)
+    b.load(blob)
+    a.run(10, 1)
+    b.run(10, 1)
+    sa, sb = a.read_state(), b.read_state()
+    for k in ("spins", "fields", "energy", "temp_of_slot"):
+        assert np.array_equal(sa[k], sb[k])
+    ref = oracle.Sim(c["graph"], c["betas"], seed=11)
+    ref.run(20, 1)
+    assert_same(b, ref)
+
+
+def test_graph_replay_matches_fresh_launches(ising):
+    """ising_run records a CUDA graph once and replays it; replays must advance
+    the device-side counters and streams exactly like fresh launches."""
+    c = W.config0()
+    dev, ref = pair(ising, c["graph"], c["betas"], 17, "philox", 16)
+    for _ in range(5):
+        dev.run(4, 2)
+        ref.run(4, 2)
+    assert_same(dev, ref)
+
+
+def test_not_initialised_is_reported(ising):
+    g = W.layered_graph(3, 3, 1)
+    h = ising.ising_create(g.n, g.row_ptr, g.col, g.J, g.h, 3)
+    with pytest.raises(ising.IsingError) as ei:
+        ising.ising_run(h, 5, 1)
+    assert ei.value.name == "NOT_INITIALISED"
+    ising.ising_destroy(h)
