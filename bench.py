@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Spin-flip attempts per second of the replica-parallel Metropolis sweep with PT.
+
+Workload (one "step" = one pass of the whole hot path over the batch): the
+32x32 lattice x 32 Trotter slices model (32768 spins, spatial degree 4-6 plus
+the 2 Trotter couplings), 256 replicas at geometric inverse temperatures
+0.05..5.0, int8 spins and int16 local fields, 200 sequential Metropolis sweeps
+with a parallel-tempering pass after every sweep.  Synthetic seeded inputs
+(paper_1004_0024_gb300.workloads).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--rng mt19937|philox]
+    python bench.py --impl reference     # the CPU oracle on the host cores
+
+Under torchrun each rank samples its own independent instance (different
+seed): the path has no data exchange between instances, so N ranks are N
+replicas of the workload ("scaling": "weak"); value = all ranks' attempts /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SWEEPS_PER_STEP = 200
+SWAP_EVERY = 1
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rng", choices=["mt19937", "philox"], default="mt19937")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1004_0024_gb300 import workloads as W
+    return W.config1()
+
+
+def attempts_per_step(c):
+    return c["graph"].n * c["R"] * SWEEPS_PER_STEP
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (200 ms period)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        smi = shutil.which("nvidia-smi")
+        if not smi:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen(
+            [smi, f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+             "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- our path
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1004_0024_gb300 import ising
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+
+    c = workload()
+    g = c["graph"]
+    seed = c["seed"] + 100003 * rank
+    per_step = attempts_per_step(c)
+
+    sim = ising.Ising(g, c["betas"], seed=seed, rng=args.rng, field_bits=c["field_bits"],
+                      stream=stream.cuda_stream)
+    info = sim.info()
+    for _ in range(args.warmup):
+        sim.run(SWEEPS_PER_STEP, SWAP_EVERY)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    sim.set_profiling(True)
+    st0 = sim.stats()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev_index)
+    sampler.start()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        sim.run(SWEEPS_PER_STEP, SWAP_EVERY)
+        ev[k][1].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    st1 = sim.stats()
+    kernel_ms = st1["kernel_ms"] - st0["kernel_ms"]
+    sweep_launches = st1["timed_launches"] - st0["timed_launches"]
+    launches = st1["launches"] - st0["launches"]
+    sim.set_profiling(False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * per_step * args.steps / (max_ms * 1e-3)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, c, seed, stream, world)
+
+    # parity spot check of the state after the timed run (invariants at full size)
+    st = sim.read_state()
+    sim.close()
+    assert int(st["sweeps"]) == SWEEPS_PER_STEP * (args.warmup + args.steps)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "spin-flip attempts/s",
+        "value": value,
+        "unit": "attempts/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": max_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int8 spins/int16 fields/uint32 RNG",
+        "data": "synthetic (seeded layered lattice + matchings)",
+        "config": {
+            "workload": "32x32 lattice x 32 Trotter slices (32768 spins), 256 replicas, betas 0.05-5.0 geometric, 200 sweeps + PT each",
+            "rng": args.rng, "field_bits": c["field_bits"], "sweeps_per_step": SWEEPS_PER_STEP,
+            "attempts_per_step": per_step, "l2": "flushed (512 MB write) between timed steps",
+            "parallelism": f"replicas-only x{world}",
+            "launch": {k: info[k] for k in ("replicas_per_block", "threads_per_block", "blocks",
+                                             "smem_bytes", "persistent_ok", "fast_kernel", "levels")},
+        },
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    line["roofline"] = roofline(c, args.rng, per_step * args.steps, kernel_ms, sweep_launches, clocks)
+    if e2e is not None:
+        line["e2e"] = e2e
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(c, args.rng, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, c, seed, stream, world):
+    """End to end through the C ABI: pinned host inputs -> ising_create +
+    ising_replicas_init (H2D inside the timed region) -> ising_run ->
+    ising_read_state into pinned host buffers (D2H), per step."""
+    import numpy as np
+    import torch
+
+    from paper_1004_0024_gb300 import ising
+
+    g = c["graph"]
+    R, n = c["R"], g.n
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t, t.numpy()
+
+    keep = [pinned(x) for x in (g.row_ptr, g.col, g.J, g.h, c["betas"])]
+    rp, col, J, h, betas = [k[1] for k in keep]
+    out_s = torch.empty((R, n), dtype=torch.int8).pin_memory()
+    out_f = torch.empty((R, n), dtype=torch.int32).pin_memory()
+    out_e = torch.empty(R, dtype=torch.int64).pin_memory()
+    out_t = torch.empty(R, dtype=torch.int32).pin_memory()
+    out_c = torch.empty(2, dtype=torch.int64).pin_memory()
+    h2d = rp.nbytes + col.nbytes + J.nbytes + h.nbytes + betas.nbytes
+    d2h = out_s.numel() + 4 * out_f.numel() + 8 * R + 4 * R + 16
+    import ctypes
+    lib = ising._lib
+    P = lambda a, t: ctypes.cast(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data, t)
+
+    def one_step():
+        hd = ising.ising_create(n, rp, col, J, h, g.n_slices)
+        ising.ising_set_stream(hd, stream.cuda_stream)
+        ising.ising_replicas_init(hd, R, betas, seed, args.rng, c["field_bits"])
+        ising.ising_run(hd, SWEEPS_PER_STEP, SWAP_EVERY)
+        ising._check(lib.ising_read_state(hd, P(out_s, ising._i8p), P(out_f, ising._i32p),
+                                          P(out_e, ising._i64p), P(out_t, ising._i32p),
+                                          P(out_c, ising._u64p)))
+        ising.ising_destroy(hd)
+
+    one_step()  # warm (allocations, module load)
+    steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    val = world * attempts_per_step(c) * steps / dt
+    return {"value": val, "unit": "attempts/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": 1e3 * dt / steps}
+
+
+# ------------------------------------------------------------- roofline
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def avg_degree(g):
+    return float(g.row_ptr[-1]) / g.n
+
+
+def ops_per_attempt(g, rng):
+    """Algorithmic integer operations of one attempt: the random word (MT19937
+    recurrence + tempering ~17, Philox4x32-10 80 per 4 words = 20), the
+    acceptance test (~6: field read, Trotter part, product, threshold read,
+    two compares) and the flip's masked neighbour updates (3 per neighbour:
+    address, product, add) on the average degree."""
+    rng_ops = 17 if rng == "mt19937" else 20
+    return rng_ops + 6 + 3 * avg_degree(g)
+
+
+def int_peak_tops(clocks):
+    """Integer issue peak: 152 SMs x 4 sub-partitions x 32 lanes x SM clock
+    (one 32-bit integer op per lane per clock).  Uses the median SM clock
+    sampled during the run, else the maximum clock."""
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    return 152 * 4 * 32 * mhz * 1e6 / 1e12, mhz
+
+
+def roofline(c, rng, attempts, kernel_ms, launches, clocks):
+    g = c["graph"]
+    peak, mhz = int_peak_tops(clocks)
+    if kernel_ms <= 0 or launches <= 0:
+        return None
+    ops = attempts * ops_per_attempt(g, rng)
+    achieved = ops / (kernel_ms * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(f"fast_kernel_cfg1_{rng}")
+        except Exception:
+            traffic = None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_basis": f"152 SM x 128 lanes x {mhz:.0f} MHz sampled SM clock (derived, not measured)",
+            "kernel_ms_per_launch": kernel_ms / launches, "launches": int(launches),
+            "ops_per_attempt": ops_per_attempt(g, rng)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_baseline(c, rng, seconds):
+    import oracle
+    sim = oracle.Sim(c["graph"], c["betas"], seed=c["seed"], rng=rng)
+    t0 = time.perf_counter()
+    sim.run(4, 1)
+    dt = time.perf_counter() - t0
+    sweeps = max(4, int(seconds / max(dt / 4, 1e-6)))
+    t0 = time.perf_counter()
+    sim.run(sweeps, 1)
+    dt = time.perf_counter() - t0
+    att = c["graph"].n * c["R"] * sweeps
+    return {"value": att / dt, "unit": "attempts/s", "cores": sim.threads, "kind": "oracle",
+            "sample": f"same model and ladder, {sweeps} sweeps + PT after each ({att:.3e} attempts, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    c = workload()
+    sim = oracle.Sim(c["graph"], c["betas"], seed=c["seed"], rng=args.rng)
+    per = 5  # sweeps per reference step (a bounded sample of the 200-sweep step)
+    for _ in range(args.warmup):
+        sim.run(per, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.run(per, 1)
+    dt = time.perf_counter() - t0
+    att = c["graph"].n * c["R"] * per * args.steps
+    val = att / dt
+    line = {"impl": "reference", "metric": "spin-flip attempts/s", "value": val,
+            "unit": "attempts/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int8 spins/int64 fields/uint32 RNG", "data": "synthetic",
+            "config": {"workload": "32x32 lattice x 32 Trotter slices (32768 spins), 256 replicas, betas 0.05-5.0 geometric, PT each sweep",
+                       "rng": args.rng, "sweeps_per_step": per},
+            "cpu_baseline": {"value": val, "unit": "attempts/s", "cores": sim.threads, "kind": "oracle",
+                             "sample": f"{per} sweeps + PT per step (bounded sample of the 200-sweep step)"},
+            "e2e": {"value": val, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -175,15 +175,39 @@ int32_t ising_load(ising_t h, const void* buf, size_t size);
 typedef struct {
     int32_t n, slices, slice_size, levels, slice_depth, replicas;
     int32_t replicas_per_block, threads_per_block, blocks, smem_bytes;
-    int32_t persistent_ok; /* 1 if ising_run uses the single persistent launch */
+    int32_t persistent_ok; /* 1 if ising_run fuses PT into one persistent launch */
     int32_t field_bits, rng_mode, kmax;
+    int32_t fast_kernel;   /* 0 generic kernel, 1 register-resident kernel,
+                              2 its lean variant (one replica per block,
+                              M in {4,8,16,32}, degree <= 6, |J| <= 63) */
 } ising_info_t;
 int32_t ising_get_info(ising_t h, ising_info_t* out);
 
-/* Override the launch shape (0 = automatic): replicas per block, threads per
- * block, and whether ising_run may use the persistent launch. */
+/* launch_flags of ising_set_launch */
+#define ISING_LAUNCH_PERSISTENT 1 /* allow the persistent launch with fused PT */
+#define ISING_LAUNCH_GENERIC 2    /* force the generic (shared-memory column) kernel */
+#define ISING_LAUNCH_NO_LEAN 4    /* do not use the lean register-resident variant */
+
+/* Override the launch shape: replicas per block (0 = automatic, else a power
+ * of two <= 32), threads per block (0 = automatic, else a multiple of 32 and
+ * of the replicas per block, <= 1024) and launch_flags (ISING_LAUNCH_*; the
+ * default of a new handle is ISING_LAUNCH_PERSISTENT).  Results are identical
+ * for every accepted shape; only speed changes.  Errors: INVALID_ARG,
+ * UNSUPPORTED (the shape does not fit the kernel's limits). */
 int32_t ising_set_launch(ising_t h, int32_t replicas_per_block, int32_t threads_per_block,
-                         int32_t allow_persistent);
+                         int32_t launch_flags);
+
+/* Launch statistics of a handle.  With profiling on, every sweep-kernel
+ * launch is bracketed by CUDA events on its stream (graphs are bypassed) and
+ * kernel_ms sums their elapsed times; ising_get_stats then synchronises. */
+typedef struct {
+    int64_t launches;       /* kernels this handle launched (all kinds)       */
+    int64_t sweep_launches; /* of which sweep kernels                         */
+    int64_t timed_launches; /* sweep launches bracketed by events             */
+    double kernel_ms;       /* summed event time of the timed sweep launches  */
+} ising_stats_t;
+int32_t ising_set_profiling(ising_t h, int32_t on);
+int32_t ising_get_stats(ising_t h, ising_stats_t* out);
 
 /* Release all device memory of the handle (NULL is ignored). */
 int32_t ising_destroy(ising_t h);

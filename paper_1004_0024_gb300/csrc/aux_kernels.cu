@@ -11,8 +11,25 @@ namespace {
 // last 1024 words, so slot w & 1023 (written) never aliases a slot read in the
 // same step (reads reach back 624 words at most).  Output j of the stream is
 // temper(x_{624+j}).
+__device__ __forceinline__ uint32_t mt_step_word(uint32_t* ring, unsigned long long w)
+{
+    const uint32_t x = mt_recur(ring[(w - 624) & (kMtRing - 1)], ring[(w - 623) & (kMtRing - 1)],
+                                ring[(w - 227) & (kMtRing - 1)]);
+    ring[w & (kMtRing - 1)] = x;
+    return mt_temper(x);
+}
+
+// Sweep words are consumed column-major ([replica][position][slice]), but the
+// stream produces them slice by slice.  Words of four consecutive slices are
+// collected in shared memory and each column's 4-word block is then written
+// with one 16-byte store; the per-step barriers therefore only wait on shared
+// memory.  `group` words of the stream = 4 slices (fewer at the end of a
+// sweep when M is not a multiple of 4).
+constexpr int kGenGroupMaxS = 4096;  // slice sizes up to this use the staged path
+
 __global__ void __launch_bounds__(256) mt_gen_kernel(const MtGenArgs a)
 {
+    extern __shared__ __align__(16) uint32_t gbuf[];  // [4][S] staged words
     __shared__ uint32_t ring[kMtRing];
     const int stream = a.first_stream + blockIdx.x;
     const bool swap = a.do_swap && stream == a.R;
@@ -20,54 +37,73 @@ __global__ void __launch_bounds__(256) mt_gen_kernel(const MtGenArgs a)
     for (int i = threadIdx.x; i < kMtRing; i += blockDim.x)
         ring[i] = gring[i];
     const unsigned long long w0 = a.pos[stream];
-
-    long long nwords = a.nwords;
-    int par0 = 0, n_first = 0, n_pair = 0;
-    if (swap) {
-        // words of `swap_passes` passes starting at pass parity par0
-        const unsigned long long p0 = a.counters[1];
-        par0 = int(p0 & 1ull);
-        const int n_even = a.R / 2;        // pairs (0,1),(2,3),...  = floor(R/2)
-        const int n_odd = (a.R - 1) / 2;   // pairs (1,2),(3,4),...  = floor((R-1)/2)
-        n_first = par0 ? n_odd : n_even;
-        n_pair = n_even + n_odd;
-        const long long full = a.swap_passes / 2;
-        nwords = full * n_pair + ((a.swap_passes & 1) ? n_first : 0);
-    }
     __syncthreads();
 
-    for (long long base = 0; base < nwords; base += kMtStep) {
-        const long long cnt = min((long long)kMtStep, nwords - base);
-        if (threadIdx.x < cnt) {
-            const long long k = base + threadIdx.x;
-            const unsigned long long w = w0 + (unsigned long long)k;
-            const uint32_t x = mt_recur(ring[(w - 624) & (kMtRing - 1)],
-                                        ring[(w - 623) & (kMtRing - 1)],
-                                        ring[(w - 227) & (kMtRing - 1)]);
-            ring[w & (kMtRing - 1)] = x;
-            const uint32_t out = mt_temper(x);
-            if (swap) {
+    long long nwords = a.nwords;
+    if (swap) {
+        // words of `swap_passes` passes starting at pass parity par0
+        const int par0 = int(a.counters[1] & 1ull);
+        const int n_even = a.R / 2;        // pairs (0,1),(2,3),...  = floor(R/2)
+        const int n_odd = (a.R - 1) / 2;   // pairs (1,2),(3,4),...  = floor((R-1)/2)
+        const int n_first = par0 ? n_odd : n_even;
+        const int n_pair = n_even + n_odd;
+        nwords = (long long)(a.swap_passes / 2) * n_pair + ((a.swap_passes & 1) ? n_first : 0);
+        for (long long base = 0; base < nwords; base += kMtStep) {
+            const long long cnt = min((long long)kMtStep, nwords - base);
+            if (threadIdx.x < cnt) {
+                const long long k = base + threadIdx.x;
+                const uint32_t out = mt_step_word(ring, w0 + (unsigned long long)k);
                 const long long cyc = k / n_pair, rem = k - cyc * n_pair;
-                long long prel;
-                int j;
-                if (rem < n_first) {
-                    prel = 2 * cyc;
-                    j = int(rem);
-                } else {
-                    prel = 2 * cyc + 1;
-                    j = int(rem - n_first);
-                }
+                const long long prel = (rem < n_first) ? 2 * cyc : 2 * cyc + 1;
+                const int j = int((rem < n_first) ? rem : rem - n_first);
                 a.swbuf[size_t(prel) * a.maxpairs + j] = out;
-            } else if (a.mode == 1) {
-                a.spins[size_t(stream) * a.N + k] = (out >> 31) ? int8_t(1) : int8_t(-1);
-            } else {
-                const long long c = k / a.N;
-                const int i = int(k - c * a.N);
-                const int t = i / a.S, q = i - t * a.S;
-                a.wbuf[size_t(c) * a.wbuf_sweep_stride + (size_t(stream) * a.S + a.pos_of_site[q]) * a.Mp + t] = out;
+            }
+            __syncthreads();
+        }
+    } else if (a.mode == 1 || a.S > kGenGroupMaxS) {
+        // initial spins, or slices too large to stage: direct stores
+        for (long long base = 0; base < nwords; base += kMtStep) {
+            const long long cnt = min((long long)kMtStep, nwords - base);
+            if (threadIdx.x < cnt) {
+                const long long k = base + threadIdx.x;
+                const uint32_t out = mt_step_word(ring, w0 + (unsigned long long)k);
+                if (a.mode == 1) {
+                    a.spins[size_t(stream) * a.N + k] = (out >> 31) ? int8_t(1) : int8_t(-1);
+                } else {
+                    const long long c = k / a.N;
+                    const int i = int(k - c * a.N);
+                    const int t = i / a.S, q = i - t * a.S;
+                    a.wbuf[size_t(c) * a.wbuf_sweep_stride +
+                           (size_t(stream) * a.S + a.pos_of_site[q]) * a.Mp + t] = out;
+                }
+            }
+            __syncthreads();
+        }
+    } else {
+        const int S = a.S, M = a.M;
+        const long long sweeps = nwords / a.N;
+        long long k0 = 0;  // stream offset of the current group
+        for (long long c = 0; c < sweeps; ++c) {
+            uint32_t* wsw = a.wbuf + size_t(c) * a.wbuf_sweep_stride + size_t(stream) * S * a.Mp;
+            for (int t0 = 0; t0 < M; t0 += 4) {
+                const int group = min(4, M - t0) * S;
+                for (int base = 0; base < group; base += kMtStep) {
+                    const int cnt = min(kMtStep, group - base);
+                    if (int(threadIdx.x) < cnt) {
+                        const int kk = base + threadIdx.x;
+                        gbuf[kk] = mt_step_word(ring, w0 + (unsigned long long)(k0 + kk));
+                    }
+                    __syncthreads();
+                }
+                // flush: column q gets words of slices t0..t0+3 as one 16-byte store
+                for (int q = threadIdx.x; q < S; q += blockDim.x) {
+                    const uint4 v = make_uint4(gbuf[q], gbuf[S + q], gbuf[2 * S + q], gbuf[3 * S + q]);
+                    *reinterpret_cast<uint4*>(wsw + size_t(a.pos_of_site[q]) * a.Mp + t0) = v;
+                }
+                __syncthreads();
+                k0 += group;
             }
         }
-        __syncthreads();
     }
     for (int i = threadIdx.x; i < kMtRing; i += blockDim.x)
         gring[i] = ring[i];
@@ -155,8 +191,17 @@ __global__ void __launch_bounds__(1024) pt_kernel(const PtArgs a)
 
 cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st)
 {
-    mt_gen_kernel<<<blocks, 256, 0, st>>>(a);
+    // staged slices: 4 x S words (the kernel reads gbuf[2S + q], gbuf[3S + q]
+    // even for a final group of fewer than 4 slices, so all 4S are allocated)
+    const size_t smem = (a.mode == 0 && a.S <= kGenGroupMaxS) ? 16u * a.S : 0u;
+    mt_gen_kernel<<<blocks, 256, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t mt_gen_set_smem_limit()
+{
+    return cudaFuncSetAttribute(mt_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                16 * kGenGroupMaxS);
 }
 
 cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst,

@@ -1,0 +1,76 @@
+// Launch helpers of the register-resident sweep kernel (fast_impl.cuh).
+#include <algorithm>
+
+#include "lean_impl.cuh"
+
+namespace isg {
+namespace {
+
+void* pick(int field_bits, int rng, int cmax, bool lean = false)
+{
+    if (lean)
+        return field_bits == 16 ? lean_kernel_i16(rng, cmax) : lean_kernel_i32(rng, cmax);
+    return field_bits == 16 ? fast_kernel_i16(rng, cmax) : fast_kernel_i32(rng, cmax);
+}
+
+size_t g_fast_max_dyn = 0;
+
+}  // namespace
+
+size_t fast_smem_bytes(const SweepArgs& a, int field_bits)
+{
+    const size_t b = fast_detail::fast_layout(a, field_bits == 16 ? 2 : 4).total;
+    return (g_fast_max_dyn && b > g_fast_max_dyn) ? size_t(-1) : b;
+}
+
+cudaError_t fast_set_smem_limits()
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess)
+        return e;
+    size_t lim = size_t(optin);
+    for (int lean : {0, 1})
+        for (int fb : {16, 32})
+            for (int rng : {0, 1})
+                for (int cm : {1, 2, 4, 8}) {
+                    void* fn = pick(fb, rng, cm, lean != 0);
+                    if (!fn)
+                        continue;
+                    cudaFuncAttributes fa;
+                    e = cudaFuncGetAttributes(&fa, fn);
+                    if (e != cudaSuccess)
+                        return e;
+                    const size_t dyn = size_t(optin) - fa.sharedSizeBytes;
+                    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
+                    if (e != cudaSuccess)
+                        return e;
+                    lim = std::min(lim, dyn);
+                }
+    g_fast_max_dyn = lim;
+    return cudaSuccess;
+}
+
+cudaError_t fast_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
+                                   int* out, bool lean)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pick(field_bits, rng, cmax, lean),
+                                                         threads, smem);
+}
+
+cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
+                        size_t smem, bool cooperative, cudaStream_t st, bool lean)
+{
+    void* fn = pick(field_bits, a.rng, cmax, lean);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    SweepArgs copy = a;
+    void* args[] = {&copy};
+    if (cooperative)
+        return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, st);
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+}  // namespace isg

@@ -84,6 +84,7 @@ int32_t upload(T** d, const std::vector<T>& h)
 }
 
 int g_num_sms = 0;
+int g_coop = 0;
 std::once_flag g_once;
 cudaError_t g_init_err = cudaSuccess;
 
@@ -96,6 +97,14 @@ cudaError_t device_setup()
             g_init_err = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_init_err == cudaSuccess)
             g_init_err = sweep_set_smem_limits();
+        if (g_init_err == cudaSuccess)
+            g_init_err = fast_set_smem_limits();
+        if (g_init_err == cudaSuccess)
+            g_init_err = mt_gen_set_smem_limit();
+        int coop = 0;
+        if (g_init_err == cudaSuccess)
+            g_init_err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        g_coop = coop;
     });
     return g_init_err;
 }
@@ -115,7 +124,7 @@ void mt_seed_ring(uint32_t seed, uint32_t* ring)
 
 struct ising_s {
     // graph
-    int n = 0, M = 1, S = 0, W = 1, Mp = 4, D0 = 0, D = 0;
+    int n = 0, M = 1, S = 0, W = 1, Mp = 4, D0 = 0, D = 0, max_sp_deg = 0, max_sp_J = 0;
     long long kmax = 0, ebound = 0;
     std::vector<int> row_ptr, col, J, h;
     std::vector<int> site, pos, lev0p, jtau, nbr_off;
@@ -138,13 +147,26 @@ struct ising_s {
     long long* d_swoff = nullptr;
     int* d_swlen = nullptr;
     uint32_t *d_wbuf = nullptr, *d_swbuf = nullptr;
+    int* d_Epub = nullptr;
+    unsigned* d_gridbar = nullptr;
     long long wbuf_cap = 0, swbuf_cap = 0;  // sweeps / passes
     // launch configuration
     int G = 1, T = 32, cmax = 1, blocks = 1, tables_smem = 1, thr_smem = 1;
     size_t smem = 0;
+    // register-resident kernel (M <= 32, tables in shared memory)
+    bool use_fast = false, use_lean = false, persistent_ok = false, fast_off = false, lean_off = false;
+    int fast_cmax = 1;
+    size_t fast_smem = 0, smem_fused = 0;
     int G_req = 0, T_req = 0, allow_persistent = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream used only to record graphs
+    // statistics
+    long long n_launches = 0, n_sweep_launches = 0;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    long long n_timed = 0;
+    double kernel_ms = 0.0;
+    std::map<std::pair<long long, int>, std::pair<long long, long long>> graph_counts;
     std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
 
     void free_replicas();
@@ -181,6 +203,8 @@ void ising_s::free_replicas()
     dfree(d_swlen);
     dfree(d_wbuf);
     dfree(d_swbuf);
+    dfree(d_Epub);
+    dfree(d_gridbar);
     wbuf_cap = swbuf_cap = 0;
     inited = false;
 }
@@ -188,6 +212,11 @@ void ising_s::free_replicas()
 void ising_s::free_all()
 {
     free_replicas();
+    for (auto& ev : ev_pending) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    ev_pending.clear();
     if (cap_stream)
         cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
@@ -320,6 +349,13 @@ int32_t extract_slices(ising_s* g)
     g->jtau.resize(S);
     g->nbr_off.assign(S + 1, 0);
     g->nbr.clear();
+    g->max_sp_deg = 0;
+    g->max_sp_J = 0;
+    for (int q = 0; q < S; ++q) {
+        g->max_sp_deg = std::max(g->max_sp_deg, int(sp[q].size()));
+        for (auto& e : sp[q])
+            g->max_sp_J = std::max(g->max_sp_J, std::abs(e.second));
+    }
     for (int p = 0; p < S; ++p) {
         const int q = g->site[p];
         g->lev0p[p] = lev[q];
@@ -332,6 +368,49 @@ int32_t extract_slices(ising_s* g)
 }
 
 // --------------------------------------------------- launch configuration
+SweepArgs base_args(ising_s* g);
+
+// The register-resident kernel keeps up to 8 columns per thread; it needs
+// M <= 32, the slice tables in shared memory and spatial degree <= 255.
+void choose_fast(ising_s* g)
+{
+    g->use_fast = false;
+    g->use_lean = false;
+    g->persistent_ok = false;
+    if (g->M > 32 || !g->tables_smem || g->max_sp_deg > 255 || g->fast_off)
+        return;
+    const long long C = ((long long)g->S * g->G + g->T - 1) / g->T;
+    int cmax = 0;
+    for (int m : {1, 2, 4, 8})
+        if (C <= m) {
+            cmax = m;
+            break;
+        }
+    if (cmax == 0 || g->T > (cmax <= 2 ? 1024 : (cmax == 4 ? 512 : 256)))
+        return;
+    // lean variant: one replica per block, power-of-two M >= 4, small degree
+    // and couplings, at most 4 columns per thread within its register budget
+    g->use_lean = g->G == 1 && (g->M == 4 || g->M == 8 || g->M == 16 || g->M == 32) &&
+                  g->max_sp_deg <= 6 && g->max_sp_J <= 63 && cmax <= 4 &&
+                  g->T <= (cmax <= 1 ? 1024 : (cmax == 2 ? 512 : 256)) && !g->lean_off;
+    SweepArgs a = base_args(g);
+    const size_t smem = fast_smem_bytes(a, g->field_bits);
+    if (smem == size_t(-1))
+        return;
+    g->use_fast = true;
+    g->fast_cmax = cmax;
+    g->fast_smem = smem;
+    a.swap_every = 1;
+    g->smem_fused = fast_smem_bytes(a, g->field_bits);
+    if (!g_coop || !g->allow_persistent || g->smem_fused == size_t(-1) || g->R > 16384)
+        return;
+    int per_sm = 0;
+    if (fast_max_blocks_per_sm(g->field_bits, cmax, g->rng, g->T, g->smem_fused, &per_sm,
+                               g->use_lean) != cudaSuccess)
+        return;
+    g->persistent_ok = (long long)per_sm * g_num_sms >= g->blocks;
+}
+
 SweepArgs base_args(ising_s* g)
 {
     SweepArgs a{};
@@ -366,6 +445,21 @@ SweepArgs base_args(ising_s* g)
     a.done_blocks = g->d_done;
     a.err = g->d_err;
     a.wbuf_sweep_stride = (long long)g->R * g->S * g->Mp;
+    int lg = 0;
+    while ((1 << lg) < g->G)
+        ++lg;
+    a.lg_G = lg;
+    a.swap_every = 0;
+    a.slot_of_temp = g->d_slot;
+    a.temp_of_slot_out = g->d_temp;
+    a.swap_acc = g->d_swap_acc;
+    a.swthr = g->d_swthr;
+    a.swoff = g->d_swoff;
+    a.swlen = g->d_swlen;
+    a.swbuf = g->d_swbuf;
+    a.maxpairs = g->maxpairs;
+    a.E_pub = g->d_Epub;
+    a.gridbar = g->d_gridbar;
     return a;
 }
 
@@ -414,6 +508,7 @@ int32_t choose_launch(ising_s* g)
             g->thr_smem = a.thr_smem;
             g->smem = smem;
             g->blocks = (g->R + G - 1) / G;
+            choose_fast(g);
             return ISING_OK;
         }
     }
@@ -422,9 +517,9 @@ int32_t choose_launch(ising_s* g)
 
 // ------------------------------------------------------- launch planning
 struct Op {
-    enum Kind { GEN, SWEEP, PT } kind;
-    int sweeps;   // GEN: sweeps of words; SWEEP: sweeps
-    int passes;   // GEN: passes of swap words
+    enum Kind { GEN, SWEEP, PT, FUSED } kind;
+    int sweeps;   // GEN: sweeps of words; SWEEP/FUSED: sweeps
+    int passes;   // GEN: passes of swap words; FUSED: sweeps between PT passes
     int offset;   // SWEEP: sweep offset into wbuf; PT: pass offset into swbuf
 };
 
@@ -438,6 +533,24 @@ std::vector<Op> plan(ising_s* g, long long n, int swap_every, long long cap)
         if (mt)
             ops.push_back({Op::GEN, 0, 1, 0});
         ops.push_back({Op::PT, 0, 0, 0});
+        return ops;
+    }
+    if (g->persistent_ok && swap_every > 0 && swap_every <= cap) {
+        // whole groups of `swap_every` sweeps run in persistent launches with
+        // the PT pass fused; a trailing partial group has no PT pass
+        const long long per = (cap / swap_every) * swap_every;
+        while (n - done >= swap_every) {
+            const long long m = std::min(per, ((n - done) / swap_every) * swap_every);
+            if (mt)
+                ops.push_back({Op::GEN, int(m), int(m / swap_every), 0});
+            ops.push_back({Op::FUSED, int(m), swap_every, 0});
+            done += m;
+        }
+        if (done < n) {
+            if (mt)
+                ops.push_back({Op::GEN, int(n - done), 0, 0});
+            ops.push_back({Op::SWEEP, int(n - done), 0, 0});
+        }
         return ops;
     }
     while (done < n) {
@@ -496,6 +609,13 @@ int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
 {
     for (const Op& op : ops) {
         cudaError_t e = cudaSuccess;
+        const bool is_sweep = op.kind == Op::SWEEP || op.kind == Op::FUSED;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (is_sweep && g->profiling) {
+            CK(cudaEventCreate(&ev0));
+            CK(cudaEventCreate(&ev1));
+            CK(cudaEventRecord(ev0, st));
+        }
         if (op.kind == Op::GEN) {
             MtGenArgs a{};
             a.ring = g->d_mtring;
@@ -525,7 +645,20 @@ int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
             SweepArgs a = base_args(g);
             a.nsweeps = op.sweeps;
             a.wbuf = g->d_wbuf ? g->d_wbuf + size_t(op.offset) * a.wbuf_sweep_stride : nullptr;
-            e = launch_sweep(a, g->field_bits, g->cmax, g->T, g->blocks, g->smem, st);
+            if (g->use_fast)
+                e = launch_fast(a, g->field_bits, g->fast_cmax, g->T, g->blocks, g->fast_smem, false, st,
+                                g->use_lean);
+            else
+                e = launch_sweep(a, g->field_bits, g->cmax, g->T, g->blocks, g->smem, st);
+        } else if (op.kind == Op::FUSED) {
+            SweepArgs a = base_args(g);
+            a.nsweeps = op.sweeps;
+            a.swap_every = op.passes;
+            a.wbuf = g->d_wbuf;
+            e = cudaMemsetAsync(g->d_gridbar, 0, sizeof(unsigned), st);
+            if (e == cudaSuccess)
+                e = launch_fast(a, g->field_bits, g->fast_cmax, g->T, g->blocks, g->smem_fused, true, st,
+                                g->use_lean);
         } else {
             PtArgs a{};
             a.R = g->R;
@@ -547,8 +680,30 @@ int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
         }
         if (e != cudaSuccess)
             return cuda_fail(e, "kernel launch");
+        if (ev1) {
+            CK(cudaEventRecord(ev1, st));
+            g->ev_pending.emplace_back(ev0, ev1);
+        }
     }
     return ISING_OK;
+}
+
+// kernels launched by a plan (GEN with nothing to do launches nothing)
+std::pair<long long, long long> count_kernels(ising_s* g, const std::vector<Op>& ops)
+{
+    long long all = 0, sweeps = 0;
+    for (const Op& op : ops) {
+        if (op.kind == Op::GEN)
+            all += (op.sweeps > 0 || op.passes > 0) ? 1 : 0;
+        else if (op.kind == Op::PT)
+            all += 1;
+        else {
+            all += 1;
+            sweeps += 1;
+        }
+    }
+    (void)g;
+    return {all, sweeps};
 }
 
 int32_t check_device_error(ising_s* g)
@@ -732,7 +887,8 @@ int32_t ising_replicas_init(ising_t g, int32_t R, const double* betas, uint32_t 
         (rc = dalloc(&g->d_swap_acc, std::max(R - 1, 1))) || (rc = dalloc(&g->d_counters, 2)) ||
         (rc = dalloc(&g->d_done, 1)) || (rc = upload(&g->d_thr, thr)) ||
         (rc = upload(&g->d_swthr, swthr)) || (rc = upload(&g->d_swoff, swoff)) ||
-        (rc = upload(&g->d_swlen, swlen))) {
+        (rc = upload(&g->d_swlen, swlen)) || (rc = dalloc(&g->d_Epub, 2 * size_t(R))) ||
+        (rc = dalloc(&g->d_gridbar, 1))) {
         g->free_replicas();
         return rc;
     }
@@ -785,7 +941,15 @@ static int32_t run_ops(ising_t g, long long n, int swap_every, bool use_graph)
     if (rc)
         return rc;
     std::vector<Op> ops = plan(g, n, swap_every, cap);
-    if (!use_graph)
+    bool has_fused = false;
+    for (const Op& op : ops)
+        has_fused |= op.kind == Op::FUSED;
+    const auto counts = count_kernels(g, ops);
+    g->n_launches += counts.first;
+    g->n_sweep_launches += counts.second;
+    // persistent runs are one or two launches and profiled runs time each
+    // launch: neither needs a graph
+    if (!use_graph || has_fused || g->profiling)
         return enqueue(g, ops, g->stream);
     const auto key = std::make_pair(n, swap_every);
     auto it = g->graphs.find(key);
@@ -1002,7 +1166,8 @@ int32_t ising_get_info(ising_t g, ising_info_t* o)
     o->threads_per_block = g->T;
     o->blocks = g->blocks;
     o->smem_bytes = int(g->smem);
-    o->persistent_ok = 0;
+    o->persistent_ok = g->persistent_ok ? 1 : 0;
+    o->fast_kernel = g->use_fast ? (g->use_lean ? 2 : 1) : 0;
     o->field_bits = g->field_bits;
     o->rng_mode = g->rng;
     o->kmax = int(std::min<long long>(g->kmax, INT32_MAX));
@@ -1010,7 +1175,7 @@ int32_t ising_get_info(ising_t g, ising_info_t* o)
 }
 
 int32_t ising_set_launch(ising_t g, int32_t replicas_per_block, int32_t threads_per_block,
-                         int32_t allow_persistent)
+                         int32_t launch_flags)
 {
     if (!g)
         return fail(ISING_ERR_INVALID_ARG, "NULL handle");
@@ -1019,10 +1184,43 @@ int32_t ising_set_launch(ising_t g, int32_t replicas_per_block, int32_t threads_
         return fail(ISING_ERR_INVALID_ARG, "replicas_per_block must be 0 or a power of two <= 32");
     g->G_req = replicas_per_block;
     g->T_req = threads_per_block;
-    g->allow_persistent = allow_persistent;
+    g->allow_persistent = (launch_flags & ISING_LAUNCH_PERSISTENT) ? 1 : 0;
+    g->fast_off = (launch_flags & ISING_LAUNCH_GENERIC) != 0;
+    g->lean_off = (launch_flags & ISING_LAUNCH_NO_LEAN) != 0;
     g->drop_graphs();
     if (g->inited)
         return choose_launch(g);
+    return ISING_OK;
+}
+
+int32_t ising_set_profiling(ising_t g, int32_t on)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    g->profiling = on != 0;
+    return ISING_OK;
+}
+
+int32_t ising_get_stats(ising_t g, ising_stats_t* out)
+{
+    if (!g || !out)
+        return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!g->ev_pending.empty()) {
+        CK(cudaStreamSynchronize(g->stream));
+        for (auto& ev : g->ev_pending) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev.first, ev.second));
+            g->kernel_ms += ms;
+            ++g->n_timed;
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+        g->ev_pending.clear();
+    }
+    out->launches = g->n_launches;
+    out->sweep_launches = g->n_sweep_launches;
+    out->timed_launches = g->n_timed;
+    out->kernel_ms = g->kernel_ms;
     return ISING_OK;
 }
 

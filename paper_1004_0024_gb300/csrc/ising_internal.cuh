@@ -56,6 +56,19 @@ struct SweepArgs {
     long long wbuf_sweep_stride;   // = R*S*Mp
     unsigned int* done_blocks;     // block-completion counter for the counter update
     int* err;
+    // parallel tempering fused into a persistent (cooperative) launch
+    int swap_every;                // 0: no PT pass inside this launch
+    int* slot_of_temp;             // [R]
+    int* temp_of_slot_out;         // [R] written back by block 0
+    unsigned long long* swap_acc;  // [R-1]
+    const uint32_t* swthr;
+    const long long* swoff;
+    const int* swlen;
+    const uint32_t* swbuf;         // MT swap words [pass][maxpairs]
+    int maxpairs;
+    int* E_pub;                    // [2][R] energies published for the PT pass
+    unsigned int* gridbar;         // grid barrier arrivals (zeroed before the launch)
+    int lg_G;                      // log2(G)
 };
 
 struct PtArgs {
@@ -177,6 +190,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     return false;
 }
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
+// Unlike a register load it is not waited for by bar.sync.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_err(int* err, int code)
 {
     atomicCAS(err, 0, code);
@@ -192,7 +218,17 @@ int sweep_cmax_for(int c);
 cudaError_t sweep_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
                                     int* out);
 cudaError_t launch_pt(const PtArgs& a, cudaStream_t st);
+// register-resident sweep for M <= 32 with tables in shared memory
+size_t fast_smem_bytes(const SweepArgs& a, int field_bits);
+cudaError_t fast_set_smem_limits();
+// lean = true selects the lean variant (lean_impl.cuh): G = 1, M in {4,8,16,32},
+// spatial degree <= 6, |J| <= 63, at most 4 columns per thread
+cudaError_t fast_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
+                                   int* out, bool lean);
+cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
+                        size_t smem, bool cooperative, cudaStream_t st, bool lean);
 cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st);
+cudaError_t mt_gen_set_smem_limit();
 cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst,
                                cudaStream_t st);
 cudaError_t launch_state_init(const int8_t* spins, void* fields, int field_bits, int* E, int R,

@@ -1,0 +1,9 @@
+// int32-field instantiations of the lean sweep kernel.
+#include "lean_impl.cuh"
+
+namespace isg {
+void* lean_kernel_i32(int rng, int cmax)
+{
+    return rng == 0 ? lean_detail::pick_lean<int32_t, 0>(cmax) : lean_detail::pick_lean<int32_t, 1>(cmax);
+}
+}  // namespace isg

@@ -43,7 +43,12 @@ class IsingInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in (
         "n", "slices", "slice_size", "levels", "slice_depth", "replicas",
         "replicas_per_block", "threads_per_block", "blocks", "smem_bytes", "persistent_ok",
-        "field_bits", "rng_mode", "kmax")]
+        "field_bits", "rng_mode", "kmax", "fast_kernel")]
+
+
+class IsingStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("sweep_launches", ctypes.c_int64),
+                ("timed_launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double)]
 
 
 _SIGS = {
@@ -62,6 +67,8 @@ _SIGS = {
     "ising_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int32),
     "ising_get_info": ([_vp, ctypes.POINTER(IsingInfo)], ctypes.c_int32),
     "ising_set_launch": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
+    "ising_set_profiling": ([_vp, ctypes.c_int32], ctypes.c_int32),
+    "ising_get_stats": ([_vp, ctypes.POINTER(IsingStats)], ctypes.c_int32),
     "ising_destroy": ([_vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -168,9 +175,24 @@ def ising_get_info(h) -> dict:
     return {name: getattr(info, name) for name, _ in IsingInfo._fields_}
 
 
-def ising_set_launch(h, replicas_per_block=0, threads_per_block=0, allow_persistent=1):
+LAUNCH_PERSISTENT = 1
+LAUNCH_GENERIC = 2
+LAUNCH_NO_LEAN = 4
+
+
+def ising_set_launch(h, replicas_per_block=0, threads_per_block=0, launch_flags=LAUNCH_PERSISTENT):
     _check(_lib.ising_set_launch(h, int(replicas_per_block), int(threads_per_block),
-                                 int(allow_persistent)))
+                                 int(launch_flags)))
+
+
+def ising_set_profiling(h, on=True):
+    _check(_lib.ising_set_profiling(h, 1 if on else 0))
+
+
+def ising_get_stats(h) -> dict:
+    st = IsingStats()
+    _check(_lib.ising_get_stats(h, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in IsingStats._fields_}
 
 
 def ising_destroy(h):
@@ -228,8 +250,14 @@ class Ising:
     def info(self) -> dict:
         return ising_get_info(self.h)
 
-    def set_launch(self, replicas_per_block=0, threads_per_block=0, allow_persistent=1):
-        ising_set_launch(self.h, replicas_per_block, threads_per_block, allow_persistent)
+    def set_launch(self, replicas_per_block=0, threads_per_block=0, launch_flags=LAUNCH_PERSISTENT):
+        ising_set_launch(self.h, replicas_per_block, threads_per_block, launch_flags)
+
+    def set_profiling(self, on=True):
+        ising_set_profiling(self.h, on)
+
+    def stats(self) -> dict:
+        return ising_get_stats(self.h)
 
     def close(self):
         if getattr(self, "h", None):

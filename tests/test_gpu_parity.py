@@ -99,7 +99,7 @@ def test_unstructured_graphs(ising, n, edges, R, rng):
     assert_same(dev, ref)
 
 
-@pytest.mark.parametrize("L,M", [(3, 2), (3, 3), (4, 4), (3, 5), (4, 33), (3, 64)])
+@pytest.mark.parametrize("L,M", [(3, 2), (3, 3), (4, 4), (3, 5), (5, 8), (4, 33), (3, 64)])
 @pytest.mark.parametrize("rng", ["mt19937", "philox"])
 def test_slice_counts(ising, L, M, rng):
     g = W.layered_graph(L, M, graph_seed=L * 100 + M, j_tau=3)
@@ -112,13 +112,43 @@ def test_slice_counts(ising, L, M, rng):
 
 @pytest.mark.parametrize("G,T", [(1, 32), (2, 64), (4, 128), (8, 256), (1, 1024), (8, 64),
                                  (2, 32)])
-def test_launch_shapes_give_identical_results(ising, G, T):
+@pytest.mark.parametrize("flags", [0, 1, 2, 4, 5])
+def test_launch_shapes_give_identical_results(ising, G, T, flags):
+    """Every accepted launch shape and kernel path gives the same chain (flags:
+    1 persistent launch with fused PT, 2 generic kernel, 4 no lean variant;
+    0 and 4 are per-sweep launches)."""
     c = W.config0()
     betas = W.geometric_betas(30, 0.1, 3.0)  # 30 replicas: ragged last block
-    dev, ref = pair(ising, c["graph"], betas, 7, "mt19937", 16, launch=(G, T, 0))
-    dev.run(25, 1)
-    ref.run(25, 1)
-    assert_same(dev, ref)
+    for rng in ("mt19937", "philox"):
+        dev, ref = pair(ising, c["graph"], betas, 7, rng, 16, launch=(G, T, flags))
+        info = dev.info()
+        if flags == 2:
+            assert info["fast_kernel"] == 0
+        dev.run(25, 1)
+        ref.run(25, 1)
+        assert_same(dev, ref, f"{rng} {info}")
+        dev.run(7, 3)
+        ref.run(7, 3)
+        assert_same(dev, ref, f"{rng} {info}")
+
+
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_config1_paths_agree(ising, rng):
+    """cfg1 through every kernel (lean, register-resident, generic), persistent
+    with fused PT (the bench path) or per-sweep launches: identical to the
+    oracle after 12 sweeps."""
+    c = W.config1()
+    ref = oracle.Sim(c["graph"], c["betas"], seed=c["seed"], rng=rng)
+    ref.run(12, 1)
+    for flags, kernel in ((1, 2), (0, 2), (5, 1), (4, 1), (2, 0)):
+        dev = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=16)
+        dev.set_launch(0, 0, flags)
+        info = dev.info()
+        assert info["fast_kernel"] == kernel
+        assert info["persistent_ok"] == (flags & 1)
+        dev.run(12, 1)
+        assert_same(dev, ref, f"flags {flags}")
+        dev.close()
 
 
 def test_separate_sweep_and_pt_calls(ising):
