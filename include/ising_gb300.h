@@ -209,6 +209,31 @@ typedef struct {
 int32_t ising_set_profiling(ising_t h, int32_t on);
 int32_t ising_get_stats(ising_t h, ising_stats_t* out);
 
+/*
+ * ising_run_noalloc -- ising_run for callers that cannot allocate device
+ * memory when they run: code executing inside another framework's
+ * allocation-free phase (a real-time loop, a region where device allocation
+ * is forbidden) creates and initialises the handle beforehand, then advances
+ * it with this call, which launches kernels and allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  The paper has no
+ * counterpart; it is a deployment convenience.
+ *   Same arguments and results as ising_run(h, n, swap_every), bit for bit.
+ *   Requires ISING_RNG_PHILOX (MT19937 words are staged in a buffer that
+ *   grows with replicas x spins), R <= 16384, and a handle whose replicas all
+ *   fit on the GPU at once (ising_get_info(...).persistent_ok == 1).
+ *   Scratch (grid-barrier and block counters, energies exchanged for the PT
+ *   passes) is one file-scope device array of 128 KB that every GPU loading
+ *   the library holds until the process exits.  The first call on a device
+ *   resolves that array's device address (cudaGetSymbolAddress); make that
+ *   first call before any stream capture.  Every call shares the array and
+ *   it keeps the last call's contents (the counters are cleared by each
+ *   call), so calls whose kernels overlap on the GPU race: issue them on one
+ *   stream, or otherwise order them.
+ * Errors: NOT_INITIALISED, INVALID_ARG (n < 0, R > 16384), UNSUPPORTED (MT19937
+ * mode, or no persistent launch for this handle), CUDA.
+ */
+int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every);
+
 /* Release all device memory of the handle (NULL is ignored). */
 int32_t ising_destroy(ising_t h);
 

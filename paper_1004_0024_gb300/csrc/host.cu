@@ -720,6 +720,34 @@ int32_t check_device_error(ising_s* g)
 
 }  // namespace
 
+// Launch description of a handle's sweep kernels, for entry points defined in
+// other translation units (noalloc.cu).  Returns NOT_INITIALISED /
+// UNSUPPORTED when the handle has no register-resident fused path.
+int32_t isg_fused_launch(ising_t g, isg::FusedLaunch* out)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    if (!g->use_fast || !g->persistent_ok)
+        return fail(ISING_ERR_UNSUPPORTED,
+                    "this model/ladder has no persistent fused launch (replicas do not all fit on the GPU)");
+    out->args = base_args(g);
+    out->field_bits = g->field_bits;
+    out->cmax = g->fast_cmax;
+    out->threads = g->T;
+    out->blocks = g->blocks;
+    out->smem_plain = g->fast_smem;
+    out->smem_fused = g->smem_fused;
+    out->lean = g->use_lean;
+    out->stream = g->stream;
+    out->R = g->R;
+    out->rng = g->rng;
+    return ISING_OK;
+}
+
+int32_t isg_fail(int32_t code, const char* msg) { return fail(code, msg); }
+
 // ====================================================================== ABI
 extern "C" {
 

@@ -208,6 +208,15 @@ __device__ __forceinline__ void set_err(int* err, int code)
     atomicCAS(err, 0, code);
 }
 
+// Everything needed to launch a handle's register-resident sweep kernel.
+struct FusedLaunch {
+    SweepArgs args;
+    int field_bits, cmax, threads, blocks, R, rng;
+    size_t smem_plain, smem_fused;
+    bool lean;
+    cudaStream_t stream;
+};
+
 // ---------------------------------------------------------- launchers
 cudaError_t launch_sweep(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
                          size_t smem, cudaStream_t st);

@@ -67,6 +67,7 @@ _SIGS = {
     "ising_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int32),
     "ising_get_info": ([_vp, ctypes.POINTER(IsingInfo)], ctypes.c_int32),
     "ising_set_launch": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
+    "ising_run_noalloc": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int32),
     "ising_set_profiling": ([_vp, ctypes.c_int32], ctypes.c_int32),
     "ising_get_stats": ([_vp, ctypes.POINTER(IsingStats)], ctypes.c_int32),
     "ising_destroy": ([_vp], ctypes.c_int32),
@@ -136,6 +137,11 @@ def ising_pt_swap(h):
 
 def ising_run(h, n, swap_every=1):
     _check(_lib.ising_run(h, int(n), int(swap_every)))
+
+
+def ising_run_noalloc(h, n, swap_every=1):
+    """ising_run without any device allocation (Philox handles only)."""
+    _check(_lib.ising_run_noalloc(h, int(n), int(swap_every)))
 
 
 def ising_read_state(h, R, n):
