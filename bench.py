@@ -207,7 +207,8 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
-    line["roofline"] = roofline(c, args.rng, per_step * args.steps, kernel_ms, sweep_launches, clocks)
+    line["roofline"] = roofline(c, args.rng, per_step * args.steps, kernel_ms, sweep_launches, clocks,
+                                info["fast_kernel"])
     if e2e is not None:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu:
@@ -296,7 +297,7 @@ def int_peak_tops(clocks):
     return 152 * 4 * 32 * mhz * 1e6 / 1e12, mhz
 
 
-def roofline(c, rng, attempts, kernel_ms, launches, clocks):
+def roofline(c, rng, attempts, kernel_ms, launches, clocks, kernel):
     g = c["graph"]
     peak, mhz = int_peak_tops(clocks)
     if kernel_ms <= 0 or launches <= 0:
@@ -304,10 +305,10 @@ def roofline(c, rng, attempts, kernel_ms, launches, clocks):
     ops = attempts * ops_per_attempt(g, rng)
     achieved = ops / (kernel_ms * 1e-3) / 1e12
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
+    prof = os.path.join(ROOT, "profiles", "lean_kernel_cfg1_dram_traffic.json")
+    if kernel == 2 and os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get(f"fast_kernel_cfg1_{rng}")
+            traffic = json.load(open(prof)).get(f"lean_kernel_cfg1_{rng}")
         except Exception:
             traffic = None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
