@@ -234,6 +234,63 @@ int32_t ising_get_stats(ising_t h, ising_stats_t* out);
  */
 int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every);
 
+/* ------------------------------------------------------------------------
+ * Ragged batches: many independent instances (different models, sizes and
+ * ladders) advanced together.  Not in the paper (its production runs sweep
+ * "millions of systems", section 1, one CPU thread each); a batch lets one
+ * GPU work on thousands of them at once.
+ *
+ * Each instance is described by ising_instance_t (host arrays, copied).
+ * Instance b behaves exactly like a handle made with ising_create +
+ * ising_replicas_init from the same arguments, except that its Philox
+ * counters use instance = b (MT19937 streams depend only on its seed).
+ * Execution: instances whose whole ladder fits one block ("resident") run all
+ * sweeps of a call in one batched launch with the PT pass inside the block;
+ * the others ("streamed") run one batched sweep launch per PT group followed
+ * by one batched PT launch.  The sequence is recorded as one CUDA graph per
+ * (n, swap_every) whose shape classes run as parallel branches.
+ * ---------------------------------------------------------------------- */
+typedef struct ising_batch_s* ising_batch_t;
+
+typedef struct {
+    int32_t n;              /* spins (see ising_create)                   */
+    const int32_t* row_ptr; /* [n+1]                                      */
+    const int32_t* col;     /* [row_ptr[n]]                               */
+    const int32_t* J;       /* [row_ptr[n]]                               */
+    const int32_t* h;       /* [n]                                        */
+    int32_t n_slices;       /* M (see ising_create)                       */
+    int32_t replicas;       /* R                                          */
+    const double* betas;    /* [R] ascending, > 0                         */
+    uint32_t seed;          /* base seed (see ising_replicas_init)        */
+} ising_instance_t;
+
+/* Create and initialise n_inst instances with one RNG mode and field width.
+ * flags reserved (0).  Errors: as ising_create / ising_replicas_init for the
+ * first failing instance (its index is in ising_last_error()). */
+int32_t ising_batch_create(int32_t n_inst, const ising_instance_t* inst, int32_t rng_mode,
+                           int32_t field_bits, uint32_t flags, ising_batch_t* out);
+int32_t ising_batch_set_stream(ising_batch_t b, void* cuda_stream);
+
+/* Autotuner: for every shape class (slice size, slices, replicas) time the
+ * candidate launch shapes (resident vs streamed, replicas and threads per
+ * block) on a representative instance and keep the cheapest in SM-time per
+ * sweep.  flags reserved (0).  Results never change, only speed.  Runs
+ * sweeps on scratch copies of the representatives, never on the batch. */
+int32_t ising_batch_autotune(ising_batch_t b, uint32_t flags);
+
+/* n sweeps of every instance with a PT pass after every swap_every-th sweep
+ * of this call (swap_every <= 0: none).  Asynchronous. */
+int32_t ising_batch_run(ising_batch_t b, int64_t n, int32_t swap_every);
+
+/* State of instance `inst` (see ising_read_state; synchronises). */
+int32_t ising_batch_read_state(ising_batch_t b, int32_t inst, int8_t* spins, int32_t* fields,
+                               int64_t* energy, int32_t* temp_of_slot, uint64_t* counters);
+int32_t ising_batch_read_swap_stats(ising_batch_t b, int32_t inst, uint64_t* accepted);
+
+/* Launch facts of instance `inst`; resident = 1 if it runs as one block. */
+int32_t ising_batch_get_info(ising_batch_t b, int32_t inst, ising_info_t* out, int32_t* resident);
+int32_t ising_batch_destroy(ising_batch_t b);
+
 /* Release all device memory of the handle (NULL is ignored). */
 int32_t ising_destroy(ising_t h);
 

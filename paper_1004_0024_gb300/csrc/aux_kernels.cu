@@ -27,11 +27,10 @@ __device__ __forceinline__ uint32_t mt_step_word(uint32_t* ring, unsigned long l
 // sweep when M is not a multiple of 4).
 constexpr int kGenGroupMaxS = 4096;  // slice sizes up to this use the staged path
 
-__global__ void __launch_bounds__(256) mt_gen_kernel(const MtGenArgs a)
+__device__ __forceinline__ void mt_gen_body(const MtGenArgs& a, const int stream)
 {
     extern __shared__ __align__(16) uint32_t gbuf[];  // [4][S] staged words
     __shared__ uint32_t ring[kMtRing];
-    const int stream = a.first_stream + blockIdx.x;
     const bool swap = a.do_swap && stream == a.R;
     uint32_t* gring = a.ring + size_t(stream) * kMtRing;
     for (int i = threadIdx.x; i < kMtRing; i += blockDim.x)
@@ -111,6 +110,23 @@ __global__ void __launch_bounds__(256) mt_gen_kernel(const MtGenArgs a)
         a.pos[stream] = w0 + (unsigned long long)nwords;
 }
 
+__global__ void __launch_bounds__(256) mt_gen_kernel(const MtGenArgs a)
+{
+    mt_gen_body(a, a.first_stream + int(blockIdx.x));
+}
+
+// Batched: block b generates stream items[b].block of instance items[b].inst.
+__global__ void __launch_bounds__(256) mt_gen_batch_kernel(const MtGenArgs* __restrict__ args,
+                                                           const BatchItem* __restrict__ items)
+{
+    __shared__ MtGenArgs sa;
+    const BatchItem it = items[blockIdx.x];
+    if (threadIdx.x == 0)
+        sa = args[it.inst];
+    __syncthreads();
+    mt_gen_body(sa, it.block);
+}
+
 // ------------------------------------------------------------ Philox init
 __global__ void philox_init_kernel(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst)
 {
@@ -157,7 +173,7 @@ __global__ void __launch_bounds__(256) state_init_kernel(const int8_t* spins, FT
 // -------------------------------------------------------- PT pass
 // Pass p tries pairs (k, k+1), k = 2j + (p & 1).  Pairs of one pass are
 // disjoint, so each thread decides and applies its own pairs.
-__global__ void __launch_bounds__(1024) pt_kernel(const PtArgs a)
+__device__ __forceinline__ void pt_body(const PtArgs& a)
 {
     const unsigned long long p = a.counters[1];
     const int par = int(p & 1ull);
@@ -187,6 +203,18 @@ __global__ void __launch_bounds__(1024) pt_kernel(const PtArgs a)
         a.counters[1] = p + 1ull;
 }
 
+__global__ void __launch_bounds__(1024) pt_kernel(const PtArgs a) { pt_body(a); }
+
+// Batched: block b runs one PT pass of instance b.
+__global__ void __launch_bounds__(1024) pt_batch_kernel(const PtArgs* __restrict__ args)
+{
+    __shared__ PtArgs sa;
+    if (threadIdx.x == 0)
+        sa = args[blockIdx.x];
+    __syncthreads();
+    pt_body(sa);
+}
+
 }  // namespace
 
 cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st)
@@ -200,8 +228,28 @@ cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st)
 
 cudaError_t mt_gen_set_smem_limit()
 {
-    return cudaFuncSetAttribute(mt_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                16 * kGenGroupMaxS);
+    cudaError_t e = cudaFuncSetAttribute(mt_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         16 * kGenGroupMaxS);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mt_gen_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 16 * kGenGroupMaxS);
+    return e;
+}
+
+cudaError_t launch_mt_gen_batch(const MtGenArgs* args, const BatchItem* items, int n_items,
+                                int max_S, cudaStream_t st)
+{
+    const size_t smem = (max_S <= kGenGroupMaxS) ? 16u * size_t(max_S) : 0u;
+    mt_gen_batch_kernel<<<n_items, 256, smem, st>>>(args, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pt_batch(const PtArgs* args, int n_inst, int max_R, cudaStream_t st)
+{
+    int threads = ((max_R / 2 + 31) / 32) * 32;
+    threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+    pt_batch_kernel<<<n_inst, threads, 0, st>>>(args);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst,

@@ -6,11 +6,11 @@
 namespace isg {
 namespace {
 
-void* pick(int field_bits, int rng, int cmax, bool lean = false)
+void* pick(int field_bits, int rng, int cmax, bool lean = false, bool batch = false)
 {
     if (lean)
-        return field_bits == 16 ? lean_kernel_i16(rng, cmax) : lean_kernel_i32(rng, cmax);
-    return field_bits == 16 ? fast_kernel_i16(rng, cmax) : fast_kernel_i32(rng, cmax);
+        return field_bits == 16 ? lean_kernel_i16(rng, cmax, batch) : lean_kernel_i32(rng, cmax, batch);
+    return field_bits == 16 ? fast_kernel_i16(rng, cmax, batch) : fast_kernel_i32(rng, cmax, batch);
 }
 
 size_t g_fast_max_dyn = 0;
@@ -32,11 +32,12 @@ cudaError_t fast_set_smem_limits()
     if (e != cudaSuccess)
         return e;
     size_t lim = size_t(optin);
+    for (int batch : {0, 1})
     for (int lean : {0, 1})
         for (int fb : {16, 32})
             for (int rng : {0, 1})
                 for (int cm : {1, 2, 4, 8}) {
-                    void* fn = pick(fb, rng, cm, lean != 0);
+                    void* fn = pick(fb, rng, cm, lean != 0, batch != 0);
                     if (!fn)
                         continue;
                     cudaFuncAttributes fa;
@@ -71,6 +72,17 @@ cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int thread
     if (cooperative)
         return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, st);
     return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+cudaError_t launch_fast_batch(const SweepArgs* args, const BatchItem* items, int n_items,
+                              int field_bits, int rng, int cmax, int threads, size_t smem, bool lean,
+                              cudaStream_t st)
+{
+    void* fn = pick(field_bits, rng, cmax, lean, true);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    void* params[] = {&args, &items};
+    return cudaLaunchKernel(fn, dim3(n_items), dim3(threads), params, smem, st);
 }
 
 }  // namespace isg

@@ -2,8 +2,8 @@
 #include "fast_impl.cuh"
 
 namespace isg {
-void* fast_kernel_i16(int rng, int cmax)
+void* fast_kernel_i16(int rng, int cmax, bool batch)
 {
-    return rng == 0 ? fast_detail::pick_fast<int16_t, 0>(cmax) : fast_detail::pick_fast<int16_t, 1>(cmax);
+    return rng == 0 ? fast_detail::pick_fast<int16_t, 0>(cmax, batch) : fast_detail::pick_fast<int16_t, 1>(cmax, batch);
 }
 }  // namespace isg

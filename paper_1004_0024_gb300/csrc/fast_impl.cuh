@@ -122,8 +122,10 @@ __host__ __device__ constexpr int fast_max_threads(int cmax)
     return cmax <= 2 ? 1024 : (cmax == 4 ? 512 : 256);
 }
 
+// Body of one block: `blk` is the block's index within its instance and
+// `nblk` the instance's number of blocks (the grid size for a single instance).
 template <typename FT, int RNG, int CMAX>
-__global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const SweepArgs a)
+__device__ __forceinline__ void fast_body(const SweepArgs& a, const int blk, const int nblk)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_flag;
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int T = blockDim.x, tid = threadIdx.x;
     const int S = a.S, M = a.M, N = a.N, G = a.G, K = a.K, R = a.R;
-    const int r0 = blockIdx.x * G;
+    const int r0 = blk * G;
     const int Gb = min(G, R - r0);
     const int* nbr_off = reinterpret_cast<const int*>(smem + L.nbr_off);
     const uint32_t* nbr = reinterpret_cast<const uint32_t*>(smem + L.nbr);
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
 
     const unsigned long long sweep0 = a.counters[0];
     const unsigned long long pass0 = a.counters[1];
-    const int nblk = (M + 3) >> 2;
+    const int nrb = (M + 3) >> 2;  // random-word blocks per column
     int npass = 0;
     int dE = 0;
 
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
                 const int p = (tid + c * T) >> a.lg_G;
                 const int q = (RNG == 1) ? site[p] : 0;
                 cur[c] = rng_block<RNG>(a, wsw, rg, p, q, 0, sid);
-                if (RNG == 0 && nblk > 1)
+                if (RNG == 0 && nrb > 1)
                     nxt[c] = rng_block<RNG>(a, wsw, rg, p, q, 1, sid);
             }
         }
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
                     const int p = (tid + c * T) >> a.lg_G;
                     if (t > 0 && (t & 3) == 0) {
                         cur[c] = nxt[c];
-                        if (RNG == 0 && (t >> 2) + 1 < nblk)
+                        if (RNG == 0 && (t >> 2) + 1 < nrb)
                             nxt[c] = rng_block<RNG>(a, wsw, rg, p, 0, (t >> 2) + 1, sid);
                     }
                     const int fidx = (p * M + t) * G + g;
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
                                          m2s * int(int16_t(en & 0xFFFFu)));
                         }
                     }
-                    if (RNG == 1 && (t & 3) == 1 && (t >> 2) + 1 < nblk)
+                    if (RNG == 1 && (t & 3) == 1 && (t >> 2) + 1 < nrb)
                         nxt[c] = rng_block<RNG>(a, wsw, rg, p, site[p], (t >> 2) + 1, sid);
                 }
             }
@@ -297,7 +299,9 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
                 Ep[r0 + tid] = e;
                 eacc[tid] = 0;
             }
-            if (!grid_sync(a.gridbar, unsigned(npass + 1) * gridDim.x, a.err, &s_flag))
+            if (nblk == 1)  // a one-block instance has nobody else to wait for
+                __syncthreads();
+            else if (!grid_sync(a.gridbar, unsigned(npass + 1) * unsigned(nblk), a.err, &s_flag))
                 return;
             if (tid < 32) {
                 const unsigned long long p = pass0 + npass;
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
                         slot_s[k + 1] = sa;
                         temp_s[sa] = k + 1;
                         temp_s[sb] = k;
-                        if (blockIdx.x == 0)
+                        if (blk == 0)
                             a.swap_acc[k] += 1ull;
                     }
                 }
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
             }
         }
     }
-    if (fused && blockIdx.x == 0)
+    if (fused && blk == 0)
         for (int i = tid; i < R; i += T) {
             a.slot_of_temp[i] = slot_s[i];
             a.temp_of_slot_out[i] = temp_s[i];
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
     if (tid == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(a.done_blocks, 1u);
-        if (prev == gridDim.x - 1) {
+        if (prev == unsigned(nblk) - 1u) {
             a.counters[0] += (unsigned long long)a.nsweeps;
             a.counters[1] += (unsigned long long)npass;
             *a.done_blocks = 0u;
@@ -371,21 +375,45 @@ __global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const S
     }
 }
 
+template <typename FT, int RNG, int CMAX>
+__global__ void __launch_bounds__(fast_max_threads(CMAX), 1) fast_kernel(const SweepArgs a)
+{
+    fast_body<FT, RNG, CMAX>(a, int(blockIdx.x), int(gridDim.x));
+}
+
+// Batched launch over many instances: each block copies its instance's
+// arguments into shared memory (so that every later read is a shared load).
+template <typename FT, int RNG, int CMAX>
+__global__ void __launch_bounds__(fast_max_threads(CMAX), 1)
+    fast_batch_kernel(const SweepArgs* __restrict__ args, const BatchItem* __restrict__ items)
+{
+    __shared__ SweepArgs sa;
+    const BatchItem it = items[blockIdx.x];
+    if (threadIdx.x == 0)
+        sa = args[it.inst];
+    __syncthreads();
+    fast_body<FT, RNG, CMAX>(sa, it.block, sa.inst_blocks);
+}
+
 template <typename FT, int RNG>
-void* pick_fast(int cmax)
+void* pick_fast(int cmax, bool batch = false)
 {
     switch (cmax) {
-    case 1: return reinterpret_cast<void*>(&fast_kernel<FT, RNG, 1>);
-    case 2: return reinterpret_cast<void*>(&fast_kernel<FT, RNG, 2>);
-    case 4: return reinterpret_cast<void*>(&fast_kernel<FT, RNG, 4>);
-    case 8: return reinterpret_cast<void*>(&fast_kernel<FT, RNG, 8>);
+    case 1: return batch ? reinterpret_cast<void*>(&fast_batch_kernel<FT, RNG, 1>)
+                   : reinterpret_cast<void*>(&fast_kernel<FT, RNG, 1>);
+    case 2: return batch ? reinterpret_cast<void*>(&fast_batch_kernel<FT, RNG, 2>)
+                   : reinterpret_cast<void*>(&fast_kernel<FT, RNG, 2>);
+    case 4: return batch ? reinterpret_cast<void*>(&fast_batch_kernel<FT, RNG, 4>)
+                   : reinterpret_cast<void*>(&fast_kernel<FT, RNG, 4>);
+    case 8: return batch ? reinterpret_cast<void*>(&fast_batch_kernel<FT, RNG, 8>)
+                   : reinterpret_cast<void*>(&fast_kernel<FT, RNG, 8>);
     default: return nullptr;
     }
 }
 
 }  // namespace fast_detail
 
-void* fast_kernel_i16(int rng, int cmax);
-void* fast_kernel_i32(int rng, int cmax);
+void* fast_kernel_i16(int rng, int cmax, bool batch = false);
+void* fast_kernel_i32(int rng, int cmax, bool batch = false);
 
 }  // namespace isg

@@ -8,6 +8,7 @@
 // that reads every mutable quantity from device memory, so a recorded CUDA
 // graph can be replayed any number of times.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <tuple>
 #include <vector>
 
 #include "ising_gb300.h"
@@ -150,6 +152,7 @@ struct ising_s {
     int* d_Epub = nullptr;
     unsigned* d_gridbar = nullptr;
     long long wbuf_cap = 0, swbuf_cap = 0;  // sweeps / passes
+    long long word_budget = 1LL << 30;     // bytes of pre-generated MT19937 words
     // launch configuration
     int G = 1, T = 32, cmax = 1, blocks = 1, tables_smem = 1, thr_smem = 1;
     size_t smem = 0;
@@ -580,8 +583,7 @@ long long words_cap(ising_s* g, long long n)
     if (g->rng != ISING_RNG_MT19937)
         return std::max<long long>(n, 1);
     const long long per_sweep = (long long)g->R * g->S * g->Mp * 4;
-    const long long budget = 1LL << 30;
-    return std::max<long long>(1, std::min<long long>(std::max<long long>(n, 1), budget / per_sweep));
+    return std::max<long long>(1, std::min<long long>(std::max<long long>(n, 1), g->word_budget / per_sweep));
 }
 
 int32_t ensure_buffers(ising_s* g, long long cap_sweeps, long long cap_passes)
@@ -605,6 +607,69 @@ int32_t ensure_buffers(ising_s* g, long long cap_sweeps, long long cap_passes)
     return ISING_OK;
 }
 
+// Kernel argument records of one planned op (also used by batched launches).
+MtGenArgs gen_args(ising_s* g, const Op& op, int* blocks)
+{
+    MtGenArgs a{};
+    a.ring = g->d_mtring;
+    a.pos = g->d_mtpos;
+    a.R = g->R;
+    a.mode = 0;
+    a.nwords = (long long)op.sweeps * g->n;
+    a.N = g->n;
+    a.S = g->S;
+    a.M = g->M;
+    a.Mp = g->Mp;
+    a.pos_of_site = g->d_pos;
+    a.wbuf = g->d_wbuf;
+    a.wbuf_sweep_stride = (long long)g->R * g->S * g->Mp;
+    a.do_swap = op.passes > 0;
+    a.swap_passes = op.passes;
+    a.swbuf = g->d_swbuf;
+    a.maxpairs = g->maxpairs;
+    a.counters = g->d_counters;
+    // blocks: the R replica streams (when sweep words are needed), then the
+    // swap stream (index R) when passes are needed
+    a.first_stream = op.sweeps > 0 ? 0 : g->R;
+    *blocks = (op.sweeps > 0 ? g->R : 0) + (a.do_swap ? 1 : 0);
+    return a;
+}
+
+SweepArgs sweep_args(ising_s* g, const Op& op)
+{
+    SweepArgs a = base_args(g);
+    a.nsweeps = op.sweeps;
+    a.inst_blocks = g->blocks;
+    if (op.kind == Op::FUSED) {
+        a.swap_every = op.passes;
+        a.wbuf = g->d_wbuf;
+    } else {
+        a.wbuf = g->d_wbuf ? g->d_wbuf + size_t(op.offset) * a.wbuf_sweep_stride : nullptr;
+    }
+    return a;
+}
+
+PtArgs pt_args(ising_s* g, const Op& op)
+{
+    PtArgs a{};
+    a.R = g->R;
+    a.E = g->d_E;
+    a.temp_of_slot = g->d_temp;
+    a.slot_of_temp = g->d_slot;
+    a.swap_acc = g->d_swap_acc;
+    a.counters = g->d_counters;
+    a.swthr = g->d_swthr;
+    a.swoff = g->d_swoff;
+    a.swlen = g->d_swlen;
+    a.rng = g->rng;
+    a.seed = g->seed;
+    a.inst = g->inst;
+    a.swbuf = g->d_swbuf;
+    a.maxpairs = g->maxpairs;
+    a.pass_rel = op.offset;
+    return a;
+}
+
 int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
 {
     for (const Op& op : ops) {
@@ -617,66 +682,25 @@ int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
             CK(cudaEventRecord(ev0, st));
         }
         if (op.kind == Op::GEN) {
-            MtGenArgs a{};
-            a.ring = g->d_mtring;
-            a.pos = g->d_mtpos;
-            a.R = g->R;
-            a.mode = 0;
-            a.nwords = (long long)op.sweeps * g->n;
-            a.N = g->n;
-            a.S = g->S;
-            a.M = g->M;
-            a.Mp = g->Mp;
-            a.pos_of_site = g->d_pos;
-            a.wbuf = g->d_wbuf;
-            a.wbuf_sweep_stride = (long long)g->R * g->S * g->Mp;
-            a.do_swap = op.passes > 0;
-            a.swap_passes = op.passes;
-            a.swbuf = g->d_swbuf;
-            a.maxpairs = g->maxpairs;
-            a.counters = g->d_counters;
-            // blocks: the R replica streams (when sweep words are needed), then
-            // the swap stream (index R) when passes are needed
-            a.first_stream = op.sweeps > 0 ? 0 : g->R;
-            const int blocks = (op.sweeps > 0 ? g->R : 0) + (a.do_swap ? 1 : 0);
+            int blocks = 0;
+            const MtGenArgs a = gen_args(g, op, &blocks);
             if (blocks > 0)
                 e = launch_mt_gen(a, blocks, st);
         } else if (op.kind == Op::SWEEP) {
-            SweepArgs a = base_args(g);
-            a.nsweeps = op.sweeps;
-            a.wbuf = g->d_wbuf ? g->d_wbuf + size_t(op.offset) * a.wbuf_sweep_stride : nullptr;
+            const SweepArgs a = sweep_args(g, op);
             if (g->use_fast)
                 e = launch_fast(a, g->field_bits, g->fast_cmax, g->T, g->blocks, g->fast_smem, false, st,
                                 g->use_lean);
             else
                 e = launch_sweep(a, g->field_bits, g->cmax, g->T, g->blocks, g->smem, st);
         } else if (op.kind == Op::FUSED) {
-            SweepArgs a = base_args(g);
-            a.nsweeps = op.sweeps;
-            a.swap_every = op.passes;
-            a.wbuf = g->d_wbuf;
+            const SweepArgs a = sweep_args(g, op);
             e = cudaMemsetAsync(g->d_gridbar, 0, sizeof(unsigned), st);
             if (e == cudaSuccess)
                 e = launch_fast(a, g->field_bits, g->fast_cmax, g->T, g->blocks, g->smem_fused, true, st,
                                 g->use_lean);
         } else {
-            PtArgs a{};
-            a.R = g->R;
-            a.E = g->d_E;
-            a.temp_of_slot = g->d_temp;
-            a.slot_of_temp = g->d_slot;
-            a.swap_acc = g->d_swap_acc;
-            a.counters = g->d_counters;
-            a.swthr = g->d_swthr;
-            a.swoff = g->d_swoff;
-            a.swlen = g->d_swlen;
-            a.rng = g->rng;
-            a.seed = g->seed;
-            a.inst = g->inst;
-            a.swbuf = g->d_swbuf;
-            a.maxpairs = g->maxpairs;
-            a.pass_rel = op.offset;
-            e = launch_pt(a, st);
+            e = launch_pt(pt_args(g, op), st);
         }
         if (e != cudaSuccess)
             return cuda_fail(e, "kernel launch");
@@ -836,8 +860,17 @@ int32_t ising_set_stream(ising_t g, void* s)
     return ISING_OK;
 }
 
+static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uint32_t seed,
+                                  int32_t rng_mode, int32_t field_bits, uint32_t inst);
+
 int32_t ising_replicas_init(ising_t g, int32_t R, const double* betas, uint32_t seed,
                             int32_t rng_mode, int32_t field_bits)
+{
+    return replicas_init_impl(g, R, betas, seed, rng_mode, field_bits, 0u);
+}
+
+static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uint32_t seed,
+                                  int32_t rng_mode, int32_t field_bits, uint32_t inst)
 {
     if (!g)
         return fail(ISING_ERR_INVALID_ARG, "NULL handle");
@@ -858,6 +891,7 @@ int32_t ising_replicas_init(ising_t g, int32_t R, const double* betas, uint32_t 
     if ((long long)R * g->n > (1LL << 36))
         return fail(ISING_ERR_INVALID_ARG, "R * n too large");
     g->free_replicas();
+    g->inst = inst;
     g->R = R;
     g->rng = rng_mode;
     g->field_bits = field_bits;
@@ -1262,3 +1296,515 @@ int32_t ising_destroy(ising_t g)
 }
 
 }  // extern "C"
+
+// ============================================================ ragged batches
+// A batch owns one ordinary handle per instance.  Instances are grouped by
+// launch shape (kernel variant, field width, generator, columns per thread,
+// threads per block); every planned op of a group becomes ONE batched launch
+// whose blocks are (instance, block) items, and the groups run as parallel
+// branches of one recorded CUDA graph.
+struct ising_batch_s {
+    std::vector<ising_s*> inst;
+    std::vector<int> resident;  // 1: the whole ladder runs as one block
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only to record graphs
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    struct Run {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<void*> bufs;  // device argument records of the graph
+    };
+    std::map<std::pair<long long, int>, Run> runs;
+
+    void drop_runs()
+    {
+        for (auto& kv : runs) {
+            if (kv.second.exec)
+                cudaGraphExecDestroy(kv.second.exec);
+            for (void* p : kv.second.bufs)
+                cudaFree(p);
+        }
+        runs.clear();
+    }
+};
+
+namespace {
+
+constexpr int kBatchSide = 32;  // parallel graph branches
+
+struct GroupKey {
+    int kind;  // 0 resident (fused PT in one block), 1 streamed, 2 generic kernel
+    int lean, field_bits, rng, cmax, T;
+    bool operator<(const GroupKey& o) const
+    {
+        return std::tie(kind, lean, field_bits, rng, cmax, T) <
+               std::tie(o.kind, o.lean, o.field_bits, o.rng, o.cmax, o.T);
+    }
+};
+
+int pow2_at_least(int x)
+{
+    int p = 1;
+    while (p < x)
+        p <<= 1;
+    return p;
+}
+
+// Launch shape of an instance: `resident` asks for the whole ladder in one
+// block (G = next power of two >= R) with `T` threads (0 = automatic); else
+// the default shape without the persistent launch.  Returns whether the
+// instance ended up resident.
+bool configure_instance(ising_s* g, bool resident, int T, int G_streamed = 0)
+{
+    if (resident) {
+        const int G = pow2_at_least(g->R);
+        int Tr = T;
+        if (Tr <= 0) {
+            // fewest columns per thread that the thread cap allows
+            const long long cols = (long long)g->S * G;
+            for (int cm : {2, 4, 8}) {
+                const int tmax = cm <= 2 ? 1024 : (cm == 4 ? 512 : 256);
+                const int step = std::max(32, G);
+                const long long t = ((cols + cm - 1) / cm + step - 1) / step * step;
+                if (t <= tmax) {
+                    Tr = int(std::max<long long>(t, step));
+                    break;
+                }
+            }
+        }
+        if (G <= 64 && Tr > 0 && Tr <= 1024 && Tr % G == 0) {
+            g->G_req = G;
+            g->T_req = Tr;
+            g->allow_persistent = 1;
+            if (choose_launch(g) == ISING_OK && g->use_fast && g->blocks == 1 && g->persistent_ok)
+                return true;
+        }
+    }
+    g->G_req = G_streamed;
+    g->T_req = resident ? 0 : T;
+    g->allow_persistent = 0;
+    if (choose_launch(g) != ISING_OK) {
+        g->G_req = 0;
+        g->T_req = 0;
+        choose_launch(g);
+    }
+    return false;
+}
+
+GroupKey key_of(ising_batch_s* b, int i)
+{
+    ising_s* g = b->inst[i];
+    GroupKey k{};
+    k.kind = b->resident[i] ? 0 : (g->use_fast ? 1 : 2);
+    k.lean = g->use_lean ? 1 : 0;
+    k.field_bits = g->field_bits;
+    k.rng = g->rng;
+    k.cmax = g->use_fast ? g->fast_cmax : g->cmax;
+    k.T = g->T;
+    return k;
+}
+
+template <typename T>
+int32_t upload_raw(std::vector<void*>& keep, const std::vector<T>& h, const T** out)
+{
+    T* d = nullptr;
+    int32_t rc = dalloc(&d, std::max<size_t>(h.size(), 1));
+    if (rc)
+        return rc;
+    keep.push_back(d);
+    if (!h.empty())
+        CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *out = d;
+    return ISING_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// A group's ops, each with the device argument records of its batched launch.
+struct BatchOp {
+    Op op;
+    const void* args = nullptr;      // MtGenArgs / SweepArgs / PtArgs per instance
+    const BatchItem* items = nullptr;
+    int n_items = 0;
+};
+
+struct BatchGroup {
+    GroupKey key;
+    std::vector<int> ids;
+    std::vector<BatchOp> ops;
+    size_t smem_plain = 0, smem_fused = 0;
+    int max_S = 0, max_R = 0;
+};
+
+int32_t batch_record(ising_batch_s* b, long long n, int swap_every, ising_batch_s::Run* run)
+{
+    std::map<GroupKey, BatchGroup> groups;
+    for (int i = 0; i < int(b->inst.size()); ++i) {
+        const GroupKey k = key_of(b, i);
+        BatchGroup& gr = groups[k];
+        gr.key = k;
+        gr.ids.push_back(i);
+    }
+    std::vector<BatchGroup*> order;
+    for (auto& kv : groups) {
+        BatchGroup& gr = kv.second;
+        order.push_back(&gr);
+        long long cap = LLONG_MAX;
+        for (int i : gr.ids) {
+            ising_s* g = b->inst[i];
+            cap = std::min(cap, n > 0 ? words_cap(g, n) : 1LL);
+            gr.smem_plain = std::max(gr.smem_plain, g->fast_smem);
+            gr.smem_fused = std::max(gr.smem_fused, g->smem_fused);
+            gr.max_S = std::max(gr.max_S, g->S);
+            gr.max_R = std::max(gr.max_R, g->R);
+        }
+        for (int i : gr.ids) {
+            int32_t rc = ensure_buffers(b->inst[i], cap, cap);
+            if (rc)
+                return rc;
+        }
+        const std::vector<Op> ops = plan(b->inst[gr.ids[0]], n, swap_every, cap);
+        if (gr.key.kind == 2) {  // generic kernel: per-instance launches at capture time
+            for (const Op& op : ops)
+                gr.ops.push_back({op});
+            continue;
+        }
+        for (const Op& op : ops) {
+            BatchOp bo{op};
+            std::vector<BatchItem> items;
+            int32_t rc = ISING_OK;
+            if (op.kind == Op::GEN) {
+                std::vector<MtGenArgs> args;
+                for (int j = 0; j < int(gr.ids.size()); ++j) {
+                    int blocks = 0;
+                    const MtGenArgs a = gen_args(b->inst[gr.ids[j]], op, &blocks);
+                    args.push_back(a);
+                    for (int k = 0; k < blocks; ++k)
+                        items.push_back({j, a.first_stream + k});
+                }
+                const MtGenArgs* d = nullptr;
+                rc = upload_raw(run->bufs, args, &d);
+                bo.args = d;
+            } else if (op.kind == Op::PT) {
+                std::vector<PtArgs> args;
+                for (int i : gr.ids)
+                    args.push_back(pt_args(b->inst[i], op));
+                const PtArgs* d = nullptr;
+                rc = upload_raw(run->bufs, args, &d);
+                bo.args = d;
+                bo.n_items = int(args.size());
+            } else {
+                std::vector<SweepArgs> args;
+                for (int j = 0; j < int(gr.ids.size()); ++j) {
+                    ising_s* g = b->inst[gr.ids[j]];
+                    args.push_back(sweep_args(g, op));
+                    for (int k = 0; k < g->blocks; ++k)
+                        items.push_back({j, k});
+                }
+                const SweepArgs* d = nullptr;
+                rc = upload_raw(run->bufs, args, &d);
+                bo.args = d;
+            }
+            if (!rc && !items.empty()) {
+                bo.n_items = int(items.size());
+                rc = upload_raw(run->bufs, items, &bo.items);
+            }
+            if (rc)
+                return rc;
+            gr.ops.push_back(bo);
+        }
+    }
+
+    // ---- record: fork to the side streams, one group per branch, join
+    if (!b->cap) {
+        CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        b->side.resize(kBatchSide);
+        b->join.resize(kBatchSide);
+        for (int k = 0; k < kBatchSide; ++k) {
+            CK(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+        }
+    }
+    const int nside = std::min<int>(kBatchSide, std::max<int>(1, int(order.size())));
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->fork, b->cap);
+    for (int k = 0; k < nside && e == cudaSuccess; ++k)
+        e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+    int32_t rc = ISING_OK;
+    for (int gi = 0; gi < int(order.size()) && e == cudaSuccess && !rc; ++gi) {
+        BatchGroup& gr = *order[gi];
+        cudaStream_t st = b->side[gi % nside];
+        const GroupKey& k = gr.key;
+        if (k.kind == 2) {
+            std::vector<Op> ops;
+            for (const BatchOp& bo : gr.ops)
+                ops.push_back(bo.op);
+            for (int i : gr.ids)
+                if ((rc = enqueue(b->inst[i], ops, st)))
+                    break;
+            continue;
+        }
+        for (const BatchOp& bo : gr.ops) {
+            if (bo.n_items == 0)
+                continue;
+            if (bo.op.kind == Op::GEN)
+                e = launch_mt_gen_batch(static_cast<const MtGenArgs*>(bo.args), bo.items, bo.n_items,
+                                        gr.max_S, st);
+            else if (bo.op.kind == Op::PT)
+                e = launch_pt_batch(static_cast<const PtArgs*>(bo.args), bo.n_items, gr.max_R, st);
+            else
+                e = launch_fast_batch(static_cast<const SweepArgs*>(bo.args), bo.items, bo.n_items,
+                                      k.field_bits, k.rng, k.cmax, k.T,
+                                      bo.op.kind == Op::FUSED ? gr.smem_fused : gr.smem_plain,
+                                      k.lean != 0, st);
+            if (e != cudaSuccess)
+                break;
+        }
+    }
+    for (int k = 0; k < nside && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->join[k], b->side[k]);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (rc || e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        if (rc)
+            return rc;
+        return cuda_fail(e != cudaSuccess ? e : e2, "recording the batch graph");
+    }
+    e = cudaGraphInstantiate(&run->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGraphInstantiate (batch)");
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ising_batch_create(int32_t n_inst, const ising_instance_t* in, int32_t rng_mode,
+                           int32_t field_bits, uint32_t flags, ising_batch_t* out)
+{
+    if (!out || !in || n_inst < 1)
+        return fail(ISING_ERR_INVALID_ARG, "need n_inst >= 1 instances and an output pointer");
+    *out = nullptr;
+    if (flags != 0)
+        return fail(ISING_ERR_INVALID_ARG, "flags must be 0");
+    ising_batch_s* b = new ising_batch_s();
+    long long words_per_sweep = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        ising_t g = nullptr;
+        int32_t rc = ising_create(in[i].n, in[i].row_ptr, in[i].col, in[i].J, in[i].h, in[i].n_slices,
+                                  0u, &g);
+        if (!rc)
+            rc = replicas_init_impl(g, in[i].replicas, in[i].betas, in[i].seed, rng_mode, field_bits,
+                                    uint32_t(i));
+        if (rc) {
+            const std::string msg = "instance " + std::to_string(i) + ": " + g_err;
+            if (g)
+                ising_destroy(g);
+            ising_batch_destroy(b);
+            return fail(rc, msg);
+        }
+        b->inst.push_back(g);
+        words_per_sweep += (long long)g->R * g->S * g->Mp * 4;
+    }
+    // pre-generated MT19937 words: about 8 GB for the whole batch, the same
+    // number of sweeps per chunk for every instance
+    const long long chunk = std::max<long long>(1, (8LL << 30) / std::max<long long>(words_per_sweep, 1));
+    for (ising_s* g : b->inst)
+        g->word_budget = chunk * (long long)g->R * g->S * g->Mp * 4;
+    b->resident.resize(n_inst);
+    for (int i = 0; i < n_inst; ++i)
+        b->resident[i] = configure_instance(b->inst[i], true, 0) ? 1 : 0;
+    *out = b;
+    return ISING_OK;
+}
+
+int32_t ising_batch_set_stream(ising_batch_t b, void* s)
+{
+    if (!b)
+        return fail(ISING_ERR_INVALID_ARG, "NULL batch");
+    b->drop_runs();
+    b->stream = static_cast<cudaStream_t>(s);
+    for (ising_s* g : b->inst)
+        ising_set_stream(g, s);
+    return ISING_OK;
+}
+
+int32_t ising_batch_run(ising_batch_t b, int64_t n, int32_t swap_every)
+{
+    if (!b)
+        return fail(ISING_ERR_INVALID_ARG, "NULL batch");
+    if (n < 0)
+        return fail(ISING_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0)
+        return ISING_OK;
+    const auto key = std::make_pair((long long)n, swap_every > 0 ? int(swap_every) : 0);
+    auto it = b->runs.find(key);
+    if (it == b->runs.end()) {
+        ising_batch_s::Run run;
+        const int32_t rc = batch_record(b, n, key.second, &run);
+        if (rc) {
+            for (void* p : run.bufs)
+                cudaFree(p);
+            return rc;
+        }
+        it = b->runs.emplace(key, run).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, b->stream));
+    return ISING_OK;
+}
+
+int32_t ising_batch_read_state(ising_batch_t b, int32_t inst, int8_t* spins, int32_t* fields,
+                               int64_t* energy, int32_t* temp_of_slot, uint64_t* counters)
+{
+    if (!b || inst < 0 || inst >= int(b->inst.size()))
+        return fail(ISING_ERR_INVALID_ARG, "no such instance");
+    CK(cudaStreamSynchronize(b->stream));
+    return ising_read_state(b->inst[inst], spins, fields, energy, temp_of_slot, counters);
+}
+
+int32_t ising_batch_read_swap_stats(ising_batch_t b, int32_t inst, uint64_t* accepted)
+{
+    if (!b || inst < 0 || inst >= int(b->inst.size()))
+        return fail(ISING_ERR_INVALID_ARG, "no such instance");
+    CK(cudaStreamSynchronize(b->stream));
+    return ising_read_swap_stats(b->inst[inst], accepted);
+}
+
+int32_t ising_batch_get_info(ising_batch_t b, int32_t inst, ising_info_t* out, int32_t* resident)
+{
+    if (!b || inst < 0 || inst >= int(b->inst.size()))
+        return fail(ISING_ERR_INVALID_ARG, "no such instance");
+    if (resident)
+        *resident = b->resident[inst];
+    return ising_get_info(b->inst[inst], out);
+}
+
+int32_t ising_batch_destroy(ising_batch_t b)
+{
+    if (!b)
+        return ISING_OK;
+    b->drop_runs();
+    for (ising_s* g : b->inst)
+        ising_destroy(g);
+    for (cudaStream_t s : b->side)
+        cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join)
+        cudaEventDestroy(e);
+    if (b->fork)
+        cudaEventDestroy(b->fork);
+    if (b->cap)
+        cudaStreamDestroy(b->cap);
+    delete b;
+    return ISING_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct TuneCand {
+    bool resident;
+    int T, G;  // threads per block (0 = automatic), replicas per block when streamed
+};
+
+// SM-time of one sweep: measured time per sweep x blocks / blocks resident per
+// SM (what the shape costs the GPU when many instances share it).
+double tune_cost(ising_s* t, const TuneCand& c, bool* ok)
+{
+    *ok = false;
+    const bool res = configure_instance(t, c.resident, c.T, c.G);
+    if (c.resident != res || !t->use_fast)
+        return 0.0;
+    int per_sm = 0;
+    if (fast_max_blocks_per_sm(t->field_bits, t->fast_cmax, t->rng, t->T,
+                               res ? t->smem_fused : t->fast_smem, &per_sm, t->use_lean) != cudaSuccess ||
+        per_sm < 1)
+        return 0.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return 0.0;
+    double cost = 0.0;
+    const int kSweeps = 4;
+    if (ising_run(t, 2, 1) == ISING_OK && cudaEventRecord(e0, t->stream) == cudaSuccess &&
+        ising_run(t, kSweeps, 1) == ISING_OK && cudaEventRecord(e1, t->stream) == cudaSuccess &&
+        cudaEventSynchronize(e1) == cudaSuccess) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cost = double(ms) / kSweeps * double(t->blocks) / double(per_sm);
+        *ok = true;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cost;
+}
+
+}  // namespace
+
+extern "C" int32_t ising_batch_autotune(ising_batch_t b, uint32_t flags)
+{
+    if (!b)
+        return fail(ISING_ERR_INVALID_ARG, "NULL batch");
+    if (flags != 0)
+        return fail(ISING_ERR_INVALID_ARG, "flags must be 0");
+    std::map<std::tuple<int, int, int>, std::vector<int>> classes;
+    for (int i = 0; i < int(b->inst.size()); ++i) {
+        ising_s* g = b->inst[i];
+        classes[std::make_tuple(g->S, g->M, pow2_at_least(g->R))].push_back(i);
+    }
+    for (auto& kv : classes) {
+        ising_s* src = b->inst[kv.second[0]];
+        ising_t t = nullptr;
+        int32_t rc = ising_create(src->n, src->row_ptr.data(), src->col.data(), src->J.data(),
+                                  src->h.data(), src->M, 0u, &t);
+        if (!rc)
+            rc = replicas_init_impl(t, src->R, src->betas.data(), src->seed, src->rng, src->field_bits,
+                                    src->inst);
+        if (rc) {
+            if (t)
+                ising_destroy(t);
+            return rc;
+        }
+        t->word_budget = src->word_budget;
+        std::vector<TuneCand> cands = {{true, 0, 0}, {false, 0, 0}, {false, 0, 2}};
+        // thread-count variants around the automatic choices
+        for (bool res : {true, false}) {
+            if (configure_instance(t, res, 0) != res)
+                continue;
+            const int T0 = t->T, step = std::max(32, t->G);
+            for (int T : {T0 / 2, T0 * 2})
+                if (T >= step && T <= 1024 && T % step == 0)
+                    cands.push_back({res, T, 0});
+        }
+        double best = 0.0;
+        TuneCand win{false, 0, 0};
+        bool have = false;
+        for (const TuneCand& c : cands) {
+            bool ok = false;
+            const double cost = tune_cost(t, c, &ok);
+            if (ok && (!have || cost < best)) {
+                best = cost;
+                win = c;
+                have = true;
+            }
+        }
+        ising_destroy(t);
+        cudaGetLastError();  // candidates that could not launch leave no sticky state
+        if (!have)
+            continue;
+        for (int i : kv.second)
+            b->resident[i] = configure_instance(b->inst[i], win.resident, win.T, win.G) ? 1 : 0;
+    }
+    b->drop_runs();
+    return ISING_OK;
+}

@@ -69,6 +69,12 @@ struct SweepArgs {
     int* E_pub;                    // [2][R] energies published for the PT pass
     unsigned int* gridbar;         // grid barrier arrivals (zeroed before the launch)
     int lg_G;                      // log2(G)
+    int inst_blocks;               // blocks of this instance (batched launches)
+};
+
+// One block of a batched launch: instance index and block index within it.
+struct BatchItem {
+    int inst, block;
 };
 
 struct PtArgs {
@@ -230,6 +236,13 @@ cudaError_t launch_pt(const PtArgs& a, cudaStream_t st);
 // register-resident sweep for M <= 32 with tables in shared memory
 size_t fast_smem_bytes(const SweepArgs& a, int field_bits);
 cudaError_t fast_set_smem_limits();
+// Batched launches: block b runs item items[b] with args[items[b].inst].
+cudaError_t launch_fast_batch(const SweepArgs* args, const BatchItem* items, int n_items,
+                              int field_bits, int rng, int cmax, int threads, size_t smem, bool lean,
+                              cudaStream_t st);
+cudaError_t launch_pt_batch(const PtArgs* args, int n_inst, int max_R, cudaStream_t st);
+cudaError_t launch_mt_gen_batch(const MtGenArgs* args, const BatchItem* items, int n_items,
+                                int max_S, cudaStream_t st);
 // lean = true selects the lean variant (lean_impl.cuh): G = 1, M in {4,8,16,32},
 // spatial degree <= 6, |J| <= 63, at most 4 columns per thread
 cudaError_t fast_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,

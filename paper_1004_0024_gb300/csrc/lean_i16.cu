@@ -2,8 +2,8 @@
 #include "lean_impl.cuh"
 
 namespace isg {
-void* lean_kernel_i16(int rng, int cmax)
+void* lean_kernel_i16(int rng, int cmax, bool batch)
 {
-    return rng == 0 ? lean_detail::pick_lean<int16_t, 0>(cmax) : lean_detail::pick_lean<int16_t, 1>(cmax);
+    return rng == 0 ? lean_detail::pick_lean<int16_t, 0>(cmax, batch) : lean_detail::pick_lean<int16_t, 1>(cmax, batch);
 }
 }  // namespace isg

@@ -48,9 +48,10 @@ __host__ __device__ constexpr int lean_max_threads(int cmax)
 // registers each): a 256-replica ladder then fits on the GPU at once
 __host__ __device__ constexpr int lean_min_blocks(int cmax) { return cmax == 4 ? 2 : 1; }
 
+// Body of one block: `blk` is the replica (block) index within its instance
+// and `nblk` the instance's number of blocks (the grid size for one instance).
 template <typename FT, int RNG, int CMAX>
-__global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
-    lean_kernel(const SweepArgs a)
+__device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, const int nblk)
 {
     constexpr bool kI16 = sizeof(FT) == 2;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int T = blockDim.x, tid = threadIdx.x;
     const int S = a.S, M = a.M, N = a.N, K = a.K, R = a.R;
-    const int r = blockIdx.x;  // one replica per block
+    const int r = blk;  // one replica per block
     const int* nbr_off = reinterpret_cast<const int*>(smem + L.nbr_off);
     const uint32_t* nbr = reinterpret_cast<const uint32_t*>(smem + L.nbr);
     const int* jtau = reinterpret_cast<const int*>(smem + L.jtau);
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
     const bool shfl_thr = K <= 32;
     uint32_t thr_lane = (shfl_thr && (tid & 31) < K) ? thr_s[tid & 31] : 0u;
     const unsigned long long pass0 = a.counters[1];
-    const int nblk = (M + 3) >> 2;
+    const int nrb = (M + 3) >> 2;  // random-word blocks per column
     int npass = 0;
     int dE = 0;
 
@@ -182,11 +183,11 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
                 if (RNG == 0) {
                     const uint32_t* src = wsw + (size_t(r) * S + p) * a.Mp;
                     cp_async16(stage + p * 32, src);
-                    if (nblk > 1)
+                    if (nrb > 1)
                         cp_async16(stage + p * 32 + 16, src + 4);
                 } else {
                     ba[c] = rng_block<RNG>(a, wsw, r, p, site[p], 0, sid);
-                    if (nblk > 1)
+                    if (nrb > 1)
                         bb[c] = rng_block<RNG>(a, wsw, r, p, site[p], 1, sid);
                 }
             }
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
                         }
                     }
                     // block (t>>2)+1 replaces block (t>>2)-1 in the idle slot
-                    if (act && (t & 3) == 0 && (t >> 2) + 1 < nblk && t > 0) {
+                    if (act && (t & 3) == 0 && (t >> 2) + 1 < nrb && t > 0) {
                         if (RNG == 0) {
                             cp_async16(stage + p * 32 + (odd ^ 1) * 16,
                                        wsw + (size_t(r) * S + p) * a.Mp + t + 4);
@@ -258,7 +259,9 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
                 Ep[r] = e;
                 eacc[0] = 0;
             }
-            if (!grid_sync(a.gridbar, unsigned(npass + 1) * gridDim.x, a.err, &s_flag))
+            if (nblk == 1)  // a one-block instance has nobody else to wait for
+                __syncthreads();
+            else if (!grid_sync(a.gridbar, unsigned(npass + 1) * unsigned(nblk), a.err, &s_flag))
                 return;
             if (tid < 32) {
                 const unsigned long long p = pass0 + npass;
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
                         slot_s[k + 1] = sa;
                         temp_s[sa] = k + 1;
                         temp_s[sb] = k;
-                        if (blockIdx.x == 0)
+                        if (blk == 0)
                             a.swap_acc[k] += 1ull;
                     }
                 }
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
             }
         }
     }
-    if (fused && blockIdx.x == 0)
+    if (fused && blk == 0)
         for (int i = tid; i < R; i += T) {
             a.slot_of_temp[i] = slot_s[i];
             a.temp_of_slot_out[i] = temp_s[i];
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
     if (tid == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(a.done_blocks, 1u);
-        if (prev == gridDim.x - 1) {
+        if (prev == unsigned(nblk) - 1u) {
             a.counters[0] += (unsigned long long)a.nsweeps;
             a.counters[1] += (unsigned long long)npass;
             *a.done_blocks = 0u;
@@ -333,20 +336,43 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
     }
 }
 
+template <typename FT, int RNG, int CMAX>
+__global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX)) lean_kernel(const SweepArgs a)
+{
+    lean_body<FT, RNG, CMAX>(a, int(blockIdx.x), int(gridDim.x));
+}
+
+// Batched launch over many instances: each block copies its instance's
+// arguments into shared memory (so that every later read is a shared load).
+template <typename FT, int RNG, int CMAX>
+__global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
+    lean_batch_kernel(const SweepArgs* __restrict__ args, const BatchItem* __restrict__ items)
+{
+    __shared__ SweepArgs sa;
+    const BatchItem it = items[blockIdx.x];
+    if (threadIdx.x == 0)
+        sa = args[it.inst];
+    __syncthreads();
+    lean_body<FT, RNG, CMAX>(sa, it.block, sa.inst_blocks);
+}
+
 template <typename FT, int RNG>
-void* pick_lean(int cmax)
+void* pick_lean(int cmax, bool batch = false)
 {
     switch (cmax) {
-    case 1: return reinterpret_cast<void*>(&lean_kernel<FT, RNG, 1>);
-    case 2: return reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2>);
-    case 4: return reinterpret_cast<void*>(&lean_kernel<FT, RNG, 4>);
+    case 1: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 1>)
+                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 1>);
+    case 2: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 2>)
+                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2>);
+    case 4: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 4>)
+                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 4>);
     default: return nullptr;
     }
 }
 
 }  // namespace lean_detail
 
-void* lean_kernel_i16(int rng, int cmax);
-void* lean_kernel_i32(int rng, int cmax);
+void* lean_kernel_i16(int rng, int cmax, bool batch = false);
+void* lean_kernel_i32(int rng, int cmax, bool batch = false);
 
 }  // namespace isg

@@ -51,6 +51,12 @@ class IsingStats(ctypes.Structure):
                 ("timed_launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double)]
 
 
+class IsingInstance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("row_ptr", _i32p), ("col", _i32p), ("J", _i32p),
+                ("h", _i32p), ("n_slices", ctypes.c_int32), ("replicas", ctypes.c_int32),
+                ("betas", _f64p), ("seed", ctypes.c_uint32)]
+
+
 _SIGS = {
     "ising_last_error": ([], ctypes.c_char_p),
     "ising_create": ([ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_uint32,
@@ -71,6 +77,17 @@ _SIGS = {
     "ising_set_profiling": ([_vp, ctypes.c_int32], ctypes.c_int32),
     "ising_get_stats": ([_vp, ctypes.POINTER(IsingStats)], ctypes.c_int32),
     "ising_destroy": ([_vp], ctypes.c_int32),
+    "ising_batch_create": ([ctypes.c_int32, ctypes.POINTER(IsingInstance), ctypes.c_int32,
+                            ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(_vp)], ctypes.c_int32),
+    "ising_batch_set_stream": ([_vp, _vp], ctypes.c_int32),
+    "ising_batch_autotune": ([_vp, ctypes.c_uint32], ctypes.c_int32),
+    "ising_batch_run": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int32),
+    "ising_batch_read_state": ([_vp, ctypes.c_int32, _i8p, _i32p, _i64p, _i32p, _u64p],
+                               ctypes.c_int32),
+    "ising_batch_read_swap_stats": ([_vp, ctypes.c_int32, _u64p], ctypes.c_int32),
+    "ising_batch_get_info": ([_vp, ctypes.c_int32, ctypes.POINTER(IsingInfo),
+                              ctypes.POINTER(ctypes.c_int32)], ctypes.c_int32),
+    "ising_batch_destroy": ([_vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -268,6 +285,85 @@ class Ising:
     def close(self):
         if getattr(self, "h", None):
             ising_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------- batches
+class Batch:
+    """Ragged batch: ``Batch([(graph, betas, seed), ...], rng, field_bits)``.
+
+    Instance b is sampled exactly like ``Ising(graph, betas, seed, ...)``
+    except that its Philox counters use instance = b.
+    """
+
+    def __init__(self, instances, rng="mt19937", field_bits=16, stream=None):
+        self._keep = []
+        arr = (IsingInstance * len(instances))()
+        self.sizes = []
+        for k, (g, betas, seed) in enumerate(instances):
+            rp, c, j, hh = (_arr(g.row_ptr, np.int32), _arr(g.col, np.int32), _arr(g.J, np.int32),
+                            _arr(g.h, np.int32))
+            if c.size == 0:
+                c = np.zeros(1, np.int32)
+                j = np.zeros(1, np.int32)
+            b = _arr(betas, np.float64)
+            self._keep += [rp, c, j, hh, b]
+            arr[k] = IsingInstance(int(g.n), _p(rp, _i32p), _p(c, _i32p), _p(j, _i32p),
+                                   _p(hh, _i32p), int(getattr(g, "n_slices", 1)), int(b.size),
+                                   _p(b, _f64p), int(seed) & 0xFFFFFFFF)
+            self.sizes.append((int(g.n), int(b.size)))
+        out = _vp()
+        _check(_lib.ising_batch_create(len(instances), arr, RNG[rng] if isinstance(rng, str) else rng,
+                                       int(field_bits), 0, ctypes.byref(out)))
+        self.h = out
+        self._keep = []  # inputs are copied by the library
+        if stream is not None:
+            _check(_lib.ising_batch_set_stream(self.h, _vp(int(stream) if stream else None)))
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def autotune(self):
+        _check(_lib.ising_batch_autotune(self.h, 0))
+
+    def run(self, n, swap_every=1):
+        _check(_lib.ising_batch_run(self.h, int(n), int(swap_every)))
+
+    def read_state(self, inst):
+        n, R = self.sizes[inst]
+        spins = np.empty((R, n), dtype=np.int8)
+        fields = np.empty((R, n), dtype=np.int32)
+        E = np.empty(R, dtype=np.int64)
+        temp = np.empty(R, dtype=np.int32)
+        cnt = np.empty(2, dtype=np.uint64)
+        _check(_lib.ising_batch_read_state(self.h, int(inst), _p(spins, _i8p), _p(fields, _i32p),
+                                           _p(E, _i64p), _p(temp, _i32p), _p(cnt, _u64p)))
+        return dict(spins=spins, fields=fields, energy=E, temp_of_slot=temp, sweeps=int(cnt[0]),
+                    passes=int(cnt[1]))
+
+    def swap_stats(self, inst):
+        R = self.sizes[inst][1]
+        acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
+        _check(_lib.ising_batch_read_swap_stats(self.h, int(inst), _p(acc, _u64p)))
+        return acc[:max(R - 1, 0)]
+
+    def info(self, inst):
+        info = IsingInfo()
+        res = ctypes.c_int32(0)
+        _check(_lib.ising_batch_get_info(self.h, int(inst), ctypes.byref(info), ctypes.byref(res)))
+        d = {name: getattr(info, name) for name, _ in IsingInfo._fields_}
+        d["resident"] = int(res.value)
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(_lib.ising_batch_destroy(self.h))
             self.h = None
 
     def __del__(self):
