@@ -212,5 +212,67 @@ class Sim:
             pass
 
 
-def _bind_mlp(lib):  # filled in by the learned-proposal oracle
-    pass
+def _bind_mlp(lib):
+    d = ctypes.c_int
+    lib.orc_mlp_forward.argtypes = [d, d, d, d] + [_f64p] * 10
+    lib.orc_mlp_backward.argtypes = [d, d, d, d] + [_f64p] * 15
+    lib.orc_mlp_backward.restype = ctypes.c_double
+    lib.orc_column_energy.argtypes = [d, d, _i32p, _i8p]
+    lib.orc_column_energy.restype = ctypes.c_int64
+    lib.orc_log_q.argtypes = [d, _f64p, _i8p]
+    lib.orc_log_q.restype = ctypes.c_double
+    lib.orc_column_log_accept.argtypes = [d, d, _i32p, _i8p, _i8p, _f64p, ctypes.c_double, _i64p]
+    lib.orc_column_log_accept.restype = ctypes.c_double
+
+
+# --------------------------------------------------- learned column proposal
+def mlp_forward(X, W1, b1, W2, b2, W3, b3):
+    """FP64 forward: returns (H1, H2, logits) for X [B, IN]."""
+    lib = _load()
+    X = _c(X, np.float64)
+    B, IN = X.shape
+    H, OUT = W1.shape[0], W3.shape[0]
+    ws = [_c(w, np.float64) for w in (W1, b1, W2, b2, W3, b3)]
+    H1 = np.empty((B, H)); H2 = np.empty((B, H)); L = np.empty((B, OUT))
+    lib.orc_mlp_forward(B, IN, H, OUT, _ptr(X, _f64p), *[_ptr(w, _f64p) for w in ws],
+                        _ptr(H1, _f64p), _ptr(H2, _f64p), _ptr(L, _f64p))
+    return H1, H2, L
+
+
+def mlp_backward(X, Y, W1, b1, W2, b2, W3, b3):
+    """FP64 mean BCE-with-logits loss and gradients (dW1, db1, dW2, db2, dW3, db3)."""
+    lib = _load()
+    X = _c(X, np.float64)
+    Y = _c(Y, np.float64)
+    B, IN = X.shape
+    H, OUT = W1.shape[0], W3.shape[0]
+    ws = [_c(w, np.float64) for w in (W1, b1, W2, b2, W3, b3)]
+    grads = [np.empty_like(w) for w in ws]
+    scratch = np.empty(B * (2 * H + OUT) + OUT + 2 * H)
+    loss = lib.orc_mlp_backward(B, IN, H, OUT, _ptr(X, _f64p), _ptr(Y, _f64p),
+                                *[_ptr(w, _f64p) for w in ws],
+                                *[_ptr(g, _f64p) for g in grads], _ptr(scratch, _f64p))
+    return float(loss), grads
+
+
+def column_energy(M, jtau, phi, s):
+    lib = _load()
+    phi = _c(phi, np.int32); s = _c(s, np.int8)
+    return int(lib.orc_column_energy(M, jtau, _ptr(phi, _i32p), _ptr(s, _i8p)))
+
+
+def log_q(logits, s):
+    lib = _load()
+    lg = _c(logits, np.float64); s = _c(s, np.int8)
+    return float(lib.orc_log_q(lg.size, _ptr(lg, _f64p), _ptr(s, _i8p)))
+
+
+def column_log_accept(M, jtau, phi, s, s2, logits, beta):
+    """(log A, dE) of the column move s -> s2 under the given logits."""
+    lib = _load()
+    phi = _c(phi, np.int32); s = _c(s, np.int8); s2 = _c(s2, np.int8)
+    lg = _c(logits, np.float64)
+    dE = ctypes.c_int64(0)
+    la = lib.orc_column_log_accept(M, jtau, _ptr(phi, _i32p), _ptr(s, _i8p), _ptr(s2, _i8p),
+                                   _ptr(lg, _f64p), float(beta), ctypes.byref(dE))
+    return float(la), int(dE.value)
