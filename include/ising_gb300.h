@@ -291,6 +291,21 @@ int32_t ising_batch_read_swap_stats(ising_batch_t b, int32_t inst, uint64_t* acc
 int32_t ising_batch_get_info(ising_batch_t b, int32_t inst, ising_info_t* out, int32_t* resident);
 int32_t ising_batch_destroy(ising_batch_t b);
 
+/*
+ * ising_tc_gemm -- the bf16 tensor-core GEMM (tcgen05, FP32 accumulation in
+ * tensor memory) used by the learned proposal's layers, exposed for tests.
+ * All pointers are DEVICE pointers; work is enqueued on `stream`.
+ *   C[m][n] = epi(sum_k A[m][k] B[n][k]), A [M][lda], B [N][ldb] bf16 row-major;
+ *   epi: + bias[n] (bias may be NULL), ReLU if relu, zero where
+ *   mask[m][ldm*...] <= 0 (mask bf16 [M][ldm] or NULL); C FP32 or bf16 (c_bf16).
+ * Requires M % 128 == 0, K % 64 == 0, N in {32, 64, 128, 256}, leading
+ * dimensions multiples of 8 and 16-byte aligned bases.  Errors: INVALID_ARG, CUDA.
+ * The paper has no dense layers; this serves the learned proposal only.
+ */
+int32_t ising_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B,
+                      int32_t ldb, const float* bias, const void* mask, int32_t ldm, int32_t relu,
+                      void* C, int32_t ldc, int32_t c_bf16, void* stream);
+
 /* Release all device memory of the handle (NULL is ignored). */
 int32_t ising_destroy(ising_t h);
 

@@ -103,6 +103,8 @@ cudaError_t device_setup()
             g_init_err = fast_set_smem_limits();
         if (g_init_err == cudaSuccess)
             g_init_err = mt_gen_set_smem_limit();
+        if (g_init_err == cudaSuccess)
+            g_init_err = tc_gemm_setup();
         int coop = 0;
         if (g_init_err == cudaSuccess)
             g_init_err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -1806,5 +1808,26 @@ extern "C" int32_t ising_batch_autotune(ising_batch_t b, uint32_t flags)
             b->resident[i] = configure_instance(b->inst[i], win.resident, win.T, win.G) ? 1 : 0;
     }
     b->drop_runs();
+    return ISING_OK;
+}
+
+extern "C" int32_t ising_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
+                                 const void* B, int32_t ldb, const float* bias, const void* mask,
+                                 int32_t ldm, int32_t relu, void* C, int32_t ldc, int32_t c_bf16,
+                                 void* stream)
+{
+    cudaError_t ce = device_setup();
+    if (ce != cudaSuccess)
+        return cuda_fail(ce, "device setup");
+    static int* d_err = nullptr;
+    if (!d_err && dalloc(&d_err, 1))
+        return ISING_ERR_OOM;
+    TcGemmArgs g{A, B, lda, ldb, M, N, K, bias, mask, ldm, relu, C, ldc, c_bf16, d_err};
+    const cudaError_t e = launch_tc_gemm(g, static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorInvalidValue)
+        return fail(ISING_ERR_INVALID_ARG,
+                    "tc_gemm: M % 128, K % 64, N in {32,64,128,256}, leading dimensions % 8");
+    if (e != cudaSuccess)
+        return cuda_fail(e, "tc_gemm launch");
     return ISING_OK;
 }

@@ -214,6 +214,21 @@ __device__ __forceinline__ void set_err(int* err, int code)
     atomicCAS(err, 0, code);
 }
 
+// bf16 tensor-core GEMM C = epi(A B^T) (tc_gemm.cu).
+struct TcGemmArgs {
+    const void* A;      // bf16 [M][lda]
+    const void* B;      // bf16 [N][ldb]
+    int lda, ldb, M, N, K;
+    const float* bias;  // [N] or null
+    const void* mask;   // bf16 [M][ldm] or null: zero where mask <= 0
+    int ldm, relu;
+    void* C;            // [M][ldc], bf16 when c_bf16 else FP32
+    int ldc, c_bf16;
+    int* err;
+};
+cudaError_t tc_gemm_setup();
+cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st);
+
 // Everything needed to launch a handle's register-resident sweep kernel.
 struct FusedLaunch {
     SweepArgs args;
