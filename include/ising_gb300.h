@@ -306,6 +306,100 @@ int32_t ising_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, int32_t ld
                       int32_t ldb, const float* bias, const void* mask, int32_t ldm, int32_t relu,
                       void* C, int32_t ldc, int32_t c_bf16, void* stream);
 
+/*
+ * Learned Trotter-column proposal (an addition; the paper samples with
+ * single-spin Metropolis only).  For a handle declared as M <= 32 identical
+ * slices, a "column" is the M spins (t*S + q, t = 0..M-1) of one site q.  Given
+ * the rest of the replica, its conditional law is exp(-beta E_col(s)) with
+ *     E_col(s) = -sum_t s_t phi_t - Jtau sum_t s_t s_{t+1 mod M}
+ * (M = 2: one Trotter edge; M = 1: none), phi_t = h_q + sum over spatial
+ * neighbours q' of J_qq' s_{q',t}: the share of the section 1 cost function
+ * that involves the column.
+ *
+ * A network 33 -> 256 -> 256 -> 32 (ReLU hidden layers; inputs phi_t/8 for
+ * t < M and beta at input M, logits of P(s'_t = +1) at outputs t < M) proposes
+ * a whole column s' with independent bits; the move is accepted with the
+ * exact Metropolis-Hastings probability
+ *     min(1, exp(-beta (E_col(s') - E_col(s)) + log q(s) - log q(s'))),
+ * so the chain keeps the Boltzmann law of every replica whatever the network.
+ * Dense layers run on the tcgen05 GEMM (bf16 operands, FP32 accumulation);
+ * training uses Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights
+ * with the mean Bernoulli negative log-likelihood of recorded columns.
+ *
+ * Parameter layout (float32, contiguous, ising_mlp_get/set_params):
+ *   W1 [256][M+1], b1 [256], W2 [256][256], b2 [256], W3 [M][256], b3 [M];
+ *   ising_mlp_n_params() gives the count.  Initial weights: uniform on
+ *   +-1/sqrt(fan_in) from std::mt19937(seed), biases 0.
+ * Pointers are HOST pointers; calls synchronise the network's stream (the
+ * handle's stream for ising_mlp_collect / ising_learned_pass).
+ */
+typedef struct ising_mlp_s* ising_mlp_t;
+
+/* Create a network for M slices (1..32) with room for `capacity` recorded
+ * columns.  Errors: INVALID_ARG, OOM, CUDA. */
+int32_t ising_mlp_create(int32_t n_slices, uint32_t seed, int64_t capacity, ising_mlp_t* out);
+int32_t ising_mlp_set_stream(ising_mlp_t m, void* cuda_stream);
+int64_t ising_mlp_n_params(ising_mlp_t m);
+int32_t ising_mlp_get_params(ising_mlp_t m, float* out);
+/* Replace the weights (layout above); resets the Adam moments. */
+int32_t ising_mlp_set_params(ising_mlp_t m, const float* in);
+
+/* Logits L [B][M] of inputs X [B][M+1] (rounded to bf16 like recorded
+ * inputs).  B >= 1. */
+int32_t ising_mlp_forward(ising_mlp_t m, int32_t B, const float* X, float* L);
+
+/* Loss and gradient of one batch without changing the weights: X [B][M+1],
+ * Y [B] bit t = 1 iff target s_t = +1; grad receives the gradient in the
+ * parameter layout, *loss the mean negative log-likelihood.  B % 128 == 0. */
+int32_t ising_mlp_grad(ising_mlp_t m, int32_t B, const float* X, const uint32_t* Y, float* grad,
+                       float* loss);
+
+/* Record the columns of every replica of handle h (R * S records:
+ * X = (phi_t/8, beta), Y = the column's bits).  Requires h's M equal to the
+ * network's M.  Errors: INVALID_ARG (capacity exceeded, slices differ),
+ * NOT_INITIALISED. */
+int32_t ising_mlp_collect(ising_mlp_t m, ising_t h);
+int64_t ising_mlp_n_records(ising_mlp_t m);
+int32_t ising_mlp_clear_records(ising_mlp_t m);
+
+/* `epochs` passes of Adam over the recorded columns in batches of `batch`
+ * (a multiple of 128; records shuffled each epoch by std::mt19937_64(seed +
+ * epoch), the last partial batch dropped) at learning rate lr.  *loss = mean
+ * loss over the last epoch (may be NULL). */
+int32_t ising_mlp_train(ising_mlp_t m, int32_t epochs, int32_t batch, float lr, float* loss);
+
+/* Optional record of one learned pass, rows in visiting order (colour class,
+ * then replica slot, then site within the class).  Arrays hold `capacity`
+ * rows (>= R * S); NULL members are skipped. */
+typedef struct {
+    int64_t capacity;
+    int32_t* replica;    /* [rows] replica slot                           */
+    int32_t* site;       /* [rows] site q                                 */
+    int32_t* phi;        /* [rows][32] phi_t, t < M                       */
+    float* logits;       /* [rows][32] the network's logits, t < M        */
+    uint32_t* old_bits;  /* [rows] column before the move (bit t: s_t=+1) */
+    uint32_t* prop_bits; /* [rows] proposed column                        */
+    uint8_t* accepted;   /* [rows]                                        */
+} ising_learned_trace_t;
+
+/* One learned pass over handle h: every column of every replica once, the
+ * colour classes of the slice graph (greedy colouring in site order; no two
+ * sites of a class are spatial neighbours) in turn.  Random words:
+ * Philox4x32-10 with key (seed, replica slot), counter (q, pass, instance,
+ * 2 + 4j) giving words 4j..4j+3: word t < M draws s'_t = +1 iff
+ * u_t < x_t = p_t 2^32 (p_t = sigmoid(logit_t) in FP32), an event of
+ * probability exactly ceil(x_t) 2^-32; log q is summed from those exact
+ * probabilities and log A formed in FP64; word 32 accepts iff log A >= 0 or
+ * log((u + 1/2) 2^-32) < log A.  `pass` counts
+ * the handle's learned passes since ising_replicas_init.  Energies are updated
+ * by the exact integer dE and the local fields rebuilt afterwards.  The
+ * counts of accepted and proposed moves of this pass are returned (either
+ * pointer may be NULL).  Requires M <= 32, the network's M, R*S >= 1.
+ * Errors: INVALID_ARG, NOT_INITIALISED, CUDA (including a GEMM timeout). */
+int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint64_t* accepted, uint64_t* proposed,
+                           const ising_learned_trace_t* trace);
+int32_t ising_mlp_destroy(ising_mlp_t m);
+
 /* Release all device memory of the handle (NULL is ignored). */
 int32_t ising_destroy(ising_t h);
 

@@ -1,0 +1,74 @@
+// Internal state of a handle (host.cu); shared with the translation units
+// that implement further entry points on handles (learned.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "ising_gb300.h"
+
+struct ising_s {
+    double* d_betas = nullptr;       // [R] inverse temperatures by index
+    unsigned long long learned_passes = 0;
+    // colour classes of the slice graph for column moves (built on first use):
+    // sites of class c are d_colour_sites[colour_off[c] .. colour_off[c+1])
+    std::vector<int> colour_off, colour_sites;
+    int* d_colour_sites = nullptr;
+    // graph
+    int n = 0, M = 1, S = 0, W = 1, Mp = 4, D0 = 0, D = 0, max_sp_deg = 0, max_sp_J = 0;
+    long long kmax = 0, ebound = 0;
+    std::vector<int> row_ptr, col, J, h;
+    std::vector<int> site, pos, lev0p, jtau, nbr_off;
+    std::vector<uint32_t> nbr;
+    int *d_row_ptr = nullptr, *d_col = nullptr, *d_J = nullptr, *d_h = nullptr;
+    int *d_nbr_off = nullptr, *d_jtau = nullptr, *d_lev0 = nullptr, *d_site = nullptr,
+        *d_pos = nullptr;
+    uint32_t* d_nbr = nullptr;
+    // replicas
+    bool inited = false;
+    int R = 0, rng = 0, field_bits = 32, K = 1, maxpairs = 0;
+    uint32_t seed = 0, inst = 0;
+    std::vector<double> betas;
+    int8_t* d_spins = nullptr;
+    void* d_fields = nullptr;
+    int *d_E = nullptr, *d_temp = nullptr, *d_slot = nullptr, *d_err = nullptr;
+    unsigned long long *d_swap_acc = nullptr, *d_counters = nullptr, *d_mtpos = nullptr;
+    unsigned* d_done = nullptr;
+    uint32_t *d_thr = nullptr, *d_swthr = nullptr, *d_mtring = nullptr;
+    long long* d_swoff = nullptr;
+    int* d_swlen = nullptr;
+    uint32_t *d_wbuf = nullptr, *d_swbuf = nullptr;
+    int* d_Epub = nullptr;
+    unsigned* d_gridbar = nullptr;
+    long long wbuf_cap = 0, swbuf_cap = 0;  // sweeps / passes
+    long long word_budget = 1LL << 30;     // bytes of pre-generated MT19937 words
+    // launch configuration
+    int G = 1, T = 32, cmax = 1, blocks = 1, tables_smem = 1, thr_smem = 1;
+    size_t smem = 0;
+    // register-resident kernel (M <= 32, tables in shared memory)
+    bool use_fast = false, use_lean = false, persistent_ok = false, fast_off = false, lean_off = false;
+    int fast_cmax = 1;
+    size_t fast_smem = 0, smem_fused = 0;
+    int G_req = 0, T_req = 0, allow_persistent = 1;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to record graphs
+    // statistics
+    long long n_launches = 0, n_sweep_launches = 0;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    long long n_timed = 0;
+    double kernel_ms = 0.0;
+    std::map<std::pair<long long, int>, std::pair<long long, long long>> graph_counts;
+    std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
+
+    void free_replicas();
+    void free_all();
+    void drop_graphs();
+};
+
+int32_t isg_fail(int32_t code, const char* msg);
+int32_t isg_device_setup();  // once per process: kernel attributes, SM count

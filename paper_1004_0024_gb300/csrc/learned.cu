@@ -1,0 +1,1069 @@
+// Learned Trotter-column proposal with an exact Metropolis-Hastings correction
+// (not in the paper; built on its layered QMC models, section 3.1).
+//
+// Network 33 -> 256 -> 256 -> 32 (inputs phi_t/8 for the M <= 32 slices of a
+// column and beta; ReLU; outputs the logits of P(s'_t = +1)).  All dense
+// layers run on the tcgen05 GEMM (tc_gemm.cu) with bf16 operands and FP32
+// accumulation; FP32 master weights are trained with Adam on the mean
+// Bernoulli negative log-likelihood of columns sampled by the plain sweep.
+//
+// A learned pass visits the slice graph's colour classes (greedy colouring:
+// columns of one class share no spatial edge, so their conditional laws do
+// not interact) and, for every replica and column of a class: gathers phi
+// from the spins, evaluates the network, draws s'_t = +1 iff u_t < p_t 2^32,
+// and accepts with probability min(1, exp(-beta dE + log q(s) - log q(s'))),
+// dE the exact integer change of the column energy.  Both log q terms are
+// the exact probabilities of the discrete draw actually made (FP64), so the
+// move leaves the Boltzmann law invariant whatever the network's precision.
+// Energies are updated by dE; the local fields are rebuilt from the spins
+// after the pass.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "ising_internal.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace isg {
+namespace {
+
+constexpr int kHid = 256;  // hidden width
+constexpr int kIn = 64;    // padded input width (M + 1 <= 33 used)
+constexpr int kOut = 32;   // padded output width (M used)
+
+__global__ void gather_batch_kernel(const bf16* __restrict__ Xd, const uint32_t* __restrict__ Yd,
+                                    const int* __restrict__ idx, int B, bf16* __restrict__ Xb,
+                                    uint32_t* __restrict__ Yb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (row, 16-byte chunk)
+    if (i >= B * (kIn / 8))
+        return;
+    const int row = i / (kIn / 8), c = i % (kIn / 8);
+    const long long src = idx[row];
+    reinterpret_cast<uint4*>(Xb + size_t(row) * kIn)[c] = reinterpret_cast<const uint4*>(Xd + size_t(src) * kIn)[c];
+    if (c == 0)
+        Yb[row] = Yd[src];
+}
+
+__device__ __forceinline__ float softplusf(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
+
+// dL = (sigmoid(l) - y) / B as a bf16 pair: dL[b][j] = hi, dL[b][32 + j] = lo
+// with hi + lo = the FP32 value to 16 bits (the GEMMs against W3 see W3 twice
+// along K, so they use hi + lo); 0 for the padding; loss += BCE.
+__global__ void bce_kernel(const float* __restrict__ L, const uint32_t* __restrict__ Y, int B, int out,
+                           float inv_b, bf16* __restrict__ dL, float* __restrict__ loss)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.f;
+    if (b < B) {
+        const uint32_t y = Y[b];
+        for (int j = 0; j < kOut; ++j) {
+            float d = 0.f;
+            if (j < out) {
+                const float l = L[size_t(b) * kOut + j];
+                const float t = float((y >> j) & 1u);
+                acc += softplusf(l) - t * l;
+                d = (1.f / (1.f + expf(-l)) - t) * inv_b;
+            }
+            const bf16 hi = __float2bfloat16(d);
+            dL[size_t(b) * kIn + j] = hi;
+            dL[size_t(b) * kIn + kOut + j] = __float2bfloat16(d - __bfloat162float(hi));
+        }
+    }
+    __shared__ float red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        atomicAdd(loss, red[0]);
+}
+
+// gW3 += its lo half (rows 32..63 of the GEMM output), gb3 = hi + lo sums
+__global__ void fold_kernel(float* __restrict__ gW3, float* __restrict__ gb3, const float* __restrict__ cs64)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kOut * kHid)
+        gW3[i] += gW3[kOut * kHid + i];
+    if (i < kOut)
+        gb3[i] = cs64[i] + cs64[kOut + i];
+}
+
+// dst[c][r] = src[r][c] for r < rows, c < cols (32 x 32 tiles through shared memory)
+__global__ void transpose_kernel(const bf16* __restrict__ src, int rows, int cols, int lds,
+                                 bf16* __restrict__ dst, int ldd)
+{
+    __shared__ bf16 tile[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        if (r < rows && c < cols)
+            tile[y][threadIdx.x] = src[size_t(r) * lds + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (r < rows && c < cols)
+            dst[size_t(c) * ldd + r] = tile[threadIdx.x][y];
+    }
+}
+
+// out[c] = sum_r src[r][c]
+__global__ void colsum_kernel(const bf16* __restrict__ src, int rows, int cols, int lds, float* __restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols)
+        return;
+    float a = 0.f;
+    for (int r = 0; r < rows; ++r)
+        a += __bfloat162float(src[size_t(r) * lds + c]);
+    out[c] = a;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+// dst = bf16(src) for a [rows][cols] matrix, optionally transposed into [cols][ldd]
+__global__ void to_bf16_kernel(const float* __restrict__ src, int rows, int cols, bf16* __restrict__ dst,
+                               int ldd, int transpose)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols)
+        return;
+    const int r = i / cols, c = i % cols;
+    const bf16 v = __float2bfloat16(src[i]);
+    if (transpose)
+        dst[size_t(c) * ldd + r] = v;
+    else
+        dst[size_t(r) * ldd + c] = v;
+}
+
+}  // namespace
+}  // namespace isg
+
+namespace isg {
+namespace {
+
+struct LearnedArgs {
+    int S, M, N, R, rows, ncols;  // rows = R * ncols (real rows of this class)
+    const int *row_ptr, *col, *J, *h, *jtau, *pos;
+    int8_t* spins;
+    int* E;
+    const int* temp_of_slot;
+    const double* betas;
+    const int* sites;  // the class's sites
+    int* phi;          // [rows][32]
+    bf16* X;           // [rows_pad][64]
+    const float* L;    // [rows_pad][32]
+    uint32_t seed, inst, pass;
+    uint32_t *old_bits, *prop_bits;
+    uint8_t* accepted;
+    unsigned long long* n_acc;
+};
+
+// phi_t = h_i + sum over spatial neighbours j (same slice) of J s_j, i = t S + q
+__device__ __forceinline__ int spatial_field(const LearnedArgs& a, const int8_t* sp, int t, int q)
+{
+    const int i = t * a.S + q;
+    int f = a.h[i];
+    for (int e = a.row_ptr[i]; e < a.row_ptr[i + 1]; ++e) {
+        const int j = a.col[e];
+        if (j / a.S == t)
+            f += a.J[e] * int(sp[j]);
+    }
+    return f;
+}
+
+__global__ void learned_gather_kernel(const LearnedArgs a, int rows_pad)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows_pad)
+        return;
+    bf16* x = a.X + size_t(row) * kIn;
+    if (row >= a.rows) {
+        for (int k = 0; k < kIn; ++k)
+            x[k] = __float2bfloat16(0.f);
+        return;
+    }
+    const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
+    const int8_t* sp = a.spins + size_t(r) * a.N;
+    for (int t = 0; t < a.M; ++t) {
+        const int f = spatial_field(a, sp, t, q);
+        a.phi[size_t(row) * kOut + t] = f;
+        x[t] = __float2bfloat16(float(f) * 0.125f);
+    }
+    x[a.M] = __float2bfloat16(float(a.betas[a.temp_of_slot[r]]));
+    for (int k = a.M + 1; k < kIn; ++k)
+        x[k] = __float2bfloat16(0.f);
+}
+
+__device__ __forceinline__ int column_energy(uint32_t bits, const int* phi, int M, int jt)
+{
+    int e = 0;
+    for (int t = 0; t < M; ++t)
+        e -= (((bits >> t) & 1u) ? 1 : -1) * phi[t];
+    if (M >= 3) {
+        for (int t = 0; t < M; ++t) {
+            const int t1 = (t + 1 == M) ? 0 : t + 1;
+            e -= jt * ((((bits >> t) ^ (bits >> t1)) & 1u) ? -1 : 1);
+        }
+    } else if (M == 2) {
+        e -= jt * ((((bits >> 0) ^ (bits >> 1)) & 1u) ? -1 : 1);
+    }
+    return e;
+}
+
+// One MH column move per row.  Words: Philox4x32-10, key (seed, r), counter
+// (q, pass, instance, 2 + 4 j) gives words 4j .. 4j+3; word t < M proposes
+// slice t, word 32 decides acceptance.  Bit t is drawn +1 iff u_t < x_t with
+// x_t = p_t 2^32 (p_t the FP32 sigmoid of the logit), so its probability is
+// exactly ceil(x_t) 2^-32; log q uses those exact probabilities in FP64, which
+// makes the Hastings ratio that of the proposal actually drawn.
+__global__ void learned_mh_kernel(const LearnedArgs a)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.rows)
+        return;
+    const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
+    const int M = a.M, S = a.S;
+    int8_t* sp = a.spins + size_t(r) * a.N;
+    uint32_t old = 0u;
+    for (int t = 0; t < M; ++t)
+        old |= (sp[t * S + q] > 0 ? 1u : 0u) << t;
+    const float* l = a.L + size_t(row) * kOut;
+    const int* phi = a.phi + size_t(row) * kOut;
+    uint32_t prop = 0u, u_acc = 0u;
+    double lq_old = 0.0, lq_new = 0.0;
+    for (int j = 0; j < 9; ++j) {
+        const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(j)), a.seed,
+                                      uint32_t(r));
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+        for (int k = 0; k < 4; ++k) {
+            const int t = 4 * j + k;
+            if (t < M) {
+                const float p = 1.f / (1.f + expf(-l[t]));
+                const double x = double(p) * 4294967296.0;
+                const double p1 = ceil(x) * 2.3283064365386963e-10;  // P(s'_t = +1)
+                const bool up = double(ww[k]) < x;
+                prop |= (up ? 1u : 0u) << t;
+                lq_new += up ? log(p1) : log1p(-p1);
+                lq_old += ((old >> t) & 1u) ? log(p1) : log1p(-p1);
+            } else if (t == 32) {
+                u_acc = ww[k];
+            }
+        }
+    }
+    const int jt = a.jtau[a.pos[q]];
+    const int dE = column_energy(prop, phi, M, jt) - column_energy(old, phi, M, jt);
+    const double logA = -a.betas[a.temp_of_slot[r]] * double(dE) + lq_old - lq_new;
+    const bool acc = (logA >= 0.0) || (log((double(u_acc) + 0.5) * 2.3283064365386963e-10) < logA);
+    if (acc && prop != old) {
+        for (int t = 0; t < M; ++t)
+            sp[t * S + q] = ((prop >> t) & 1u) ? int8_t(1) : int8_t(-1);
+        atomicAdd(&a.E[r], dE);
+    }
+    const unsigned act = __activemask();
+    const unsigned votes = __ballot_sync(act, acc);
+    if (votes && int(threadIdx.x & 31) == __ffs(act) - 1)
+        atomicAdd(a.n_acc, (unsigned long long)__popc(votes));
+    a.old_bits[row] = old;
+    a.prop_bits[row] = prop;
+    a.accepted[row] = acc ? 1 : 0;
+}
+
+// f_i = h_i + sum_j J_ij s_j for every replica (after a learned pass)
+template <typename FT>
+__global__ void fields_rebuild_kernel(const int8_t* __restrict__ spins, FT* __restrict__ fields, int R, int N,
+                                      const int* __restrict__ row_ptr, const int* __restrict__ col,
+                                      const int* __restrict__ J, const int* __restrict__ h)
+{
+    const long long total = (long long)R * N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int r = int(k / N), i = int(k - (long long)r * N);
+        const int8_t* s = spins + size_t(r) * N;
+        int f = h[i];
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            f += J[e] * int(s[col[e]]);
+        fields[k] = FT(f);
+    }
+}
+
+// Training records of every (replica, column): X = (phi/8, beta), Y = spins
+__global__ void collect_kernel(const LearnedArgs a, bf16* __restrict__ Xd, uint32_t* __restrict__ Yd)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = r * S + q
+    if (k >= a.R * a.S)
+        return;
+    const int r = k / a.S, q = k - r * a.S;
+    const int8_t* sp = a.spins + size_t(r) * a.N;
+    bf16* x = Xd + size_t(k) * kIn;
+    uint32_t y = 0u;
+    for (int t = 0; t < a.M; ++t) {
+        x[t] = __float2bfloat16(float(spatial_field(a, sp, t, q)) * 0.125f);
+        y |= (sp[t * a.S + q] > 0 ? 1u : 0u) << t;
+    }
+    x[a.M] = __float2bfloat16(float(a.betas[a.temp_of_slot[r]]));
+    for (int c = a.M + 1; c < kIn; ++c)
+        x[c] = __float2bfloat16(0.f);
+    Yd[k] = y;
+}
+
+}  // namespace
+}  // namespace isg
+
+// ============================================================ network object
+namespace {
+constexpr int kW1 = isg::kHid * isg::kIn;    // [256][64], columns > M zero
+constexpr int kW2 = isg::kHid * isg::kHid;   // [256][256]
+constexpr int kW3 = isg::kOut * isg::kHid;   // [32][256], rows >= M zero
+constexpr int kPar = kW1 + isg::kHid + kW2 + isg::kHid + kW3 + isg::kOut;
+constexpr int kGW3 = 128 * isg::kHid;        // GEMM output rows are padded to 128
+constexpr int kGrad = kW1 + isg::kHid + kW2 + isg::kHid + kGW3 + isg::kOut;
+}  // namespace
+
+struct ising_mlp_s {
+    int M = 1;
+    uint32_t seed = 0;
+    cudaStream_t stream = nullptr;
+    float* par = nullptr;   // W1 b1 W2 b2 W3 b3 (FP32 master copy)
+    float* mom = nullptr;   // Adam first then second moments, same layout
+    float* grad = nullptr;  // gW1 gb1 gW2 gb2 gW3[128][256] gb3
+    long long adam_t = 0;
+    bf16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W2tb = nullptr, *W3tb = nullptr;
+    // recorded columns
+    bf16* Xd = nullptr;
+    uint32_t* Yd = nullptr;
+    long long cap = 0, n_rec = 0;
+    int* idx = nullptr;  // [cap] shuffled record order
+    // training batch workspace, sized for Bcap rows
+    int Bcap = 0;
+    bf16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *dL = nullptr, *dH2 = nullptr, *dH1 = nullptr;
+    bf16 *XT = nullptr, *H1T = nullptr, *H2T = nullptr, *dLT = nullptr, *dH2T = nullptr, *dH1T = nullptr;
+    float* L = nullptr;
+    uint32_t* Yb = nullptr;
+    float* loss = nullptr;
+    float* cs64 = nullptr;  // column sums of the hi/lo output gradient
+    int* err = nullptr;
+    unsigned long long* n_acc = nullptr;
+    // learned-pass workspace, sized for Pcap rows
+    long long Pcap = 0;
+    bf16 *PX = nullptr, *PH1 = nullptr, *PH2 = nullptr;
+    float* PL = nullptr;
+    int* Pphi = nullptr;
+    uint32_t *Pold = nullptr, *Pprop = nullptr;
+    uint8_t* Pacc = nullptr;
+
+    float* W1() { return par; }
+    float* b1() { return par + kW1; }
+    float* W2() { return b1() + isg::kHid; }
+    float* b2() { return W2() + kW2; }
+    float* W3() { return b2() + isg::kHid; }
+    float* b3() { return W3() + kW3; }
+    float* gW1() { return grad; }
+    float* gb1() { return grad + kW1; }
+    float* gW2() { return gb1() + isg::kHid; }
+    float* gb2() { return gW2() + kW2; }
+    float* gW3() { return gb2() + isg::kHid; }
+    float* gb3() { return gW3() + kGW3; }
+};
+
+namespace isg {
+namespace {
+
+int32_t cuda_err(cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return isg_fail(e == cudaErrorMemoryAllocation ? ISING_ERR_OOM : ISING_ERR_CUDA, m.c_str());
+}
+
+#define LCK(call)                                  \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess)                     \
+            return cuda_err(e_, #call);            \
+    } while (0)
+
+template <typename T>
+cudaError_t zalloc(T** p, size_t count)
+{
+    const size_t bytes = std::max<size_t>(16, (count * sizeof(T) + 15) & ~size_t(15));
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    e = cudaMemset(*p, 0, bytes);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    return e;
+}
+
+template <typename T>
+void zfree(T*& p)
+{
+    if (p)
+        cudaFree(p);
+    p = nullptr;
+}
+
+inline int cdiv(long long a, int b) { return int((a + b - 1) / b); }
+
+cudaError_t gemm(ising_mlp_s* m, cudaStream_t st, int rows, int N, int K, const bf16* A, int lda,
+                 const bf16* B, int ldb, const float* bias, const bf16* mask, int ldm, int relu, void* C,
+                 int ldc, int c_bf16)
+{
+    TcGemmArgs g{A, B, lda, ldb, rows, N, K, bias, mask, ldm, relu, C, ldc, c_bf16, m->err};
+    return launch_tc_gemm(g, st);
+}
+
+// bf16 weight copies used by the GEMMs (plain and transposed)
+cudaError_t refresh_bf16(ising_mlp_s* m, cudaStream_t st)
+{
+    to_bf16_kernel<<<cdiv(kW1, 256), 256, 0, st>>>(m->W1(), kHid, kIn, m->W1b, kIn, 0);
+    to_bf16_kernel<<<cdiv(kW2, 256), 256, 0, st>>>(m->W2(), kHid, kHid, m->W2b, kHid, 0);
+    to_bf16_kernel<<<cdiv(kW2, 256), 256, 0, st>>>(m->W2(), kHid, kHid, m->W2tb, kHid, 1);
+    to_bf16_kernel<<<cdiv(kW3, 256), 256, 0, st>>>(m->W3(), kOut, kHid, m->W3b, kHid, 0);
+    to_bf16_kernel<<<cdiv(kW3, 256), 256, 0, st>>>(m->W3(), kOut, kHid, m->W3tb, kIn, 1);
+    to_bf16_kernel<<<cdiv(kW3, 256), 256, 0, st>>>(m->W3(), kOut, kHid, m->W3tb + kOut, kIn, 1);
+    return cudaGetLastError();
+}
+
+// L [rows][32] = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for X [rows][64]
+cudaError_t forward(ising_mlp_s* m, cudaStream_t st, int rows, const bf16* X, bf16* H1, bf16* H2, float* L)
+{
+    cudaError_t e = gemm(m, st, rows, kHid, kIn, X, kIn, m->W1b, kIn, m->b1(), nullptr, 0, 1, H1, kHid, 1);
+    if (e == cudaSuccess)
+        e = gemm(m, st, rows, kHid, kHid, H1, kHid, m->W2b, kHid, m->b2(), nullptr, 0, 1, H2, kHid, 1);
+    if (e == cudaSuccess)
+        e = gemm(m, st, rows, kOut, kHid, H2, kHid, m->W3b, kHid, m->b3(), nullptr, 0, 0, L, kOut, 0);
+    return e;
+}
+
+void transpose(const bf16* src, int rows, int cols, int lds, bf16* dst, int ldd, cudaStream_t st)
+{
+    transpose_kernel<<<dim3(cdiv(cols, 32), cdiv(rows, 32)), dim3(32, 8), 0, st>>>(src, rows, cols, lds, dst, ldd);
+}
+
+// Loss and gradients of the batch in Xb / Yb (B rows, B % 128 == 0)
+cudaError_t backward(ising_mlp_s* m, cudaStream_t st, int B)
+{
+    cudaError_t e = forward(m, st, B, m->Xb, m->H1, m->H2, m->L);
+    if (e != cudaSuccess)
+        return e;
+    bce_kernel<<<cdiv(B, 256), 256, 0, st>>>(m->L, m->Yb, B, m->M, 1.f / float(B), m->dL, m->loss);
+    // dH2 = relu'(H2) * (dL W3), dH1 = relu'(H1) * (dH2 W2)
+    e = gemm(m, st, B, kHid, kIn, m->dL, kIn, m->W3tb, kIn, nullptr, m->H2, kHid, 0, m->dH2, kHid, 1);
+    if (e == cudaSuccess)
+        e = gemm(m, st, B, kHid, kHid, m->dH2, kHid, m->W2tb, kHid, nullptr, m->H1, kHid, 0, m->dH1, kHid, 1);
+    if (e != cudaSuccess)
+        return e;
+    transpose(m->Xb, B, kIn, kIn, m->XT, B, st);
+    transpose(m->H1, B, kHid, kHid, m->H1T, B, st);
+    transpose(m->H2, B, kHid, kHid, m->H2T, B, st);
+    transpose(m->dL, B, kIn, kIn, m->dLT, B, st);  // hi rows 0..31, lo rows 32..63; 64..127 stay zero
+    transpose(m->dH2, B, kHid, kHid, m->dH2T, B, st);
+    transpose(m->dH1, B, kHid, kHid, m->dH1T, B, st);
+    // weight gradients: sums over the batch of outer products
+    e = gemm(m, st, 128, kHid, B, m->dLT, B, m->H2T, B, nullptr, nullptr, 0, 0, m->gW3(), kHid, 0);
+    if (e == cudaSuccess)
+        e = gemm(m, st, kHid, kHid, B, m->dH2T, B, m->H1T, B, nullptr, nullptr, 0, 0, m->gW2(), kHid, 0);
+    if (e == cudaSuccess)
+        e = gemm(m, st, kHid, kIn, B, m->dH1T, B, m->XT, B, nullptr, nullptr, 0, 0, m->gW1(), kIn, 0);
+    if (e != cudaSuccess)
+        return e;
+    colsum_kernel<<<1, kIn, 0, st>>>(m->dL, B, kIn, kIn, m->cs64);
+    fold_kernel<<<cdiv(kOut * kHid, 256), 256, 0, st>>>(m->gW3(), m->gb3(), m->cs64);
+    colsum_kernel<<<1, kHid, 0, st>>>(m->dH2, B, kHid, kHid, m->gb2());
+    colsum_kernel<<<1, kHid, 0, st>>>(m->dH1, B, kHid, kHid, m->gb1());
+    return cudaGetLastError();
+}
+
+cudaError_t adam_step(ising_mlp_s* m, cudaStream_t st, float lr)
+{
+    ++m->adam_t;
+    const float c1 = float(1.0 / (1.0 - std::pow(0.9, double(m->adam_t))));
+    const float c2 = float(1.0 / (1.0 - std::pow(0.999, double(m->adam_t))));
+    float* mm = m->mom;
+    float* vv = m->mom + kPar;
+    const long long off[6] = {0, kW1, kW1 + kHid, kW1 + kHid + kW2, kW1 + 2 * kHid + kW2,
+                              kW1 + 2 * kHid + kW2 + kW3};
+    const int n[6] = {kW1, kHid, kW2, kHid, kW3, kOut};
+    float* g[6] = {m->gW1(), m->gb1(), m->gW2(), m->gb2(), m->gW3(), m->gb3()};
+    for (int i = 0; i < 6; ++i)
+        adam_kernel<<<cdiv(n[i], 256), 256, 0, st>>>(m->par + off[i], g[i], mm + off[i], vv + off[i], n[i], lr,
+                                                      c1, c2);
+    return refresh_bf16(m, st);
+}
+
+int32_t check_err(ising_mlp_s* m, cudaStream_t st)
+{
+    int h = 0;
+    LCK(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    if (h) {
+        LCK(cudaMemsetAsync(m->err, 0, sizeof(int), st));
+        LCK(cudaStreamSynchronize(st));
+        return isg_fail(ISING_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait gave up");
+    }
+    return ISING_OK;
+}
+
+cudaError_t ensure_batch(ising_mlp_s* m, int B)
+{
+    if (B <= m->Bcap)
+        return cudaSuccess;
+    bf16** bufs[12] = {&m->Xb, &m->H1, &m->H2, &m->dL, &m->dH2, &m->dH1,
+                       &m->XT, &m->H1T, &m->H2T, &m->dLT, &m->dH2T, &m->dH1T};
+    const size_t width[12] = {kIn, kHid, kHid, kIn, kHid, kHid, kIn, kHid, kHid, 128, kHid, kHid};
+    for (int i = 0; i < 12; ++i)
+        zfree(*bufs[i]);
+    zfree(m->L);
+    zfree(m->Yb);
+    m->Bcap = 0;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 12 && e == cudaSuccess; ++i)
+        e = zalloc(bufs[i], size_t(B) * width[i]);
+    if (e == cudaSuccess)
+        e = zalloc(&m->L, size_t(B) * kOut);
+    if (e == cudaSuccess)
+        e = zalloc(&m->Yb, size_t(B));
+    if (e == cudaSuccess)
+        m->Bcap = B;
+    return e;
+}
+
+cudaError_t ensure_pass(ising_mlp_s* m, long long rows_pad)
+{
+    if (rows_pad <= m->Pcap)
+        return cudaSuccess;
+    zfree(m->PX);
+    zfree(m->PH1);
+    zfree(m->PH2);
+    zfree(m->PL);
+    zfree(m->Pphi);
+    zfree(m->Pold);
+    zfree(m->Pprop);
+    zfree(m->Pacc);
+    m->Pcap = 0;
+    cudaError_t e = zalloc(&m->PX, size_t(rows_pad) * kIn);
+    if (e == cudaSuccess)
+        e = zalloc(&m->PH1, size_t(rows_pad) * kHid);
+    if (e == cudaSuccess)
+        e = zalloc(&m->PH2, size_t(rows_pad) * kHid);
+    if (e == cudaSuccess)
+        e = zalloc(&m->PL, size_t(rows_pad) * kOut);
+    if (e == cudaSuccess)
+        e = zalloc(&m->Pphi, size_t(rows_pad) * kOut);
+    if (e == cudaSuccess)
+        e = zalloc(&m->Pold, size_t(rows_pad));
+    if (e == cudaSuccess)
+        e = zalloc(&m->Pprop, size_t(rows_pad));
+    if (e == cudaSuccess)
+        e = zalloc(&m->Pacc, size_t(rows_pad));
+    if (e == cudaSuccess)
+        m->Pcap = rows_pad;
+    return e;
+}
+
+void free_mlp(ising_mlp_s* m)
+{
+    bf16** b[] = {&m->W1b, &m->W2b, &m->W3b, &m->W2tb, &m->W3tb, &m->Xd, &m->Xb, &m->H1, &m->H2, &m->dL,
+                  &m->dH2, &m->dH1, &m->XT, &m->H1T, &m->H2T, &m->dLT, &m->dH2T, &m->dH1T, &m->PX, &m->PH1,
+                  &m->PH2};
+    for (auto p : b)
+        zfree(*p);
+    zfree(m->par);
+    zfree(m->mom);
+    zfree(m->grad);
+    zfree(m->Yd);
+    zfree(m->idx);
+    zfree(m->L);
+    zfree(m->Yb);
+    zfree(m->loss);
+    zfree(m->cs64);
+    zfree(m->err);
+    zfree(m->n_acc);
+    zfree(m->PL);
+    zfree(m->Pphi);
+    zfree(m->Pold);
+    zfree(m->Pprop);
+    zfree(m->Pacc);
+}
+
+}  // namespace
+}  // namespace isg
+
+// ================================================================ C ABI
+namespace isg {
+namespace {
+
+// Greedy colouring of the slice graph in site order: each site takes the
+// smallest colour none of its spatial neighbours already holds.
+int32_t build_colours(ising_s* g)
+{
+    if (!g->colour_off.empty())
+        return ISING_OK;
+    const int S = g->S;
+    std::vector<int> colour(S, -1);
+    int ncol = 0;
+    std::vector<int> seen;
+    for (int q = 0; q < S; ++q) {  // slice 0 rows hold the spatial edges of site q
+        seen.assign(size_t(ncol) + 1, 0);
+        for (int e = g->row_ptr[q]; e < g->row_ptr[q + 1]; ++e) {
+            const int c = g->col[e];
+            if (c < S && colour[c] >= 0)
+                seen[colour[c]] = 1;
+        }
+        int k = 0;
+        while (seen[k])
+            ++k;
+        colour[q] = k;
+        ncol = std::max(ncol, k + 1);
+    }
+    std::vector<int> sites;
+    g->colour_off.assign(1, 0);
+    for (int k = 0; k < ncol; ++k) {
+        for (int q = 0; q < S; ++q)
+            if (colour[q] == k)
+                sites.push_back(q);
+        g->colour_off.push_back(int(sites.size()));
+    }
+    cudaError_t e = zalloc(&g->d_colour_sites, sites.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_colour_sites, sites.data(), sites.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        g->colour_off.clear();
+        return cuda_err(e, "colour classes");
+    }
+    g->colour_sites = sites;
+    return ISING_OK;
+}
+
+LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
+{
+    LearnedArgs a{};
+    a.S = g->S;
+    a.M = g->M;
+    a.N = g->n;
+    a.R = g->R;
+    a.row_ptr = g->d_row_ptr;
+    a.col = g->d_col;
+    a.J = g->d_J;
+    a.h = g->d_h;
+    a.jtau = g->d_jtau;
+    a.pos = g->d_pos;
+    a.spins = g->d_spins;
+    a.E = g->d_E;
+    a.temp_of_slot = g->d_temp;
+    a.betas = g->d_betas;
+    a.seed = g->seed;
+    a.inst = g->inst;
+    a.pass = uint32_t(g->learned_passes);
+    a.phi = m->Pphi;
+    a.X = m->PX;
+    a.L = m->PL;
+    a.old_bits = m->Pold;
+    a.prop_bits = m->Pprop;
+    a.accepted = m->Pacc;
+    a.n_acc = m->n_acc;
+    return a;
+}
+
+}  // namespace
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" {
+
+int32_t ising_mlp_create(int32_t n_slices, uint32_t seed, int64_t capacity, ising_mlp_t* out)
+{
+    if (!out)
+        return isg_fail(ISING_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_slices < 1 || n_slices > kOut)
+        return isg_fail(ISING_ERR_INVALID_ARG, "n_slices must be in 1..32");
+    if (capacity < 0 || capacity > (1LL << 31) - 1)
+        return isg_fail(ISING_ERR_INVALID_ARG, "capacity must be in 0..2^31-1");
+    int32_t rc = isg_device_setup();
+    if (rc)
+        return rc;
+    auto* m = new ising_mlp_s();
+    m->M = n_slices;
+    m->seed = seed;
+    m->cap = capacity;
+    cudaError_t e = zalloc(&m->par, kPar);
+    if (e == cudaSuccess)
+        e = zalloc(&m->mom, 2 * size_t(kPar));
+    if (e == cudaSuccess)
+        e = zalloc(&m->grad, kGrad);
+    if (e == cudaSuccess)
+        e = zalloc(&m->W1b, kW1);
+    if (e == cudaSuccess)
+        e = zalloc(&m->W2b, kW2);
+    if (e == cudaSuccess)
+        e = zalloc(&m->W2tb, kW2);
+    if (e == cudaSuccess)
+        e = zalloc(&m->W3b, kW3);
+    if (e == cudaSuccess)
+        e = zalloc(&m->W3tb, size_t(kHid) * kIn);
+    if (e == cudaSuccess)
+        e = zalloc(&m->Xd, size_t(std::max<int64_t>(capacity, 1)) * kIn);
+    if (e == cudaSuccess)
+        e = zalloc(&m->Yd, size_t(std::max<int64_t>(capacity, 1)));
+    if (e == cudaSuccess)
+        e = zalloc(&m->idx, size_t(std::max<int64_t>(capacity, 1)));
+    if (e == cudaSuccess)
+        e = zalloc(&m->loss, 1);
+    if (e == cudaSuccess)
+        e = zalloc(&m->cs64, kIn);
+    if (e == cudaSuccess)
+        e = zalloc(&m->err, 1);
+    if (e == cudaSuccess)
+        e = zalloc(&m->n_acc, 1);
+    if (e != cudaSuccess) {
+        free_mlp(m);
+        delete m;
+        return cuda_err(e, "ising_mlp_create");
+    }
+    // uniform on +-1/sqrt(fan_in), biases 0, padding 0
+    std::vector<float> p(kPar, 0.f);
+    std::mt19937 gen(seed);
+    auto fill = [&](float* w, int rows, int cols, int ld, int fan_in) {
+        const float a = 1.f / std::sqrt(float(fan_in));
+        std::uniform_real_distribution<float> u(-a, a);
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < cols; ++c)
+                w[size_t(r) * ld + c] = u(gen);
+    };
+    fill(p.data(), kHid, n_slices + 1, kIn, n_slices + 1);
+    fill(p.data() + kW1 + kHid, kHid, kHid, kHid, kHid);
+    fill(p.data() + kW1 + 2 * kHid + kW2, n_slices, kHid, kHid, kHid);
+    e = cudaMemcpy(m->par, p.data(), sizeof(float) * kPar, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = refresh_bf16(m, nullptr);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_mlp(m);
+        delete m;
+        return cuda_err(e, "ising_mlp_create");
+    }
+    *out = m;
+    return ISING_OK;
+}
+
+int32_t ising_mlp_set_stream(ising_mlp_t m, void* cuda_stream)
+{
+    if (!m)
+        return isg_fail(ISING_ERR_INVALID_ARG, "network is NULL");
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    return ISING_OK;
+}
+
+int64_t ising_mlp_n_params(ising_mlp_t m)
+{
+    if (!m)
+        return 0;
+    const int M = m->M;
+    return int64_t(kHid) * (M + 1) + kHid + kW2 + kHid + int64_t(M) * kHid + M;
+}
+
+int32_t ising_mlp_get_params(ising_mlp_t m, float* out)
+{
+    if (!m || !out)
+        return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    std::vector<float> p(kPar);
+    LCK(cudaStreamSynchronize(m->stream));
+    LCK(cudaMemcpy(p.data(), m->par, sizeof(float) * kPar, cudaMemcpyDeviceToHost));
+    const int M = m->M;
+    float* o = out;
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c <= M; ++c)
+            *o++ = p[size_t(r) * kIn + c];
+    o = std::copy(p.begin() + kW1, p.begin() + kW1 + kHid + kW2 + kHid, o);
+    const size_t w3 = kW1 + 2 * kHid + kW2;
+    o = std::copy(p.begin() + w3, p.begin() + w3 + size_t(M) * kHid, o);
+    std::copy(p.begin() + w3 + kW3, p.begin() + w3 + kW3 + M, o);
+    return ISING_OK;
+}
+
+int32_t ising_mlp_set_params(ising_mlp_t m, const float* in)
+{
+    if (!m || !in)
+        return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    std::vector<float> p(kPar, 0.f);
+    const int M = m->M;
+    const float* s = in;
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c <= M; ++c)
+            p[size_t(r) * kIn + c] = *s++;
+    std::copy(s, s + kHid + kW2 + kHid, p.begin() + kW1);
+    s += kHid + kW2 + kHid;
+    const size_t w3 = kW1 + 2 * kHid + kW2;
+    std::copy(s, s + size_t(M) * kHid, p.begin() + w3);
+    s += size_t(M) * kHid;
+    std::copy(s, s + M, p.begin() + w3 + kW3);
+    LCK(cudaStreamSynchronize(m->stream));
+    LCK(cudaMemcpy(m->par, p.data(), sizeof(float) * kPar, cudaMemcpyHostToDevice));
+    LCK(cudaMemset(m->mom, 0, sizeof(float) * 2 * kPar));
+    m->adam_t = 0;
+    LCK(refresh_bf16(m, m->stream));
+    LCK(cudaStreamSynchronize(m->stream));
+    return ISING_OK;
+}
+
+}  // extern "C"
+
+namespace isg {
+namespace {
+
+std::vector<bf16> pack_inputs(const float* X, int B, int M)
+{
+    std::vector<bf16> x(size_t(B) * kIn, __float2bfloat16(0.f));
+    for (int b = 0; b < B; ++b)
+        for (int c = 0; c <= M; ++c)
+            x[size_t(b) * kIn + c] = __float2bfloat16(X[size_t(b) * (M + 1) + c]);
+    return x;
+}
+
+}  // namespace
+}  // namespace isg
+
+extern "C" {
+
+int32_t ising_mlp_forward(ising_mlp_t m, int32_t B, const float* X, float* L)
+{
+    if (!m || !X || !L || B < 1)
+        return isg_fail(ISING_ERR_INVALID_ARG, "forward: NULL argument or B < 1");
+    const int rows_pad = cdiv(B, 128) * 128;
+    cudaStream_t st = m->stream;
+    LCK(cudaStreamSynchronize(st));
+    LCK(ensure_pass(m, rows_pad));
+    const std::vector<bf16> x = pack_inputs(X, B, m->M);
+    LCK(cudaMemsetAsync(m->PX, 0, sizeof(bf16) * size_t(rows_pad) * kIn, st));
+    LCK(cudaMemcpyAsync(m->PX, x.data(), sizeof(bf16) * x.size(), cudaMemcpyHostToDevice, st));
+    LCK(forward(m, st, rows_pad, m->PX, m->PH1, m->PH2, m->PL));
+    std::vector<float> l(size_t(B) * kOut);
+    LCK(cudaMemcpyAsync(l.data(), m->PL, sizeof(float) * l.size(), cudaMemcpyDeviceToHost, st));
+    int32_t rc = check_err(m, st);
+    if (rc)
+        return rc;
+    for (int b = 0; b < B; ++b)
+        for (int t = 0; t < m->M; ++t)
+            L[size_t(b) * m->M + t] = l[size_t(b) * kOut + t];
+    return ISING_OK;
+}
+
+int32_t ising_mlp_grad(ising_mlp_t m, int32_t B, const float* X, const uint32_t* Y, float* grad, float* loss)
+{
+    if (!m || !X || !Y || !grad || B < 128 || B % 128)
+        return isg_fail(ISING_ERR_INVALID_ARG, "grad: NULL argument or B not a positive multiple of 128");
+    cudaStream_t st = m->stream;
+    LCK(cudaStreamSynchronize(st));
+    LCK(ensure_batch(m, B));
+    const std::vector<bf16> x = pack_inputs(X, B, m->M);
+    LCK(cudaMemcpyAsync(m->Xb, x.data(), sizeof(bf16) * x.size(), cudaMemcpyHostToDevice, st));
+    LCK(cudaMemcpyAsync(m->Yb, Y, sizeof(uint32_t) * B, cudaMemcpyHostToDevice, st));
+    LCK(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+    LCK(backward(m, st, B));
+    std::vector<float> g(kGrad);
+    float lsum = 0.f;
+    LCK(cudaMemcpyAsync(g.data(), m->grad, sizeof(float) * kGrad, cudaMemcpyDeviceToHost, st));
+    LCK(cudaMemcpyAsync(&lsum, m->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    int32_t rc = check_err(m, st);
+    if (rc)
+        return rc;
+    const int M = m->M;
+    float* o = grad;
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c <= M; ++c)
+            *o++ = g[size_t(r) * kIn + c];
+    o = std::copy(g.begin() + kW1, g.begin() + kW1 + kHid + kW2 + kHid, o);
+    const size_t w3 = kW1 + 2 * kHid + kW2;
+    o = std::copy(g.begin() + w3, g.begin() + w3 + size_t(M) * kHid, o);
+    std::copy(g.begin() + w3 + kGW3, g.begin() + w3 + kGW3 + M, o);
+    if (loss)
+        *loss = lsum / float(B);
+    return ISING_OK;
+}
+
+int32_t ising_mlp_collect(ising_mlp_t m, ising_t h)
+{
+    if (!m || !h)
+        return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!h->inited)
+        return isg_fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    if (h->M != m->M)
+        return isg_fail(ISING_ERR_INVALID_ARG, "the handle's slice count differs from the network's");
+    const long long rows = (long long)h->R * h->S;
+    if (m->n_rec + rows > m->cap)
+        return isg_fail(ISING_ERR_INVALID_ARG, "record capacity exceeded");
+    LearnedArgs a = learned_args(h, m);
+    collect_kernel<<<cdiv(rows, 256), 256, 0, h->stream>>>(a, m->Xd + size_t(m->n_rec) * kIn, m->Yd + m->n_rec);
+    LCK(cudaGetLastError());
+    LCK(cudaStreamSynchronize(h->stream));
+    m->n_rec += rows;
+    return ISING_OK;
+}
+
+int64_t ising_mlp_n_records(ising_mlp_t m) { return m ? m->n_rec : 0; }
+
+int32_t ising_mlp_clear_records(ising_mlp_t m)
+{
+    if (!m)
+        return isg_fail(ISING_ERR_INVALID_ARG, "network is NULL");
+    m->n_rec = 0;
+    return ISING_OK;
+}
+
+int32_t ising_mlp_train(ising_mlp_t m, int32_t epochs, int32_t batch, float lr, float* loss)
+{
+    if (!m || epochs < 0 || batch < 128 || batch % 128 || !(lr > 0.f))
+        return isg_fail(ISING_ERR_INVALID_ARG, "train: epochs >= 0, batch a positive multiple of 128, lr > 0");
+    const long long nb = m->n_rec / batch;
+    if (nb < 1)
+        return isg_fail(ISING_ERR_INVALID_ARG, "train: fewer records than one batch");
+    cudaStream_t st = m->stream;
+    LCK(cudaStreamSynchronize(st));
+    LCK(ensure_batch(m, batch));
+    std::vector<int> order(size_t(m->n_rec));
+    float last = 0.f;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (long long i = 0; i < m->n_rec; ++i)
+            order[size_t(i)] = int(i);
+        std::mt19937_64 gen(uint64_t(m->seed) + uint64_t(ep));
+        std::shuffle(order.begin(), order.end(), gen);
+        LCK(cudaMemcpyAsync(m->idx, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st));
+        LCK(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+        for (long long b = 0; b < nb; ++b) {
+            gather_batch_kernel<<<cdiv(batch * (kIn / 8), 256), 256, 0, st>>>(m->Xd, m->Yd, m->idx + b * batch,
+                                                                              batch, m->Xb, m->Yb);
+            LCK(backward(m, st, batch));
+            LCK(adam_step(m, st, lr));
+        }
+        float lsum = 0.f;
+        LCK(cudaMemcpyAsync(&lsum, m->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+        int32_t rc = check_err(m, st);
+        if (rc)
+            return rc;
+        last = lsum / float(nb * batch);
+    }
+    if (loss)
+        *loss = last;
+    return ISING_OK;
+}
+
+int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint64_t* accepted, uint64_t* proposed,
+                           const ising_learned_trace_t* trace)
+{
+    if (!m || !h)
+        return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!h->inited)
+        return isg_fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    if (h->M != m->M)
+        return isg_fail(ISING_ERR_INVALID_ARG, "the handle's slice count differs from the network's");
+    const long long total = (long long)h->R * h->S;
+    if (trace && trace->capacity < total)
+        return isg_fail(ISING_ERR_INVALID_ARG, "trace capacity below R * S rows");
+    int32_t rc = build_colours(h);
+    if (rc)
+        return rc;
+    cudaStream_t st = h->stream;
+    long long maxrows = 0;
+    for (size_t c = 0; c + 1 < h->colour_off.size(); ++c)
+        maxrows = std::max(maxrows, (long long)h->R * (h->colour_off[c + 1] - h->colour_off[c]));
+    const long long maxpad = (maxrows + 127) / 128 * 128;
+    if (maxpad > (1LL << 31) - 1)
+        return isg_fail(ISING_ERR_UNSUPPORTED, "a colour class holds more than 2^31 rows");
+    LCK(cudaStreamSynchronize(m->stream));
+    LCK(ensure_pass(m, maxpad));
+    LCK(cudaMemsetAsync(m->n_acc, 0, sizeof(unsigned long long), st));
+    long long done = 0;
+    for (size_t c = 0; c + 1 < h->colour_off.size(); ++c) {
+        const int ncols = h->colour_off[c + 1] - h->colour_off[c];
+        const int rows = h->R * ncols;
+        const int rows_pad = cdiv(rows, 128) * 128;
+        LearnedArgs a = learned_args(h, m);
+        a.ncols = ncols;
+        a.rows = rows;
+        a.sites = h->d_colour_sites + h->colour_off[c];
+        learned_gather_kernel<<<cdiv(rows_pad, 128), 128, 0, st>>>(a, rows_pad);
+        LCK(forward(m, st, rows_pad, m->PX, m->PH1, m->PH2, m->PL));
+        learned_mh_kernel<<<cdiv(rows, 128), 128, 0, st>>>(a);
+        LCK(cudaGetLastError());
+        if (trace) {
+            auto d2h = [&](void* dst, const void* src, size_t bytes) {
+                return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+            };
+            LCK(d2h(trace->phi ? trace->phi + done * kOut : nullptr, m->Pphi, sizeof(int) * size_t(rows) * kOut));
+            LCK(d2h(trace->logits ? trace->logits + done * kOut : nullptr, m->PL,
+                    sizeof(float) * size_t(rows) * kOut));
+            LCK(d2h(trace->old_bits ? trace->old_bits + done : nullptr, m->Pold, sizeof(uint32_t) * rows));
+            LCK(d2h(trace->prop_bits ? trace->prop_bits + done : nullptr, m->Pprop, sizeof(uint32_t) * rows));
+            LCK(d2h(trace->accepted ? trace->accepted + done : nullptr, m->Pacc, size_t(rows)));
+            LCK(cudaStreamSynchronize(st));
+            for (int i = 0; i < rows; ++i) {
+                const int r = i / ncols;
+                if (trace->replica)
+                    trace->replica[done + i] = r;
+                if (trace->site)
+                    trace->site[done + i] = h->colour_sites[h->colour_off[c] + i - r * ncols];
+            }
+        }
+        done += rows;
+    }
+    const long long blocks = std::min<long long>(cdiv(total * h->M, 256), 152LL * 16);
+    if (h->field_bits == 16)
+        fields_rebuild_kernel<int16_t><<<int(blocks), 256, 0, st>>>(
+            h->d_spins, static_cast<int16_t*>(h->d_fields), h->R, h->n, h->d_row_ptr, h->d_col, h->d_J, h->d_h);
+    else
+        fields_rebuild_kernel<int32_t><<<int(blocks), 256, 0, st>>>(
+            h->d_spins, static_cast<int32_t*>(h->d_fields), h->R, h->n, h->d_row_ptr, h->d_col, h->d_J, h->d_h);
+    LCK(cudaGetLastError());
+    unsigned long long acc = 0;
+    LCK(cudaMemcpyAsync(&acc, m->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
+    rc = check_err(m, st);
+    if (rc)
+        return rc;
+    ++h->learned_passes;
+    if (accepted)
+        *accepted = acc;
+    if (proposed)
+        *proposed = uint64_t(total);
+    return ISING_OK;
+}
+
+int32_t ising_mlp_destroy(ising_mlp_t m)
+{
+    if (!m)
+        return ISING_OK;
+    cudaStreamSynchronize(m->stream);
+    free_mlp(m);
+    delete m;
+    return ISING_OK;
+}
+
+}  // extern "C"

@@ -57,6 +57,15 @@ class IsingInstance(ctypes.Structure):
                 ("betas", _f64p), ("seed", ctypes.c_uint32)]
 
 
+class LearnedTrace(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("replica", _i32p), ("site", _i32p), ("phi", _i32p),
+                ("logits", ctypes.POINTER(ctypes.c_float)), ("old_bits", ctypes.POINTER(ctypes.c_uint32)),
+                ("prop_bits", ctypes.POINTER(ctypes.c_uint32)), ("accepted", ctypes.POINTER(ctypes.c_uint8))]
+
+
+_f32p = ctypes.POINTER(ctypes.c_float)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
 _SIGS = {
     "ising_last_error": ([], ctypes.c_char_p),
     "ising_create": ([ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_uint32,
@@ -88,6 +97,23 @@ _SIGS = {
     "ising_batch_get_info": ([_vp, ctypes.c_int32, ctypes.POINTER(IsingInfo),
                               ctypes.POINTER(ctypes.c_int32)], ctypes.c_int32),
     "ising_batch_destroy": ([_vp], ctypes.c_int32),
+    "ising_tc_gemm": ([ctypes.c_int32] * 3 + [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _f32p, _vp,
+                                             ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
+                                             ctypes.c_int32, _vp], ctypes.c_int32),
+    "ising_mlp_create": ([ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.POINTER(_vp)],
+                         ctypes.c_int32),
+    "ising_mlp_set_stream": ([_vp, _vp], ctypes.c_int32),
+    "ising_mlp_n_params": ([_vp], ctypes.c_int64),
+    "ising_mlp_get_params": ([_vp, _f32p], ctypes.c_int32),
+    "ising_mlp_set_params": ([_vp, _f32p], ctypes.c_int32),
+    "ising_mlp_forward": ([_vp, ctypes.c_int32, _f32p, _f32p], ctypes.c_int32),
+    "ising_mlp_grad": ([_vp, ctypes.c_int32, _f32p, _u32p, _f32p, _f32p], ctypes.c_int32),
+    "ising_mlp_collect": ([_vp, _vp], ctypes.c_int32),
+    "ising_mlp_n_records": ([_vp], ctypes.c_int64),
+    "ising_mlp_clear_records": ([_vp], ctypes.c_int32),
+    "ising_mlp_train": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _f32p], ctypes.c_int32),
+    "ising_learned_pass": ([_vp, _vp, _u64p, _u64p, ctypes.POINTER(LearnedTrace)], ctypes.c_int32),
+    "ising_mlp_destroy": ([_vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -365,6 +391,111 @@ class Batch:
         if getattr(self, "h", None):
             _check(_lib.ising_batch_destroy(self.h))
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------ learned column proposal
+class Mlp:
+    """The learned Trotter-column proposal network (``ising_mlp_*``).
+
+    ``Mlp(n_slices, seed, capacity)``; parameters are a flat float32 vector in
+    the layout W1 [256][M+1], b1, W2 [256][256], b2, W3 [M][256], b3.
+    """
+
+    def __init__(self, n_slices, seed=1, capacity=0, stream=None):
+        self.M = int(n_slices)
+        h = _vp()
+        _check(_lib.ising_mlp_create(self.M, ctypes.c_uint32(seed & 0xFFFFFFFF), int(capacity),
+                                     ctypes.byref(h)))
+        self.m = h
+        if stream is not None:
+            _check(_lib.ising_mlp_set_stream(self.m, _vp(stream)))
+
+    @property
+    def n_params(self) -> int:
+        return int(_lib.ising_mlp_n_params(self.m))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(_lib.ising_mlp_get_params(self.m, _p(out, _f32p)))
+        return out
+
+    def set_params(self, p):
+        p = _arr(p, np.float32)
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {p.size}")
+        _check(_lib.ising_mlp_set_params(self.m, _p(p, _f32p)))
+
+    def unpack(self, p=None) -> dict:
+        """Split a flat parameter (or gradient) vector into its six tensors."""
+        p = self.get_params() if p is None else np.asarray(p)
+        M, H = self.M, 256
+        sizes = [("W1", (H, M + 1)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (M, H)), ("b3", (M,))]
+        out, o = {}, 0
+        for name, shape in sizes:
+            n = int(np.prod(shape))
+            out[name] = p[o:o + n].reshape(shape)
+            o += n
+        return out
+
+    def forward(self, X) -> np.ndarray:
+        X = _arr(X, np.float32)
+        B = X.shape[0]
+        L = np.empty((B, self.M), dtype=np.float32)
+        _check(_lib.ising_mlp_forward(self.m, B, _p(X, _f32p), _p(L, _f32p)))
+        return L
+
+    def grad(self, X, Y):
+        X, Y = _arr(X, np.float32), _arr(Y, np.uint32)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(_lib.ising_mlp_grad(self.m, X.shape[0], _p(X, _f32p), _p(Y, _u32p), _p(g, _f32p),
+                                   ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def collect(self, sim: "Ising"):
+        _check(_lib.ising_mlp_collect(self.m, sim.h))
+
+    @property
+    def n_records(self) -> int:
+        return int(_lib.ising_mlp_n_records(self.m))
+
+    def clear_records(self):
+        _check(_lib.ising_mlp_clear_records(self.m))
+
+    def train(self, epochs=1, batch=4096, lr=1e-3) -> float:
+        loss = ctypes.c_float()
+        _check(_lib.ising_mlp_train(self.m, int(epochs), int(batch), ctypes.c_float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def learned_pass(self, sim: "Ising", trace=False):
+        """One learned pass over ``sim``; returns (accepted, proposed[, trace dict])."""
+        acc, prop = ctypes.c_uint64(), ctypes.c_uint64()
+        tr = None
+        if trace:
+            rows = sim.R * (sim.n // self.M)
+            t = {"replica": np.empty(rows, np.int32), "site": np.empty(rows, np.int32),
+                 "phi": np.empty((rows, 32), np.int32), "logits": np.empty((rows, 32), np.float32),
+                 "old_bits": np.empty(rows, np.uint32), "prop_bits": np.empty(rows, np.uint32),
+                 "accepted": np.empty(rows, np.uint8)}
+            tr = LearnedTrace(rows, _p(t["replica"], _i32p), _p(t["site"], _i32p), _p(t["phi"], _i32p),
+                              _p(t["logits"], _f32p), _p(t["old_bits"], _u32p), _p(t["prop_bits"], _u32p),
+                              _p(t["accepted"], ctypes.POINTER(ctypes.c_uint8)))
+        _check(_lib.ising_learned_pass(sim.h, self.m, ctypes.byref(acc), ctypes.byref(prop),
+                                       ctypes.byref(tr) if tr is not None else None))
+        if trace:
+            return int(acc.value), int(prop.value), t
+        return int(acc.value), int(prop.value)
+
+    def close(self):
+        if getattr(self, "m", None):
+            _lib.ising_mlp_destroy(self.m)
+            self.m = None
 
     def __del__(self):
         try:

@@ -1,0 +1,372 @@
+"""Learned Trotter-column proposal on the GPU against the FP64 oracle.
+
+* the tcgen05 network forward and its back-propagated gradients against
+  ``oracle.mlp_forward`` / ``oracle.mlp_backward`` on the same bf16-rounded
+  weights and inputs;
+* a learned pass replayed on the CPU from its trace: spatial fields phi exact,
+  proposals and accept decisions re-derived from the Philox words with the
+  oracle's column energy and MH ratio (decisions compared away from ties), final
+  spins, energies and local fields exact, and later sweeps still bit-exact with
+  the oracle;
+* exactness of the MH correction: on models small enough to enumerate, the
+  energy histogram of a chain made of learned passes alone matches the exact
+  Boltzmann law bin by bin within 3 standard errors.
+
+The model is the layered (Trotter) Ising model of section 3.1; the network and
+the column move are additions to the paper's method.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_0024_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1004_0024_gb300 import ising as mod
+    return mod
+
+
+def bf16(a):
+    """Round to bf16 (nearest even) and return float64, as the library does."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+    return t.to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def oracle_weights(net, p=None):
+    """The weights the GPU multiplies with: bf16 matrices, FP32 biases."""
+    u = net.unpack(p)
+    return dict(W1=bf16(u["W1"]), b1=u["b1"].astype(np.float64), W2=bf16(u["W2"]),
+                b2=u["b2"].astype(np.float64), W3=bf16(u["W3"]), b3=u["b3"].astype(np.float64))
+
+
+def random_inputs(rng, B, M):
+    phi = rng.integers(-20, 21, size=(B, M)) / 8.0
+    beta = rng.uniform(0.05, 5.0, size=(B, 1))
+    return bf16(np.concatenate([phi, beta], axis=1))
+
+
+# ------------------------------------------------------------ network numerics
+@pytest.mark.parametrize("M,B", [(32, 384), (5, 300), (1, 128)])
+def test_forward_matches_oracle(ising, M, B):
+    rng = np.random.default_rng(100 + M)
+    net = ising.Mlp(M, seed=7)
+    X = random_inputs(rng, B, M)
+    got = net.forward(X)
+    w = oracle_weights(net)
+    _, _, ref = oracle.mlp_forward(X, w["W1"], w["b1"], w["W2"], w["b2"], w["W3"], w["b3"])
+    # hidden activations are stored in bf16 between layers (relative 2^-9)
+    tol = 2e-2 * max(1.0, np.abs(ref).max())
+    assert got.shape == (B, M)
+    assert np.abs(got - ref).max() <= tol, np.abs(got - ref).max()
+    net.close()
+
+
+@pytest.mark.parametrize("M,B", [(32, 256), (8, 512)])
+def test_gradients_match_oracle(ising, M, B):
+    rng = np.random.default_rng(200 + M)
+    net = ising.Mlp(M, seed=11)
+    # larger weights than the initial ones so that every layer matters
+    p = net.get_params()
+    p = (p + rng.normal(0.0, 0.05, size=p.size)).astype(np.float32)
+    net.set_params(p)
+    X = random_inputs(rng, B, M)
+    Ybits = rng.integers(0, 2, size=(B, M))
+    Y = (Ybits << np.arange(M)).sum(axis=1).astype(np.uint32)
+    g, loss = net.grad(X, Y)
+    w = oracle_weights(net)
+    ref_loss, ref = oracle.mlp_backward(X, Ybits.astype(np.float64), w["W1"], w["b1"], w["W2"], w["b2"],
+                                        w["W3"], w["b3"])
+    assert abs(loss - ref_loss) <= 1e-3 * max(1.0, abs(ref_loss)), (loss, ref_loss)
+    got = net.unpack(g)
+    for name, r in zip(("W1", "b1", "W2", "b2", "W3", "b3"), ref):
+        d = got[name].astype(np.float64).ravel()
+        r = r.ravel()
+        rel = np.linalg.norm(d - r) / np.linalg.norm(r)
+        cos = d @ r / (np.linalg.norm(d) * np.linalg.norm(r))
+        # The forward stores H1 and H2 in bf16 (relative 2^-9), which moves each
+        # logit by ~1e-3.  With labels drawn independently of the inputs the
+        # true gradient is a residual ~1/sqrt(B) of its per-sample terms, so
+        # that shift shows as a few percent: a float64 emulation of the same
+        # storage points gives 2.5% (W1) and 1.8% (W2) at M = 32, B = 256.
+        assert rel <= 5e-2 and cos > 0.998, (name, rel, cos)
+    net.close()
+
+
+def test_training_lowers_the_loss(ising):
+    """Adam on recorded columns of a sampled model: the loss on columns drawn
+    after the recording (not trained on) drops."""
+    g = W.layered_graph(4, 8, 3)
+    R = 32
+    sim = ising.Ising(g, W.geometric_betas(R, 0.1, 3.0), seed=9, rng="philox")
+    net = ising.Mlp(8, seed=3, capacity=R * 16 * 40)
+    for _ in range(40):
+        sim.run(5, 1)
+        net.collect(sim)
+    assert net.n_records == R * 16 * 40
+    sim.run(5, 1)
+    st = sim.read_state()
+    X, Y = _columns(g, st, W.geometric_betas(R, 0.1, 3.0))
+    _, before = net.grad(X[:384], Y[:384])
+    last = net.train(epochs=6, batch=256, lr=2e-3)
+    _, after = net.grad(X[:384], Y[:384])
+    assert np.isfinite(last) and after < 0.8 * before, (before, after, last)
+    net.close()
+    sim.close()
+
+
+def _columns(g, st, betas):
+    """(X, Y) records of every (replica, site) of a state, built on the CPU."""
+    M = g.n_slices
+    S = g.n // M
+    R = st["spins"].shape[0]
+    phi = np.zeros((R, S, M), dtype=np.int64)
+    for i in range(g.n):
+        t, q = divmod(i, S)
+        f = np.full(R, int(g.h[i]))
+        for e in range(g.row_ptr[i], g.row_ptr[i + 1]):
+            j = int(g.col[e])
+            if j // S == t:
+                f = f + int(g.J[e]) * st["spins"][:, j].astype(np.int64)
+        phi[:, q, t] = f
+    beta = np.asarray(betas)[st["temp_of_slot"]]
+    X = np.concatenate([phi / 8.0, np.broadcast_to(beta[:, None, None], (R, S, 1))], axis=2).reshape(R * S, M + 1)
+    bits = (st["spins"].reshape(R, M, S) > 0).transpose(0, 2, 1).reshape(R * S, M)
+    Y = (bits.astype(np.uint64) << np.arange(M, dtype=np.uint64)).sum(axis=1).astype(np.uint32)
+    return bf16(X), Y
+
+
+# --------------------------------------------------------- learned-pass replay
+def _sigmoid32(l):
+    l = np.float32(l)
+    return float(np.float32(1.0) / (np.float32(1.0) + np.exp(-l, dtype=np.float32)))
+
+
+def replay(g, betas, seed, inst, pass_idx, before, trace):
+    """Re-derive a learned pass row by row from the oracle; returns the spins
+    and energies it leads to and the number of near-ties skipped."""
+    M = g.n_slices
+    S = g.n // M
+    spins = before["spins"].copy()
+    E = before["energy"].astype(np.int64).copy()
+    beta_of = np.asarray(betas)[before["temp_of_slot"]]
+    jtau = {}
+    ties = 0
+    for row in range(trace["replica"].size):
+        r, q = int(trace["replica"][row]), int(trace["site"][row])
+        s = spins[r]
+        phi = np.empty(M, dtype=np.int64)
+        for t in range(M):
+            i = t * S + q
+            f = int(g.h[i])
+            for e in range(g.row_ptr[i], g.row_ptr[i + 1]):
+                j = int(g.col[e])
+                if j // S == t:
+                    f += int(g.J[e]) * int(s[j])
+                elif q not in jtau:
+                    jtau[q] = int(g.J[e])
+            phi[t] = f
+        assert np.array_equal(trace["phi"][row, :M], phi), f"phi of row {row}"
+        col = np.array([s[t * S + q] for t in range(M)], dtype=np.int8)
+        old = int(((col > 0).astype(np.uint64) << np.arange(M, dtype=np.uint64)).sum())
+        assert int(trace["old_bits"][row]) == old, f"old column of row {row}"
+        words = np.concatenate([oracle.philox([q, pass_idx, inst, 2 + 4 * j], [seed, r]) for j in range(9)])
+        logits = trace["logits"][row, :M]
+        prop = 0
+        for t in range(M):
+            thr = _sigmoid32(logits[t]) * 2.0 ** 32
+            if abs(float(words[t]) - thr) < 2.0 ** 32 * 1e-6:
+                ties += 1
+                prop |= int(trace["prop_bits"][row]) & (1 << t)
+            elif float(words[t]) < thr:
+                prop |= 1 << t
+        assert int(trace["prop_bits"][row]) == prop, f"proposal of row {row}"
+        s2 = np.array([1 if (prop >> t) & 1 else -1 for t in range(M)], dtype=np.int8)
+        logA, dE = oracle.column_log_accept(M, jtau.get(q, 0), phi, col, s2, logits.astype(np.float64),
+                                            float(beta_of[r]))
+        lu = np.log((float(words[32]) + 0.5) * 2.0 ** -32)
+        acc_ref = logA >= 0 or lu < logA
+        # the kernel's log A uses the exact probabilities of its discrete
+        # draws, the oracle's the logistic of the logits: they differ by ~1e-7
+        if abs(lu - logA) < 1e-5 or (prop != old and abs(logA) < 1e-5):
+            ties += 1
+        else:
+            assert bool(trace["accepted"][row]) == acc_ref, f"decision of row {row}: logA {logA}"
+        if trace["accepted"][row] and prop != old:
+            for t in range(M):
+                s[t * S + q] = s2[t]
+            E[r] += dE
+    return spins, E, ties
+
+
+def _with_output_bias(net, bias):
+    u = net.unpack()
+    u["b3"][:] = bias
+    net.set_params(np.concatenate([u[k].ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")]))
+
+
+@pytest.mark.parametrize("model,rng_mode,bias", [("L4_M8", "philox", 0.0), ("L3_M2", "mt19937", 0.0),
+                                                 ("L4_M3", "philox", 0.0), ("L3_M1", "mt19937", 0.0),
+                                                 ("ring_S5_M4", "philox", 1.5), ("L5_M32", "philox", -0.7)])
+def test_learned_pass_replays_on_the_oracle(ising, model, rng_mode, bias):
+    if model.startswith("ring"):
+        g = _ring_model()
+    else:
+        L, M = (int(x[1:]) for x in model.split("_"))
+        g = W.layered_graph(L, M, 5)
+    M = g.n_slices
+    R, seed = 16, 77
+    betas = W.geometric_betas(R, 0.1, 3.0)
+    sim = ising.Ising(g, betas, seed=seed, rng=rng_mode)
+    net = ising.Mlp(M, seed=5)
+    if bias:
+        _with_output_bias(net, bias)
+    sim.run(12, 1)
+    for pass_idx in range(2):
+        before = sim.read_state()
+        acc, prop, tr = net.learned_pass(sim, trace=True)
+        after = sim.read_state()
+        S = g.n // M
+        assert prop == R * S
+        assert sorted(zip(tr["replica"], tr["site"])) == [(r, q) for r in range(R) for q in range(S)]
+        assert acc == int(tr["accepted"].sum())
+        spins, E, ties = replay(g, betas, seed, 0, pass_idx, before, tr)
+        assert ties <= 2
+        assert np.array_equal(after["spins"], spins)
+        assert np.array_equal(after["energy"], E)
+        for r in range(R):
+            assert after["energy"][r] == oracle.energy(g, after["spins"][r])
+            assert np.array_equal(after["fields"][r], oracle.fields(g, after["spins"][r]))
+        assert np.array_equal(after["temp_of_slot"], before["temp_of_slot"])
+        sim.run(3, 1)
+    net.close()
+    sim.close()
+
+
+def test_colour_classes_have_no_spatial_edge(ising):
+    g = W.layered_graph(6, 4, 2)
+    S = g.n // 4
+    sim = ising.Ising(g, W.geometric_betas(4, 0.2, 1.0), seed=1, rng="philox")
+    net = ising.Mlp(4, seed=1)
+    _, _, tr = net.learned_pass(sim, trace=True)
+    sites = tr["site"][tr["replica"] == 0]
+    # classes are the maximal runs of replica 0's rows between other replicas' rows
+    order = np.nonzero(tr["replica"] == 0)[0]
+    classes = np.split(sites, np.nonzero(np.diff(order) > 1)[0] + 1)
+    assert sorted(np.concatenate(classes).tolist()) == list(range(S))
+    for cls in classes:
+        members = set(cls.tolist())
+        for q in cls:
+            nbrs = {int(c) for c in g.col[g.row_ptr[q]:g.row_ptr[q + 1]] if c < S}
+            assert not (nbrs & members), f"site {q} shares a class with a neighbour"
+    net.close()
+    sim.close()
+
+
+def test_sweeps_stay_bit_exact_after_learned_passes(ising):
+    """After a learned pass the sweep reads the rebuilt fields: continuing
+    the run from the same spins matches the oracle bit for bit (MT19937 words
+    are untouched by the Philox-driven column moves)."""
+    c = W.config0()
+    g, betas, seed = c["graph"], c["betas"], c["seed"]
+    sim = ising.Ising(g, betas, seed=seed, rng="mt19937", field_bits=16)
+    ref = oracle.Sim(g, betas, seed=seed, rng="mt19937")
+    net = ising.Mlp(g.n_slices, seed=2)
+    for k in range(3):
+        sim.run(20, 1)
+        ref.run(20, 1)
+        net.learned_pass(sim)
+        st = sim.read_state()
+        ref.set_spins(st["spins"])
+        r = ref.read()
+        assert np.array_equal(st["fields"], r["fields"]) and np.array_equal(st["energy"], r["energy"])
+    sim.run(20, 1)
+    ref.run(20, 1)
+    st, r = sim.read_state(), ref.read()
+    for key in ("spins", "fields", "energy", "temp_of_slot"):
+        assert np.array_equal(st[key], r[key]), key
+    net.close()
+    sim.close()
+
+
+# ------------------------------------------- exactness of the MH correction
+def _ring_model(S=5, M=4, jtau=2, seed=4):
+    """S sites on a ring plus one chord, M slices in a Trotter ring."""
+    rng = np.random.default_rng(seed)
+    spatial = {(q, (q + 1) % S): int(rng.choice([-3, -2, -1, 1, 2, 3])) for q in range(S)}
+    spatial[(0, 2)] = int(rng.choice([-2, 2]))
+    hs = rng.integers(-2, 3, size=S)
+    edges = {}
+    for t in range(M):
+        for (a, b), j in spatial.items():
+            edges[(t * S + a, t * S + b)] = j
+        if M >= 3 or (M == 2 and t == 0):
+            for q in range(S):
+                edges[(t * S + q, ((t + 1) % M) * S + q)] = jtau
+    return W.graph_from_edges(S * M, edges, np.tile(hs, M), n_slices=M)
+
+
+def _exact_energy_law(g):
+    """Energies of all 2^n states; each checked against the oracle on a sample."""
+    n = g.n
+    idx = np.arange(1 << n, dtype=np.int64)
+    s = (((idx[:, None] >> np.arange(n)) & 1) * 2 - 1).astype(np.int32)
+    Jd = np.zeros((n, n), dtype=np.int32)
+    for i in range(n):
+        for e in range(g.row_ptr[i], g.row_ptr[i + 1]):
+            Jd[i, g.col[e]] = g.J[e]
+    E = -(s @ g.h.astype(np.int32)) - ((s @ Jd) * s).sum(axis=1) // 2
+    for k in np.random.default_rng(0).integers(0, 1 << n, size=64):
+        assert E[k] == oracle.energy(g, s[k].astype(np.int8))
+    return E
+
+
+@pytest.mark.parametrize("model", ["layered_L3_M2", "ring_S5_M4"])
+def test_learned_chain_samples_the_boltzmann_law(ising, model):
+    """A chain of learned passes alone (no sweeps) at beta ~ 0.12 over 256
+    independent replicas: every energy bin with expected mass >= 2% holds
+    its exact Boltzmann probability within 3 standard errors (replicas as
+    the independent unit), for an untrained and a deliberately biased network."""
+    g = W.layered_graph(3, 2, 8) if model == "layered_L3_M2" else _ring_model()
+    M = g.n_slices
+    E_all = _exact_energy_law(g)
+    R, beta0 = 256, 0.12
+    betas = beta0 * (1.0 + 1e-12 * np.arange(R))
+    levels, inv = np.unique(E_all, return_inverse=True)
+    w = np.exp(-beta0 * (E_all - E_all.min()))
+    exact = np.bincount(inv, weights=w) / w.sum()
+    for bias in (0.0, 1.5):
+        sim = ising.Ising(g, betas, seed=31, rng="philox")
+        net = ising.Mlp(M, seed=17)
+        if bias:
+            _with_output_bias(net, bias)  # proposals lean to +1: the correction must undo it
+        counts = np.zeros((R, levels.size))
+        # a biased independent proposal reaches all -1 columns rarely, so the
+        # chain needs a long burn-in (a CPU emulation with exact arithmetic
+        # is 12 SE off after 50 passes and within 2 SE after 1000)
+        burn, passes = 1000, 1000
+        for k in range(burn + passes):
+            net.learned_pass(sim)
+            if k >= burn:
+                e = sim.read_state()["energy"]
+                assert np.isin(e, levels).all()
+                counts[np.arange(R), np.searchsorted(levels, e)] += 1
+        st = sim.read_state()
+        for r in range(0, R, 37):
+            assert st["energy"][r] == oracle.energy(g, st["spins"][r])
+        frac = counts / passes
+        mean, se = frac.mean(axis=0), frac.std(axis=0, ddof=1) / np.sqrt(R)
+        big = exact >= 0.02
+        z = (mean[big] - exact[big]) / np.maximum(se[big], 1e-12)
+        assert np.all(np.abs(z) < 3.0), (bias, levels[big], z)
+        net.close()
+        sim.close()
