@@ -160,6 +160,11 @@ int32_t ising_read_state(ising_t h, int8_t* spins, int32_t* fields, int64_t* ene
 /* accepted[R-1]: accepted swaps of pair (k, k+1) so far (host, synchronises). */
 int32_t ising_read_swap_stats(ising_t h, uint64_t* accepted);
 
+/* Energy and magnetisation m = sum_i s_i of the replica holding each
+ * temperature index k (arrays [R], either may be NULL).  Synchronises. */
+int32_t ising_read_observables(ising_t h, int64_t* energy_by_temp, int64_t* magnetisation_by_temp);
+
+
 /*
  * ising_save / ising_load -- checkpoint blob of the full replica state (spins,
  * fields, energies, labels, RNG states and positions, counters).  save: pass
@@ -380,7 +385,10 @@ typedef struct {
     uint32_t* old_bits;  /* [rows] column before the move (bit t: s_t=+1) */
     uint32_t* prop_bits; /* [rows] proposed column                        */
     uint8_t* accepted;   /* [rows]                                        */
+    uint64_t exact_decisions; /* out: decisions left to the FP64 product    */
 } ising_learned_trace_t;
+
+#define ISING_LEARNED_FP64_ONLY 1 /* decide every move by the FP64 product */
 
 /* One learned pass over handle h: every column of every replica once, the
  * colour classes of the slice graph (greedy colouring in site order; no two
@@ -388,16 +396,20 @@ typedef struct {
  * Philox4x32-10 with key (seed, replica slot), counter (q, pass, instance,
  * 2 + 4j) giving words 4j..4j+3: word t < M draws s'_t = +1 iff
  * u_t < x_t = p_t 2^32 (p_t = sigmoid(logit_t) in FP32), an event of
- * probability exactly ceil(x_t) 2^-32; log q is summed from those exact
- * probabilities and log A formed in FP64; word 32 accepts iff log A >= 0 or
- * log((u + 1/2) 2^-32) < log A.  `pass` counts
+ * probability exactly c_t 2^-32, c_t = ceil(x_t); q(s)/q(s') is the product of
+ * those probabilities over the changed bits and log A is formed in FP64; word
+ * 32 accepts iff log A >= 0 or log((u + 1/2) 2^-32) < log A.  The kernel
+ * first evaluates both sides in FP32 with a proven error bound and falls back
+ * to the FP64 product only when the bound cannot separate them, so every
+ * decision equals the FP64 one (flags ISING_LEARNED_FP64_ONLY forces the
+ * FP64 product for every move).  `pass` counts
  * the handle's learned passes since ising_replicas_init.  Energies are updated
  * by the exact integer dE and the local fields rebuilt afterwards.  The
  * counts of accepted and proposed moves of this pass are returned (either
  * pointer may be NULL).  Requires M <= 32, the network's M, R*S >= 1.
  * Errors: INVALID_ARG, NOT_INITIALISED, CUDA (including a GEMM timeout). */
-int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint64_t* accepted, uint64_t* proposed,
-                           const ising_learned_trace_t* trace);
+int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, uint64_t* accepted, uint64_t* proposed,
+                           ising_learned_trace_t* trace);
 int32_t ising_mlp_destroy(ising_mlp_t m);
 
 /* Release all device memory of the handle (NULL is ignored). */

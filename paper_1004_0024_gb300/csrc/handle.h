@@ -13,11 +13,15 @@
 
 struct ising_s {
     double* d_betas = nullptr;       // [R] inverse temperatures by index
+    float* d_betas32 = nullptr;      // [R] the same rounded to FP32
     unsigned long long learned_passes = 0;
     // colour classes of the slice graph for column moves (built on first use):
     // sites of class c are d_colour_sites[colour_off[c] .. colour_off[c+1])
     std::vector<int> colour_off, colour_sites;
     int* d_colour_sites = nullptr;
+    int* d_sp_off = nullptr;  // [S+1] spatial neighbour list of each site
+    int2* d_sp_nbr = nullptr; // (site, J) entries
+    long long* d_obs = nullptr;  // [R] per-slot magnetisation (ising_read_observables)
     // graph
     int n = 0, M = 1, S = 0, W = 1, Mp = 4, D0 = 0, D = 0, max_sp_deg = 0, max_sp_J = 0;
     long long kmax = 0, ebound = 0;

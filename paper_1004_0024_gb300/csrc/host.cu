@@ -138,6 +138,7 @@ void ising_s::drop_graphs()
 
 void ising_s::free_replicas()
 {
+    dfree(d_obs);
     drop_graphs();
     dfree(d_spins);
     if (d_fields)
@@ -157,6 +158,7 @@ void ising_s::free_replicas()
     dfree(d_swoff);
     dfree(d_swlen);
     dfree(d_betas);
+    dfree(d_betas32);
     dfree(d_wbuf);
     dfree(d_swbuf);
     dfree(d_Epub);
@@ -187,6 +189,8 @@ void ising_s::free_all()
     dfree(d_pos);
     dfree(d_nbr);
     dfree(d_colour_sites);
+    dfree(d_sp_off);
+    dfree(d_sp_nbr);
     colour_off.clear();
     colour_sites.clear();
 }
@@ -914,6 +918,7 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
         (rc = upload(&g->d_swthr, swthr)) || (rc = upload(&g->d_swoff, swoff)) ||
         (rc = upload(&g->d_swlen, swlen)) || (rc = dalloc(&g->d_Epub, 2 * size_t(R))) ||
         (rc = upload(&g->d_betas, g->betas)) ||
+        (rc = upload(&g->d_betas32, std::vector<float>(g->betas.begin(), g->betas.end()))) ||
         (rc = dalloc(&g->d_gridbar, 1))) {
         g->free_replicas();
         return rc;

@@ -172,7 +172,10 @@ struct LearnedArgs {
     int* E;
     const int* temp_of_slot;
     const double* betas;
+    const float* betas32;
     const int* sites;  // the class's sites
+    const int* sp_off; // [S+1] spatial neighbour list of each site
+    const int2* sp_nbr; // (site, J) entries
     int* phi;          // [rows][32]
     bf16* X;           // [rows_pad][64]
     const float* L;    // [rows_pad][32]
@@ -180,6 +183,8 @@ struct LearnedArgs {
     uint32_t *old_bits, *prop_bits;
     uint8_t* accepted;
     unsigned long long* n_acc;
+    unsigned long long* n_exact;  // decisions taken by the FP64 product
+    int fp64_only;                // decide every move by the FP64 product
 };
 
 // phi_t = h_i + sum over spatial neighbours j (same slice) of J s_j, i = t S + q
@@ -195,101 +200,180 @@ __device__ __forceinline__ int spatial_field(const LearnedArgs& a, const int8_t*
     return f;
 }
 
-__global__ void learned_gather_kernel(const LearnedArgs a, int rows_pad)
+// One warp per (replica, column) row, lane t = slice t: phi_t from the
+// spins of the column's spatial neighbours in slice t, then the input row
+// X = (phi_t/8 for t < M, beta at M, zeros) written as two coalesced halves.
+__global__ void __launch_bounds__(256) learned_gather_kernel(const LearnedArgs a, int rows_pad)
 {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int t = threadIdx.x & 31;
     if (row >= rows_pad)
         return;
     bf16* x = a.X + size_t(row) * kIn;
     if (row >= a.rows) {
-        for (int k = 0; k < kIn; ++k)
-            x[k] = __float2bfloat16(0.f);
+        x[t] = __float2bfloat16(0.f);
+        x[32 + t] = __float2bfloat16(0.f);
         return;
     }
     const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
-    const int8_t* sp = a.spins + size_t(r) * a.N;
-    for (int t = 0; t < a.M; ++t) {
-        const int f = spatial_field(a, sp, t, q);
+    const float beta = a.betas32[a.temp_of_slot[r]];
+    float v = 0.f;
+    if (t < a.M) {
+        const int8_t* sp = a.spins + size_t(r) * a.N + size_t(t) * a.S;
+        int f = a.h[q];
+        for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
+            const int2 nb = a.sp_nbr[e];
+            f += nb.y * int(sp[nb.x]);
+        }
         a.phi[size_t(row) * kOut + t] = f;
-        x[t] = __float2bfloat16(float(f) * 0.125f);
+        v = float(f) * 0.125f;
+    } else if (t == a.M) {
+        v = beta;
     }
-    x[a.M] = __float2bfloat16(float(a.betas[a.temp_of_slot[r]]));
-    for (int k = a.M + 1; k < kIn; ++k)
-        x[k] = __float2bfloat16(0.f);
+    x[t] = __float2bfloat16(v);
+    x[32 + t] = __float2bfloat16(t == 0 && a.M == 32 ? beta : 0.f);
 }
 
-__device__ __forceinline__ int column_energy(uint32_t bits, const int* phi, int M, int jt)
+// Term of slice t in E_col: -s_t phi_t - Jtau s_t s_{t+1 mod M} (the Trotter
+// term on every slice for M >= 3, on slice 0 only for M == 2, none for M == 1)
+__device__ __forceinline__ int column_term(uint32_t bits, int t, int M, int phi, int jt)
 {
-    int e = 0;
-    for (int t = 0; t < M; ++t)
-        e -= (((bits >> t) & 1u) ? 1 : -1) * phi[t];
-    if (M >= 3) {
-        for (int t = 0; t < M; ++t) {
-            const int t1 = (t + 1 == M) ? 0 : t + 1;
-            e -= jt * ((((bits >> t) ^ (bits >> t1)) & 1u) ? -1 : 1);
-        }
-    } else if (M == 2) {
-        e -= jt * ((((bits >> 0) ^ (bits >> 1)) & 1u) ? -1 : 1);
+    const int s = ((bits >> t) & 1u) ? 1 : -1;
+    int e = -s * phi;
+    if (M >= 3 || (M == 2 && t == 0)) {
+        const int t1 = (t + 1 == M) ? 0 : t + 1;
+        e -= jt * s * (((bits >> t1) & 1u) ? 1 : -1);
     }
     return e;
 }
 
-// One MH column move per row.  Words: Philox4x32-10, key (seed, r), counter
-// (q, pass, instance, 2 + 4 j) gives words 4j .. 4j+3; word t < M proposes
-// slice t, word 32 decides acceptance.  Bit t is drawn +1 iff u_t < x_t with
-// x_t = p_t 2^32 (p_t the FP32 sigmoid of the logit), so its probability is
-// exactly ceil(x_t) 2^-32; log q uses those exact probabilities in FP64, which
-// makes the Hastings ratio that of the proposal actually drawn.
-__global__ void learned_mh_kernel(const LearnedArgs a)
+// c = ceil(p 2^32) for an FP32 p in [0, 1], in integer arithmetic: with
+// p = m 2^(x - 23) (m the 24-bit significand), p 2^32 = m 2^(x + 9).
+__device__ __forceinline__ unsigned long long ceil_p32(float p)
 {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= a.rows)
-        return;
-    const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
-    const int M = a.M, S = a.S;
-    int8_t* sp = a.spins + size_t(r) * a.N;
-    uint32_t old = 0u;
-    for (int t = 0; t < M; ++t)
-        old |= (sp[t * S + q] > 0 ? 1u : 0u) << t;
-    const float* l = a.L + size_t(row) * kOut;
-    const int* phi = a.phi + size_t(row) * kOut;
-    uint32_t prop = 0u, u_acc = 0u;
-    double lq_old = 0.0, lq_new = 0.0;
-    for (int j = 0; j < 9; ++j) {
-        const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(j)), a.seed,
-                                      uint32_t(r));
-        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-        for (int k = 0; k < 4; ++k) {
-            const int t = 4 * j + k;
-            if (t < M) {
-                const float p = 1.f / (1.f + expf(-l[t]));
-                const double x = double(p) * 4294967296.0;
-                const double p1 = ceil(x) * 2.3283064365386963e-10;  // P(s'_t = +1)
-                const bool up = double(ww[k]) < x;
-                prop |= (up ? 1u : 0u) << t;
-                lq_new += up ? log(p1) : log1p(-p1);
-                lq_old += ((old >> t) & 1u) ? log(p1) : log1p(-p1);
-            } else if (t == 32) {
-                u_acc = ww[k];
+    const uint32_t b = __float_as_uint(p);
+    if ((b & 0x7FFFFFFFu) == 0u)
+        return 0ull;
+    const int ex = int((b >> 23) & 0xFFu);
+    const unsigned long long m = (b & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
+    const int sh = (ex ? ex : 1) - 127 - 23 + 32;
+    if (sh >= 0)
+        return m << sh;
+    const int k = -sh;
+    return k >= 40 ? 1ull : (m + (1ull << k) - 1ull) >> k;
+}
+
+// One MH column move per warp (lane t = slice t).  Words: Philox4x32-10, key
+// (seed, r), counter (q, pass, instance, 2 + 4 j) gives words 4j .. 4j+3; word
+// t < M proposes slice t, word 32 decides acceptance.  Bit t is drawn +1 iff
+// u_t < p_t 2^32 (p_t the FP32 sigmoid of the logit), i.e. iff u_t < c_t with
+// c_t = ceil(p_t 2^32): an event of probability exactly c_t 2^-32.  The
+// Hastings ratio q(s)/q(s') is the product over the changed bits of
+// c(old bit) / c(new bit) (c(+1) = c_t, c(-1) = 2^32 - c_t), formed in FP64
+// with exact exponents, so it is the ratio of the probabilities of the draws
+// actually made.
+__global__ void __launch_bounds__(256) learned_mh_kernel(const LearnedArgs a)
+{
+    __shared__ unsigned s_acc;
+    __shared__ unsigned long long s_c[8][32];
+    if (threadIdx.x == 0)
+        s_acc = 0u;
+    __syncthreads();
+    const int wib = threadIdx.x >> 5;
+    const int row = blockIdx.x * 8 + wib;
+    const int t = threadIdx.x & 31;
+    if (row < a.rows) {
+        const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
+        const int M = a.M, S = a.S;
+        const bool live = t < M;
+        int8_t* sp = a.spins + size_t(r) * a.N + size_t(t) * S + q;
+        const uint32_t old = __ballot_sync(0xFFFFFFFFu, live && *(live ? sp : a.spins) > 0);
+        const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(t >> 2)),
+                                      a.seed, uint32_t(r));
+        const uint32_t u = pick4(w, t & 3);
+        unsigned long long c1 = 0ull;
+        if (live)
+            c1 = ceil_p32(1.f / (1.f + expf(-a.L[size_t(row) * kOut + t])));
+        const bool up = live && (unsigned long long)u < c1;
+        const uint32_t prop = __ballot_sync(0xFFFFFFFFu, up);
+        const int phi = live ? a.phi[size_t(row) * kOut + t] : 0;
+        const int jt = a.jtau[a.pos[q]];
+        int dE = live ? column_term(prop, t, M, phi, jt) - column_term(old, t, M, phi, jt) : 0;
+        dE = __reduce_add_sync(0xFFFFFFFFu, dE);
+        // FP32 estimate of log q(s)/q(s') with a bound on its error; the FP64
+        // product below decides only when the estimate cannot
+        float term = 0.f;
+        if (live && (((old ^ prop) >> t) & 1u)) {
+            const float cp = float(c1), cm = float(4294967296ull - c1);
+            term = logf(up ? cm / cp : cp / cm);
+        }
+        float lq = term, mag = fabsf(term);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lq += __shfl_xor_sync(0xFFFFFFFFu, lq, o);
+            mag += __shfl_xor_sync(0xFFFFFFFFu, mag, o);
+        }
+        s_c[wib][t] = c1;
+        __syncwarp();
+        bool acc = false;
+        if (t == 0) {
+            const uint32_t ua = pick4(philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 34u), a.seed,
+                                                    uint32_t(r)), 0);
+            const float bdE = a.betas32[a.temp_of_slot[r]] * float(dE);
+            const float la = -bdE + lq;
+            const float lu = logf((float(ua) + 0.5f) * 2.3283064365386963e-10f);
+            // Bound on |la - logA| + |lu - log u'|: each term's ratio carries 3
+            // roundings (1.8e-7 in the log) and logf 1 ulp (1.2e-7 |term|), the
+            // shuffle sum 5 roundings (3e-7 mag); beta, the product and the sum
+            // 1.8e-7 |bdE|; lu 2.9e-6.  Below 8.7e-6 + 1.8e-7 |bdE| + 4.8e-7 mag.
+            const float eps = 1e-5f * (1.f + fabsf(bdE) + mag);
+            int decided = 1;
+            if (a.fp64_only)
+                decided = 0;
+            else if (la >= eps || lu < la - eps)
+                acc = true;
+            else if (la < -eps && lu > la + eps)
+                acc = false;
+            else
+                decided = 0;
+            if (!decided) {  // exact: the FP64 product of the integer ratios
+                double num = 1.0, den = 1.0;
+                int en = 0, ed = 0, n = 0;
+                for (uint32_t ch = old ^ prop; ch; ch &= ch - 1u) {
+                    const int b = __ffs(ch) - 1;
+                    const double cp = double(s_c[wib][b]), cm = 4294967296.0 - cp;
+                    const bool ob = (old >> b) & 1u;
+                    num *= ob ? cp : cm;
+                    den *= ob ? cm : cp;
+                    if ((++n & 15) == 0) {  // 16 factors of <= 2^32: renormalise
+                        int k;
+                        num = frexp(num, &k);
+                        en += k;
+                        den = frexp(den, &k);
+                        ed += k;
+                    }
+                }
+                const double logA = -a.betas[a.temp_of_slot[r]] * double(dE) + log(num / den) +
+                                    double(en - ed) * 0.6931471805599453;
+                acc = (logA >= 0.0) || (log((double(ua) + 0.5) * 2.3283064365386963e-10) < logA);
+                atomicAdd(a.n_exact, 1ull);
+            }
+            a.old_bits[row] = old;
+            a.prop_bits[row] = prop;
+            a.accepted[row] = acc ? 1 : 0;
+            if (acc) {
+                atomicAdd(&s_acc, 1u);
+                if (prop != old)
+                    atomicAdd(&a.E[r], dE);
             }
         }
+        acc = __shfl_sync(0xFFFFFFFFu, acc, 0);
+        if (acc && live && (((old ^ prop) >> t) & 1u))
+            *sp = up ? int8_t(1) : int8_t(-1);
     }
-    const int jt = a.jtau[a.pos[q]];
-    const int dE = column_energy(prop, phi, M, jt) - column_energy(old, phi, M, jt);
-    const double logA = -a.betas[a.temp_of_slot[r]] * double(dE) + lq_old - lq_new;
-    const bool acc = (logA >= 0.0) || (log((double(u_acc) + 0.5) * 2.3283064365386963e-10) < logA);
-    if (acc && prop != old) {
-        for (int t = 0; t < M; ++t)
-            sp[t * S + q] = ((prop >> t) & 1u) ? int8_t(1) : int8_t(-1);
-        atomicAdd(&a.E[r], dE);
-    }
-    const unsigned act = __activemask();
-    const unsigned votes = __ballot_sync(act, acc);
-    if (votes && int(threadIdx.x & 31) == __ffs(act) - 1)
-        atomicAdd(a.n_acc, (unsigned long long)__popc(votes));
-    a.old_bits[row] = old;
-    a.prop_bits[row] = prop;
-    a.accepted[row] = acc ? 1 : 0;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_acc)
+        atomicAdd(a.n_acc, (unsigned long long)s_acc);
 }
 
 // f_i = h_i + sum_j J_ij s_j for every replica (after a learned pass)
@@ -324,7 +408,7 @@ __global__ void collect_kernel(const LearnedArgs a, bf16* __restrict__ Xd, uint3
         x[t] = __float2bfloat16(float(spatial_field(a, sp, t, q)) * 0.125f);
         y |= (sp[t * a.S + q] > 0 ? 1u : 0u) << t;
     }
-    x[a.M] = __float2bfloat16(float(a.betas[a.temp_of_slot[r]]));
+    x[a.M] = __float2bfloat16(a.betas32[a.temp_of_slot[r]]);
     for (int c = a.M + 1; c < kIn; ++c)
         x[c] = __float2bfloat16(0.f);
     Yd[k] = y;
@@ -650,9 +734,25 @@ int32_t build_colours(ising_s* g)
                 sites.push_back(q);
         g->colour_off.push_back(int(sites.size()));
     }
+    std::vector<int> sp_off(1, 0);
+    std::vector<int2> sp_nbr;
+    for (int q = 0; q < S; ++q) {
+        for (int e = g->row_ptr[q]; e < g->row_ptr[q + 1]; ++e)
+            if (g->col[e] < S)
+                sp_nbr.push_back(make_int2(g->col[e], g->J[e]));
+        sp_off.push_back(int(sp_nbr.size()));
+    }
     cudaError_t e = zalloc(&g->d_colour_sites, sites.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(g->d_colour_sites, sites.data(), sites.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = zalloc(&g->d_sp_off, sp_off.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_sp_off, sp_off.data(), sp_off.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = zalloc(&g->d_sp_nbr, sp_nbr.size());
+    if (e == cudaSuccess && !sp_nbr.empty())
+        e = cudaMemcpy(g->d_sp_nbr, sp_nbr.data(), sp_nbr.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         g->colour_off.clear();
         return cuda_err(e, "colour classes");
@@ -678,6 +778,9 @@ LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
     a.E = g->d_E;
     a.temp_of_slot = g->d_temp;
     a.betas = g->d_betas;
+    a.betas32 = g->d_betas32;
+    a.sp_off = g->d_sp_off;
+    a.sp_nbr = g->d_sp_nbr;
     a.seed = g->seed;
     a.inst = g->inst;
     a.pass = uint32_t(g->learned_passes);
@@ -688,6 +791,7 @@ LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
     a.prop_bits = m->Pprop;
     a.accepted = m->Pacc;
     a.n_acc = m->n_acc;
+    a.n_exact = m->n_acc + 1;
     return a;
 }
 
@@ -742,7 +846,7 @@ int32_t ising_mlp_create(int32_t n_slices, uint32_t seed, int64_t capacity, isin
     if (e == cudaSuccess)
         e = zalloc(&m->err, 1);
     if (e == cudaSuccess)
-        e = zalloc(&m->n_acc, 1);
+        e = zalloc(&m->n_acc, 2);
     if (e != cudaSuccess) {
         free_mlp(m);
         delete m;
@@ -976,8 +1080,8 @@ int32_t ising_mlp_train(ising_mlp_t m, int32_t epochs, int32_t batch, float lr, 
     return ISING_OK;
 }
 
-int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint64_t* accepted, uint64_t* proposed,
-                           const ising_learned_trace_t* trace)
+int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, uint64_t* accepted, uint64_t* proposed,
+                           ising_learned_trace_t* trace)
 {
     if (!m || !h)
         return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
@@ -1000,7 +1104,7 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint64_t* accepted, uint64_
         return isg_fail(ISING_ERR_UNSUPPORTED, "a colour class holds more than 2^31 rows");
     LCK(cudaStreamSynchronize(m->stream));
     LCK(ensure_pass(m, maxpad));
-    LCK(cudaMemsetAsync(m->n_acc, 0, sizeof(unsigned long long), st));
+    LCK(cudaMemsetAsync(m->n_acc, 0, 2 * sizeof(unsigned long long), st));
     long long done = 0;
     for (size_t c = 0; c + 1 < h->colour_off.size(); ++c) {
         const int ncols = h->colour_off[c + 1] - h->colour_off[c];
@@ -1010,9 +1114,10 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint64_t* accepted, uint64_
         a.ncols = ncols;
         a.rows = rows;
         a.sites = h->d_colour_sites + h->colour_off[c];
-        learned_gather_kernel<<<cdiv(rows_pad, 128), 128, 0, st>>>(a, rows_pad);
+        a.fp64_only = (flags & ISING_LEARNED_FP64_ONLY) ? 1 : 0;
+        learned_gather_kernel<<<cdiv(rows_pad, 8), 256, 0, st>>>(a, rows_pad);
         LCK(forward(m, st, rows_pad, m->PX, m->PH1, m->PH2, m->PL));
-        learned_mh_kernel<<<cdiv(rows, 128), 128, 0, st>>>(a);
+        learned_mh_kernel<<<cdiv(rows, 8), 256, 0, st>>>(a);
         LCK(cudaGetLastError());
         if (trace) {
             auto d2h = [&](void* dst, const void* src, size_t bytes) {
@@ -1043,14 +1148,16 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint64_t* accepted, uint64_
         fields_rebuild_kernel<int32_t><<<int(blocks), 256, 0, st>>>(
             h->d_spins, static_cast<int32_t*>(h->d_fields), h->R, h->n, h->d_row_ptr, h->d_col, h->d_J, h->d_h);
     LCK(cudaGetLastError());
-    unsigned long long acc = 0;
-    LCK(cudaMemcpyAsync(&acc, m->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
+    unsigned long long acc[2] = {0, 0};
+    LCK(cudaMemcpyAsync(acc, m->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
     rc = check_err(m, st);
     if (rc)
         return rc;
     ++h->learned_passes;
     if (accepted)
-        *accepted = acc;
+        *accepted = acc[0];
+    if (trace)
+        trace->exact_decisions = acc[1];
     if (proposed)
         *proposed = uint64_t(total);
     return ISING_OK;

@@ -60,11 +60,13 @@ class IsingInstance(ctypes.Structure):
 class LearnedTrace(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int64), ("replica", _i32p), ("site", _i32p), ("phi", _i32p),
                 ("logits", ctypes.POINTER(ctypes.c_float)), ("old_bits", ctypes.POINTER(ctypes.c_uint32)),
-                ("prop_bits", ctypes.POINTER(ctypes.c_uint32)), ("accepted", ctypes.POINTER(ctypes.c_uint8))]
+                ("prop_bits", ctypes.POINTER(ctypes.c_uint32)), ("accepted", ctypes.POINTER(ctypes.c_uint8)),
+                ("exact_decisions", ctypes.c_uint64)]
 
 
 _f32p = ctypes.POINTER(ctypes.c_float)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
+LEARNED_FP64_ONLY = 1
 
 _SIGS = {
     "ising_last_error": ([], ctypes.c_char_p),
@@ -112,8 +114,10 @@ _SIGS = {
     "ising_mlp_n_records": ([_vp], ctypes.c_int64),
     "ising_mlp_clear_records": ([_vp], ctypes.c_int32),
     "ising_mlp_train": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _f32p], ctypes.c_int32),
-    "ising_learned_pass": ([_vp, _vp, _u64p, _u64p, ctypes.POINTER(LearnedTrace)], ctypes.c_int32),
+    "ising_learned_pass": ([_vp, _vp, ctypes.c_uint32, _u64p, _u64p, ctypes.POINTER(LearnedTrace)],
+                           ctypes.c_int32),
     "ising_mlp_destroy": ([_vp], ctypes.c_int32),
+    "ising_read_observables": ([_vp, _i64p, _i64p], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -289,6 +293,13 @@ class Ising:
 
     def swap_stats(self):
         return ising_read_swap_stats(self.h, self.R)
+
+    def observables(self):
+        """(E, m) of the replica at each temperature index, m = sum of spins."""
+        E = np.empty(self.R, dtype=np.int64)
+        m = np.empty(self.R, dtype=np.int64)
+        _check(_lib.ising_read_observables(self.h, _p(E, _i64p), _p(m, _i64p)))
+        return E, m
 
     def save(self) -> bytes:
         return ising_save(self.h)
@@ -473,7 +484,7 @@ class Mlp:
         _check(_lib.ising_mlp_train(self.m, int(epochs), int(batch), ctypes.c_float(lr), ctypes.byref(loss)))
         return float(loss.value)
 
-    def learned_pass(self, sim: "Ising", trace=False):
+    def learned_pass(self, sim: "Ising", trace=False, fp64_only=False):
         """One learned pass over ``sim``; returns (accepted, proposed[, trace dict])."""
         acc, prop = ctypes.c_uint64(), ctypes.c_uint64()
         tr = None
@@ -486,9 +497,10 @@ class Mlp:
             tr = LearnedTrace(rows, _p(t["replica"], _i32p), _p(t["site"], _i32p), _p(t["phi"], _i32p),
                               _p(t["logits"], _f32p), _p(t["old_bits"], _u32p), _p(t["prop_bits"], _u32p),
                               _p(t["accepted"], ctypes.POINTER(ctypes.c_uint8)))
-        _check(_lib.ising_learned_pass(sim.h, self.m, ctypes.byref(acc), ctypes.byref(prop),
-                                       ctypes.byref(tr) if tr is not None else None))
+        _check(_lib.ising_learned_pass(sim.h, self.m, LEARNED_FP64_ONLY if fp64_only else 0, ctypes.byref(acc),
+                                       ctypes.byref(prop), ctypes.byref(tr) if tr is not None else None))
         if trace:
+            t["exact_decisions"] = int(tr.exact_decisions)
             return int(acc.value), int(prop.value), t
         return int(acc.value), int(prop.value)
 

@@ -370,3 +370,43 @@ def test_learned_chain_samples_the_boltzmann_law(ising, model):
         assert np.all(np.abs(z) < 3.0), (bias, levels[big], z)
         net.close()
         sim.close()
+
+
+def test_observables_follow_the_temperature_labels(ising):
+    c = W.config0()
+    sim = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng="mt19937")
+    sim.run(30, 1)
+    E, m = sim.observables()
+    st = sim.read_state()
+    for r in range(sim.R):
+        k = st["temp_of_slot"][r]
+        assert E[k] == st["energy"][r]
+        assert m[k] == int(st["spins"][r].astype(np.int64).sum())
+    sim.close()
+
+
+def test_fp32_screen_gives_the_fp64_decisions(ising):
+    """Moves decided by the FP32 estimate with its error bound equal the moves
+    decided by the FP64 product alone, pass after pass (identical Philox words,
+    so any disagreement would show in the spins)."""
+    c = W.config0()
+    runs = []
+    for fp64_only in (False, True):
+        sim = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng="philox")
+        net = ising.Mlp(c["graph"].n_slices, seed=9)
+        _with_output_bias(net, 0.8)
+        exact, acc = 0, []
+        for _ in range(6):
+            sim.run(2, 1)
+            a, p, tr = net.learned_pass(sim, trace=True, fp64_only=fp64_only)
+            exact += tr["exact_decisions"]
+            acc.append(tr["accepted"].copy())
+        st = sim.read_state()
+        runs.append((st, np.concatenate(acc), exact, p))
+        net.close()
+        sim.close()
+    (s0, a0, e0, p0), (s1, a1, e1, p1) = runs
+    assert e1 == 6 * p1 and e0 < 6 * p0 // 100
+    assert np.array_equal(a0, a1)
+    for key in ("spins", "energy", "fields", "temp_of_slot"):
+        assert np.array_equal(s0[key], s1[key]), key
