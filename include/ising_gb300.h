@@ -385,8 +385,15 @@ typedef struct {
     uint32_t* old_bits;  /* [rows] column before the move (bit t: s_t=+1) */
     uint32_t* prop_bits; /* [rows] proposed column                        */
     uint8_t* accepted;   /* [rows]                                        */
-    uint64_t exact_decisions; /* out: decisions left to the FP64 product    */
 } ising_learned_trace_t;
+
+/* Counts of one learned pass. */
+typedef struct {
+    uint64_t proposed;        /* R * S                                        */
+    uint64_t accepted;        /* accepted moves (including s' == s)           */
+    uint64_t changed;         /* accepted moves with s' != s                  */
+    uint64_t exact_decisions; /* decisions left to the FP64 product           */
+} ising_learned_stats_t;
 
 #define ISING_LEARNED_FP64_ONLY 1 /* decide every move by the FP64 product */
 
@@ -404,12 +411,14 @@ typedef struct {
  * decision equals the FP64 one (flags ISING_LEARNED_FP64_ONLY forces the
  * FP64 product for every move).  `pass` counts
  * the handle's learned passes since ising_replicas_init.  Energies are updated
- * by the exact integer dE and the local fields rebuilt afterwards.  The
- * counts of accepted and proposed moves of this pass are returned (either
- * pointer may be NULL).  Requires M <= 32, the network's M, R*S >= 1.
+ * by the exact integer dE and the local fields incrementally.  `stats`
+ * (may be NULL) receives the counts of this pass.  With stats and trace both
+ * NULL the pass is only enqueued on the handle's stream (no synchronisation);
+ * a device-side error of such a pass is reported by the next call on the
+ * network that synchronises.  Requires M <= 32, the network's M, R*S >= 1.
  * Errors: INVALID_ARG, NOT_INITIALISED, CUDA (including a GEMM timeout). */
-int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, uint64_t* accepted, uint64_t* proposed,
-                           ising_learned_trace_t* trace);
+int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learned_stats_t* stats,
+                           const ising_learned_trace_t* trace);
 int32_t ising_mlp_destroy(ising_mlp_t m);
 
 /* Release all device memory of the handle (NULL is ignored). */

@@ -76,3 +76,4 @@ struct ising_s {
 
 int32_t isg_fail(int32_t code, const char* msg);
 int32_t isg_device_setup();  // once per process: kernel attributes, SM count
+int isg_num_sms();           // SMs of the current device (after isg_device_setup)

@@ -105,6 +105,8 @@ cudaError_t device_setup()
             g_init_err = mt_gen_set_smem_limit();
         if (g_init_err == cudaSuccess)
             g_init_err = tc_gemm_setup();
+        if (g_init_err == cudaSuccess)
+            g_init_err = mlp_fused_setup();
         int coop = 0;
         if (g_init_err == cudaSuccess)
             g_init_err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -731,6 +733,8 @@ int32_t isg_fused_launch(ising_t g, isg::FusedLaunch* out)
 }
 
 int32_t isg_fail(int32_t code, const char* msg) { return fail(code, msg); }
+
+int isg_num_sms() { return g_num_sms > 0 ? g_num_sms : 1; }
 
 int32_t isg_device_setup()
 {

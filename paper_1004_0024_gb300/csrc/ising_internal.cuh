@@ -229,6 +229,29 @@ struct TcGemmArgs {
 cudaError_t tc_gemm_setup();
 cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st);
 
+// The learned proposal's 3-layer network in one tcgen05 kernel (mlp_fused.cu).
+// Operands are pre-tiled in the canonical K-major core-matrix layout of the
+// shared-memory descriptors: X in tiles of 128 rows x 64 (16 KB each), W1
+// [256][64] (32 KB), W2 [256][256] as four K chunks of 32 KB, W3 [32][256] as
+// four K chunks of 4 KB.
+struct MlpFusedArgs {
+    const void* X;
+    const void *W1t, *W2t, *W3t;
+    const float *b1, *b2, *b3;  // [256], [256], [32]
+    float* L;                   // [tiles * 128][32] logits
+    int tiles;
+    int* err;
+};
+cudaError_t mlp_fused_setup();
+cudaError_t launch_mlp_fused(const MlpFusedArgs& a, int grid, cudaStream_t st);
+// byte offset of element (row, k) of a K-major tile with `rows` rows in the
+// core-matrix layout, K split into chunks of 64
+__host__ __device__ __forceinline__ size_t tiled_offset(int rows, int row, int k)
+{
+    return size_t(k >> 6) * size_t(rows) * 128 + size_t(row >> 3) * 1024 + size_t((k & 63) >> 3) * 128 +
+           size_t(row & 7) * 16 + size_t(k & 7) * 2;
+}
+
 // Everything needed to launch a handle's register-resident sweep kernel.
 struct FusedLaunch {
     SweepArgs args;

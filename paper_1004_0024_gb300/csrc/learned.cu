@@ -15,8 +15,10 @@
 // dE the exact integer change of the column energy.  Both log q terms are
 // the exact probabilities of the discrete draw actually made (FP64), so the
 // move leaves the Boltzmann law invariant whatever the network's precision.
-// Energies are updated by dE; the local fields are rebuilt from the spins
-// after the pass.
+// Energies are updated by dE; local fields incrementally: a moved column's
+// own fields are phi_t plus its new Trotter neighbours, and every flipped
+// spin moves its spatial neighbours' fields by 2 J s' (atomically: two
+// columns of a class may share a neighbour).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -159,6 +161,17 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, int rows, int cols
         dst[size_t(r) * ldd + c] = v;
 }
 
+// dst = bf16(src) for a [rows][cols] matrix in the tiled operand layout of
+// the fused network kernel (tiled_offset with `rows` rows)
+__global__ void tile_bf16_kernel(const float* __restrict__ src, int rows, int cols, unsigned char* __restrict__ dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols)
+        return;
+    const int r = i / cols, c = i % cols;
+    *reinterpret_cast<bf16*>(dst + tiled_offset(rows, r, c)) = __float2bfloat16(src[i]);
+}
+
 }  // namespace
 }  // namespace isg
 
@@ -184,7 +197,11 @@ struct LearnedArgs {
     uint8_t* accepted;
     unsigned long long* n_acc;
     unsigned long long* n_exact;  // decisions taken by the FP64 product
+    unsigned long long* n_changed;  // accepted moves with s' != s
     int fp64_only;                // decide every move by the FP64 product
+    void* fields;                 // [R][N] local fields, int16 or int32
+    int field_bits;
+    int* err;
 };
 
 // phi_t = h_i + sum over spatial neighbours j (same slice) of J s_j, i = t S + q
@@ -200,38 +217,56 @@ __device__ __forceinline__ int spatial_field(const LearnedArgs& a, const int8_t*
     return f;
 }
 
-// One warp per (replica, column) row, lane t = slice t: phi_t from the
-// spins of the column's spatial neighbours in slice t, then the input row
-// X = (phi_t/8 for t < M, beta at M, zeros) written as two coalesced halves.
+// Trotter part of the local field of slice t of a column: Jtau (s_{t-1} +
+// s_{t+1}) on the ring (M >= 3), Jtau s_{1-t} for M == 2, 0 for M == 1
+__device__ __forceinline__ int column_trotter(uint32_t bits, int t, int M, int jt)
+{
+    if (M == 1)
+        return 0;
+    const int tp = (t + 1 == M) ? 0 : t + 1;
+    const int sp = ((bits >> tp) & 1u) ? 1 : -1;
+    if (M == 2)
+        return jt * sp;
+    const int tm = (t == 0) ? M - 1 : t - 1;
+    return jt * (sp + (((bits >> tm) & 1u) ? 1 : -1));
+}
+
+// One warp per (replica, column) row, lane t = slice t: phi_t is the local
+// field of spin (t, q) less its Trotter part (the fields are exact at every
+// class: the sweep leaves them so and the learned moves update them), then
+// the input row X = (phi_t/8 for t < M, beta at M, zeros) in the tiled layout.
 __global__ void __launch_bounds__(256) learned_gather_kernel(const LearnedArgs a, int rows_pad)
 {
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int t = threadIdx.x & 31;
     if (row >= rows_pad)
         return;
-    bf16* x = a.X + size_t(row) * kIn;
+    // X in tiles of 128 rows in the fused network's operand layout
+    unsigned char* xt = reinterpret_cast<unsigned char*>(a.X) + size_t(row >> 7) * (128 * 128);
+    bf16* x0 = reinterpret_cast<bf16*>(xt + tiled_offset(128, row & 127, t));
+    bf16* x1 = reinterpret_cast<bf16*>(xt + tiled_offset(128, row & 127, 32 + t));
     if (row >= a.rows) {
-        x[t] = __float2bfloat16(0.f);
-        x[32 + t] = __float2bfloat16(0.f);
+        *x0 = __float2bfloat16(0.f);
+        *x1 = __float2bfloat16(0.f);
         return;
     }
     const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
     const float beta = a.betas32[a.temp_of_slot[r]];
+    const bool live = t < a.M;
+    const size_t i = size_t(r) * a.N + size_t(live ? t : 0) * a.S + q;
+    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, live && a.spins[i] > 0);
     float v = 0.f;
-    if (t < a.M) {
-        const int8_t* sp = a.spins + size_t(r) * a.N + size_t(t) * a.S;
-        int f = a.h[q];
-        for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
-            const int2 nb = a.sp_nbr[e];
-            f += nb.y * int(sp[nb.x]);
-        }
-        a.phi[size_t(row) * kOut + t] = f;
-        v = float(f) * 0.125f;
+    if (live) {
+        const int f = a.field_bits == 16 ? int(static_cast<const int16_t*>(a.fields)[i])
+                                         : static_cast<const int*>(a.fields)[i];
+        const int phi = f - column_trotter(bits, t, a.M, a.jtau[a.pos[q]]);
+        a.phi[size_t(row) * kOut + t] = phi;
+        v = float(phi) * 0.125f;
     } else if (t == a.M) {
         v = beta;
     }
-    x[t] = __float2bfloat16(v);
-    x[32 + t] = __float2bfloat16(t == 0 && a.M == 32 ? beta : 0.f);
+    *x0 = __float2bfloat16(v);
+    *x1 = __float2bfloat16(t == 0 && a.M == 32 ? beta : 0.f);
 }
 
 // Term of slice t in E_col: -s_t phi_t - Jtau s_t s_{t+1 mod M} (the Trotter
@@ -245,6 +280,23 @@ __device__ __forceinline__ int column_term(uint32_t bits, int t, int M, int phi,
         e -= jt * s * (((bits >> t1) & 1u) ? 1 : -1);
     }
     return e;
+}
+
+// int16 += d through a compare-and-swap on the aligned 32-bit word (the
+// retries are bounded; false if the bound was reached)
+__device__ __forceinline__ bool atomic_add_i16(int16_t* p, int d)
+{
+    unsigned* w = reinterpret_cast<unsigned*>(reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3));
+    const unsigned sh = (reinterpret_cast<uintptr_t>(p) & 2u) ? 16u : 0u;
+    unsigned cur = *reinterpret_cast<volatile unsigned*>(w);
+    for (int it = 0; it < (1 << 20); ++it) {
+        const unsigned v = ((cur >> sh) + unsigned(d)) & 0xFFFFu;
+        const unsigned prev = atomicCAS(w, cur, (cur & ~(0xFFFFu << sh)) | (v << sh));
+        if (prev == cur)
+            return true;
+        cur = prev;
+    }
+    return false;
 }
 
 // c = ceil(p 2^32) for an FP32 p in [0, 1], in integer arithmetic: with
@@ -274,10 +326,10 @@ __device__ __forceinline__ unsigned long long ceil_p32(float p)
 // actually made.
 __global__ void __launch_bounds__(256) learned_mh_kernel(const LearnedArgs a)
 {
-    __shared__ unsigned s_acc;
+    __shared__ unsigned s_acc, s_chg;
     __shared__ unsigned long long s_c[8][32];
     if (threadIdx.x == 0)
-        s_acc = 0u;
+        s_acc = s_chg = 0u;
     __syncthreads();
     const int wib = threadIdx.x >> 5;
     const int row = blockIdx.x * 8 + wib;
@@ -288,9 +340,13 @@ __global__ void __launch_bounds__(256) learned_mh_kernel(const LearnedArgs a)
         const bool live = t < M;
         int8_t* sp = a.spins + size_t(r) * a.N + size_t(t) * S + q;
         const uint32_t old = __ballot_sync(0xFFFFFFFFu, live && *(live ? sp : a.spins) > 0);
-        const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(t >> 2)),
+        // lane j < 9 draws block j (words 4j .. 4j+3); lane t takes word t
+        const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(t < 9 ? t : 0)),
                                       a.seed, uint32_t(r));
-        const uint32_t u = pick4(w, t & 3);
+        const uint32_t w0 = __shfl_sync(0xFFFFFFFFu, w.x, t >> 2), w1 = __shfl_sync(0xFFFFFFFFu, w.y, t >> 2);
+        const uint32_t w2 = __shfl_sync(0xFFFFFFFFu, w.z, t >> 2), w3 = __shfl_sync(0xFFFFFFFFu, w.w, t >> 2);
+        const uint32_t u = (t & 2) ? ((t & 1) ? w3 : w2) : ((t & 1) ? w1 : w0);
+        const uint32_t ua = __shfl_sync(0xFFFFFFFFu, w.x, 8);  // word 32
         unsigned long long c1 = 0ull;
         if (live)
             c1 = ceil_p32(1.f / (1.f + expf(-a.L[size_t(row) * kOut + t])));
@@ -317,8 +373,6 @@ __global__ void __launch_bounds__(256) learned_mh_kernel(const LearnedArgs a)
         __syncwarp();
         bool acc = false;
         if (t == 0) {
-            const uint32_t ua = pick4(philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 34u), a.seed,
-                                                    uint32_t(r)), 0);
             const float bdE = a.betas32[a.temp_of_slot[r]] * float(dE);
             const float la = -bdE + lq;
             const float lu = logf((float(ua) + 0.5f) * 2.3283064365386963e-10f);
@@ -363,34 +417,47 @@ __global__ void __launch_bounds__(256) learned_mh_kernel(const LearnedArgs a)
             a.accepted[row] = acc ? 1 : 0;
             if (acc) {
                 atomicAdd(&s_acc, 1u);
-                if (prop != old)
+                if (prop != old) {
                     atomicAdd(&a.E[r], dE);
+                    atomicAdd(&s_chg, 1u);
+                }
             }
         }
         acc = __shfl_sync(0xFFFFFFFFu, acc, 0);
-        if (acc && live && (((old ^ prop) >> t) & 1u))
-            *sp = up ? int8_t(1) : int8_t(-1);
+        if (acc && prop != old && live) {
+            // the column's own fields: phi_t plus its new Trotter neighbours;
+            // each changed spin moves its spatial neighbours' fields by 2 J s'
+            const int f = phi + column_trotter(prop, t, M, jt);
+            const size_t base = size_t(r) * a.N + size_t(t) * S;
+            const bool flip = ((old ^ prop) >> t) & 1u;
+            if (flip)
+                *sp = up ? int8_t(1) : int8_t(-1);
+            const int d = up ? 2 : -2;
+            if (a.field_bits == 16) {
+                int16_t* fl = static_cast<int16_t*>(a.fields) + base;
+                fl[q] = int16_t(f);
+                if (flip)
+                    for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
+                        const int2 nb = a.sp_nbr[e];
+                        if (!atomic_add_i16(fl + nb.x, nb.y * d))
+                            set_err(a.err, kErrTimeout);
+                    }
+            } else {
+                int* fl = static_cast<int*>(a.fields) + base;
+                fl[q] = f;
+                if (flip)
+                    for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
+                        const int2 nb = a.sp_nbr[e];
+                        atomicAdd(fl + nb.x, nb.y * d);
+                    }
+            }
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && s_acc)
+    if (threadIdx.x == 0 && s_acc) {
         atomicAdd(a.n_acc, (unsigned long long)s_acc);
-}
-
-// f_i = h_i + sum_j J_ij s_j for every replica (after a learned pass)
-template <typename FT>
-__global__ void fields_rebuild_kernel(const int8_t* __restrict__ spins, FT* __restrict__ fields, int R, int N,
-                                      const int* __restrict__ row_ptr, const int* __restrict__ col,
-                                      const int* __restrict__ J, const int* __restrict__ h)
-{
-    const long long total = (long long)R * N;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int r = int(k / N), i = int(k - (long long)r * N);
-        const int8_t* s = spins + size_t(r) * N;
-        int f = h[i];
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-            f += J[e] * int(s[col[e]]);
-        fields[k] = FT(f);
+        if (s_chg)
+            atomicAdd(a.n_changed, (unsigned long long)s_chg);
     }
 }
 
@@ -436,6 +503,7 @@ struct ising_mlp_s {
     float* grad = nullptr;  // gW1 gb1 gW2 gb2 gW3[128][256] gb3
     long long adam_t = 0;
     bf16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W2tb = nullptr, *W3tb = nullptr;
+    unsigned char *W1t = nullptr, *W2t = nullptr, *W3t = nullptr;  // tiled for the fused kernel
     // recorded columns
     bf16* Xd = nullptr;
     uint32_t* Yd = nullptr;
@@ -531,6 +599,9 @@ cudaError_t refresh_bf16(ising_mlp_s* m, cudaStream_t st)
     to_bf16_kernel<<<cdiv(kW3, 256), 256, 0, st>>>(m->W3(), kOut, kHid, m->W3b, kHid, 0);
     to_bf16_kernel<<<cdiv(kW3, 256), 256, 0, st>>>(m->W3(), kOut, kHid, m->W3tb, kIn, 1);
     to_bf16_kernel<<<cdiv(kW3, 256), 256, 0, st>>>(m->W3(), kOut, kHid, m->W3tb + kOut, kIn, 1);
+    tile_bf16_kernel<<<cdiv(kW1, 256), 256, 0, st>>>(m->W1(), kHid, kIn, m->W1t);
+    tile_bf16_kernel<<<cdiv(kW2, 256), 256, 0, st>>>(m->W2(), kHid, kHid, m->W2t);
+    tile_bf16_kernel<<<cdiv(kW3, 256), 256, 0, st>>>(m->W3(), kOut, kHid, m->W3t);
     return cudaGetLastError();
 }
 
@@ -543,6 +614,13 @@ cudaError_t forward(ising_mlp_s* m, cudaStream_t st, int rows, const bf16* X, bf
     if (e == cudaSuccess)
         e = gemm(m, st, rows, kOut, kHid, H2, kHid, m->W3b, kHid, m->b3(), nullptr, 0, 0, L, kOut, 0);
     return e;
+}
+
+// logits of `rows` (a multiple of 128) tiled input rows by the fused kernel
+cudaError_t forward_fused(ising_mlp_s* m, cudaStream_t st, int rows, const void* Xt, float* L)
+{
+    MlpFusedArgs f{Xt, m->W1t, m->W2t, m->W3t, m->b1(), m->b2(), m->b3(), L, rows / 128, m->err};
+    return launch_mlp_fused(f, isg_num_sms(), st);
 }
 
 void transpose(const bf16* src, int rows, int cols, int lds, bf16* dst, int ldd, cudaStream_t st)
@@ -678,6 +756,9 @@ void free_mlp(ising_mlp_s* m)
                   &m->PH2};
     for (auto p : b)
         zfree(*p);
+    zfree(m->W1t);
+    zfree(m->W2t);
+    zfree(m->W3t);
     zfree(m->par);
     zfree(m->mom);
     zfree(m->grad);
@@ -792,6 +873,10 @@ LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
     a.accepted = m->Pacc;
     a.n_acc = m->n_acc;
     a.n_exact = m->n_acc + 1;
+    a.fields = g->d_fields;
+    a.field_bits = g->field_bits;
+    a.err = m->err;
+    a.n_changed = m->n_acc + 2;
     return a;
 }
 
@@ -834,6 +919,12 @@ int32_t ising_mlp_create(int32_t n_slices, uint32_t seed, int64_t capacity, isin
     if (e == cudaSuccess)
         e = zalloc(&m->W3tb, size_t(kHid) * kIn);
     if (e == cudaSuccess)
+        e = zalloc(&m->W1t, size_t(kW1) * 2);
+    if (e == cudaSuccess)
+        e = zalloc(&m->W2t, size_t(kW2) * 2);
+    if (e == cudaSuccess)
+        e = zalloc(&m->W3t, size_t(kW3) * 2);
+    if (e == cudaSuccess)
         e = zalloc(&m->Xd, size_t(std::max<int64_t>(capacity, 1)) * kIn);
     if (e == cudaSuccess)
         e = zalloc(&m->Yd, size_t(std::max<int64_t>(capacity, 1)));
@@ -846,7 +937,7 @@ int32_t ising_mlp_create(int32_t n_slices, uint32_t seed, int64_t capacity, isin
     if (e == cudaSuccess)
         e = zalloc(&m->err, 1);
     if (e == cudaSuccess)
-        e = zalloc(&m->n_acc, 2);
+        e = zalloc(&m->n_acc, 3);
     if (e != cudaSuccess) {
         free_mlp(m);
         delete m;
@@ -967,9 +1058,12 @@ int32_t ising_mlp_forward(ising_mlp_t m, int32_t B, const float* X, float* L)
     LCK(cudaStreamSynchronize(st));
     LCK(ensure_pass(m, rows_pad));
     const std::vector<bf16> x = pack_inputs(X, B, m->M);
-    LCK(cudaMemsetAsync(m->PX, 0, sizeof(bf16) * size_t(rows_pad) * kIn, st));
-    LCK(cudaMemcpyAsync(m->PX, x.data(), sizeof(bf16) * x.size(), cudaMemcpyHostToDevice, st));
-    LCK(forward(m, st, rows_pad, m->PX, m->PH1, m->PH2, m->PL));
+    std::vector<unsigned char> xt(size_t(rows_pad) * kIn * 2, 0);
+    for (int b = 0; b < B; ++b)
+        for (int c = 0; c < kIn; ++c)
+            std::memcpy(xt.data() + size_t(b >> 7) * 16384 + tiled_offset(128, b & 127, c), &x[size_t(b) * kIn + c], 2);
+    LCK(cudaMemcpyAsync(m->PX, xt.data(), xt.size(), cudaMemcpyHostToDevice, st));
+    LCK(forward_fused(m, st, rows_pad, m->PX, m->PL));
     std::vector<float> l(size_t(B) * kOut);
     LCK(cudaMemcpyAsync(l.data(), m->PL, sizeof(float) * l.size(), cudaMemcpyDeviceToHost, st));
     int32_t rc = check_err(m, st);
@@ -1080,8 +1174,8 @@ int32_t ising_mlp_train(ising_mlp_t m, int32_t epochs, int32_t batch, float lr, 
     return ISING_OK;
 }
 
-int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, uint64_t* accepted, uint64_t* proposed,
-                           ising_learned_trace_t* trace)
+int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learned_stats_t* stats,
+                           const ising_learned_trace_t* trace)
 {
     if (!m || !h)
         return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
@@ -1102,9 +1196,12 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, uint64_t* a
     const long long maxpad = (maxrows + 127) / 128 * 128;
     if (maxpad > (1LL << 31) - 1)
         return isg_fail(ISING_ERR_UNSUPPORTED, "a colour class holds more than 2^31 rows");
-    LCK(cudaStreamSynchronize(m->stream));
-    LCK(ensure_pass(m, maxpad));
-    LCK(cudaMemsetAsync(m->n_acc, 0, 2 * sizeof(unsigned long long), st));
+    if (maxpad > m->Pcap) {  // growing the workspace needs the network idle
+        LCK(cudaStreamSynchronize(m->stream));
+        LCK(cudaStreamSynchronize(st));
+        LCK(ensure_pass(m, maxpad));
+    }
+    LCK(cudaMemsetAsync(m->n_acc, 0, 3 * sizeof(unsigned long long), st));
     long long done = 0;
     for (size_t c = 0; c + 1 < h->colour_off.size(); ++c) {
         const int ncols = h->colour_off[c + 1] - h->colour_off[c];
@@ -1116,7 +1213,7 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, uint64_t* a
         a.sites = h->d_colour_sites + h->colour_off[c];
         a.fp64_only = (flags & ISING_LEARNED_FP64_ONLY) ? 1 : 0;
         learned_gather_kernel<<<cdiv(rows_pad, 8), 256, 0, st>>>(a, rows_pad);
-        LCK(forward(m, st, rows_pad, m->PX, m->PH1, m->PH2, m->PL));
+        LCK(forward_fused(m, st, rows_pad, m->PX, m->PL));
         learned_mh_kernel<<<cdiv(rows, 8), 256, 0, st>>>(a);
         LCK(cudaGetLastError());
         if (trace) {
@@ -1140,26 +1237,20 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, uint64_t* a
         }
         done += rows;
     }
-    const long long blocks = std::min<long long>(cdiv(total * h->M, 256), 152LL * 16);
-    if (h->field_bits == 16)
-        fields_rebuild_kernel<int16_t><<<int(blocks), 256, 0, st>>>(
-            h->d_spins, static_cast<int16_t*>(h->d_fields), h->R, h->n, h->d_row_ptr, h->d_col, h->d_J, h->d_h);
-    else
-        fields_rebuild_kernel<int32_t><<<int(blocks), 256, 0, st>>>(
-            h->d_spins, static_cast<int32_t*>(h->d_fields), h->R, h->n, h->d_row_ptr, h->d_col, h->d_J, h->d_h);
-    LCK(cudaGetLastError());
-    unsigned long long acc[2] = {0, 0};
+    ++h->learned_passes;
+    if (!stats && !trace)
+        return ISING_OK;  // asynchronous: errors surface at the next synchronising call
+    unsigned long long acc[3] = {0, 0, 0};
     LCK(cudaMemcpyAsync(acc, m->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
     rc = check_err(m, st);
     if (rc)
         return rc;
-    ++h->learned_passes;
-    if (accepted)
-        *accepted = acc[0];
-    if (trace)
-        trace->exact_decisions = acc[1];
-    if (proposed)
-        *proposed = uint64_t(total);
+    if (stats) {
+        stats->proposed = uint64_t(total);
+        stats->accepted = acc[0];
+        stats->exact_decisions = acc[1];
+        stats->changed = acc[2];
+    }
     return ISING_OK;
 }
 

@@ -8,9 +8,9 @@ W the smallest window with W >= c tau(W), c = 5.  The effective sample size
 of n correlated samples is n / (2 tau).
 
 ``compare`` drives the CUDA library only (no sampling on the host): it runs
-both chains from the same equilibrated state, records the energy and
-magnetisation of every temperature index after each step, and times the
-steps with CUDA events on the handle's stream.
+both chains from the same state, records the energy and magnetisation of
+every temperature index after each step, and times the steps separately
+(CUDA events around steps enqueued back to back on the handle's stream).
 """
 from __future__ import annotations
 
@@ -77,31 +77,36 @@ def histogram_agreement(a: np.ndarray, b: np.ndarray, bins: int = 8) -> np.ndarr
     return np.asarray(z)
 
 
-def _timed_steps(sim, step, n_steps, observe):
-    """Run n_steps of ``step``; returns (E [n][R], m [n][R], seconds of
-    sampler time measured with CUDA events around the steps only)."""
+def _observe(sim, step, n_steps):
+    """Run n_steps of ``step``, recording (E, m) per temperature after each."""
+    Es, ms = [], []
+    for _ in range(n_steps):
+        step()
+        E, m = sim.observables()
+        Es.append(E)
+        ms.append(m)
+    return np.asarray(Es), np.asarray(ms)
+
+
+def _seconds_per_step(sim, step, n_steps):
+    """Device time per step of n_steps enqueued back to back (CUDA events on
+    the handle's stream, no synchronisation in between)."""
     import torch
 
     stream = torch.cuda.current_stream()
     sim.set_stream(stream.cuda_stream)
-    Es, ms = [], []
-    total = 0.0
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     for _ in range(n_steps):
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
         step()
-        ev1.record(stream)
-        ev1.synchronize()
-        total += ev0.elapsed_time(ev1) / 1e3
-        if observe:
-            E, m = sim.observables()
-            Es.append(E)
-            ms.append(m)
-    return (np.asarray(Es), np.asarray(ms), total)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / n_steps
 
 
-def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20):
+def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time: int = 200):
     """Plain chain (one sweep + PT per step) against the 1:1 chain (one sweep
     + PT, then one learned pass per step), both from the handle's current
     state.  Returns per-temperature ESS/s of E and m for both chains, the
@@ -111,28 +116,38 @@ def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20):
     def plain():
         sim.run(1, swap_every)
 
-    acc = [0, 0]
-
     def learned():
         sim.run(1, swap_every)
-        a, p = net.learned_pass(sim)
-        acc[0] += a
-        acc[1] += p
+        net.learned_pass(sim, sync=False)
 
     out = {}
     for name, step in (("plain", plain), ("learned", learned)):
         sim.load(blob)
-        _timed_steps(sim, step, warm, observe=False)
+        for _ in range(warm):
+            step()
+        sps = _seconds_per_step(sim, step, n_time)
+        sim.load(blob)
         t0 = time.perf_counter()
-        E, m, secs = _timed_steps(sim, step, n_steps, observe=True)
+        E, m = _observe(sim, step, n_steps)
         wall = time.perf_counter() - t0
+        secs = sps * n_steps
         R = E.shape[1]
         essE = np.array([ess(E[:, k]) for k in range(R)])
         essM = np.array([ess(m[:, k]) for k in range(R)])
-        out[name] = dict(E=E, m=m, seconds=secs, wall=wall, ess_E=essE, ess_m=essM,
+        out[name] = dict(E=E, m=m, seconds=secs, seconds_per_step=sps, wall=wall, ess_E=essE, ess_m=essM,
                          ess_E_per_s=essE / secs, ess_m_per_s=essM / secs)
+    # acceptance counts from a separate short run (the timed passes do not
+    # synchronise to report them)
+    acc = [0, 0, 0]
+    for _ in range(min(50, n_steps)):
+        sim.run(1, swap_every)
+        st = net.learned_pass(sim)
+        acc[0] += st["accepted"]
+        acc[1] += st["proposed"]
+        acc[2] += st["changed"]
     sim.load(blob)
     out["accept_rate"] = acc[0] / max(1, acc[1])
+    out["change_rate"] = acc[2] / max(1, acc[1])
     R = out["plain"]["E"].shape[1]
     z = [histogram_agreement(out["plain"][o][:, k], out["learned"][o][:, k])
          for o in ("E", "m") for k in range(R)]

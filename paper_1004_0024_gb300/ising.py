@@ -60,7 +60,11 @@ class IsingInstance(ctypes.Structure):
 class LearnedTrace(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int64), ("replica", _i32p), ("site", _i32p), ("phi", _i32p),
                 ("logits", ctypes.POINTER(ctypes.c_float)), ("old_bits", ctypes.POINTER(ctypes.c_uint32)),
-                ("prop_bits", ctypes.POINTER(ctypes.c_uint32)), ("accepted", ctypes.POINTER(ctypes.c_uint8)),
+                ("prop_bits", ctypes.POINTER(ctypes.c_uint32)), ("accepted", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class LearnedStats(ctypes.Structure):
+    _fields_ = [("proposed", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("changed", ctypes.c_uint64),
                 ("exact_decisions", ctypes.c_uint64)]
 
 
@@ -114,8 +118,8 @@ _SIGS = {
     "ising_mlp_n_records": ([_vp], ctypes.c_int64),
     "ising_mlp_clear_records": ([_vp], ctypes.c_int32),
     "ising_mlp_train": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _f32p], ctypes.c_int32),
-    "ising_learned_pass": ([_vp, _vp, ctypes.c_uint32, _u64p, _u64p, ctypes.POINTER(LearnedTrace)],
-                           ctypes.c_int32),
+    "ising_learned_pass": ([_vp, _vp, ctypes.c_uint32, ctypes.POINTER(LearnedStats),
+                            ctypes.POINTER(LearnedTrace)], ctypes.c_int32),
     "ising_mlp_destroy": ([_vp], ctypes.c_int32),
     "ising_read_observables": ([_vp, _i64p, _i64p], ctypes.c_int32),
 }
@@ -484,9 +488,15 @@ class Mlp:
         _check(_lib.ising_mlp_train(self.m, int(epochs), int(batch), ctypes.c_float(lr), ctypes.byref(loss)))
         return float(loss.value)
 
-    def learned_pass(self, sim: "Ising", trace=False, fp64_only=False):
-        """One learned pass over ``sim``; returns (accepted, proposed[, trace dict])."""
-        acc, prop = ctypes.c_uint64(), ctypes.c_uint64()
+    def learned_pass(self, sim: "Ising", trace=False, fp64_only=False, sync=True):
+        """One learned pass over ``sim``.  Returns a dict of its counts
+        (proposed, accepted, changed, exact_decisions) and, with trace=True,
+        the per-row record as a second value.  sync=False only enqueues the
+        pass and returns None."""
+        if not sync and not trace:
+            _check(_lib.ising_learned_pass(sim.h, self.m, LEARNED_FP64_ONLY if fp64_only else 0, None, None))
+            return None
+        st = LearnedStats()
         tr = None
         if trace:
             rows = sim.R * (sim.n // self.M)
@@ -497,12 +507,10 @@ class Mlp:
             tr = LearnedTrace(rows, _p(t["replica"], _i32p), _p(t["site"], _i32p), _p(t["phi"], _i32p),
                               _p(t["logits"], _f32p), _p(t["old_bits"], _u32p), _p(t["prop_bits"], _u32p),
                               _p(t["accepted"], ctypes.POINTER(ctypes.c_uint8)))
-        _check(_lib.ising_learned_pass(sim.h, self.m, LEARNED_FP64_ONLY if fp64_only else 0, ctypes.byref(acc),
-                                       ctypes.byref(prop), ctypes.byref(tr) if tr is not None else None))
-        if trace:
-            t["exact_decisions"] = int(tr.exact_decisions)
-            return int(acc.value), int(prop.value), t
-        return int(acc.value), int(prop.value)
+        _check(_lib.ising_learned_pass(sim.h, self.m, LEARNED_FP64_ONLY if fp64_only else 0, ctypes.byref(st),
+                                       ctypes.byref(tr) if tr is not None else None))
+        stats = {k: int(getattr(st, k)) for k in ("proposed", "accepted", "changed", "exact_decisions")}
+        return (stats, t) if trace else stats
 
     def close(self):
         if getattr(self, "m", None):

@@ -233,12 +233,14 @@ def test_learned_pass_replays_on_the_oracle(ising, model, rng_mode, bias):
     sim.run(12, 1)
     for pass_idx in range(2):
         before = sim.read_state()
-        acc, prop, tr = net.learned_pass(sim, trace=True)
+        stats, tr = net.learned_pass(sim, trace=True)
         after = sim.read_state()
         S = g.n // M
-        assert prop == R * S
+        assert stats["proposed"] == R * S
         assert sorted(zip(tr["replica"], tr["site"])) == [(r, q) for r in range(R) for q in range(S)]
-        assert acc == int(tr["accepted"].sum())
+        assert stats["accepted"] == int(tr["accepted"].sum())
+        moved = (tr["accepted"] > 0) & (tr["old_bits"] != tr["prop_bits"])
+        assert stats["changed"] == int(moved.sum())
         spins, E, ties = replay(g, betas, seed, 0, pass_idx, before, tr)
         assert ties <= 2
         assert np.array_equal(after["spins"], spins)
@@ -257,7 +259,7 @@ def test_colour_classes_have_no_spatial_edge(ising):
     S = g.n // 4
     sim = ising.Ising(g, W.geometric_betas(4, 0.2, 1.0), seed=1, rng="philox")
     net = ising.Mlp(4, seed=1)
-    _, _, tr = net.learned_pass(sim, trace=True)
+    _, tr = net.learned_pass(sim, trace=True)
     sites = tr["site"][tr["replica"] == 0]
     # classes are the maximal runs of replica 0's rows between other replicas' rows
     order = np.nonzero(tr["replica"] == 0)[0]
@@ -398,11 +400,11 @@ def test_fp32_screen_gives_the_fp64_decisions(ising):
         exact, acc = 0, []
         for _ in range(6):
             sim.run(2, 1)
-            a, p, tr = net.learned_pass(sim, trace=True, fp64_only=fp64_only)
-            exact += tr["exact_decisions"]
+            stats, tr = net.learned_pass(sim, trace=True, fp64_only=fp64_only)
+            exact += stats["exact_decisions"]
             acc.append(tr["accepted"].copy())
         st = sim.read_state()
-        runs.append((st, np.concatenate(acc), exact, p))
+        runs.append((st, np.concatenate(acc), exact, stats["proposed"]))
         net.close()
         sim.close()
     (s0, a0, e0, p0), (s1, a1, e1, p1) = runs
