@@ -47,6 +47,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-proposal study (ESS/s against the plain sweep)")
+    ap.add_argument("--learned-passes", type=int, default=0,
+                    help="only run N learned passes on the 32x32x32 system (a short case for profilers)")
     return ap.parse_args()
 
 
@@ -213,6 +217,8 @@ def run_ours(args):
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(c, args.rng, args.cpu_seconds)
+    if world == 1 and not args.no_learned:
+        line["learned"] = learned_study()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -334,6 +340,31 @@ def cpu_baseline(c, rng, seconds):
             "sample": f"same model and ladder, {sweeps} sweeps + PT after each ({att:.3e} attempts, {dt:.1f} s)"}
 
 
+def learned_study():
+    """ESS/s of E and m with the learned column proposal interleaved 1:1
+    with the sweep, against the plain sweep, on the same system (Philox
+    streams), plus the fused network kernel against the bf16 tensor peak."""
+    from paper_1004_0024_gb300 import ess, ising
+    from paper_1004_0024_gb300 import workloads as W
+    out = ess.study(ising, W, burn=20000, n_steps=4000, epochs=6)
+    peak = measured_peak("bf16_tflops")
+    net = out.pop("network")
+    out["network_roofline"] = {
+        "bound": "tensor", "achieved": net["tflops"], "peak": peak[0], "unit": "TFLOP/s",
+        "frac": net["tflops"] / peak[0] if net["tflops"] and peak[0] else None, "peak_source": peak[1],
+        "flop_per_column": net["flop_per_column"], "columns": net["columns"], "launches": net["launches"],
+        "kernel": "mlp_fused_kernel (33->256->256->32, bf16 operands, FP32 accumulation in TMEM)"}
+    return out
+
+
+def measured_peak(key):
+    try:
+        with open(MEASURED) as f:
+            return float(json.load(f)[key]), "measured (burst)"
+    except (OSError, KeyError, ValueError):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}[key], "fallback"
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -363,8 +394,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_passes_only(n):
+    """A short learned-pass case for profilers: 200 sweeps, one recording of
+    R*S columns, one epoch, then n learned passes."""
+    import torch
+
+    from paper_1004_0024_gb300 import ising
+    c = workload()
+    sim = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng="philox", field_bits=c["field_bits"])
+    sim.run(200, 1)
+    S = c["graph"].n // c["graph"].n_slices
+    net = ising.Mlp(c["graph"].n_slices, seed=1, capacity=c["R"] * S)
+    net.collect(sim)
+    loss = net.train(1, 4096, 1e-3)
+    stats = [net.learned_pass(sim) for _ in range(n)]
+    torch.cuda.synchronize()
+    print(json.dumps({"learned_passes": n, "loss": loss, "accepted": [s["accepted"] for s in stats]}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.learned_passes > 0:
+        learned_passes_only(args.learned_passes)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

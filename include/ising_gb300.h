@@ -419,6 +419,16 @@ typedef struct {
  * Errors: INVALID_ARG, NOT_INITIALISED, CUDA (including a GEMM timeout). */
 int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learned_stats_t* stats,
                            const ising_learned_trace_t* trace);
+/* Profiling of the fused network kernel inside learned passes: with it on,
+ * each launch is bracketed by CUDA events on the handle's stream and the
+ * totals (launches, real rows evaluated, milliseconds) accumulate. */
+typedef struct {
+    int64_t network_launches;
+    int64_t network_rows;
+    double network_ms;
+} ising_mlp_stats_t;
+int32_t ising_mlp_set_profiling(ising_mlp_t m, int32_t on);
+int32_t ising_mlp_get_stats(ising_mlp_t m, ising_mlp_stats_t* out);
 int32_t ising_mlp_destroy(ising_mlp_t m);
 
 /* Release all device memory of the handle (NULL is ignored). */

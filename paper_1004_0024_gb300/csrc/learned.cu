@@ -527,6 +527,13 @@ struct ising_mlp_s {
     uint32_t *Pold = nullptr, *Pprop = nullptr;
     uint8_t* Pacc = nullptr;
 
+    // profiling of the fused network kernel in learned passes
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<long long> ev_rows;
+    long long prof_launches = 0, prof_rows = 0;
+    double prof_ms = 0.0;
+
     float* W1() { return par; }
     float* b1() { return par + kW1; }
     float* W2() { return b1() + isg::kHid; }
@@ -749,8 +756,33 @@ cudaError_t ensure_pass(ising_mlp_s* m, long long rows_pad)
     return e;
 }
 
+// fold finished profiling events into the totals (synchronises on them)
+cudaError_t resolve_profile(ising_mlp_s* m)
+{
+    cudaError_t err = cudaSuccess;
+    for (size_t i = 0; i < m->ev_pending.size(); ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(m->ev_pending[i].second);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, m->ev_pending[i].first, m->ev_pending[i].second);
+        if (e == cudaSuccess) {
+            m->prof_ms += ms;
+            ++m->prof_launches;
+            m->prof_rows += m->ev_rows[i];
+        } else if (err == cudaSuccess) {
+            err = e;
+        }
+        cudaEventDestroy(m->ev_pending[i].first);
+        cudaEventDestroy(m->ev_pending[i].second);
+    }
+    m->ev_pending.clear();
+    m->ev_rows.clear();
+    return err;
+}
+
 void free_mlp(ising_mlp_s* m)
 {
+    resolve_profile(m);
     bf16** b[] = {&m->W1b, &m->W2b, &m->W3b, &m->W2tb, &m->W3tb, &m->Xd, &m->Xb, &m->H1, &m->H2, &m->dL,
                   &m->dH2, &m->dH1, &m->XT, &m->H1T, &m->H2T, &m->dLT, &m->dH2T, &m->dH1T, &m->PX, &m->PH1,
                   &m->PH2};
@@ -1213,7 +1245,18 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
         a.sites = h->d_colour_sites + h->colour_off[c];
         a.fp64_only = (flags & ISING_LEARNED_FP64_ONLY) ? 1 : 0;
         learned_gather_kernel<<<cdiv(rows_pad, 8), 256, 0, st>>>(a, rows_pad);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (m->profiling) {
+            LCK(cudaEventCreate(&e0));
+            LCK(cudaEventCreate(&e1));
+            LCK(cudaEventRecord(e0, st));
+        }
         LCK(forward_fused(m, st, rows_pad, m->PX, m->PL));
+        if (m->profiling) {
+            LCK(cudaEventRecord(e1, st));
+            m->ev_pending.emplace_back(e0, e1);
+            m->ev_rows.push_back(rows);
+        }
         learned_mh_kernel<<<cdiv(rows, 8), 256, 0, st>>>(a);
         LCK(cudaGetLastError());
         if (trace) {
@@ -1251,6 +1294,25 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
         stats->exact_decisions = acc[1];
         stats->changed = acc[2];
     }
+    return ISING_OK;
+}
+
+int32_t ising_mlp_set_profiling(ising_mlp_t m, int32_t on)
+{
+    if (!m)
+        return isg_fail(ISING_ERR_INVALID_ARG, "network is NULL");
+    m->profiling = on != 0;
+    return ISING_OK;
+}
+
+int32_t ising_mlp_get_stats(ising_mlp_t m, ising_mlp_stats_t* out)
+{
+    if (!m || !out)
+        return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    LCK(resolve_profile(m));
+    out->network_launches = m->prof_launches;
+    out->network_rows = m->prof_rows;
+    out->network_ms = m->prof_ms;
     return ISING_OK;
 }
 

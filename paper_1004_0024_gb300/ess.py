@@ -106,11 +106,14 @@ def _seconds_per_step(sim, step, n_steps):
     return e0.elapsed_time(e1) / 1e3 / n_steps
 
 
-def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time: int = 200):
+def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time: int = 200, ctrl=None):
     """Plain chain (one sweep + PT per step) against the 1:1 chain (one sweep
     + PT, then one learned pass per step), both from the handle's current
-    state.  Returns per-temperature ESS/s of E and m for both chains, the
-    z-scores of their histogram comparison and the learned acceptance rate."""
+    state.  With ``ctrl`` (a second handle of the same configuration and
+    another seed) a second plain chain runs from the same state with other
+    random numbers: the spread between two correct chains calibrates the
+    comparison.  Returns per-temperature series, ESS and ESS/s of E and m,
+    and the learned acceptance and change rates."""
     blob = sim.save()
 
     def plain():
@@ -120,15 +123,21 @@ def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time:
         sim.run(1, swap_every)
         net.learned_pass(sim, sync=False)
 
+    def plain_ctrl():
+        ctrl.run(1, swap_every)
+
+    chains = [("plain", sim, plain), ("learned", sim, learned)]
+    if ctrl is not None:
+        chains.append(("plain_ctrl", ctrl, plain_ctrl))
     out = {}
-    for name, step in (("plain", plain), ("learned", learned)):
-        sim.load(blob)
+    for name, h, step in chains:
+        h.load(blob)
         for _ in range(warm):
             step()
-        sps = _seconds_per_step(sim, step, n_time)
-        sim.load(blob)
+        sps = _seconds_per_step(h, step, n_time)
+        h.load(blob)
         t0 = time.perf_counter()
-        E, m = _observe(sim, step, n_steps)
+        E, m = _observe(h, step, n_steps)
         wall = time.perf_counter() - t0
         secs = sps * n_steps
         R = E.shape[1]
@@ -136,8 +145,19 @@ def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time:
         essM = np.array([ess(m[:, k]) for k in range(R)])
         out[name] = dict(E=E, m=m, seconds=secs, seconds_per_step=sps, wall=wall, ess_E=essE, ess_m=essM,
                          ess_E_per_s=essE / secs, ess_m_per_s=essM / secs)
+    # the plain chain for the device time the learned chain took: the same
+    # number of observed steps at the end (the coldest temperatures barely
+    # move under the plain sweep, so they are compared by the energy reached)
+    tail = max(1, n_steps // 5)
+    total = int(round(n_steps * out["learned"]["seconds_per_step"] / out["plain"]["seconds_per_step"]))
+    sim.load(blob)
+    if total > tail:
+        sim.run(total - tail, swap_every)
+    E, _ = _observe(sim, plain, tail)
+    out["plain_equal_time"] = {"steps": max(total, tail), "E_tail": E}
     # acceptance counts from a separate short run (the timed passes do not
     # synchronise to report them)
+    sim.load(blob)
     acc = [0, 0, 0]
     for _ in range(min(50, n_steps)):
         sim.run(1, swap_every)
@@ -148,8 +168,121 @@ def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time:
     sim.load(blob)
     out["accept_rate"] = acc[0] / max(1, acc[1])
     out["change_rate"] = acc[2] / max(1, acc[1])
-    R = out["plain"]["E"].shape[1]
-    z = [histogram_agreement(out["plain"][o][:, k], out["learned"][o][:, k])
-         for o in ("E", "m") for k in range(R)]
-    out["hist_z"] = np.concatenate([v for v in z if v.size])
+    return out
+
+
+def equilibrated(x: np.ndarray) -> bool:
+    """Both halves of the series have means within 3 standard errors and the
+    series is not constant."""
+    x = np.asarray(x, dtype=np.float64)
+    if x.min() == x.max():
+        return False
+    h = x.size // 2
+    m1, s1 = mean_and_se(x[:h])
+    m2, s2 = mean_and_se(x[h:])
+    return abs(m1 - m2) < 3.0 * max(np.hypot(s1, s2), 1e-300)
+
+
+def fast_mixing(res: dict, names, max_tau_frac: float = 1.0 / 500) -> np.ndarray:
+    """Temperatures where E and m of every named chain pass the split-half
+    check with tau_int below max_tau_frac of the run."""
+    R = res["plain"]["E"].shape[1]
+    n = res["plain"]["E"].shape[0]
+    ok = np.ones(R, dtype=bool)
+    for name in names:
+        for o in ("E", "m"):
+            x = res[name][o]
+            for k in range(R):
+                if ok[k]:
+                    ok[k] = equilibrated(x[:, k]) and tau_int(x[:, k]) < max_tau_frac * n
+    return ok
+
+
+def _hist_stats(res, a, b, temps):
+    z = [histogram_agreement(res[a][o][:, k], res[b][o][:, k]) for o in ("E", "m") for k in np.nonzero(temps)[0]]
+    z = np.concatenate(z) if z else np.zeros(0)
+    return {"bins": int(z.size), "beyond_3se": int((np.abs(z) > 3).sum()),
+            "max_abs_z": float(np.abs(z).max()) if z.size else None}
+
+
+def summarize(res: dict, betas) -> dict:
+    """JSON-ready summary of ``compare``.  ESS/s ratios (learned / plain) are
+    medians over the fast-mixing temperatures (split-half check passed, tau
+    below 1/500 of the run, for every chain); the histogram comparison is
+    made there too, for learned vs plain and, as calibration, for the second
+    plain chain vs plain.  The coldest quarter, where the plain sweep barely
+    moves on this time scale, is reported by the energies reached."""
+    P, L = res["plain"], res["learned"]
+    R = P["E"].shape[1]
+    names = ["plain", "learned"] + (["plain_ctrl"] if "plain_ctrl" in res else [])
+    fm = fast_mixing(res, names)
+    out = {"accept_rate": res["accept_rate"], "change_rate": res["change_rate"],
+           "ms_per_step": {"plain": 1e3 * P["seconds_per_step"], "learned": 1e3 * L["seconds_per_step"]},
+           "steps": int(P["E"].shape[0]), "fast_mixing_temps": int(fm.sum()),
+           "fast_mixing_betas": [float(betas[k]) for k in np.nonzero(fm)[0][[0, -1]]] if fm.any() else None}
+    for o in ("E", "m"):
+        ratio = L[f"ess_{o}_per_s"] / P[f"ess_{o}_per_s"]
+        per_step = L[f"ess_{o}"] / P[f"ess_{o}"]
+        out[o] = {"ess_per_s_ratio_median": float(np.median(ratio[fm])) if fm.any() else None,
+                  "ess_per_step_ratio_median": float(np.median(per_step[fm])) if fm.any() else None,
+                  "ess_per_s_plain_median": float(np.median(P[f"ess_{o}_per_s"][fm])) if fm.any() else None,
+                  "ess_per_s_learned_median": float(np.median(L[f"ess_{o}_per_s"][fm])) if fm.any() else None}
+    out["histograms_learned_vs_plain"] = _hist_stats(res, "learned", "plain", fm)
+    if "plain_ctrl" in res:
+        out["histograms_plain_vs_plain"] = _hist_stats(res, "plain_ctrl", "plain", fm)
+    cold = slice(3 * R // 4, R)
+    eP, eL = P["E"][:, cold], L["E"][:, cold]
+    tail = max(1, eP.shape[0] // 5)
+    out["coldest_quarter"] = {"betas": [float(betas[3 * R // 4]), float(betas[R - 1])],
+                              "mean_E_last_fifth_plain": float(eP[-tail:].mean()),
+                              "mean_E_last_fifth_learned": float(eL[-tail:].mean()),
+                              "min_E_plain": int(eP.min()), "min_E_learned": int(eL.min())}
+    if "plain_equal_time" in res:
+        et = res["plain_equal_time"]
+        out["coldest_quarter"]["plain_equal_time_steps"] = et["steps"]
+        out["coldest_quarter"]["mean_E_last_fifth_plain_equal_time"] = float(et["E_tail"][:, cold].mean())
+    return out
+
+
+def study(ising, W, burn: int, n_steps: int, epochs: int, records: int = 1 << 20, seed_net: int = 1):
+    """The learned-proposal study on the 32x32x32 system (Philox streams, so
+    that a control handle can continue the same state with other random
+    numbers): burn-in, record `records` columns (snapshots 10 sweeps apart),
+    train, compare."""
+    c = W.config1()
+    sim = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng="philox", field_bits=c["field_bits"])
+    ctrl = ising.Ising(c["graph"], c["betas"], seed=c["seed"] + 7919, rng="philox", field_bits=c["field_bits"])
+    done = 0
+    while done < burn:
+        k = min(1000, burn - done)
+        sim.run(k, 1)
+        done += k
+    S = c["graph"].n // c["graph"].n_slices
+    net = ising.Mlp(c["graph"].n_slices, seed=seed_net, capacity=records)
+    while net.n_records + c["R"] * S <= records:
+        sim.run(10, 1)
+        net.collect(sim)
+    t0 = time.perf_counter()
+    losses = [net.train(1, 4096, 1e-3) for _ in range(epochs)]
+    train_s = time.perf_counter() - t0
+    res = compare(sim, net, n_steps, ctrl=ctrl)
+    out = summarize(res, c["betas"])
+    # the fused network kernel alone, timed with CUDA events around each launch
+    net.set_profiling(True)
+    for _ in range(20):
+        net.learned_pass(sim, sync=False)
+    prof = net.stats()
+    net.set_profiling(False)
+    M = c["graph"].n_slices
+    flop = 2 * ((M + 1) * 256 + 256 * 256 + 256 * M)  # per column, 33 -> 256 -> 256 -> 32
+    out["network"] = {"launches": prof["network_launches"], "columns": prof["network_rows"],
+                      "ms": prof["network_ms"], "flop_per_column": flop,
+                      "tflops": prof["network_rows"] * flop / (prof["network_ms"] * 1e-3) / 1e12
+                      if prof["network_ms"] > 0 else None}
+    out.update({"burn_in_sweeps": burn, "records": int(net.n_records), "epochs": epochs,
+                "loss_first_last": [losses[0], losses[-1]] if losses else None, "train_seconds": train_s,
+                "rng": "philox"})
+    net.close()
+    ctrl.close()
+    sim.close()
     return out

@@ -63,6 +63,11 @@ class LearnedTrace(ctypes.Structure):
                 ("prop_bits", ctypes.POINTER(ctypes.c_uint32)), ("accepted", ctypes.POINTER(ctypes.c_uint8))]
 
 
+class MlpStats(ctypes.Structure):
+    _fields_ = [("network_launches", ctypes.c_int64), ("network_rows", ctypes.c_int64),
+                ("network_ms", ctypes.c_double)]
+
+
 class LearnedStats(ctypes.Structure):
     _fields_ = [("proposed", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("changed", ctypes.c_uint64),
                 ("exact_decisions", ctypes.c_uint64)]
@@ -121,6 +126,8 @@ _SIGS = {
     "ising_learned_pass": ([_vp, _vp, ctypes.c_uint32, ctypes.POINTER(LearnedStats),
                             ctypes.POINTER(LearnedTrace)], ctypes.c_int32),
     "ising_mlp_destroy": ([_vp], ctypes.c_int32),
+    "ising_mlp_set_profiling": ([_vp, ctypes.c_int32], ctypes.c_int32),
+    "ising_mlp_get_stats": ([_vp, ctypes.POINTER(MlpStats)], ctypes.c_int32),
     "ising_read_observables": ([_vp, _i64p, _i64p], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -511,6 +518,15 @@ class Mlp:
                                        ctypes.byref(tr) if tr is not None else None))
         stats = {k: int(getattr(st, k)) for k in ("proposed", "accepted", "changed", "exact_decisions")}
         return (stats, t) if trace else stats
+
+    def set_profiling(self, on=True):
+        _check(_lib.ising_mlp_set_profiling(self.m, int(bool(on))))
+
+    def stats(self) -> dict:
+        st = MlpStats()
+        _check(_lib.ising_mlp_get_stats(self.m, ctypes.byref(st)))
+        return {"network_launches": int(st.network_launches), "network_rows": int(st.network_rows),
+                "network_ms": float(st.network_ms)}
 
     def close(self):
         if getattr(self, "m", None):
