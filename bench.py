@@ -188,7 +188,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     line = {
-        "metric": "spin-flip attempts/s",
+        "metric": "spin-flip attempts/sec vs roofline; ESS/sec learned proposal vs plain sweep",
         "value": value,
         "unit": "attempts/s",
         "n_gpus": world,
@@ -381,7 +381,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     att = c["graph"].n * c["R"] * per * args.steps
     val = att / dt
-    line = {"impl": "reference", "metric": "spin-flip attempts/s", "value": val,
+    line = {"impl": "reference", "metric": "spin-flip attempts/sec vs roofline; ESS/sec learned proposal vs plain sweep", "value": val,
             "unit": "attempts/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
