@@ -10,6 +10,11 @@ with a parallel-tempering pass after every sweep.  Synthetic seeded inputs
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--rng mt19937|philox]
     python bench.py --impl reference     # the CPU oracle on the host cores
+    python bench.py --workload cfg3      # 4096 spins x 65536 replicas, 500 sweeps, no PT
+    python bench.py --learned-passes 3   # a short learned-proposal case for profilers
+
+The default line also carries `learned`: the ESS/s study of the learned
+Trotter-column proposal against the plain sweep on the same system.
 
 Under torchrun each rank samples its own independent instance (different
 seed): the path has no data exchange between instances, so N ranks are N
@@ -32,9 +37,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-SWEEPS_PER_STEP = 200
-SWAP_EVERY = 1
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+WORKLOAD_NAMES = {
+    "cfg1": "32x32 lattice x 32 Trotter slices (32768 spins), 256 replicas, betas 0.05-5.0 geometric, 200 sweeps + PT each",
+    "cfg3": "16x16 lattice x 16 Trotter slices (4096 spins), 65536 replicas, betas 0.1-3.0 geometric, 500 sweeps, no PT",
+}
 
 
 def parse_args():
@@ -49,18 +56,22 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposal study (ESS/s against the plain sweep)")
+    ap.add_argument("--workload", choices=["cfg1", "cfg3"], default="cfg1",
+                    help="cfg1: the headline 32768-spin x 256-replica model; cfg3: 4096 spins x 65536 replicas")
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="override the sweeps per step (short cases for profilers; 0 = the workload's)")
     ap.add_argument("--learned-passes", type=int, default=0,
                     help="only run N learned passes on the 32x32x32 system (a short case for profilers)")
     return ap.parse_args()
 
 
-def workload():
+def workload(name="cfg1"):
     from paper_1004_0024_gb300 import workloads as W
-    return W.config1()
+    return W.config1() if name == "cfg1" else W.config3()
 
 
 def attempts_per_step(c):
-    return c["graph"].n * c["R"] * SWEEPS_PER_STEP
+    return c["graph"].n * c["R"] * c["sweeps"]
 
 
 # ------------------------------------------------------------------ clocks
@@ -128,16 +139,19 @@ def run_ours(args):
     dev_index = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
 
-    c = workload()
+    c = workload(args.workload)
+    if args.sweeps > 0:
+        c = dict(c, sweeps=args.sweeps)
     g = c["graph"]
     seed = c["seed"] + 100003 * rank
     per_step = attempts_per_step(c)
+    sweeps, swap_every = c["sweeps"], c["swap_every"]
 
     sim = ising.Ising(g, c["betas"], seed=seed, rng=args.rng, field_bits=c["field_bits"],
                       stream=stream.cuda_stream)
     info = sim.info()
     for _ in range(args.warmup):
-        sim.run(SWEEPS_PER_STEP, SWAP_EVERY)
+        sim.run(sweeps, swap_every)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     sim.set_profiling(True)
@@ -156,7 +170,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
         ev[k][0].record(stream)
-        sim.run(SWEEPS_PER_STEP, SWAP_EVERY)
+        sim.run(sweeps, swap_every)
         ev[k][1].record(stream)
     barrier()
     clocks = sampler.stop()
@@ -174,13 +188,13 @@ def run_ours(args):
     value = world * per_step * args.steps / (max_ms * 1e-3)
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.workload == "cfg1":
         e2e = run_e2e(args, c, seed, stream, world)
 
     # parity spot check of the state after the timed run (invariants at full size)
     st = sim.read_state()
     sim.close()
-    assert int(st["sweeps"]) == SWEEPS_PER_STEP * (args.warmup + args.steps)
+    assert int(st["sweeps"]) == sweeps * (args.warmup + args.steps)
 
     if rank != 0:
         if world > 1:
@@ -201,8 +215,8 @@ def run_ours(args):
         "dtype": "int8 spins/int16 fields/uint32 RNG",
         "data": "synthetic (seeded layered lattice + matchings)",
         "config": {
-            "workload": "32x32 lattice x 32 Trotter slices (32768 spins), 256 replicas, betas 0.05-5.0 geometric, 200 sweeps + PT each",
-            "rng": args.rng, "field_bits": c["field_bits"], "sweeps_per_step": SWEEPS_PER_STEP,
+            "workload": WORKLOAD_NAMES[args.workload],
+            "rng": args.rng, "field_bits": c["field_bits"], "sweeps_per_step": sweeps,
             "attempts_per_step": per_step, "l2": "flushed (512 MB write) between timed steps",
             "parallelism": f"replicas-only x{world}",
             "launch": {k: info[k] for k in ("replicas_per_block", "threads_per_block", "blocks",
@@ -212,12 +226,12 @@ def run_ours(args):
         "gpu_launches": int(launches),
     }
     line["roofline"] = roofline(c, args.rng, per_step * args.steps, kernel_ms, sweep_launches, clocks,
-                                info["fast_kernel"])
+                                info["fast_kernel"], args.workload)
     if e2e is not None:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(c, args.rng, args.cpu_seconds)
-    if world == 1 and not args.no_learned:
+    if world == 1 and not args.no_learned and args.workload == "cfg1":
         line["learned"] = learned_study()
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -258,7 +272,7 @@ def run_e2e(args, c, seed, stream, world):
         hd = ising.ising_create(n, rp, col, J, h, g.n_slices)
         ising.ising_set_stream(hd, stream.cuda_stream)
         ising.ising_replicas_init(hd, R, betas, seed, args.rng, c["field_bits"])
-        ising.ising_run(hd, SWEEPS_PER_STEP, SWAP_EVERY)
+        ising.ising_run(hd, c["sweeps"], c["swap_every"])
         ising._check(lib.ising_read_state(hd, P(out_s, ising._i8p), P(out_f, ising._i32p),
                                           P(out_e, ising._i64p), P(out_t, ising._i32p),
                                           P(out_c, ising._u64p)))
@@ -303,16 +317,26 @@ def int_peak_tops(clocks):
     return 152 * 4 * 32 * mhz * 1e6 / 1e12, mhz
 
 
-def roofline(c, rng, attempts, kernel_ms, launches, clocks, kernel):
+def roofline(c, rng, attempts, kernel_ms, launches, clocks, kernel, name="cfg1"):
     g = c["graph"]
     peak, mhz = int_peak_tops(clocks)
     if kernel_ms <= 0 or launches <= 0:
         return None
+    if name == "cfg3" and rng == "mt19937":
+        # one sweep per launch (the MT19937 words of a sweep fill the word
+        # buffer): each attempt streams its word (4 B) and its replica's spin
+        # and int16 field in and out (2 x 3 B) through HBM
+        bpa = 10.0
+        hbm, src = measured_peak("hbm_gbs")
+        gbs = attempts * bpa / (kernel_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": None, "peak_basis": src, "bytes_per_attempt": bpa,
+                "kernel_ms_per_launch": kernel_ms / launches, "launches": int(launches)}
     ops = attempts * ops_per_attempt(g, rng)
     achieved = ops / (kernel_ms * 1e-3) / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "lean_kernel_cfg1_dram_traffic.json")
-    if kernel == 2 and os.path.exists(prof):
+    if kernel == 2 and name == "cfg1" and os.path.exists(prof):
         try:
             traffic = json.load(open(prof)).get(f"lean_kernel_cfg1_{rng}")
         except Exception:
@@ -327,17 +351,21 @@ def roofline(c, rng, attempts, kernel_ms, launches, clocks, kernel):
 # ------------------------------------------------------------- CPU oracle
 def cpu_baseline(c, rng, seconds):
     import oracle
+    if c["R"] > 512:  # a bounded sample: the first 512 replicas (no PT in this workload)
+        c = dict(c, R=512, betas=c["betas"][:512])
     sim = oracle.Sim(c["graph"], c["betas"], seed=c["seed"], rng=rng)
     t0 = time.perf_counter()
-    sim.run(4, 1)
+    sw = 1 if c["swap_every"] else 0
+    sim.run(4, sw)
     dt = time.perf_counter() - t0
     sweeps = max(4, int(seconds / max(dt / 4, 1e-6)))
     t0 = time.perf_counter()
-    sim.run(sweeps, 1)
+    sim.run(sweeps, sw)
     dt = time.perf_counter() - t0
     att = c["graph"].n * c["R"] * sweeps
     return {"value": att / dt, "unit": "attempts/s", "cores": sim.threads, "kind": "oracle",
-            "sample": f"same model and ladder, {sweeps} sweeps + PT after each ({att:.3e} attempts, {dt:.1f} s)"}
+            "sample": f"same model, {c['R']} replicas, {sweeps} sweeps{' + PT after each' if sw else ''} "
+                      f"({att:.3e} attempts, {dt:.1f} s)"}
 
 
 def learned_study():

@@ -107,7 +107,10 @@ int32_t ising_set_stream(ising_t h, void* cuda_stream);
  * Builds, in FP64 on the host, the flip thresholds
  * T_beta(k) = floor(2^32 exp(-2 beta k)) (flip iff k = s_i f_i <= 0 or
  * u < T_beta(k), Figure 1 with the Metropolis probability) and the swap
- * thresholds floor(2^32 exp(-(beta_{k+1}-beta_k) d)).
+ * thresholds floor(2^32 exp(-(beta_{k+1}-beta_k) d)) up to their first zero.
+ * When the swap tables would exceed 2^28 entries (a long, finely spaced
+ * ladder) they are not built: sweeps work, and every call that would run a
+ * PT pass returns UNSUPPORTED.
  * Re-initialising an initialised handle discards its replicas.
  * Errors: INVALID_ARG, FIELD_OVERFLOW, UNSUPPORTED, OOM, CUDA.
  */

@@ -37,6 +37,7 @@ struct ising_s {
     int R = 0, rng = 0, field_bits = 32, K = 1, maxpairs = 0;
     uint32_t seed = 0, inst = 0;
     std::vector<double> betas;
+    bool pt_ok = true;  // false when the FP64 swap tables would exceed 2^28 entries
     int8_t* d_spins = nullptr;
     void* d_fields = nullptr;
     int *d_E = nullptr, *d_temp = nullptr, *d_slot = nullptr, *d_err = nullptr;
@@ -77,3 +78,4 @@ struct ising_s {
 int32_t isg_fail(int32_t code, const char* msg);
 int32_t isg_device_setup();  // once per process: kernel attributes, SM count
 int isg_num_sms();           // SMs of the current device (after isg_device_setup)
+bool isg_pt_ok(const ising_s* g);

@@ -736,6 +736,8 @@ int32_t isg_fail(int32_t code, const char* msg) { return fail(code, msg); }
 
 int isg_num_sms() { return g_num_sms > 0 ? g_num_sms : 1; }
 
+bool isg_pt_ok(const ising_s* g) { return g->pt_ok; }
+
 int32_t isg_device_setup()
 {
     const cudaError_t e = device_setup();
@@ -862,6 +864,7 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
         return fail(ISING_ERR_INVALID_ARG, "R * n too large");
     g->free_replicas();
     g->learned_passes = 0;
+    g->pt_ok = true;
     g->inst = inst;
     g->R = R;
     g->rng = rng_mode;
@@ -899,9 +902,18 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
                 break;
             swthr.push_back(uint32_t(v));
             if (swthr.size() > (size_t(1) << 28))
-                return fail(ISING_ERR_UNSUPPORTED, "swap threshold tables exceed 2^28 entries");
+                break;
         }
         swlen[k] = int(d);
+        if (swthr.size() > (size_t(1) << 28)) {
+            // a long, finely spaced ladder: the FP64 tables would exceed 2^28
+            // entries; sweeps stay available, PT passes are refused
+            g->pt_ok = false;
+            swthr.assign(1, 0u);
+            std::fill(swoff.begin(), swoff.end(), 0LL);
+            std::fill(swlen.begin(), swlen.end(), 1);
+            break;
+        }
     }
     int32_t rc;
     const size_t RN = size_t(R) * g->n;
@@ -1024,7 +1036,12 @@ int32_t ising_sweep(ising_t g, int64_t n)
     return run_ops(g, n, 0, false);
 }
 
-int32_t ising_pt_swap(ising_t g) { return run_ops(g, 0, -1, false); }
+int32_t ising_pt_swap(ising_t g)
+{
+    if (g && g->inited && !g->pt_ok)
+        return fail(ISING_ERR_UNSUPPORTED, "PT swap tables exceed 2^28 entries for this ladder: sweeps only");
+    return run_ops(g, 0, -1, false);
+}
 
 int32_t ising_run(ising_t g, int64_t n, int32_t swap_every)
 {
@@ -1032,6 +1049,8 @@ int32_t ising_run(ising_t g, int64_t n, int32_t swap_every)
         return fail(ISING_ERR_INVALID_ARG, "n must be >= 0");
     if (n == 0)
         return (g && g->inited) ? ISING_OK : fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    if (g && g->inited && swap_every > 0 && swap_every <= n && !g->pt_ok)
+        return fail(ISING_ERR_UNSUPPORTED, "PT swap tables exceed 2^28 entries for this ladder: sweeps only");
     return run_ops(g, n, swap_every > 0 ? swap_every : 0, true);
 }
 

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "handle.h"
 #include "ising_gb300.h"
 #include "ising_internal.cuh"
 
@@ -69,6 +70,8 @@ extern "C" int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every)
     if (info.replicas > kNoAllocMaxReplicas)
         return isg_fail(ISING_ERR_INVALID_ARG,
                         "ising_run_noalloc supports at most 16384 replicas (static scratch size)");
+    if (swap_every > 0 && !isg_pt_ok(h))
+        return isg_fail(ISING_ERR_UNSUPPORTED, "PT swap tables exceed 2^28 entries for this ladder: sweeps only");
     isg::FusedLaunch fl;
     if ((rc = isg_fused_launch(h, &fl)))
         return rc;

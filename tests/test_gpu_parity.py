@@ -217,3 +217,27 @@ def test_not_initialised_is_reported(ising):
         ising.ising_run(h, 5, 1)
     assert ei.value.name == "NOT_INITIALISED"
     ising.ising_destroy(h)
+
+
+@pytest.mark.parametrize("rng", ["philox", "mt19937"])
+def test_config3_sampled_replicas(ising, rng):
+    """The 4096-spin x 65536-replica throughput workload: without PT every
+    replica is an independent chain, so the first 16 slots are checked
+    against an oracle run of those 16 replicas alone; the swap tables of this
+    ladder exceed 2^28 entries, so PT is refused and sweeps go on."""
+    c = W.config3()
+    dev = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=16)
+    dev.run(12, 0)
+    with pytest.raises(ising.IsingError) as e:
+        dev.pt_swap()
+    assert e.value.name == "UNSUPPORTED"
+    dev.run(8, 0)
+    st = dev.read_state()
+    ref = oracle.Sim(c["graph"], c["betas"][:16], seed=c["seed"], rng=rng)
+    ref.run(20, 0)
+    r = ref.read()
+    for key in ("spins", "fields", "energy"):
+        assert np.array_equal(st[key][:16], r[key]), key
+    assert int(st["sweeps"]) == 20
+    assert np.array_equal(st["temp_of_slot"], np.arange(c["R"]))
+    dev.close()
