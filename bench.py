@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--workload", choices=["cfg1", "cfg3", "batch"], default="cfg1",
                     help="cfg1: the headline 32768-spin x 256-replica model; cfg3: 4096 spins x 65536 replicas; "
                          "batch: 4096 ragged instances, 100 sweeps + PT per step in one CUDA graph")
+    ap.add_argument("--launch-flags", type=int, default=-1,
+                    help="ising_set_launch flags for the handle (-1: the library's choice)")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="override the sweeps per step (short cases for profilers; 0 = the workload's)")
     ap.add_argument("--learned-passes", type=int, default=0,
@@ -150,6 +152,8 @@ def run_ours(args):
 
     sim = ising.Ising(g, c["betas"], seed=seed, rng=args.rng, field_bits=c["field_bits"],
                       stream=stream.cuda_stream)
+    if args.launch_flags >= 0:
+        sim.set_launch(0, 0, args.launch_flags)
     info = sim.info()
     for _ in range(args.warmup):
         sim.run(sweeps, swap_every)

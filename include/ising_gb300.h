@@ -187,7 +187,10 @@ typedef struct {
     int32_t field_bits, rng_mode, kmax;
     int32_t fast_kernel;   /* 0 generic kernel, 1 register-resident kernel,
                               2 its lean variant (one replica per block,
-                              M in {4,8,16,32}, degree <= 6, |J| <= 63) */
+                              M in {4,8,16,32}, degree <= 6, |J| <= 63),
+                              3 the track-scheduled variant (lean's limits,
+                              one thread per track of columns; opt-in with
+                              ISING_LAUNCH_TRACK) */
 } ising_info_t;
 int32_t ising_get_info(ising_t h, ising_info_t* out);
 
@@ -195,6 +198,7 @@ int32_t ising_get_info(ising_t h, ising_info_t* out);
 #define ISING_LAUNCH_PERSISTENT 1 /* allow the persistent launch with fused PT */
 #define ISING_LAUNCH_GENERIC 2    /* force the generic (shared-memory column) kernel */
 #define ISING_LAUNCH_NO_LEAN 4    /* do not use the lean register-resident variant */
+#define ISING_LAUNCH_TRACK 8      /* use the track-scheduled variant where it applies */
 
 /* Override the launch shape: replicas per block (0 = automatic, else a power
  * of two <= 32), threads per block (0 = automatic, else a multiple of 32 and

@@ -2,13 +2,16 @@
 #include <algorithm>
 
 #include "lean_impl.cuh"
+#include "track_impl.cuh"
 
 namespace isg {
 namespace {
 
-void* pick(int field_bits, int rng, int cmax, bool lean = false, bool batch = false)
+void* pick(int field_bits, int rng, int cmax, int variant = 0, bool batch = false)
 {
-    if (lean)
+    if (variant == 2)
+        return field_bits == 16 ? track_kernel_i16(rng, batch) : track_kernel_i32(rng, batch);
+    if (variant == 1)
         return field_bits == 16 ? lean_kernel_i16(rng, cmax, batch) : lean_kernel_i32(rng, cmax, batch);
     return field_bits == 16 ? fast_kernel_i16(rng, cmax, batch) : fast_kernel_i32(rng, cmax, batch);
 }
@@ -17,9 +20,11 @@ size_t g_fast_max_dyn = 0;
 
 }  // namespace
 
-size_t fast_smem_bytes(const SweepArgs& a, int field_bits)
+size_t fast_smem_bytes(const SweepArgs& a, int field_bits, int variant, int threads)
 {
-    const size_t b = fast_detail::fast_layout(a, field_bits == 16 ? 2 : 4).total;
+    const int fb = field_bits == 16 ? 2 : 4;
+    const size_t b = variant == 2 ? track_detail::track_layout(a, fb, threads).total
+                                  : fast_detail::fast_layout(a, fb).total;
     return (g_fast_max_dyn && b > g_fast_max_dyn) ? size_t(-1) : b;
 }
 
@@ -33,11 +38,13 @@ cudaError_t fast_set_smem_limits()
         return e;
     size_t lim = size_t(optin);
     for (int batch : {0, 1})
-    for (int lean : {0, 1})
+    for (int variant : {0, 1, 2})
         for (int fb : {16, 32})
             for (int rng : {0, 1})
                 for (int cm : {1, 2, 4, 8}) {
-                    void* fn = pick(fb, rng, cm, lean != 0, batch != 0);
+                    if (variant == 2 && cm != 1)
+                        continue;
+                    void* fn = pick(fb, rng, cm, variant, batch != 0);
                     if (!fn)
                         continue;
                     cudaFuncAttributes fa;
@@ -55,16 +62,16 @@ cudaError_t fast_set_smem_limits()
 }
 
 cudaError_t fast_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
-                                   int* out, bool lean)
+                                   int* out, int variant)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pick(field_bits, rng, cmax, lean),
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pick(field_bits, rng, cmax, variant),
                                                          threads, smem);
 }
 
 cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
-                        size_t smem, bool cooperative, cudaStream_t st, bool lean)
+                        size_t smem, bool cooperative, cudaStream_t st, int variant)
 {
-    void* fn = pick(field_bits, a.rng, cmax, lean);
+    void* fn = pick(field_bits, a.rng, cmax, variant);
     if (!fn)
         return cudaErrorInvalidValue;
     SweepArgs copy = a;
@@ -75,10 +82,10 @@ cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int thread
 }
 
 cudaError_t launch_fast_batch(const SweepArgs* args, const BatchItem* items, int n_items,
-                              int field_bits, int rng, int cmax, int threads, size_t smem, bool lean,
+                              int field_bits, int rng, int cmax, int threads, size_t smem, int variant,
                               cudaStream_t st)
 {
-    void* fn = pick(field_bits, rng, cmax, lean, true);
+    void* fn = pick(field_bits, rng, cmax, variant, true);
     if (!fn)
         return cudaErrorInvalidValue;
     void* params[] = {&args, &items};

@@ -56,6 +56,12 @@ struct ising_s {
     size_t smem = 0;
     // register-resident kernel (M <= 32, tables in shared memory)
     bool use_fast = false, use_lean = false, persistent_ok = false, fast_off = false, lean_off = false;
+    bool use_track = false, track_on = false;
+    // track schedule: columns (positions) in time order, track k =
+    // track_col[track_off_v[k] .. track_off_v[k+1])
+    std::vector<int> track_off_v, track_col;
+    int ntracks = 0;
+    int *d_track_off = nullptr, *d_track_col = nullptr;
     int fast_cmax = 1;
     size_t fast_smem = 0, smem_fused = 0;
     int G_req = 0, T_req = 0, allow_persistent = 1;

@@ -191,6 +191,8 @@ void ising_s::free_all()
     dfree(d_pos);
     dfree(d_nbr);
     dfree(d_colour_sites);
+    dfree(d_track_off);
+    dfree(d_track_col);
     dfree(d_sp_off);
     dfree(d_sp_nbr);
     colour_off.clear();
@@ -329,6 +331,36 @@ int32_t extract_slices(ising_s* g)
             g->nbr.push_back((uint32_t(g->pos[e.first]) << 16) | (uint32_t(e.second) & 0xFFFFu));
         g->nbr_off[p + 1] = int(g->nbr.size());
     }
+    // tracks: positions (in lev0 order) packed greedily into sequences whose
+    // busy windows [lev0, lev0 + M) do not overlap; with equal window lengths
+    // and sorted starts the earliest-freed track is the oldest one
+    {
+        std::vector<std::vector<int>> tr;
+        std::vector<int> fifo;  // track indices in the order they free up
+        size_t head = 0;
+        std::vector<int> free_at;
+        for (int p = 0; p < S; ++p) {
+            const int start = g->lev0p[p];
+            int k;
+            if (head < fifo.size() && free_at[fifo[head]] <= start) {
+                k = fifo[head++];
+            } else {
+                k = int(tr.size());
+                tr.emplace_back();
+                free_at.push_back(0);
+            }
+            tr[k].push_back(p);
+            free_at[k] = start + M;
+            fifo.push_back(k);
+        }
+        g->ntracks = int(tr.size());
+        g->track_off_v.assign(1, 0);
+        g->track_col.clear();
+        for (auto& t : tr) {
+            g->track_col.insert(g->track_col.end(), t.begin(), t.end());
+            g->track_off_v.push_back(int(g->track_col.size()));
+        }
+    }
     return ISING_OK;
 }
 
@@ -337,10 +369,23 @@ SweepArgs base_args(ising_s* g);
 
 // The register-resident kernel keeps up to 8 columns per thread; it needs
 // M <= 32, the slice tables in shared memory and spatial degree <= 255.
+int kernel_variant(const ising_s* g) { return g->use_track ? 2 : (g->use_lean ? 1 : 0); }
+
+// The track kernel (opt-in, ISING_LAUNCH_TRACK) and its limits (lean's, with
+// one thread per track): power-of-two M in 4..32, spatial degree <= 6,
+// |J| <= 63, at most 512 tracks, and the block size left to the library.
+bool track_eligible(const ising_s* g)
+{
+    return (g->M == 4 || g->M == 8 || g->M == 16 || g->M == 32) && g->max_sp_deg <= 6 &&
+           g->max_sp_J <= 63 && g->ntracks >= 1 && ((g->ntracks + 31) / 32) * 32 <= 512 && g->T_req <= 0 &&
+           g->track_on && !g->lean_off && !g->fast_off;
+}
+
 void choose_fast(ising_s* g)
 {
     g->use_fast = false;
     g->use_lean = false;
+    g->use_track = false;
     g->persistent_ok = false;
     if (g->M > 32 || !g->tables_smem || g->max_sp_deg > 255 || g->fast_off)
         return;
@@ -358,20 +403,35 @@ void choose_fast(ising_s* g)
     g->use_lean = g->G == 1 && (g->M == 4 || g->M == 8 || g->M == 16 || g->M == 32) &&
                   g->max_sp_deg <= 6 && g->max_sp_J <= 63 && cmax <= 4 &&
                   g->T <= (cmax <= 1 ? 1024 : (cmax == 2 ? 512 : 256)) && !g->lean_off;
+    // track variant: the lean kernel's limits with the columns walked as
+    // tracks, one thread per track (when the block size is left automatic)
+    const int T_track = ((g->ntracks + 31) / 32) * 32;
+    if (g->G == 1 && track_eligible(g)) {
+        SweepArgs t = base_args(g);
+        t.G = 1;
+        const size_t sm = fast_smem_bytes(t, g->field_bits, 2, T_track);
+        if (sm != size_t(-1)) {  // the fused (PT) layout is checked below with persistence
+            g->use_track = true;
+            g->use_lean = false;
+            g->T = T_track;
+            cmax = 1;
+        }
+    }
+    const int variant = g->use_track ? 2 : (g->use_lean ? 1 : 0);
     SweepArgs a = base_args(g);
-    const size_t smem = fast_smem_bytes(a, g->field_bits);
+    const size_t smem = fast_smem_bytes(a, g->field_bits, variant, g->T);
     if (smem == size_t(-1))
         return;
     g->use_fast = true;
     g->fast_cmax = cmax;
     g->fast_smem = smem;
     a.swap_every = 1;
-    g->smem_fused = fast_smem_bytes(a, g->field_bits);
+    g->smem_fused = fast_smem_bytes(a, g->field_bits, variant, g->T);
     if (!g_coop || !g->allow_persistent || g->smem_fused == size_t(-1) || g->R > 16384)
         return;
     int per_sm = 0;
-    if (fast_max_blocks_per_sm(g->field_bits, cmax, g->rng, g->T, g->smem_fused, &per_sm,
-                               g->use_lean) != cudaSuccess)
+    if (fast_max_blocks_per_sm(g->field_bits, cmax, g->rng, g->T, g->smem_fused, &per_sm, variant) !=
+        cudaSuccess)
         return;
     g->persistent_ok = (long long)per_sm * g_num_sms >= g->blocks;
 }
@@ -425,6 +485,9 @@ SweepArgs base_args(ising_s* g)
     a.maxpairs = g->maxpairs;
     a.E_pub = g->d_Epub;
     a.gridbar = g->d_gridbar;
+    a.track_off = g->d_track_off;
+    a.track_col = g->d_track_col;
+    a.ntracks = g->ntracks;
     return a;
 }
 
@@ -436,6 +499,8 @@ int32_t choose_launch(ising_s* g)
     std::vector<int> Gs;
     if (g->G_req > 0) {
         Gs.push_back(g->G_req);
+    } else if (track_eligible(g)) {
+        Gs.push_back(1);  // the track kernel runs one replica per block
     } else {
         for (int G : {8, 4, 2, 1})
             if ((long long)((g->R + G - 1) / G) >= 2LL * sms || G == 1)
@@ -652,7 +717,7 @@ int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
             const SweepArgs a = sweep_args(g, op);
             if (g->use_fast)
                 e = launch_fast(a, g->field_bits, g->fast_cmax, g->T, g->blocks, g->fast_smem, false, st,
-                                g->use_lean);
+                                kernel_variant(g));
             else
                 e = launch_sweep(a, g->field_bits, g->cmax, g->T, g->blocks, g->smem, st);
         } else if (op.kind == Op::FUSED) {
@@ -660,7 +725,7 @@ int32_t enqueue(ising_s* g, const std::vector<Op>& ops, cudaStream_t st)
             e = cudaMemsetAsync(g->d_gridbar, 0, sizeof(unsigned), st);
             if (e == cudaSuccess)
                 e = launch_fast(a, g->field_bits, g->fast_cmax, g->T, g->blocks, g->smem_fused, true, st,
-                                g->use_lean);
+                                kernel_variant(g));
         } else {
             e = launch_pt(pt_args(g, op), st);
         }
@@ -725,7 +790,7 @@ int32_t isg_fused_launch(ising_t g, isg::FusedLaunch* out)
     out->blocks = g->blocks;
     out->smem_plain = g->fast_smem;
     out->smem_fused = g->smem_fused;
-    out->lean = g->use_lean;
+    out->variant = kernel_variant(g);
     out->stream = g->stream;
     out->R = g->R;
     out->rng = g->rng;
@@ -813,7 +878,8 @@ int32_t ising_create(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
         (rc = upload(&g->d_J, g->J)) || (rc = upload(&g->d_h, g->h)) ||
         (rc = upload(&g->d_nbr_off, g->nbr_off)) || (rc = upload(&g->d_nbr, g->nbr)) ||
         (rc = upload(&g->d_jtau, g->jtau)) || (rc = upload(&g->d_lev0, g->lev0p)) ||
-        (rc = upload(&g->d_site, g->site)) || (rc = upload(&g->d_pos, g->pos))) {
+        (rc = upload(&g->d_site, g->site)) || (rc = upload(&g->d_pos, g->pos)) ||
+        (rc = upload(&g->d_track_off, g->track_off_v)) || (rc = upload(&g->d_track_col, g->track_col))) {
         g->free_all();
         delete g;
         return rc;
@@ -1221,7 +1287,7 @@ int32_t ising_get_info(ising_t g, ising_info_t* o)
     o->blocks = g->blocks;
     o->smem_bytes = int(g->smem);
     o->persistent_ok = g->persistent_ok ? 1 : 0;
-    o->fast_kernel = g->use_fast ? (g->use_lean ? 2 : 1) : 0;
+    o->fast_kernel = g->use_fast ? (g->use_track ? 3 : (g->use_lean ? 2 : 1)) : 0;
     o->field_bits = g->field_bits;
     o->rng_mode = g->rng;
     o->kmax = int(std::min<long long>(g->kmax, INT32_MAX));
@@ -1241,6 +1307,7 @@ int32_t ising_set_launch(ising_t g, int32_t replicas_per_block, int32_t threads_
     g->allow_persistent = (launch_flags & ISING_LAUNCH_PERSISTENT) ? 1 : 0;
     g->fast_off = (launch_flags & ISING_LAUNCH_GENERIC) != 0;
     g->lean_off = (launch_flags & ISING_LAUNCH_NO_LEAN) != 0;
+    g->track_on = (launch_flags & ISING_LAUNCH_TRACK) != 0;
     g->drop_graphs();
     if (g->inited)
         return choose_launch(g);
@@ -1389,7 +1456,7 @@ GroupKey key_of(ising_batch_s* b, int i)
     ising_s* g = b->inst[i];
     GroupKey k{};
     k.kind = b->resident[i] ? 0 : (g->use_fast ? 1 : 2);
-    k.lean = g->use_lean ? 1 : 0;
+    k.lean = kernel_variant(g);
     k.field_bits = g->field_bits;
     k.rng = g->rng;
     k.cmax = g->use_fast ? g->fast_cmax : g->cmax;
@@ -1552,7 +1619,7 @@ int32_t batch_record(ising_batch_s* b, long long n, int swap_every, ising_batch_
                 e = launch_fast_batch(static_cast<const SweepArgs*>(bo.args), bo.items, bo.n_items,
                                       k.field_bits, k.rng, k.cmax, k.T,
                                       bo.op.kind == Op::FUSED ? gr.smem_fused : gr.smem_plain,
-                                      k.lean != 0, st);
+                                      k.lean, st);
             if (e != cudaSuccess)
                 break;
         }
@@ -1720,7 +1787,7 @@ double tune_cost(ising_s* t, const TuneCand& c, bool* ok)
         return 0.0;
     int per_sm = 0;
     if (fast_max_blocks_per_sm(t->field_bits, t->fast_cmax, t->rng, t->T,
-                               res ? t->smem_fused : t->fast_smem, &per_sm, t->use_lean) != cudaSuccess ||
+                               res ? t->smem_fused : t->fast_smem, &per_sm, kernel_variant(t)) != cudaSuccess ||
         per_sm < 1)
         return 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

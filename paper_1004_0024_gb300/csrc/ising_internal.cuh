@@ -70,6 +70,11 @@ struct SweepArgs {
     unsigned int* gridbar;         // grid barrier arrivals (zeroed before the launch)
     int lg_G;                      // log2(G)
     int inst_blocks;               // blocks of this instance (batched launches)
+    // track schedule (track kernel): columns track_col[track_off[k] ..
+    // track_off[k+1]) in time order form track k
+    const int* track_off;
+    const int* track_col;
+    int ntracks;
 };
 
 // One block of a batched launch: instance index and block index within it.
@@ -257,7 +262,7 @@ struct FusedLaunch {
     SweepArgs args;
     int field_bits, cmax, threads, blocks, R, rng;
     size_t smem_plain, smem_fused;
-    bool lean;
+    int variant;  // 0 fast, 1 lean, 2 track
     cudaStream_t stream;
 };
 
@@ -272,21 +277,23 @@ cudaError_t sweep_max_blocks_per_sm(int field_bits, int cmax, int rng, int threa
                                     int* out);
 cudaError_t launch_pt(const PtArgs& a, cudaStream_t st);
 // register-resident sweep for M <= 32 with tables in shared memory
-size_t fast_smem_bytes(const SweepArgs& a, int field_bits);
+// variant: 0 the register-resident kernel (fast_impl.cuh), 1 its lean
+// one-replica form (lean_impl.cuh: G = 1, M in {4,8,16,32}, spatial degree
+// <= 6, |J| <= 63, at most 4 columns per thread), 2 the track-scheduled form
+// (track_impl.cuh: lean's limits, one thread per track, cmax unused)
+size_t fast_smem_bytes(const SweepArgs& a, int field_bits, int variant = 0, int threads = 0);
 cudaError_t fast_set_smem_limits();
 // Batched launches: block b runs item items[b] with args[items[b].inst].
 cudaError_t launch_fast_batch(const SweepArgs* args, const BatchItem* items, int n_items,
-                              int field_bits, int rng, int cmax, int threads, size_t smem, bool lean,
+                              int field_bits, int rng, int cmax, int threads, size_t smem, int variant,
                               cudaStream_t st);
 cudaError_t launch_pt_batch(const PtArgs* args, int n_inst, int max_R, cudaStream_t st);
 cudaError_t launch_mt_gen_batch(const MtGenArgs* args, const BatchItem* items, int n_items,
                                 int max_S, cudaStream_t st);
-// lean = true selects the lean variant (lean_impl.cuh): G = 1, M in {4,8,16,32},
-// spatial degree <= 6, |J| <= 63, at most 4 columns per thread
 cudaError_t fast_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
-                                   int* out, bool lean);
+                                   int* out, int variant = 0);
 cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
-                        size_t smem, bool cooperative, cudaStream_t st, bool lean);
+                        size_t smem, bool cooperative, cudaStream_t st, int variant = 0);
 cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st);
 cudaError_t mt_gen_set_smem_limit();
 cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst,

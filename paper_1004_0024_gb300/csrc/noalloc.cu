@@ -110,7 +110,7 @@ extern "C" int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every)
             a.nsweeps = int(m);
             a.swap_every = fused ? int(every) : 0;
             e = isg::launch_fast(a, fl.field_bits, fl.cmax, fl.threads, fl.blocks,
-                                 fused ? fl.smem_fused : fl.smem_plain, fused, st, fl.lean);
+                                 fused ? fl.smem_fused : fl.smem_plain, fused, st, fl.variant);
         }
         if (e != cudaSuccess)
             return isg_fail(e == cudaErrorCooperativeLaunchTooLarge ? ISING_ERR_UNSUPPORTED : ISING_ERR_CUDA,

@@ -242,6 +242,7 @@ def ising_get_info(h) -> dict:
 LAUNCH_PERSISTENT = 1
 LAUNCH_GENERIC = 2
 LAUNCH_NO_LEAN = 4
+LAUNCH_TRACK = 8
 
 
 def ising_set_launch(h, replicas_per_block=0, threads_per_block=0, launch_flags=LAUNCH_PERSISTENT):

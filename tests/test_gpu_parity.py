@@ -134,13 +134,13 @@ def test_launch_shapes_give_identical_results(ising, G, T, flags):
 
 @pytest.mark.parametrize("rng", ["mt19937", "philox"])
 def test_config1_paths_agree(ising, rng):
-    """cfg1 through every kernel (lean, register-resident, generic), persistent
-    with fused PT (the bench path) or per-sweep launches: identical to the
-    oracle after 12 sweeps."""
+    """cfg1 through every kernel (track, lean, register-resident, generic),
+    persistent with fused PT (the bench path) or per-sweep launches:
+    identical to the oracle after 12 sweeps."""
     c = W.config1()
     ref = oracle.Sim(c["graph"], c["betas"], seed=c["seed"], rng=rng)
     ref.run(12, 1)
-    for flags, kernel in ((1, 2), (0, 2), (5, 1), (4, 1), (2, 0)):
+    for flags, kernel in ((9, 3), (8, 3), (1, 2), (0, 2), (5, 1), (4, 1), (2, 0)):
         dev = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=16)
         dev.set_launch(0, 0, flags)
         info = dev.info()
@@ -241,3 +241,24 @@ def test_config3_sampled_replicas(ising, rng):
     assert int(st["sweeps"]) == 20
     assert np.array_equal(st["temp_of_slot"], np.arange(c["R"]))
     dev.close()
+
+
+
+@pytest.mark.parametrize("L,M,R,rng,fb", [(8, 16, 32, "mt19937", 32), (6, 8, 9, "philox", 16), (5, 4, 6, "mt19937", 16),
+                                          (7, 32, 5, "philox", 32), (3, 4, 2, "philox", 16)])
+def test_track_kernel_matches_lean_and_oracle(ising, L, M, R, rng, fb):
+    """The track-scheduled kernel (opt-in) against the oracle on several slice
+    counts, replica counts and field widths, persistent (fused PT) and per
+    sweep."""
+    g = W.layered_graph(L, M, L + M)
+    betas = W.geometric_betas(R, 0.2, 2.5)
+    for flags in (9, 8):
+        ref = oracle.Sim(g, betas, seed=77, rng=rng)
+        dev = ising.Ising(g, betas, seed=77, rng=rng, field_bits=fb)
+        dev.set_launch(0, 0, flags)
+        assert dev.info()["fast_kernel"] == 3
+        for n, every in ((9, 2), (5, 1), (4, 0)):
+            dev.run(n, every)
+            ref.run(n, every)
+            assert_same(dev, ref, f"flags {flags} after ({n}, {every})")
+        dev.close()
