@@ -11,6 +11,7 @@ with a parallel-tempering pass after every sweep.  Synthetic seeded inputs
     python bench.py [--gpus N] [--steps K] [--warmup W] [--rng mt19937|philox]
     python bench.py --impl reference     # the CPU oracle on the host cores
     python bench.py --workload cfg3      # 4096 spins x 65536 replicas, 500 sweeps, no PT
+    python bench.py --workload paper     # the paper's 96 x 256-layer x 115-model shape, 30000 sweeps
     python bench.py --learned-passes 3   # a short learned-proposal case for profilers
 
 The default line also carries `learned`: the ESS/s study of the learned
@@ -41,7 +42,13 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 WORKLOAD_NAMES = {
     "cfg1": "32x32 lattice x 32 Trotter slices (32768 spins), 256 replicas, betas 0.05-5.0 geometric, 200 sweeps + PT each",
     "cfg3": "16x16 lattice x 16 Trotter slices (4096 spins), 65536 replicas, betas 0.1-3.0 geometric, 500 sweeps, no PT",
+    "paper": "the paper's shape: 256 Trotter layers x 96 spins (8x12 lattice, 24576 spins), 115 models at betas "
+             "0.1-3.0 geometric, 30000 sweeps, no PT",
 }
+# The paper's figures for its own workload shape (30000 sweeps x 115 models x
+# 24576 spins), derived from section 4 / Figure 13: other hardware, context only
+PAPER_GTX285_ATTEMPTS = 4.3e8   # B.2, coalesced CUDA on a GTX-285
+PAPER_I7_ATTEMPTS = 8.8e8       # A.4, SSE assembly, 8 threads on a Core i7-965
 
 
 def parse_args():
@@ -56,9 +63,10 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposal study (ESS/s against the plain sweep)")
-    ap.add_argument("--workload", choices=["cfg1", "cfg3", "batch"], default="cfg1",
+    ap.add_argument("--workload", choices=["cfg1", "cfg3", "batch", "paper"], default="cfg1",
                     help="cfg1: the headline 32768-spin x 256-replica model; cfg3: 4096 spins x 65536 replicas; "
-                         "batch: 4096 ragged instances, 100 sweeps + PT per step in one CUDA graph")
+                         "batch: 4096 ragged instances, 100 sweeps + PT per step in one CUDA graph; "
+                         "paper: the paper's 96 x 256-layer x 115-model shape")
     ap.add_argument("--launch-flags", type=int, default=-1,
                     help="ising_set_launch flags for the handle (-1: the library's choice)")
     ap.add_argument("--sweeps", type=int, default=0,
@@ -70,7 +78,7 @@ def parse_args():
 
 def workload(name="cfg1"):
     from paper_1004_0024_gb300 import workloads as W
-    return W.config1() if name == "cfg1" else W.config3()
+    return {"cfg1": W.config1, "cfg3": W.config3, "paper": W.config_paper}[name]()
 
 
 def attempts_per_step(c):
@@ -234,6 +242,12 @@ def run_ours(args):
                                 info["fast_kernel"], args.workload)
     if e2e is not None:
         line["e2e"] = e2e
+    if args.workload == "paper" and c["sweeps"] == 30000:
+        line["vs_baseline"] = value / PAPER_GTX285_ATTEMPTS
+        line["paper_context"] = {"gtx285_b2_attempts_per_s": PAPER_GTX285_ATTEMPTS,
+                                 "i7_965_8threads_a4_attempts_per_s": PAPER_I7_ATTEMPTS,
+                                 "vs_i7": value / PAPER_I7_ATTEMPTS,
+                                 "basis": "derived from the paper's section 4 and Figure 13 (other hardware)"}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(c, args.rng, args.cpu_seconds)
     if world == 1 and not args.no_learned and args.workload == "cfg1":

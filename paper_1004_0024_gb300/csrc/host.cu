@@ -519,7 +519,10 @@ int32_t choose_launch(ising_s* g)
                 continue;
             int T = g->T_req;
             if (T <= 0) {
-                const long long want = ((long long)g->S * G + 3) / 4;
+                // four columns per thread for the register-resident kernels (M <= 32);
+                // one per thread for the generic kernel, whose per-level loop over a
+                // thread's columns is serial (the paper-shaped 96 x 256 model: 2.2x)
+                const long long want = g->M > 32 ? (long long)g->S * G : ((long long)g->S * G + 3) / 4;
                 T = int(std::min<long long>(1024, std::max<long long>(32, ((want + 31) / 32) * 32)));
             }
             if (T % 32 != 0 || T > 1024 || T % G != 0)

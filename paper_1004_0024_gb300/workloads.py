@@ -53,23 +53,24 @@ def _csr(n: int, rows: list[list[tuple[int, int]]], h: np.ndarray, n_slices: int
     return Graph(n, row_ptr, col, J, np.asarray(h, dtype=np.int32), n_slices, meta or {})
 
 
-def spatial_model(L: int, graph_seed: int):
-    """One slice: periodic L x L lattice plus two partial matchings.
+def spatial_model(L: int, graph_seed: int, Ly: int | None = None):
+    """One slice: periodic L x L (or L x Ly) lattice plus two partial matchings.
 
     Returns (neighbour sets, J dict keyed by (min, max), h per site).  Draw
     order: matching A, matching B, then J per spatial edge in lexicographic
     (min, max) order from {-3,-2,-1,1,2,3}, then h per site from {-2..2}.
     """
-    if L < 3:
-        raise ValueError("L must be >= 3 so that the 4 lattice neighbours are distinct")
+    Ly = L if Ly is None else Ly
+    if L < 3 or Ly < 3:
+        raise ValueError("the lattice sides must be >= 3 so that the 4 lattice neighbours are distinct")
     rng = np.random.default_rng(graph_seed)
-    S = L * L
+    S = L * Ly
 
     def site(x, y):
-        return (y % L) * L + (x % L)
+        return (y % Ly) * L + (x % L)
 
     adj = [set() for _ in range(S)]
-    for y in range(L):
+    for y in range(Ly):
         for x in range(L):
             a = site(x, y)
             for b in (site(x + 1, y), site(x, y + 1)):
@@ -94,10 +95,10 @@ def spatial_model(L: int, graph_seed: int):
     return adj, Jd, h
 
 
-def layered_graph(L: int, M: int, graph_seed: int, j_tau: int = 4) -> Graph:
-    """M identical copies of ``spatial_model(L)`` coupled in a Trotter ring."""
-    adj, Jd, hs = spatial_model(L, graph_seed)
-    S = L * L
+def layered_graph(L: int, M: int, graph_seed: int, j_tau: int = 4, Ly: int | None = None) -> Graph:
+    """M identical copies of ``spatial_model(L, Ly)`` coupled in a Trotter ring."""
+    adj, Jd, hs = spatial_model(L, graph_seed, Ly)
+    S = L * (L if Ly is None else Ly)
     n = S * M
     # one slice's row template: per site, spatial entries (ascending target)
     # then the Trotter entries; kind 0 = spatial, 1 = slice t-1, 2 = slice t+1,
@@ -122,7 +123,8 @@ def layered_graph(L: int, M: int, graph_seed: int, j_tau: int = 4) -> Graph:
     row_ptr = np.zeros(n + 1, dtype=np.int32)
     row_ptr[1:] = np.cumsum(np.tile(deg, M))
     h = np.tile(hs, M).astype(np.int32)
-    return Graph(n, row_ptr, col, J, h, M, dict(L=L, M=M, graph_seed=graph_seed, j_tau=j_tau))
+    return Graph(n, row_ptr, col, J, h, M, dict(L=L, Ly=L if Ly is None else Ly, M=M, graph_seed=graph_seed,
+                                                 j_tau=j_tau))
 
 
 def random_graph(n: int, n_edges: int, seed: int, jmax: int = 3, hmax: int = 2) -> Graph:
@@ -183,6 +185,17 @@ def config3(R: int = 65536):
     """16x16 lattice x M=16 (4096 spins), 65536 replicas, betas 0.1..3.0, int16 fields."""
     return dict(name=f"cfg3_L16_M16_R{R}", graph=layered_graph(16, 16, 1), R=R,
                 betas=geometric_betas(R, 0.1, 3.0), seed=5489, field_bits=16, sweeps=500,
+                swap_every=0)
+
+
+def config_paper():
+    """The paper's workload shape (section 4): 256 Trotter layers of 96 spins
+    (an 8 x 12 lattice plus matchings; 24576 spins, degree 6-8), 115 models
+    (replicas) at geometric betas 0.1..3.0, 30000 sweeps, no PT in the timing.
+    The paper's 115 QMC models are not available; this synthetic model of the
+    same shape stands in for them."""
+    return dict(name="paper_96x256_R115", graph=layered_graph(8, 256, 1, Ly=12), R=115,
+                betas=geometric_betas(115, 0.1, 3.0), seed=5489, field_bits=16, sweeps=30000,
                 swap_every=0)
 
 

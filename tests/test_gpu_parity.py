@@ -262,3 +262,22 @@ def test_track_kernel_matches_lean_and_oracle(ising, L, M, R, rng, fb):
             ref.run(n, every)
             assert_same(dev, ref, f"flags {flags} after ({n}, {every})")
         dev.close()
+
+
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_paper_shape_sampled_replicas(ising, rng):
+    """The paper's workload shape (96-spin layers, 256 Trotter slices: the
+    generic kernel, M > 32), 115 replicas without PT: the first 6 slots
+    against an oracle run of those replicas alone."""
+    c = W.config_paper()
+    dev = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=16)
+    assert dev.info()["fast_kernel"] == 0
+    dev.run(3, 0)
+    dev.run(2, 0)
+    st = dev.read_state()
+    ref = oracle.Sim(c["graph"], c["betas"][:6], seed=c["seed"], rng=rng)
+    ref.run(5, 0)
+    r = ref.read()
+    for key in ("spins", "fields", "energy"):
+        assert np.array_equal(st[key][:6], r[key]), key
+    dev.close()
