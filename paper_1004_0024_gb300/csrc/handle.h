@@ -52,7 +52,7 @@ struct ising_s {
     long long wbuf_cap = 0, swbuf_cap = 0;  // sweeps / passes
     long long word_budget = 1LL << 30;     // bytes of pre-generated MT19937 words
     // launch configuration
-    int G = 1, T = 32, cmax = 1, blocks = 1, tables_smem = 1, thr_smem = 1;
+    int G = 1, T = 32, cmax = 1, blocks = 1, tables_smem = 1, thr_smem = 1, stage_words = 0;
     size_t smem = 0;
     // register-resident kernel (M <= 32, tables in shared memory)
     bool use_fast = false, use_lean = false, persistent_ok = false, fast_off = false, lean_off = false;

@@ -75,6 +75,11 @@ struct SweepArgs {
     const int* track_off;
     const int* track_col;
     int ntracks;
+    // generic kernel: stage each column's random words in shared memory,
+    // two 4-word blocks ahead of use (cp.async for MT19937 words, one Philox
+    // call per block), when the staging area fits; the host enables it for
+    // MT19937 only
+    int stage_words;
 };
 
 // One block of a batched launch: instance index and block index within it.

@@ -31,7 +31,7 @@ namespace isg {
 namespace sweep_detail {
 
 struct SmemLayout {
-    uint32_t nbr_off, nbr, jtau, pos, site, colbits, fsp, thr, eacc, total;
+    uint32_t nbr_off, nbr, jtau, pos, site, colbits, fsp, thr, eacc, stage, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(const SweepArgs& a, int fbytes)
@@ -49,6 +49,7 @@ __host__ __device__ inline SmemLayout smem_layout(const SweepArgs& a, int fbytes
     L.fsp = o;     o += r16(uint32_t(fbytes) * a.N * a.G);
     if (a.thr_smem) { L.thr = o; o += r16(4u * a.G * a.K); }
     L.eacc = o;    o += r16(4u * a.G);
+    if (a.stage_words) { L.stage = o; o += r16(32u * a.S * a.G); }  // [column x][2 blocks][4 words]
     L.total = o;
     return L;
 }
@@ -147,11 +148,34 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(const SweepArgs a)
         a.thr_smem ? thr_s + g * K : a.thr + size_t(live ? a.temp_of_slot[r0 + g] : 0) * K;
     const int rg = r0 + g;
     const unsigned long long sweep0 = a.counters[0];
+    const int nrb = (M + 3) >> 2;  // 4-word blocks per column
+    unsigned char* stage = smem + L.stage;
     int dE = 0;
+    // words t = 4b .. 4b+3 of column x (position p) into staging slot b & 1
+    auto fill = [&](const uint32_t* wsw, uint32_t sid, int x, int p, int b) {
+        unsigned char* dst = stage + x * 32 + (b & 1) * 16;
+        if (RNG == 0) {
+            cp_async16(dst, wsw + (size_t(rg) * S + p) * a.Mp + 4 * b);
+        } else {
+            const uint4 ctr = make_uint4(uint32_t(b * S + site[p]), sid, a.inst, 0u);
+            *reinterpret_cast<uint4*>(dst) = philox4x32_10(ctr, a.seed, uint32_t(rg));
+        }
+    };
 
     for (int sw = 0; sw < a.nsweeps; ++sw) {
         const uint32_t sid = uint32_t(sweep0 + sw);
         const uint32_t* wsw = (RNG == 0) ? a.wbuf + size_t(sw) * a.wbuf_sweep_stride : nullptr;
+        if (a.stage_words) {  // blocks 0 and 1 of every owned column
+#pragma unroll
+            for (int c = 0; c < CMAX; ++c) {
+                const int x = tid + c * T;
+                if (lv[c] < INT_MAX / 2) {
+                    fill(wsw, sid, x, x / G, 0);
+                    if (nrb > 1)
+                        fill(wsw, sid, x, x / G, 1);
+                }
+            }
+        }
         for (int l = 0; l < a.D; ++l) {
 #pragma unroll
             for (int c = 0; c < CMAX; ++c) {
@@ -166,7 +190,15 @@ __global__ void __launch_bounds__(1024, 1) sweep_kernel(const SweepArgs a)
                     const int s = 2 * up - 1;
                     const int k = s * f;
                     uint32_t u;
-                    if (RNG == 0) {
+                    if (a.stage_words) {
+                        const int x = tid + c * T;
+                        if (RNG == 0 && (t & 3) == 0)
+                            cp_async_wait_all();  // block t>>2 has landed
+                        u = reinterpret_cast<const uint32_t*>(stage + x * 32 + ((t >> 2) & 1) * 16)[t & 3];
+                        // block (t>>2)+1 replaces block (t>>2)-1 in the idle slot
+                        if ((t & 3) == 0 && t > 0 && (t >> 2) + 1 < nrb)
+                            fill(wsw, sid, x, p, (t >> 2) + 1);
+                    } else if (RNG == 0) {
                         u = wsw[(size_t(rg) * S + p) * a.Mp + t];
                     } else {
                         const uint4 ctr = make_uint4(uint32_t((t >> 2) * S + site[p]), sid, a.inst, 0u);
