@@ -85,6 +85,31 @@ def attempts_per_step(c):
     return c["graph"].n * c["R"] * c["sweeps"]
 
 
+# ------------------------------------------------------- multi-rank helpers
+def rank_seed(base, rank):
+    """Each rank samples its own instance: the workload with seed base +
+    100003 * rank (independent Philox keys / MT19937 streams, no exchange)."""
+    return base + 100003 * rank
+
+
+def max_over_ranks(ms, world):
+    """The slowest rank's time (all-reduce MAX over the default process
+    group; on the CPU for gloo, on the device for NCCL)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, per_step, steps, max_ms):
+    """All ranks' attempts over the slowest rank's time (weak scaling)."""
+    return world * per_step * steps / (max_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples during the timed region (200 ms period)."""
@@ -154,7 +179,7 @@ def run_ours(args):
     if args.sweeps > 0:
         c = dict(c, sweeps=args.sweeps)
     g = c["graph"]
-    seed = c["seed"] + 100003 * rank
+    seed = rank_seed(c["seed"], rank)
     per_step = attempts_per_step(c)
     sweeps, swap_every = c["sweeps"], c["swap_every"]
 
@@ -194,11 +219,8 @@ def run_ours(args):
     sweep_launches = st1["timed_launches"] - st0["timed_launches"]
     launches = st1["launches"] - st0["launches"]
     sim.set_profiling(False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * per_step * args.steps / (max_ms * 1e-3)
+    max_ms = max_over_ranks(total_ms, world)
+    value = whole_job_value(world, per_step, args.steps, max_ms)
 
     e2e = None
     if not args.no_e2e and args.workload == "cfg1":
