@@ -438,6 +438,21 @@ int32_t ising_mlp_set_profiling(ising_mlp_t m, int32_t on);
 int32_t ising_mlp_get_stats(ising_mlp_t m, ising_mlp_stats_t* out);
 int32_t ising_mlp_destroy(ising_mlp_t m);
 
+/*
+ * Failure detection without a GPU fault (test support; the paper has no
+ * counterpart).
+ *   ising_set_alloc_cap(bytes): every later device allocation of the library
+ *     larger than `bytes` fails with ISING_ERR_OOM before reaching the driver
+ *     (0 removes the cap; process-wide).  An out-of-memory stand-in.
+ *   ising_selftest_wait(kind, stream): launches a kernel whose bounded wait is
+ *     made to run out -- kind 0 a grid barrier that one block never reaches,
+ *     kind 1 an mbarrier phase that nothing completes -- and returns
+ *     ISING_ERR_TIMEOUT when the kernel reported it (the normal outcome);
+ *     the context stays usable.  Synchronises `stream` (a cudaStream_t).
+ */
+int32_t ising_set_alloc_cap(uint64_t bytes);
+int32_t ising_selftest_wait(int32_t kind, void* stream);
+
 /* Release all device memory of the handle (NULL is ignored). */
 int32_t ising_destroy(ising_t h);
 

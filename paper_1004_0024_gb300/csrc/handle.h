@@ -85,3 +85,4 @@ int32_t isg_fail(int32_t code, const char* msg);
 int32_t isg_device_setup();  // once per process: kernel attributes, SM count
 int isg_num_sms();           // SMs of the current device (after isg_device_setup)
 bool isg_pt_ok(const ising_s* g);
+bool isg_alloc_allowed(size_t bytes);  // the cap of ising_set_alloc_cap

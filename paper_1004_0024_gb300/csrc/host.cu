@@ -8,6 +8,7 @@
 // that reads every mutable quantity from device memory, so a recorded CUDA
 // graph can be replayed any number of times.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -47,12 +48,26 @@ int32_t cuda_fail(cudaError_t e, const char* what)
             return cuda_fail(e_, #call);           \
     } while (0)
 
+// Process-wide cap on one device allocation (ising_set_alloc_cap; 0 = none):
+// an out-of-memory stand-in for tests of the error paths.
+std::atomic<unsigned long long> g_alloc_cap{0};
+
+bool alloc_allowed(size_t bytes)
+{
+    const unsigned long long cap = g_alloc_cap.load();
+    return cap == 0 || bytes <= cap;
+}
+
 template <typename T>
 int32_t dalloc(T** p, size_t count)
 {
     size_t bytes = ((count * sizeof(T)) + 15) & ~size_t(15);
     if (bytes == 0)
         bytes = 16;
+    if (!alloc_allowed(bytes)) {
+        *p = nullptr;
+        return fail(ISING_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes exceeds the cap");
+    }
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -813,6 +828,8 @@ int32_t isg_fail(int32_t code, const char* msg) { return fail(code, msg); }
 
 int isg_num_sms() { return g_num_sms > 0 ? g_num_sms : 1; }
 
+bool isg_alloc_allowed(size_t bytes) { return alloc_allowed(bytes); }
+
 bool isg_pt_ok(const ising_s* g) { return g->pt_ok; }
 
 int32_t isg_device_setup()
@@ -825,6 +842,12 @@ int32_t isg_device_setup()
 extern "C" {
 
 const char* ising_last_error(void) { return g_err.c_str(); }
+
+int32_t ising_set_alloc_cap(uint64_t bytes)
+{
+    g_alloc_cap.store(bytes);
+    return ISING_OK;
+}
 
 int32_t ising_create(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* J,
                      const int32_t* h, int32_t n_slices, uint32_t flags, ising_t* out)
@@ -998,7 +1021,10 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
     if ((rc = dalloc(&g->d_spins, RN)))
         return rc;
     {
-        cudaError_t e = cudaMalloc(&g->d_fields, ((RN * (field_bits / 8)) + 15) & ~size_t(15));
+        const size_t fbytes = ((RN * (field_bits / 8)) + 15) & ~size_t(15);
+        if (!alloc_allowed(fbytes))
+            return fail(ISING_ERR_OOM, "device allocation of " + std::to_string(fbytes) + " bytes exceeds the cap");
+        cudaError_t e = cudaMalloc(&g->d_fields, fbytes);
         if (e != cudaSuccess)
             return cuda_fail(e, "cudaMalloc fields");
     }

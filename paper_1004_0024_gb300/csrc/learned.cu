@@ -568,6 +568,10 @@ template <typename T>
 cudaError_t zalloc(T** p, size_t count)
 {
     const size_t bytes = std::max<size_t>(16, (count * sizeof(T) + 15) & ~size_t(15));
+    if (!isg_alloc_allowed(bytes)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
     if (e != cudaSuccess) {
         *p = nullptr;

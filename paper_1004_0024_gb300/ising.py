@@ -129,6 +129,8 @@ _SIGS = {
     "ising_mlp_set_profiling": ([_vp, ctypes.c_int32], ctypes.c_int32),
     "ising_mlp_get_stats": ([_vp, ctypes.POINTER(MlpStats)], ctypes.c_int32),
     "ising_read_observables": ([_vp, _i64p, _i64p], ctypes.c_int32),
+    "ising_set_alloc_cap": ([ctypes.c_uint64], ctypes.c_int32),
+    "ising_selftest_wait": ([ctypes.c_int32, _vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -258,6 +260,16 @@ def ising_get_stats(h) -> dict:
     st = IsingStats()
     _check(_lib.ising_get_stats(h, ctypes.byref(st)))
     return {name: getattr(st, name) for name, _ in IsingStats._fields_}
+
+
+def ising_set_alloc_cap(nbytes):
+    """Cap every later device allocation of the library at `nbytes` (0: none)."""
+    _check(_lib.ising_set_alloc_cap(int(nbytes)))
+
+
+def ising_selftest_wait(kind, stream=None):
+    """Run a kernel whose bounded wait runs out; returns the status code."""
+    return int(_lib.ising_selftest_wait(int(kind), _vp(stream) if stream else None))
 
 
 def ising_destroy(h):
