@@ -386,6 +386,14 @@ SweepArgs base_args(ising_s* g);
 // M <= 32, the slice tables in shared memory and spatial degree <= 255.
 int kernel_variant(const ising_s* g) { return g->use_track ? 2 : (g->use_lean ? 1 : 0); }
 
+// The lean kernel's model limits (one replica per block; the block size is
+// checked when the launch is chosen).
+bool lean_eligible(const ising_s* g)
+{
+    return (g->M == 4 || g->M == 8 || g->M == 16 || g->M == 32) && g->max_sp_deg <= 6 && g->max_sp_J <= 63 &&
+           g->G_req <= 1 && !g->lean_off && !g->fast_off;
+}
+
 // The track kernel (opt-in, ISING_LAUNCH_TRACK) and its limits (lean's, with
 // one thread per track): power-of-two M in 4..32, spatial degree <= 6,
 // |J| <= 63, at most 512 tracks, and the block size left to the library.
@@ -417,7 +425,8 @@ void choose_fast(ising_s* g)
     // and couplings, at most 4 columns per thread within its register budget
     g->use_lean = g->G == 1 && (g->M == 4 || g->M == 8 || g->M == 16 || g->M == 32) &&
                   g->max_sp_deg <= 6 && g->max_sp_J <= 63 && cmax <= 4 &&
-                  g->T <= (cmax <= 1 ? 1024 : (cmax == 2 ? 512 : 256)) && !g->lean_off;
+                  g->T <= (cmax <= 1 ? 1024 : (cmax == 2 ? 512 : 256)) && !g->lean_off &&
+                  (g->rng == ISING_RNG_MT19937 || (g->ntracks >= 1 && g->ntracks <= g->T));
     // track variant: the lean kernel's limits with the columns walked as
     // tracks, one thread per track (when the block size is left automatic)
     const int T_track = ((g->ntracks + 31) / 32) * 32;
@@ -504,6 +513,9 @@ SweepArgs base_args(ising_s* g)
     a.track_col = g->d_track_col;
     a.ntracks = g->ntracks;
     a.stage_words = g->stage_words;
+    // busy columns of a level form a contiguous range of positions no longer
+    // than ntracks (the widest level); a thread's columns are T positions apart
+    a.one_active = (g->ntracks >= 1 && g->ntracks <= g->T) ? 1 : 0;
     return a;
 }
 
@@ -515,8 +527,8 @@ int32_t choose_launch(ising_s* g)
     std::vector<int> Gs;
     if (g->G_req > 0) {
         Gs.push_back(g->G_req);
-    } else if (track_eligible(g)) {
-        Gs.push_back(1);  // the track kernel runs one replica per block
+    } else if (track_eligible(g) || lean_eligible(g)) {
+        Gs.push_back(1);  // the track and lean kernels run one replica per block
     } else {
         for (int G : {8, 4, 2, 1})
             if ((long long)((g->R + G - 1) / G) >= 2LL * sms || G == 1)
@@ -545,7 +557,16 @@ int32_t choose_launch(ising_s* g)
                 // four columns per thread for the register-resident kernels (M <= 32);
                 // one per thread for the generic kernel, whose per-level loop over a
                 // thread's columns is serial (the paper-shaped 96 x 256 model: 2.2x)
-                const long long want = g->M > 32 ? (long long)g->S * G : ((long long)g->S * G + 3) / 4;
+                long long want = g->M > 32 ? (long long)g->S * G : ((long long)g->S * G + 3) / 4;
+                if (G == 1 && g->M <= 32) {
+                    // a ladder too large to stay resident (no fused PT) runs two
+                    // columns per thread (cfg3, 65536 replicas: 1.3x over four);
+                    // at least as many threads as the widest level has busy columns
+                    // (the lean kernel's Philox state is per thread)
+                    if ((long long)g->R > 4LL * sms)
+                        want = ((long long)g->S + 1) / 2;
+                    want = std::max<long long>(want, g->ntracks);
+                }
                 T = int(std::min<long long>(1024, std::max<long long>(32, ((want + 31) / 32) * 32)));
             }
             if (T % 32 != 0 || T > 1024 || T % G != 0)

@@ -80,6 +80,9 @@ struct SweepArgs {
     // call per block), when the staging area fits; the host enables it for
     // MT19937 only
     int stage_words;
+    // lean kernel: at most one owned column of a thread is busy per level
+    // (no level has more busy columns than the block has threads)
+    int one_active;
 };
 
 // One block of a batched launch: instance index and block index within it.

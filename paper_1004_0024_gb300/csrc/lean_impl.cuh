@@ -16,12 +16,14 @@
 //    neighbours are padded with a zero delta aimed at the item's own field
 //    word (no other item of the level touches it), so the six atomics are
 //    issued unconditionally once the flip is accepted.
-//  * Random words come in blocks of four (t>>2), two blocks per column in
-//    flight, alternating by block parity: block b+1 is fetched or computed
-//    while block b is consumed.  MT19937 words are staged global -> shared
-//    with cp.async: a barrier must wait for a warp's outstanding register
-//    loads, but not for its asynchronous copies, so the staging latency never
-//    lands on a level.  Philox blocks are computed into two registers.
+//  * Random words come in blocks of four (t>>2): block b+1 is fetched or
+//    computed while block b is consumed.  MT19937 words are staged global ->
+//    shared with cp.async, two blocks per column: a barrier must wait for a
+//    warp's outstanding register loads, but not for its asynchronous copies,
+//    so the staging latency never lands on a level.  Philox: the ten rounds
+//    of block b+1 are spread over the four levels of block b (one state per
+//    thread: the block size is at least the widest level, so a thread has at
+//    most one busy column per level).
 //  * With at most 32 tabulated thresholds, lane k of every warp holds T[k] and
 //    the lookup of T[k] is a warp shuffle in a converged section.
 #pragma once
@@ -125,7 +127,7 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     int lv[CMAX], jd[CMAX], fb[CMAX];
     uint32_t bits[CMAX];
     uint32_t nb[CMAX][kMaxDeg];
-    uint4 ba[CMAX], bb[CMAX];  // Philox word blocks of even / odd index
+    uint4 ba[CMAX];  // Philox: the current word block of each column
     unsigned char* stage = smem + L.nbr_off;  // MT19937: [S][2 blocks][16 B]
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
@@ -134,7 +136,7 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
         jd[c] = 0;
         fb[c] = 0;
         bits[c] = 0u;
-        ba[c] = bb[c] = make_uint4(0u, 0u, 0u, 0u);
+        ba[c] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int e = 0; e < kMaxDeg; ++e)
             nb[c][e] = 0u;
@@ -172,6 +174,10 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     const int nrb = (M + 3) >> 2;  // random-word blocks per column
     int npass = 0;
     int dE = 0;
+    // Philox block in progress: one per thread, as a thread has at most one busy
+    // column per level (the host sizes the block to the widest level)
+    uint4 pc = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t pk0 = 0u, pk1 = 0u;
 
     for (int sw = 0; sw < a.nsweeps; ++sw) {
         const uint32_t sid = uint32_t(sweep0 + sw);
@@ -186,9 +192,7 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                     if (nrb > 1)
                         cp_async16(stage + p * 32 + 16, src + 4);
                 } else {
-                    ba[c] = rng_block<RNG>(a, wsw, r, p, site[p], 0, sid);
-                    if (nrb > 1)
-                        bb[c] = rng_block<RNG>(a, wsw, r, p, site[p], 1, sid);
+                    ba[c] = rng_block<RNG>(a, wsw, r, p, site[p], 0, sid);  // later blocks: see pc
                 }
             }
         }
@@ -205,9 +209,11 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                     if (RNG == 0 && act && (t & 3) == 0)
                         cp_async_wait_all();  // block t>>2 has landed in `stage`
                     const int fs = Fsp<FT>::ld(fsp, act ? fb[c] + t : 0);
+                    if (RNG != 0 && act && (t & 3) == 0 && t > 0)
+                        ba[c] = pc;  // block t>>2, finished over the previous four levels
                     const uint32_t u = (RNG == 0)
                         ? *reinterpret_cast<const uint32_t*>(stage + p * 32 + odd * 16 + (t & 3) * 4)
-                        : pick4(odd ? bb[c] : ba[c], t & 3);
+                        : pick4(ba[c], t & 3);
                     const uint32_t w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
                     const int s = 2 * int((w3 >> 1) & 1u) - 1;
                     const int ft = (jd[c] >> 8) * (2 * int((w3 & 1u) + ((w3 >> 2) & 1u)) - 2);
@@ -229,18 +235,29 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                             atomicAdd(fsw + (v >> 8) + tw, unsigned(d) << sh);
                         }
                     }
-                    // block (t>>2)+1 replaces block (t>>2)-1 in the idle slot
-                    if (act && (t & 3) == 0 && (t >> 2) + 1 < nrb && t > 0) {
-                        if (RNG == 0) {
-                            cp_async16(stage + p * 32 + (odd ^ 1) * 16,
-                                       wsw + (size_t(r) * S + p) * a.Mp + t + 4);
-                        } else {
-                            const uint4 v = rng_block<RNG>(a, wsw, r, p, site[p], (t >> 2) + 1, sid);
-                            if (odd)
-                                ba[c] = v;
-                            else
-                                bb[c] = v;
+                    if (RNG == 0) {
+                        // block (t>>2)+1 replaces block (t>>2)-1 in the idle slot
+                        if (act && (t & 3) == 0 && (t >> 2) + 1 < nrb && t > 0)
+                            cp_async16(stage + p * 32 + (odd ^ 1) * 16, wsw + (size_t(r) * S + p) * a.Mp + t + 4);
+                    } else if (act && (t >> 2) + 1 < nrb) {
+                        // Philox: the ten rounds of block (t>>2)+1 spread over the four
+                        // levels of block t>>2 (3, 3, 3, 1), so no level carries a whole
+                        // call; the state is the thread's (one busy column per level)
+                        const int ph = t & 3;
+                        if (ph == 0) {
+                            pc = make_uint4(uint32_t(((t >> 2) + 1) * S + site[p]), sid, a.inst, 0u);
+                            pk0 = a.seed;
+                            pk1 = uint32_t(r);
                         }
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+                            if (3 * ph + i < 10) {
+                                const uint32_t lo0 = 0xD2511F53u * pc.x, hi0 = __umulhi(0xD2511F53u, pc.x);
+                                const uint32_t lo1 = 0xCD9E8D57u * pc.z, hi1 = __umulhi(0xCD9E8D57u, pc.z);
+                                pc = make_uint4(hi1 ^ pc.y ^ pk0, lo1, hi0 ^ pc.w ^ pk1, lo0);
+                                pk0 += 0x9E3779B9u;
+                                pk1 += 0xBB67AE85u;
+                            }
                     }
                 }
             }
