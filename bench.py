@@ -364,14 +364,15 @@ def roofline(c, rng, attempts, kernel_ms, launches, clocks, kernel, name="cfg1")
     if kernel_ms <= 0 or launches <= 0:
         return None
     if name == "cfg3" and rng == "mt19937":
-        # one sweep per launch (the MT19937 words of a sweep fill the word
-        # buffer): each attempt streams its word (4 B) and its replica's spin
-        # and int16 field in and out (2 x 3 B) through HBM
-        bpa = 10.0
+        # each attempt streams its pre-generated word (4 B) from HBM; a launch
+        # loads every replica's spins and int16 fields once and writes them
+        # back (2 x 3 B per spin), amortised over the sweeps of the launch
+        sweeps_per_launch = (attempts / (g.n * c["R"])) / launches
+        bpa = 4.0 + 6.0 / sweeps_per_launch
         hbm, src = measured_peak("hbm_gbs")
         gbs = attempts * bpa / (kernel_ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": None, "peak_basis": src, "bytes_per_attempt": bpa,
+                "traffic": None, "peak_basis": src, "bytes_per_attempt": bpa, "sweeps_per_launch": sweeps_per_launch,
                 "kernel_ms_per_launch": kernel_ms / launches, "launches": int(launches)}
     ops = attempts * ops_per_attempt(g, rng)
     achieved = ops / (kernel_ms * 1e-3) / 1e12

@@ -50,7 +50,7 @@ struct ising_s {
     int* d_Epub = nullptr;
     unsigned* d_gridbar = nullptr;
     long long wbuf_cap = 0, swbuf_cap = 0;  // sweeps / passes
-    long long word_budget = 1LL << 30;     // bytes of pre-generated MT19937 words
+    long long word_budget = 8LL << 30;     // bytes of pre-generated MT19937 words
     // launch configuration
     int G = 1, T = 32, cmax = 1, blocks = 1, tables_smem = 1, thr_smem = 1, stage_words = 0;
     size_t smem = 0;
