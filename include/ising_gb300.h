@@ -442,7 +442,7 @@ int32_t ising_mlp_destroy(ising_mlp_t m);
  * Failure detection without a GPU fault (test support; the paper has no
  * counterpart).
  *   ising_set_alloc_cap(bytes): every later device allocation of the library
- *     larger than `bytes` fails with ISING_ERR_OOM before reaching the driver
+ *     larger than `bytes` fails with ISING_ERR_OOM before any CUDA call
  *     (0 removes the cap; process-wide).  An out-of-memory stand-in.
  *   ising_selftest_wait(kind, stream): launches a kernel whose bounded wait is
  *     made to run out -- kind 0 a grid barrier that one block never reaches,

@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_aggregate_like_the_driver_expects():
+def test_two_gloo_ranks_aggregate_over_the_whole_job():
     ctx = mp.get_context("spawn")
     with ctx.Manager() as mgr:
         out = mgr.dict()
