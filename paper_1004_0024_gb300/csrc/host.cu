@@ -210,6 +210,7 @@ void ising_s::free_all()
     dfree(d_track_col);
     dfree(d_sp_off);
     dfree(d_sp_nbr);
+    dfree(d_colbits);
     colour_off.clear();
     colour_sites.clear();
 }

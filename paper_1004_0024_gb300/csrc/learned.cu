@@ -26,6 +26,7 @@
 #include <cstring>
 #include <random>
 #include <string>
+#include <set>
 #include <vector>
 
 #include "handle.h"
@@ -189,6 +190,7 @@ struct LearnedArgs {
     const int* sites;  // the class's sites
     const int* sp_off; // [S+1] spatial neighbour list of each site
     const int2* sp_nbr; // (site, J) entries
+    uint32_t* colbits;  // [R][S] column bits: bit t = (spin (t, q) > 0)
     int* phi;          // [rows][32]
     bf16* X;           // [rows_pad][64]
     const float* L;    // [rows_pad][32]
@@ -231,42 +233,117 @@ __device__ __forceinline__ int column_trotter(uint32_t bits, int t, int M, int j
     return jt * (sp + (((bits >> tm) & 1u) ? 1 : -1));
 }
 
-// One warp per (replica, column) row, lane t = slice t: phi_t is the local
-// field of spin (t, q) less its Trotter part (the fields are exact at every
-// class: the sweep leaves them so and the learned moves update them), then
-// the input row X = (phi_t/8 for t < M, beta at M, zeros) in the tiled layout.
-__global__ void __launch_bounds__(256) learned_gather_kernel(const LearnedArgs a, int rows_pad)
+// Column bits of every (replica, site) from the spins: bit t = (s_(t, q) > 0).
+// Thread per column; for each slice the lanes read consecutive bytes.
+__global__ void __launch_bounds__(256) learned_colbits_kernel(const LearnedArgs a)
 {
-    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int t = threadIdx.x & 31;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = r S + q
+    if (k >= a.R * a.S)
+        return;
+    const int r = k / a.S, q = k - r * a.S;
+    const int8_t* sp = a.spins + size_t(r) * a.N + q;
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int t = 0; t < kOut; ++t)
+        if (t < a.M)
+            bits |= uint32_t(sp[size_t(t) * a.S] > 0) << t;
+    a.colbits[k] = bits;
+}
+
+// phi_t = h_q + sum over the spatial neighbours j of site q of J_qj s_(t, j)
+// for t < 32 (every slice holds the same h and couplings), from the column
+// bits of replica r's neighbours: s = 2 b - 1, so phi_t = h_q - sum_j J_qj +
+// sum_j 2 J_qj b_j(t).
+__device__ __forceinline__ void column_phi(const LearnedArgs& a, const uint32_t* cb, int q, int (&f)[kOut])
+{
+    int base = a.h[q];
+#pragma unroll
+    for (int t = 0; t < kOut; ++t)
+        f[t] = 0;
+    for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
+        const int2 nb = a.sp_nbr[e];
+        const uint32_t b = cb[nb.x];
+        const int j2 = 2 * nb.y;
+        base -= nb.y;
+#pragma unroll
+        for (int t = 0; t < kOut; ++t)
+            f[t] += ((b >> t) & 1u) ? j2 : 0;
+    }
+#pragma unroll
+    for (int t = 0; t < kOut; ++t)
+        f[t] += base;
+}
+
+// One thread per (replica, column) row: phi of the column from the current
+// column bits (the moves of earlier classes are seen without any field being
+// maintained during the pass), then the input row X = (phi_t/8 for t < M,
+// beta at M, zeros) in the tiled operand layout of the fused network, 16
+// bytes (8 inputs) at a time, and the column's bits to old_bits.
+__global__ void __launch_bounds__(128) learned_gather_kernel(const LearnedArgs a, int rows_pad)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= rows_pad)
         return;
-    // X in tiles of 128 rows in the fused network's operand layout
     unsigned char* xt = reinterpret_cast<unsigned char*>(a.X) + size_t(row >> 7) * (128 * 128);
-    bf16* x0 = reinterpret_cast<bf16*>(xt + tiled_offset(128, row & 127, t));
-    bf16* x1 = reinterpret_cast<bf16*>(xt + tiled_offset(128, row & 127, 32 + t));
+    const int rt = row & 127;
     if (row >= a.rows) {
-        *x0 = __float2bfloat16(0.f);
-        *x1 = __float2bfloat16(0.f);
+#pragma unroll
+        for (int k0 = 0; k0 < 64; k0 += 8)
+            *reinterpret_cast<uint4*>(xt + tiled_offset(128, rt, k0)) = make_uint4(0u, 0u, 0u, 0u);
         return;
     }
     const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
+    const int M = a.M;
+    const uint32_t* cb = a.colbits + size_t(r) * a.S;
+    int f[kOut];
+    column_phi(a, cb, q, f);
     const float beta = a.betas32[a.temp_of_slot[r]];
-    const bool live = t < a.M;
-    const size_t i = size_t(r) * a.N + size_t(live ? t : 0) * a.S + q;
-    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, live && a.spins[i] > 0);
-    float v = 0.f;
-    if (live) {
-        const int f = a.field_bits == 16 ? int(static_cast<const int16_t*>(a.fields)[i])
-                                         : static_cast<const int*>(a.fields)[i];
-        const int phi = f - column_trotter(bits, t, a.M, a.jtau[a.pos[q]]);
-        a.phi[size_t(row) * kOut + t] = phi;
-        v = float(phi) * 0.125f;
-    } else if (t == a.M) {
-        v = beta;
+    int* phi = a.phi + size_t(row) * kOut;
+#pragma unroll
+    for (int k0 = 0; k0 < 64; k0 += 8) {
+        uint32_t packed[4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = k0 + u + h;
+                v[h] = (k < kOut && k < M) ? float(f[k < kOut ? k : 0]) * 0.125f : (k == M ? beta : 0.f);
+            }
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+            packed[u >> 1] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(xt + tiled_offset(128, rt, k0)) =
+            make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        if (k0 < kOut) {
+            *reinterpret_cast<int4*>(phi + k0) = make_int4(f[k0], f[k0 + 1], f[k0 + 2], f[k0 + 3]);
+            *reinterpret_cast<int4*>(phi + k0 + 4) = make_int4(f[k0 + 4], f[k0 + 5], f[k0 + 6], f[k0 + 7]);
+        }
     }
-    *x0 = __float2bfloat16(v);
-    *x1 = __float2bfloat16(t == 0 && a.M == 32 ? beta : 0.f);
+    a.old_bits[row] = cb[q];
+}
+
+// Local fields of every spin after a pass: f_(t,q) = phi_t of column q plus
+// its Trotter part J_tau (s_(t-1,q) + s_(t+1,q)) on the ring (J_tau s_(1-t,q)
+// for M == 2, none for M == 1).  Thread per (replica, column); for each slice
+// the lanes write consecutive fields.
+template <typename F>
+__global__ void __launch_bounds__(256) learned_fields_kernel(const LearnedArgs a)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = r S + q
+    if (k >= a.R * a.S)
+        return;
+    const int r = k / a.S, q = k - r * a.S;
+    const uint32_t* cb = a.colbits + size_t(r) * a.S;
+    int f[kOut];
+    column_phi(a, cb, q, f);
+    const uint32_t bits = cb[q];
+    const int jt = a.jtau[a.pos[q]];
+    F* fl = static_cast<F*>(a.fields) + size_t(r) * a.N + q;
+#pragma unroll
+    for (int t = 0; t < kOut; ++t)
+        if (t < a.M)
+            fl[size_t(t) * a.S] = F(f[t] + column_trotter(bits, t, a.M, jt));
 }
 
 // Term of slice t in E_col: -s_t phi_t - Jtau s_t s_{t+1 mod M} (the Trotter
@@ -280,23 +357,6 @@ __device__ __forceinline__ int column_term(uint32_t bits, int t, int M, int phi,
         e -= jt * s * (((bits >> t1) & 1u) ? 1 : -1);
     }
     return e;
-}
-
-// int16 += d through a compare-and-swap on the aligned 32-bit word (the
-// retries are bounded; false if the bound was reached)
-__device__ __forceinline__ bool atomic_add_i16(int16_t* p, int d)
-{
-    unsigned* w = reinterpret_cast<unsigned*>(reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3));
-    const unsigned sh = (reinterpret_cast<uintptr_t>(p) & 2u) ? 16u : 0u;
-    unsigned cur = *reinterpret_cast<volatile unsigned*>(w);
-    for (int it = 0; it < (1 << 20); ++it) {
-        const unsigned v = ((cur >> sh) + unsigned(d)) & 0xFFFFu;
-        const unsigned prev = atomicCAS(w, cur, (cur & ~(0xFFFFu << sh)) | (v << sh));
-        if (prev == cur)
-            return true;
-        cur = prev;
-    }
-    return false;
 }
 
 // c = ceil(p 2^32) for an FP32 p in [0, 1], in integer arithmetic: with
@@ -315,87 +375,126 @@ __device__ __forceinline__ unsigned long long ceil_p32(float p)
     return k >= 40 ? 1ull : (m + (1ull << k) - 1ull) >> k;
 }
 
-// One MH column move per warp (lane t = slice t).  Words: Philox4x32-10, key
-// (seed, r), counter (q, pass, instance, 2 + 4 j) gives words 4j .. 4j+3; word
-// t < M proposes slice t, word 32 decides acceptance.  Bit t is drawn +1 iff
-// u_t < p_t 2^32 (p_t the FP32 sigmoid of the logit), i.e. iff u_t < c_t with
-// c_t = ceil(p_t 2^32): an event of probability exactly c_t 2^-32.  The
+// c_t = ceil(p_t 2^32) of slice t's logit, p_t = 1 / (1 + exp(-l)) in FP32
+__device__ __forceinline__ unsigned long long proposal_c(float l)
+{
+    return ceil_p32(1.f / (1.f + expf(-l)));
+}
+
+// FP32 value (round to nearest) of an integer c in [0, 2^32], converted from
+// 32 bits: a conversion from a 64-bit integer would occupy the FP64 pipe
+__device__ __forceinline__ float c_to_float(unsigned long long c)
+{
+    return (c >> 32) ? 4294967296.f : float(uint32_t(c));
+}
+
+// One MH column move per group of 8 lanes (kMhLanes): lane g of the group
+// draws Philox block g, proposes slices 4g .. 4g+3 and adds their terms; the
+// group combines bits and sums by shuffles.  Words: Philox4x32-10, key
+// (seed, r), counter (q, pass, instance, 2 + 4 j) gives words 4j .. 4j+3;
+// word t < M proposes slice t, word 32 decides acceptance.  Bit t is drawn +1
+// iff u_t < p_t 2^32 (p_t the FP32 sigmoid of the logit), i.e. iff u_t < c_t
+// with c_t = ceil(p_t 2^32): an event of probability exactly c_t 2^-32.  The
 // Hastings ratio q(s)/q(s') is the product over the changed bits of
 // c(old bit) / c(new bit) (c(+1) = c_t, c(-1) = 2^32 - c_t), formed in FP64
 // with exact exponents, so it is the ratio of the probabilities of the draws
-// actually made.
-__global__ void __launch_bounds__(256) learned_mh_kernel(const LearnedArgs a)
+// actually made.  An FP32 estimate of its logarithm, with a bound on its
+// error, decides whenever the bound allows.
+constexpr int kMhLanes = 8;
+constexpr int kMhThreads = 256;
+constexpr int kMhRows = kMhThreads / kMhLanes;  // rows per block
+
+__global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArgs a)
 {
-    __shared__ unsigned s_acc, s_chg;
-    __shared__ unsigned long long s_c[8][32];
-    if (threadIdx.x == 0)
-        s_acc = s_chg = 0u;
+    __shared__ unsigned s_cnt[2][kMhThreads / 32];
+    __shared__ int s_dE[kMhRows + 2];  // energy change per replica of the block's rows
+    const int r0 = int(blockIdx.x) * kMhRows / a.ncols;
+    const int nrep = min((int(blockIdx.x) * kMhRows + kMhRows - 1) / a.ncols, a.R - 1) - r0 + 1;
+    for (int k = threadIdx.x; k < nrep; k += blockDim.x)
+        s_dE[k] = 0;
     __syncthreads();
-    const int wib = threadIdx.x >> 5;
-    const int row = blockIdx.x * 8 + wib;
-    const int t = threadIdx.x & 31;
-    if (row < a.rows) {
+    const int row = int(blockIdx.x) * kMhRows + int(threadIdx.x) / kMhLanes;
+    const int g = threadIdx.x & (kMhLanes - 1);
+    const unsigned gmask = 0xFFu << (threadIdx.x & 24);  // the lanes of this row's group
+    bool acc = false, moved = false;
+    if (row < a.rows) {  // uniform over the group
         const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
         const int M = a.M, S = a.S;
-        const bool live = t < M;
-        int8_t* sp = a.spins + size_t(r) * a.N + size_t(t) * S + q;
-        const uint32_t old = __ballot_sync(0xFFFFFFFFu, live && *(live ? sp : a.spins) > 0);
-        // lane j < 9 draws block j (words 4j .. 4j+3); lane t takes word t
-        const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(t < 9 ? t : 0)),
-                                      a.seed, uint32_t(r));
-        const uint32_t w0 = __shfl_sync(0xFFFFFFFFu, w.x, t >> 2), w1 = __shfl_sync(0xFFFFFFFFu, w.y, t >> 2);
-        const uint32_t w2 = __shfl_sync(0xFFFFFFFFu, w.z, t >> 2), w3 = __shfl_sync(0xFFFFFFFFu, w.w, t >> 2);
-        const uint32_t u = (t & 2) ? ((t & 1) ? w3 : w2) : ((t & 1) ? w1 : w0);
-        const uint32_t ua = __shfl_sync(0xFFFFFFFFu, w.x, 8);  // word 32
-        unsigned long long c1 = 0ull;
-        if (live)
-            c1 = ceil_p32(1.f / (1.f + expf(-a.L[size_t(row) * kOut + t])));
-        const bool up = live && (unsigned long long)u < c1;
-        const uint32_t prop = __ballot_sync(0xFFFFFFFFu, up);
-        const int phi = live ? a.phi[size_t(row) * kOut + t] : 0;
+        const uint32_t old = a.old_bits[row];
+        const float* Lr = a.L + size_t(row) * kOut;
         const int jt = a.jtau[a.pos[q]];
-        int dE = live ? column_term(prop, t, M, phi, jt) - column_term(old, t, M, phi, jt) : 0;
-        dE = __reduce_add_sync(0xFFFFFFFFu, dE);
-        // FP32 estimate of log q(s)/q(s') with a bound on its error; the FP64
-        // product below decides only when the estimate cannot
-        float term = 0.f;
-        if (live && (((old ^ prop) >> t) & 1u)) {
-            const float cp = float(c1), cm = float(4294967296ull - c1);
-            term = logf(up ? cm / cp : cp / cm);
-        }
-        float lq = term, mag = fabsf(term);
+        const bool live = 4 * g < M;
+        uint32_t prop = 0u;
+        float lq = 0.f, mag = 0.f;
+        if (live) {
+            const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(g)), a.seed,
+                                          uint32_t(r));
+            const float4 l4 = *reinterpret_cast<const float4*>(Lr + 4 * g);
+            const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+            const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lq += __shfl_xor_sync(0xFFFFFFFFu, lq, o);
-            mag += __shfl_xor_sync(0xFFFFFFFFu, mag, o);
+            for (int u = 0; u < 4; ++u) {
+                const int t = 4 * g + u;
+                if (t < M) {
+                    const unsigned long long c1 = proposal_c(lv[u]);
+                    const bool up = (unsigned long long)wv[u] < c1;
+                    prop |= uint32_t(up) << t;
+                    if (up != bool((old >> t) & 1u)) {  // FP32 log of this bit's ratio
+                        const float cp = c_to_float(c1), cm = c_to_float(4294967296ull - c1);
+                        const float term = logf(up ? cm / cp : cp / cm);
+                        lq += term;
+                        mag += fabsf(term);
+                    }
+                }
+            }
         }
-        s_c[wib][t] = c1;
-        __syncwarp();
-        bool acc = false;
-        if (t == 0) {
+#pragma unroll
+        for (int o = kMhLanes / 2; o > 0; o >>= 1) {
+            prop |= __shfl_xor_sync(gmask, prop, o);
+            lq += __shfl_xor_sync(gmask, lq, o);
+            mag += __shfl_xor_sync(gmask, mag, o);
+        }
+        int dE = 0;
+        if (live) {
+            const int4 p4 = *reinterpret_cast<const int4*>(a.phi + size_t(row) * kOut + 4 * g);
+            const int pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = 4 * g + u;
+                if (t < M)
+                    dE += column_term(prop, t, M, pv[u], jt) - column_term(old, t, M, pv[u], jt);
+            }
+        }
+#pragma unroll
+        for (int o = kMhLanes / 2; o > 0; o >>= 1)
+            dE += __shfl_xor_sync(gmask, dE, o);
+        if (g == 0) {
+            const uint32_t ua =
+                philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 34u), a.seed, uint32_t(r)).x;
             const float bdE = a.betas32[a.temp_of_slot[r]] * float(dE);
             const float la = -bdE + lq;
             const float lu = logf((float(ua) + 0.5f) * 2.3283064365386963e-10f);
             // Bound on |la - logA| + |lu - log u'|: each term's ratio carries 3
-            // roundings (1.8e-7 in the log) and logf 1 ulp (1.2e-7 |term|), the
-            // shuffle sum 5 roundings (3e-7 mag); beta, the product and the sum
-            // 1.8e-7 |bdE|; lu 2.9e-6.  Below 8.7e-6 + 1.8e-7 |bdE| + 4.8e-7 mag.
+            // roundings (1.8e-7 in the log, 5.8e-6 over 32 terms) and logf 1
+            // ulp (1.2e-7 |term|); the sums at most 31 roundings (1.9e-6 mag);
+            // beta, the product and the sum 1.8e-7 |bdE|; lu 2.9e-6.  Below
+            // 8.7e-6 + 1.8e-7 |bdE| + 2.1e-6 mag.
             const float eps = 1e-5f * (1.f + fabsf(bdE) + mag);
-            int decided = 1;
-            if (a.fp64_only)
-                decided = 0;
-            else if (la >= eps || lu < la - eps)
-                acc = true;
-            else if (la < -eps && lu > la + eps)
-                acc = false;
-            else
-                decided = 0;
+            bool decided = !a.fp64_only;
+            if (decided) {
+                if (la >= eps || lu < la - eps)
+                    acc = true;
+                else if (la < -eps && lu > la + eps)
+                    acc = false;
+                else
+                    decided = false;
+            }
             if (!decided) {  // exact: the FP64 product of the integer ratios
                 double num = 1.0, den = 1.0;
                 int en = 0, ed = 0, n = 0;
                 for (uint32_t ch = old ^ prop; ch; ch &= ch - 1u) {
                     const int b = __ffs(ch) - 1;
-                    const double cp = double(s_c[wib][b]), cm = 4294967296.0 - cp;
+                    const double cp = double(proposal_c(Lr[b])), cm = 4294967296.0 - cp;
                     const bool ob = (old >> b) & 1u;
                     num *= ob ? cp : cm;
                     den *= ob ? cm : cp;
@@ -412,53 +511,45 @@ __global__ void __launch_bounds__(256) learned_mh_kernel(const LearnedArgs a)
                 acc = (logA >= 0.0) || (log((double(ua) + 0.5) * 2.3283064365386963e-10) < logA);
                 atomicAdd(a.n_exact, 1ull);
             }
-            a.old_bits[row] = old;
             a.prop_bits[row] = prop;
             a.accepted[row] = acc ? 1 : 0;
-            if (acc) {
-                atomicAdd(&s_acc, 1u);
-                if (prop != old) {
-                    atomicAdd(&a.E[r], dE);
-                    atomicAdd(&s_chg, 1u);
-                }
+            moved = acc && prop != old;
+            if (moved) {  // the fields are rebuilt after the pass
+                atomicAdd(&s_dE[r - r0], dE);
+                a.colbits[size_t(r) * S + q] = prop;
             }
         }
-        acc = __shfl_sync(0xFFFFFFFFu, acc, 0);
-        if (acc && prop != old && live) {
-            // the column's own fields: phi_t plus its new Trotter neighbours;
-            // each changed spin moves its spatial neighbours' fields by 2 J s'
-            const int f = phi + column_trotter(prop, t, M, jt);
-            const size_t base = size_t(r) * a.N + size_t(t) * S;
-            const bool flip = ((old ^ prop) >> t) & 1u;
-            if (flip)
-                *sp = up ? int8_t(1) : int8_t(-1);
-            const int d = up ? 2 : -2;
-            if (a.field_bits == 16) {
-                int16_t* fl = static_cast<int16_t*>(a.fields) + base;
-                fl[q] = int16_t(f);
-                if (flip)
-                    for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
-                        const int2 nb = a.sp_nbr[e];
-                        if (!atomic_add_i16(fl + nb.x, nb.y * d))
-                            set_err(a.err, kErrTimeout);
-                    }
-            } else {
-                int* fl = static_cast<int*>(a.fields) + base;
-                fl[q] = f;
-                if (flip)
-                    for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
-                        const int2 nb = a.sp_nbr[e];
-                        atomicAdd(fl + nb.x, nb.y * d);
-                    }
+        const bool mv = __shfl_sync(gmask, moved, threadIdx.x & 24);
+        if (mv && live) {  // this lane's slices of the new column
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = 4 * g + u;
+                if (t < M && (((old ^ prop) >> t) & 1u))
+                    a.spins[size_t(r) * a.N + size_t(t) * S + q] = ((prop >> t) & 1u) ? int8_t(1) : int8_t(-1);
             }
         }
+    }
+    const unsigned n_acc = __reduce_add_sync(0xFFFFFFFFu, acc ? 1u : 0u);
+    const unsigned n_mov = __reduce_add_sync(0xFFFFFFFFu, moved ? 1u : 0u);
+    if ((threadIdx.x & 31) == 0) {
+        s_cnt[0][threadIdx.x >> 5] = n_acc;
+        s_cnt[1][threadIdx.x >> 5] = n_mov;
     }
     __syncthreads();
-    if (threadIdx.x == 0 && s_acc) {
-        atomicAdd(a.n_acc, (unsigned long long)s_acc);
-        if (s_chg)
-            atomicAdd(a.n_changed, (unsigned long long)s_chg);
+    if (threadIdx.x == 0) {
+        unsigned na = 0u, nm = 0u;
+        for (int w = 0; w < kMhThreads / 32; ++w) {
+            na += s_cnt[0][w];
+            nm += s_cnt[1][w];
+        }
+        if (na)
+            atomicAdd(a.n_acc, (unsigned long long)na);
+        if (nm)
+            atomicAdd(a.n_changed, (unsigned long long)nm);
     }
+    for (int k = threadIdx.x; k < nrep; k += blockDim.x)
+        if (s_dE[k])
+            atomicAdd(&a.E[r0 + k], s_dE[k]);
 }
 
 // Training records of every (replica, column): X = (phi/8, beta), Y = spins
@@ -827,16 +918,46 @@ int32_t build_colours(ising_s* g)
     if (!g->colour_off.empty())
         return ISING_OK;
     const int S = g->S;
+    // spatial neighbours of each site (slice 0 rows hold the spatial edges)
+    std::vector<std::vector<int>> nbr(S);
+    for (int q = 0; q < S; ++q) {
+        for (int e = g->row_ptr[q]; e < g->row_ptr[q + 1]; ++e)
+            if (g->col[e] < S && g->col[e] != q)
+                nbr[q].push_back(g->col[e]);
+        std::sort(nbr[q].begin(), nbr[q].end());
+        nbr[q].erase(std::unique(nbr[q].begin(), nbr[q].end()), nbr[q].end());
+    }
+    // smallest-last order: repeatedly remove a site of least remaining degree
+    // (lowest index on ties); greedy colouring in the reverse order uses at
+    // most (degeneracy + 1) colours, and fewer classes mean fewer launches
+    std::vector<int> deg(S);
+    std::set<std::pair<int, int>> heap;
+    for (int q = 0; q < S; ++q) {
+        deg[q] = int(nbr[q].size());
+        heap.insert({deg[q], q});
+    }
+    std::vector<int> order;
+    std::vector<char> gone(S, 0);
+    while (!heap.empty()) {
+        const int q = heap.begin()->second;
+        heap.erase(heap.begin());
+        gone[q] = 1;
+        order.push_back(q);
+        for (int j : nbr[q])
+            if (!gone[j]) {
+                heap.erase({deg[j], j});
+                heap.insert({--deg[j], j});
+            }
+    }
     std::vector<int> colour(S, -1);
     int ncol = 0;
     std::vector<int> seen;
-    for (int q = 0; q < S; ++q) {  // slice 0 rows hold the spatial edges of site q
+    for (auto it = order.rbegin(); it != order.rend(); ++it) {
+        const int q = *it;
         seen.assign(size_t(ncol) + 1, 0);
-        for (int e = g->row_ptr[q]; e < g->row_ptr[q + 1]; ++e) {
-            const int c = g->col[e];
-            if (c < S && colour[c] >= 0)
-                seen[colour[c]] = 1;
-        }
+        for (int j : nbr[q])
+            if (colour[j] >= 0)
+                seen[colour[j]] = 1;
         int k = 0;
         while (seen[k])
             ++k;
@@ -870,6 +991,8 @@ int32_t build_colours(ising_s* g)
         e = zalloc(&g->d_sp_nbr, sp_nbr.size());
     if (e == cudaSuccess && !sp_nbr.empty())
         e = cudaMemcpy(g->d_sp_nbr, sp_nbr.data(), sp_nbr.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = zalloc(&g->d_colbits, size_t(g->R) * S);
     if (e != cudaSuccess) {
         g->colour_off.clear();
         return cuda_err(e, "colour classes");
@@ -898,6 +1021,7 @@ LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
     a.betas32 = g->d_betas32;
     a.sp_off = g->d_sp_off;
     a.sp_nbr = g->d_sp_nbr;
+    a.colbits = g->d_colbits;
     a.seed = g->seed;
     a.inst = g->inst;
     a.pass = uint32_t(g->learned_passes);
@@ -1220,6 +1344,8 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
     if (h->M != m->M)
         return isg_fail(ISING_ERR_INVALID_ARG, "the handle's slice count differs from the network's");
     const long long total = (long long)h->R * h->S;
+    if (total > (1LL << 31) - 256)
+        return isg_fail(ISING_ERR_UNSUPPORTED, "learned passes need R * S below 2^31");
     if (trace && trace->capacity < total)
         return isg_fail(ISING_ERR_INVALID_ARG, "trace capacity below R * S rows");
     int32_t rc = build_colours(h);
@@ -1238,6 +1364,10 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
         LCK(ensure_pass(m, maxpad));
     }
     LCK(cudaMemsetAsync(m->n_acc, 0, 3 * sizeof(unsigned long long), st));
+    {
+        const LearnedArgs a = learned_args(h, m);
+        learned_colbits_kernel<<<cdiv(total, 256), 256, 0, st>>>(a);
+    }
     long long done = 0;
     for (size_t c = 0; c + 1 < h->colour_off.size(); ++c) {
         const int ncols = h->colour_off[c + 1] - h->colour_off[c];
@@ -1248,7 +1378,7 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
         a.rows = rows;
         a.sites = h->d_colour_sites + h->colour_off[c];
         a.fp64_only = (flags & ISING_LEARNED_FP64_ONLY) ? 1 : 0;
-        learned_gather_kernel<<<cdiv(rows_pad, 8), 256, 0, st>>>(a, rows_pad);
+        learned_gather_kernel<<<cdiv(rows_pad, 128), 128, 0, st>>>(a, rows_pad);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (m->profiling) {
             LCK(cudaEventCreate(&e0));
@@ -1261,7 +1391,7 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
             m->ev_pending.emplace_back(e0, e1);
             m->ev_rows.push_back(rows);
         }
-        learned_mh_kernel<<<cdiv(rows, 8), 256, 0, st>>>(a);
+        learned_mh_kernel<<<cdiv(rows, kMhRows), kMhThreads, 0, st>>>(a);
         LCK(cudaGetLastError());
         if (trace) {
             auto d2h = [&](void* dst, const void* src, size_t bytes) {
@@ -1283,6 +1413,14 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
             }
         }
         done += rows;
+    }
+    {
+        const LearnedArgs a = learned_args(h, m);
+        if (h->field_bits == 16)
+            learned_fields_kernel<int16_t><<<cdiv(total, 256), 256, 0, st>>>(a);
+        else
+            learned_fields_kernel<int><<<cdiv(total, 256), 256, 0, st>>>(a);
+        LCK(cudaGetLastError());
     }
     ++h->learned_passes;
     if (!stats && !trace)

@@ -3,18 +3,25 @@
 // 128 rows, bf16 operands, FP32 accumulation in tensor memory.
 //
 // One CTA per SM, persistent over tiles, nine warps.  Warp 8 is the producer:
-// it issues the 1-D bulk copies (W1 and W3 once, X tiles double-buffered, the
-// four 32 KB K chunks of W2 streamed from L2 through two buffers) and the
-// MMAs.  Warps 0-7 run the epilogues (warp e reads TMEM lanes = rows
-// 32 (e % 4) .. +31 and half of each 64-column chunk): TMEM -> +bias, ReLU
-// -> bf16 -> the hidden activation H in shared memory in the operand layout,
-// 64 columns (one K chunk of the next
-// layer) at a time, each chunk signalled on its own mbarrier so that the next
-// layer's MMAs on that chunk start while the warps convert the next chunk.
-// TMEM (512 columns): layer 1 accumulates in columns 0..255, layer 2 in
-// 256..511 and layer 3 in 256..287 (free once layer 2's first chunk has been
-// read), so layer 1 of the next tile overlaps layers 2 and 3 of this one.
-// H1 and H2 never leave the SM.
+// it issues the 1-D bulk copies (W1, W2 and W3 once: all three stay resident
+// in shared memory; X tiles double-buffered) and the MMAs.  Warps 0-7 run the
+// epilogues.  Epilogue warp e reads the TMEM lanes of quadrant e % 4 (rows
+// 32 (e % 4) .. +31) and the half h = e / 4 of the accumulator's columns,
+// 32 columns at a time: + bias, ReLU, bf16 pairs, stored back into TMEM in
+// columns of its own half that it has already read (the hidden activation
+// is packed two per 32-bit column).  The next layer takes that activation as
+// its A operand straight from TMEM, so H1 and H2 never leave tensor memory.
+// Each 32-column step of all eight warps is signalled on its own mbarrier
+// and the next layer's MMAs on that K range start while the warps convert
+// the next step.
+//
+// TMEM (512 columns): layer 1 accumulates in 0..255 and H1 is packed in
+// place into 0..63 and 128..191; layer 2 accumulates in 256..511 and H2 is
+// packed into the columns of layer 1 that are no longer used, 64..127 and
+// 192..255; layer 3 accumulates in 256..287, which the first step of layer
+// 2's epilogue has read.  Layer 1 of the next tile (columns 0..255) is
+// issued right after layer 3 of this one; layer 2 of the next tile waits for
+// the first step of its own epilogue, which follows the reads of layer 3.
 //
 // Every wait is bounded.  A role whose wait gives up raises the error flag
 // and an abort flag the other roles poll; the producer then drains its
@@ -30,21 +37,19 @@ namespace {
 constexpr long long kPolls = 1LL << 22;
 constexpr int kXTile = 128 * 128;     // bytes of one X tile (128 rows x 64 bf16)
 constexpr int kW1 = 256 * 128;        // W1 tile bytes
-constexpr int kW3Chunk = 32 * 128;    // one K chunk of W3
-constexpr int kW2Chunk = 256 * 128;   // one K chunk of W2
-constexpr int kHChunk = 128 * 128;    // one K chunk of H
+constexpr int kW3Chunk = 32 * 128;    // one K chunk (64) of W3
+constexpr int kW2Chunk = 256 * 128;   // one K chunk (64) of W2
 constexpr int kOffW1 = 0;
 constexpr int kOffW3 = kOffW1 + kW1;
-constexpr int kOffX = kOffW3 + 4 * kW3Chunk;
-constexpr int kOffH = kOffX + 2 * kXTile;
-constexpr int kOffW2 = kOffH + 4 * kHChunk;
-constexpr int kSmem = kOffW2 + 2 * kW2Chunk;  // 212992 bytes
-constexpr int kEpiWarps = 8;                  // two per TMEM lane quadrant
+constexpr int kOffW2 = kOffW3 + 4 * kW3Chunk;
+constexpr int kOffX = kOffW2 + 4 * kW2Chunk;
+constexpr int kSmem = kOffX + 2 * kXTile;  // 212992 bytes
+constexpr int kEpiWarps = 8;               // two per TMEM lane quadrant
 constexpr int kThreads = 32 * (kEpiWarps + 1);  // + 1 producer warp
-constexpr uint32_t kD1 = 0, kD2 = 256, kD3 = 256;  // TMEM column bases
+constexpr uint32_t kD1 = 0, kH1 = 0, kH2 = 64, kD2 = 256, kD3 = 256;  // TMEM column bases
 
 struct Bars {
-    uint64_t w, x[2], full[2], free[2], m1, m2, m3, h1[4], h2[4];
+    uint64_t w, x[2], m1, m2, m3, h1[4], h2[4];
 };
 
 // Bounded wait that also gives up when another role has aborted.
@@ -72,39 +77,53 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 
 // Phase bookkeeping of one mbarrier as seen by the producer.
 struct Phase {
-    uint32_t issued = 0, waited = 0;
+    uint32_t issued = 0;
 };
 
-// Epilogue of one 64-column chunk of a hidden layer by epilogue warp e: rows
-// 32 (e % 4) + lane (the TMEM lanes of its quadrant), columns 32 (e / 4) ..
-// +31 of the chunk: + bias, ReLU, bf16, written into K chunk c of H in the
-// operand layout.
-__device__ __forceinline__ void hidden_chunk(uint32_t tmem, uint32_t dcol, int c, int e, int lane,
-                                             const float* bias, unsigned char* H)
+// Epilogue of a hidden layer by epilogue warp e, in four steps j: the
+// accumulator's columns dcol + 128 h + 32 j .. +31 (h = e / 4) of the rows of
+// lane quadrant e % 4: + bias, ReLU, bf16 pairs written to columns
+// ocol + 128 h + 16 j .. +15 (K elements 128 h + 32 j .. +31 of the next
+// layer), then an arrival on hbar[j].  For layer 1 ocol = dcol: the output
+// goes into columns this warp has already read.  The load of step j + 1 is
+// in flight while step j is converted and stored.
+__device__ __forceinline__ void hidden_layer(uint32_t tmem, uint32_t dcol, uint32_t ocol, int e,
+                                             const float* bias, uint64_t* hbar)
 {
-    const int quad = e & 3, row = 32 * quad + lane;
-    {
-        const int n0 = 64 * c + 32 * (e >> 2);
-        float v[32];
-        tc::tmem_ld32(tmem + (uint32_t(32 * quad) << 16) + dcol + uint32_t(n0), v);
+    const uint32_t lanes = uint32_t(32 * (e & 3)) << 16;
+    const int h = e >> 2;
+    uint32_t ra[32], rb[32];
+    tc::tmem_ld32_async(tmem + lanes + dcol + uint32_t(128 * h), ra);
+    auto step = [&](int j, uint32_t (&cur)[32], uint32_t (&nxt)[32]) {
+        tc::tmem_wait_ld(cur);
+        if (j < 3)
+            tc::tmem_ld32_async(tmem + lanes + dcol + uint32_t(128 * h + 32 * (j + 1)), nxt);
+        const int n0 = 128 * h + 32 * j;
         uint32_t w[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const float x0 = fmaxf(v[2 * i] + bias[n0 + 2 * i], 0.f);
-            const float x1 = fmaxf(v[2 * i + 1] + bias[n0 + 2 * i + 1], 0.f);
-            const __nv_bfloat162 p = __floats2bfloat162_rn(x0, x1);
+            const float2 b = *reinterpret_cast<const float2*>(bias + n0 + 2 * i);
+            const __nv_bfloat162 p = __floats2bfloat162_rn(fmaxf(__uint_as_float(cur[2 * i]) + b.x, 0.f),
+                                                           fmaxf(__uint_as_float(cur[2 * i + 1]) + b.y, 0.f));
             w[i] = *reinterpret_cast<const uint32_t*>(&p);
         }
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const int k = n0 + 8 * g;
-            *reinterpret_cast<uint4*>(H + tiled_offset(128, row, k)) =
-                make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
-        }
-    }
-    // the chunk is visible to the tensor core and its TMEM reads are done
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
+        tc::tmem_st16(tmem + lanes + ocol + uint32_t(128 * h + 16 * j), w);
+        tc::tmem_wait_st();
+        // the step's TMEM reads and writes are done before the arrival
+        tc::fence_before_sync();
+        mbar_arrive(&hbar[j]);
+    };
+    step(0, ra, rb);
+    step(1, rb, ra);
+    step(2, ra, rb);
+    step(3, rb, ra);
+}
+
+// Byte address of K elements k0 .. k0+15 of a weight matrix stored as K
+// chunks of 64 (chunk bytes apart), each in the canonical layout
+__device__ __forceinline__ uint32_t weight_k(uint32_t base, int chunk_bytes, int k0)
+{
+    return base + uint32_t((k0 >> 6) * chunk_bytes + ((k0 & 63) >> 4) * 256);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedArgs a)
@@ -113,11 +132,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
     constexpr uint32_t IDESC32 = tc::idesc_bf16(128, 32);
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ Bars bars;
-    __shared__ float sb1[256], sb2[256], sb3[32];
+    __shared__ __align__(16) float sb1[256], sb2[256], sb3[32];
     __shared__ uint32_t tslot;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* H = smem + kOffH;
     volatile int* abort = &s_abort;
 
     for (int i = tid; i < 256; i += kThreads) {
@@ -133,11 +151,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
         mbar_init(&bars.m1, 1);
         mbar_init(&bars.m2, 1);
         mbar_init(&bars.m3, 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 2; ++b)
             mbar_init(&bars.x[b], 1);
-            mbar_init(&bars.full[b], 1);
-            mbar_init(&bars.free[b], 1);
-        }
         for (int c = 0; c < 4; ++c) {
             mbar_init(&bars.h1[c], 32 * kEpiWarps);
             mbar_init(&bars.h2[c], 32 * kEpiWarps);
@@ -160,7 +175,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
         if (lane == 0 && n_it > 0) {
             const unsigned char* gX = static_cast<const unsigned char*>(a.X);
             const unsigned char* gW2 = static_cast<const unsigned char*>(a.W2t);
-            Phase ph_w, ph_x[2], ph_full[2], ph_free[2], ph_m1, ph_m2, ph_m3;
+            const uint32_t w1 = smem_u32(smem + kOffW1), w2 = smem_u32(smem + kOffW2),
+                           w3 = smem_u32(smem + kOffW3);
+            Phase ph_w, ph_x[2], ph_m1, ph_m2, ph_m3;
             auto load_x = [&](int it) {
                 const int b = it & 1;
                 const size_t tile = size_t(blockIdx.x) + size_t(it) * G;
@@ -168,73 +185,77 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                 bulk_g2s(smem + kOffX + b * kXTile, gX + tile * kXTile, kXTile, &bars.x[b]);
                 ++ph_x[b].issued;
             };
-            auto load_w2 = [&](uint32_t n) {  // K chunk n & 3 of W2 into buffer n & 1
-                const int b = int(n & 1u);
-                mbar_expect_tx(&bars.full[b], kW2Chunk);
-                bulk_g2s(smem + kOffW2 + b * kW2Chunk, gW2 + size_t(n & 3u) * kW2Chunk, kW2Chunk,
-                         &bars.full[b]);
-                ++ph_full[b].issued;
-            };
             auto commit = [&](uint64_t* bar, Phase& ph) {
                 tc::mma_commit(bar);
                 ++ph.issued;
             };
             auto mma1 = [&](int it) {  // D1 = X W1^T
-                const uint32_t xa = smem_u32(smem + kOffX + (it & 1) * kXTile), wa = smem_u32(smem + kOffW1);
+                const uint32_t xa = smem_u32(smem + kOffX + (it & 1) * kXTile);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    tc::mma_bf16(tmem + kD1, tc::smem_desc(xa + kk * 256), tc::smem_desc(wa + kk * 256),
-                                 IDESC256, kk > 0 ? 1u : 0u);
+                    tc::mma_bf16(tmem + kD1, tc::smem_desc(xa + kk * 256), tc::smem_desc(w1 + kk * 256), IDESC256,
+                                 kk > 0 ? 1u : 0u);
                 commit(&bars.m1, ph_m1);
             };
-            mbar_expect_tx(&bars.w, kW1 + 4 * kW3Chunk);
+            // the next layer on the K elements of epilogue step c: 32c .. +31
+            // (first half of the columns) and 128 + 32c .. +31 (second half),
+            // A packed in TMEM at hcol + 128 h + 16 c
+            auto mma_step = [&](uint32_t dcol, uint32_t hcol, uint32_t wbase, int chunk_bytes, uint32_t idesc,
+                                int c) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const int k0 = 128 * h + 32 * c + 16 * s;
+                        tc::mma_bf16_tmem_a(tmem + dcol, tmem + hcol + uint32_t(128 * h + 16 * c + 8 * s),
+                                            tc::smem_desc(weight_k(wbase, chunk_bytes, k0)), idesc,
+                                            (c == 0 && h == 0 && s == 0) ? 0u : 1u);
+                    }
+            };
+            mbar_expect_tx(&bars.w, kW1 + 4 * kW3Chunk + 4 * kW2Chunk);
             bulk_g2s(smem + kOffW1, a.W1t, kW1, &bars.w);
             bulk_g2s(smem + kOffW3, a.W3t, 4 * kW3Chunk, &bars.w);
+            for (int c = 0; c < 4; ++c)
+                bulk_g2s(smem + kOffW2 + c * kW2Chunk, gW2 + size_t(c) * kW2Chunk, kW2Chunk, &bars.w);
             ++ph_w.issued;
             load_x(0);
             if (n_it > 1)
                 load_x(1);
-            load_w2(0);
-            load_w2(1);
             bool ok = wait_phase(&bars.w, 0, abort) && wait_phase(&bars.x[0], 0, abort);
             if (ok) {
                 tc::fence_after_sync();
                 mma1(0);
             }
             for (int it = 0; ok && it < n_it; ++it) {
+                const uint32_t par = uint32_t(it) & 1u;
                 // X buffer of this tile is free once layer 1 has read it
-                if (!(ok = wait_phase(&bars.m1, uint32_t(it) & 1u, abort)))
+                if (!(ok = wait_phase(&bars.m1, par, abort)))
                     break;
                 if (it + 2 < n_it)
                     load_x(it + 2);
-                // layer 2, chunk by chunk as the epilogue of layer 1 delivers H1
+                // layer 2, step by step as the epilogue of layer 1 delivers H1
                 for (int c = 0; c < 4 && ok; ++c) {
-                    const uint32_t n = 4u * uint32_t(it) + uint32_t(c);
-                    const int b = int(n & 1u);
-                    if (!(ok = wait_phase(&bars.full[b], (n >> 1) & 1u, abort) &&
-                               wait_phase(&bars.h1[c], uint32_t(it) & 1u, abort)))
+                    if (!(ok = wait_phase(&bars.h1[c], par, abort)))
                         break;
                     tc::fence_after_sync();
-                    const uint32_t ha = smem_u32(H + c * kHChunk), wa = smem_u32(smem + kOffW2 + b * kW2Chunk);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc::mma_bf16(tmem + kD2, tc::smem_desc(ha + kk * 256), tc::smem_desc(wa + kk * 256),
-                                     IDESC256, (c > 0 || kk > 0) ? 1u : 0u);
-                    commit(&bars.free[b], ph_free[b]);
-                    // refill the buffer of chunk n - 1 with chunk n + 1 once its MMAs are done
-                    const bool next_exists = c < 3 || it + 1 < n_it;
-                    if (n >= 1u && next_exists) {
-                        const int pb = int((n - 1u) & 1u);
-                        if ((ok = wait_phase(&bars.free[pb], ph_free[pb].waited & 1u, abort))) {
-                            ++ph_free[pb].waited;
-                            load_w2(n + 1u);
-                        }
-                    }
+                    mma_step(kD2, kH1, w2, kW2Chunk, IDESC256, c);
                 }
                 if (!ok)
                     break;
                 commit(&bars.m2, ph_m2);
-                // layer 1 of the next tile: D1 was last read by this tile's epilogue 1
+                // layer 3, step by step as the epilogue of layer 2 delivers H2;
+                // it accumulates in columns 256..287, read by the first step
+                for (int c = 0; c < 4 && ok; ++c) {
+                    if (!(ok = wait_phase(&bars.h2[c], par, abort)))
+                        break;
+                    tc::fence_after_sync();
+                    mma_step(kD3, kH2, w3, kW3Chunk, IDESC32, c);
+                }
+                if (!ok)
+                    break;
+                commit(&bars.m3, ph_m3);
+                // layer 1 of the next tile: columns 0..255 hold only this
+                // tile's H1, read by the layer-2 MMAs issued before
                 if (it + 1 < n_it) {
                     const int nb = (it + 1) & 1;
                     if (!(ok = wait_phase(&bars.x[nb], uint32_t((it + 1) >> 1) & 1u, abort)))
@@ -242,19 +263,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                     tc::fence_after_sync();
                     mma1(it + 1);
                 }
-                // layer 3, chunk by chunk as the epilogue of layer 2 delivers H2
-                for (int c = 0; c < 4 && ok; ++c) {
-                    if (!(ok = wait_phase(&bars.h2[c], uint32_t(it) & 1u, abort)))
-                        break;
-                    tc::fence_after_sync();
-                    const uint32_t ha = smem_u32(H + c * kHChunk), wa = smem_u32(smem + kOffW3 + c * kW3Chunk);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc::mma_bf16(tmem + kD3, tc::smem_desc(ha + kk * 256), tc::smem_desc(wa + kk * 256),
-                                     IDESC32, (c > 0 || kk > 0) ? 1u : 0u);
-                }
-                if (ok)
-                    commit(&bars.m3, ph_m3);
             }
             if (!ok) {
                 fail();
@@ -266,11 +274,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                 last(&bars.m1, ph_m1);
                 last(&bars.m2, ph_m2);
                 last(&bars.m3, ph_m3);
-                for (int b = 0; b < 2; ++b) {
-                    last(&bars.free[b], ph_free[b]);
-                    last(&bars.full[b], ph_full[b]);
+                for (int b = 0; b < 2; ++b)
                     last(&bars.x[b], ph_x[b]);
-                }
                 last(&bars.w, ph_w);
             }
         }
@@ -283,19 +288,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                 break;
             }
             tc::fence_after_sync();
-            for (int c = 0; c < 4; ++c) {
-                hidden_chunk(tmem, kD1, c, warp, lane, sb1, H);
-                mbar_arrive(&bars.h1[c]);
-            }
+            hidden_layer(tmem, kD1, kH1, warp, sb1, bars.h1);
             if (!wait_phase(&bars.m2, par, abort)) {
                 fail();
                 break;
             }
             tc::fence_after_sync();
-            for (int c = 0; c < 4; ++c) {
-                hidden_chunk(tmem, kD2, c, warp, lane, sb2, H);
-                mbar_arrive(&bars.h2[c]);
-            }
+            hidden_layer(tmem, kD2, kH2, warp, sb2, bars.h2);
             if (!wait_phase(&bars.m3, par, abort)) {
                 fail();
                 break;
@@ -312,6 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                         make_float4(v[4 * i] + sb3[4 * i], v[4 * i + 1] + sb3[4 * i + 1],
                                     v[4 * i + 2] + sb3[4 * i + 2], v[4 * i + 3] + sb3[4 * i + 3]);
             }
+            // the D3 reads are done before the next tile's first arrival,
+            // which layer 2 of that tile (overwriting 256..287) waits for
             tc::fence_before_sync();
         }
     }
