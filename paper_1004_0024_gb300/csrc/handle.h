@@ -22,6 +22,7 @@ struct ising_s {
     int* d_sp_off = nullptr;  // [S+1] spatial neighbour list of each site
     int2* d_sp_nbr = nullptr; // (site, J) entries
     uint32_t* d_colbits = nullptr;  // [R][S] bit t = (spin (t, q) > 0), kept during a learned pass
+    int sp_simd = 0;                // every site has sum_j 2 |J_qj| <= 127 over its spatial neighbours
     long long* d_obs = nullptr;  // [R] per-slot magnetisation (ising_read_observables)
     // graph
     int n = 0, M = 1, S = 0, W = 1, Mp = 4, D0 = 0, D = 0, max_sp_deg = 0, max_sp_J = 0;

@@ -191,11 +191,13 @@ struct LearnedArgs {
     const int* sp_off; // [S+1] spatial neighbour list of each site
     const int2* sp_nbr; // (site, J) entries
     uint32_t* colbits;  // [R][S] column bits: bit t = (spin (t, q) > 0)
+    int sp_simd;        // every site has sum_j 2 |J_qj| <= 127 (byte-lane phi)
     int* phi;          // [rows][32]
     bf16* X;           // [rows_pad][64]
     const float* L;    // [rows_pad][32]
     uint32_t seed, inst, pass;
     uint32_t *old_bits, *prop_bits;
+    uint32_t* acc_word;  // [rows] the acceptance word of each row (Philox word 32)
     uint8_t* accepted;
     unsigned long long* n_acc;
     unsigned long long* n_exact;  // decisions taken by the FP64 product
@@ -253,14 +255,39 @@ __global__ void __launch_bounds__(256) learned_colbits_kernel(const LearnedArgs 
 // phi_t = h_q + sum over the spatial neighbours j of site q of J_qj s_(t, j)
 // for t < 32 (every slice holds the same h and couplings), from the column
 // bits of replica r's neighbours: s = 2 b - 1, so phi_t = h_q - sum_j J_qj +
-// sum_j 2 J_qj b_j(t).
+// sum_j 2 J_qj b_j(t).  The last sum is kept in byte lanes, four slices per
+// 32-bit word starting at 128 per byte: each neighbour spreads four of its
+// bits to the low bit of four bytes (x * 0x00204081 & 0x01010101) and adds
+// 2 J times that.  Every partial sum stays within 128 -+ sum_j 2 |J_qj|, so
+// with that bound at most 127 (checked on the host: simd) no byte carries or
+// borrows into the next.  Otherwise the sum is formed slice by slice.
 __device__ __forceinline__ void column_phi(const LearnedArgs& a, const uint32_t* cb, int q, int (&f)[kOut])
 {
     int base = a.h[q];
+    const int e0 = a.sp_off[q], e1 = a.sp_off[q + 1];
+    if (a.sp_simd) {
+        uint32_t acc[kOut / 4];
+#pragma unroll
+        for (int w = 0; w < kOut / 4; ++w)
+            acc[w] = 0x80808080u;
+        for (int e = e0; e < e1; ++e) {
+            const int2 nb = a.sp_nbr[e];
+            const uint32_t b = cb[nb.x];
+            const uint32_t j2 = uint32_t(2 * nb.y);
+            base -= nb.y;
+#pragma unroll
+            for (int w = 0; w < kOut / 4; ++w)
+                acc[w] += ((((b >> (4 * w)) & 0xFu) * 0x00204081u) & 0x01010101u) * j2;
+        }
+#pragma unroll
+        for (int t = 0; t < kOut; ++t)
+            f[t] = base - 128 + int((acc[t >> 2] >> (8 * (t & 3))) & 0xFFu);
+        return;
+    }
 #pragma unroll
     for (int t = 0; t < kOut; ++t)
         f[t] = 0;
-    for (int e = a.sp_off[q]; e < a.sp_off[q + 1]; ++e) {
+    for (int e = e0; e < e1; ++e) {
         const int2 nb = a.sp_nbr[e];
         const uint32_t b = cb[nb.x];
         const int j2 = 2 * nb.y;
@@ -321,6 +348,9 @@ __global__ void __launch_bounds__(128) learned_gather_kernel(const LearnedArgs a
         }
     }
     a.old_bits[row] = cb[q];
+    // word 32 of the row (block 8, counter 2 + 32), drawn here where the
+    // issue slots are idle behind the loads
+    a.acc_word[row] = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 34u), a.seed, uint32_t(r)).x;
 }
 
 // Local fields of every spin after a pass: f_(t,q) = phi_t of column q plus
@@ -390,7 +420,7 @@ __device__ __forceinline__ float c_to_float(unsigned long long c)
 
 // One MH column move per group of 8 lanes (kMhLanes): lane g of the group
 // draws Philox block g, proposes slices 4g .. 4g+3 and adds their terms; the
-// group combines bits and sums by shuffles.  Words: Philox4x32-10, key
+// group combines bits and sums by shuffles (word 32 was drawn by the gather).  Words: Philox4x32-10, key
 // (seed, r), counter (q, pass, instance, 2 + 4 j) gives words 4j .. 4j+3;
 // word t < M proposes slice t, word 32 decides acceptance.  Bit t is drawn +1
 // iff u_t < p_t 2^32 (p_t the FP32 sigmoid of the logit), i.e. iff u_t < c_t
@@ -469,8 +499,7 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
         for (int o = kMhLanes / 2; o > 0; o >>= 1)
             dE += __shfl_xor_sync(gmask, dE, o);
         if (g == 0) {
-            const uint32_t ua =
-                philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 34u), a.seed, uint32_t(r)).x;
+            const uint32_t ua = a.acc_word[row];
             const float bdE = a.betas32[a.temp_of_slot[r]] * float(dE);
             const float la = -bdE + lq;
             const float lu = logf((float(ua) + 0.5f) * 2.3283064365386963e-10f);
@@ -612,10 +641,10 @@ struct ising_mlp_s {
     unsigned long long* n_acc = nullptr;
     // learned-pass workspace, sized for Pcap rows
     long long Pcap = 0;
-    bf16 *PX = nullptr, *PH1 = nullptr, *PH2 = nullptr;
+    bf16* PX = nullptr;
     float* PL = nullptr;
     int* Pphi = nullptr;
-    uint32_t *Pold = nullptr, *Pprop = nullptr;
+    uint32_t *Pold = nullptr, *Pprop = nullptr, *Pua = nullptr;
     uint8_t* Pacc = nullptr;
 
     // profiling of the fused network kernel in learned passes
@@ -823,19 +852,14 @@ cudaError_t ensure_pass(ising_mlp_s* m, long long rows_pad)
     if (rows_pad <= m->Pcap)
         return cudaSuccess;
     zfree(m->PX);
-    zfree(m->PH1);
-    zfree(m->PH2);
     zfree(m->PL);
     zfree(m->Pphi);
     zfree(m->Pold);
     zfree(m->Pprop);
+    zfree(m->Pua);
     zfree(m->Pacc);
     m->Pcap = 0;
     cudaError_t e = zalloc(&m->PX, size_t(rows_pad) * kIn);
-    if (e == cudaSuccess)
-        e = zalloc(&m->PH1, size_t(rows_pad) * kHid);
-    if (e == cudaSuccess)
-        e = zalloc(&m->PH2, size_t(rows_pad) * kHid);
     if (e == cudaSuccess)
         e = zalloc(&m->PL, size_t(rows_pad) * kOut);
     if (e == cudaSuccess)
@@ -844,6 +868,8 @@ cudaError_t ensure_pass(ising_mlp_s* m, long long rows_pad)
         e = zalloc(&m->Pold, size_t(rows_pad));
     if (e == cudaSuccess)
         e = zalloc(&m->Pprop, size_t(rows_pad));
+    if (e == cudaSuccess)
+        e = zalloc(&m->Pua, size_t(rows_pad));
     if (e == cudaSuccess)
         e = zalloc(&m->Pacc, size_t(rows_pad));
     if (e == cudaSuccess)
@@ -879,8 +905,7 @@ void free_mlp(ising_mlp_s* m)
 {
     resolve_profile(m);
     bf16** b[] = {&m->W1b, &m->W2b, &m->W3b, &m->W2tb, &m->W3tb, &m->Xd, &m->Xb, &m->H1, &m->H2, &m->dL,
-                  &m->dH2, &m->dH1, &m->XT, &m->H1T, &m->H2T, &m->dLT, &m->dH2T, &m->dH1T, &m->PX, &m->PH1,
-                  &m->PH2};
+                  &m->dH2, &m->dH1, &m->XT, &m->H1T, &m->H2T, &m->dLT, &m->dH2T, &m->dH1T, &m->PX};
     for (auto p : b)
         zfree(*p);
     zfree(m->W1t);
@@ -901,6 +926,7 @@ void free_mlp(ising_mlp_s* m)
     zfree(m->Pphi);
     zfree(m->Pold);
     zfree(m->Pprop);
+    zfree(m->Pua);
     zfree(m->Pacc);
 }
 
@@ -974,12 +1000,18 @@ int32_t build_colours(ising_s* g)
     }
     std::vector<int> sp_off(1, 0);
     std::vector<int2> sp_nbr;
+    long long max_j2 = 0;
     for (int q = 0; q < S; ++q) {
+        long long j2 = 0;
         for (int e = g->row_ptr[q]; e < g->row_ptr[q + 1]; ++e)
-            if (g->col[e] < S)
+            if (g->col[e] < S) {
                 sp_nbr.push_back(make_int2(g->col[e], g->J[e]));
+                j2 += 2LL * std::llabs((long long)g->J[e]);
+            }
+        max_j2 = std::max(max_j2, j2);
         sp_off.push_back(int(sp_nbr.size()));
     }
+    g->sp_simd = max_j2 <= 127 ? 1 : 0;
     cudaError_t e = zalloc(&g->d_colour_sites, sites.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(g->d_colour_sites, sites.data(), sites.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -1022,6 +1054,7 @@ LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
     a.sp_off = g->d_sp_off;
     a.sp_nbr = g->d_sp_nbr;
     a.colbits = g->d_colbits;
+    a.sp_simd = g->sp_simd;
     a.seed = g->seed;
     a.inst = g->inst;
     a.pass = uint32_t(g->learned_passes);
@@ -1030,6 +1063,7 @@ LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
     a.L = m->PL;
     a.old_bits = m->Pold;
     a.prop_bits = m->Pprop;
+    a.acc_word = m->Pua;
     a.accepted = m->Pacc;
     a.n_acc = m->n_acc;
     a.n_exact = m->n_acc + 1;

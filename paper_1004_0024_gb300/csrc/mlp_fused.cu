@@ -80,6 +80,23 @@ struct Phase {
     uint32_t issued = 0;
 };
 
+// relu(v + b) of two FP32 values as a bf16 pair (v0 + b0 in the low half):
+// one packed FP32x2 add, then one converting instruction that also clamps
+// negatives to zero
+__device__ __forceinline__ uint32_t bias_relu_bf16x2(uint32_t v0, uint32_t v1, float b0, float b1)
+{
+    uint32_t r;
+    asm("{ .reg .b64 v, b, s; .reg .f32 lo, hi;\n"
+        "  mov.b64 v, {%1, %2};\n"
+        "  mov.b64 b, {%3, %4};\n"
+        "  add.rn.f32x2 s, v, b;\n"
+        "  mov.b64 {lo, hi}, s;\n"
+        "  cvt.rn.relu.bf16x2.f32 %0, hi, lo; }"
+        : "=r"(r)
+        : "r"(v0), "r"(v1), "f"(b0), "f"(b1));
+    return r;
+}
+
 // Epilogue of a hidden layer by epilogue warp e, in four steps j: the
 // accumulator's columns dcol + 128 h + 32 j .. +31 (h = e / 4) of the rows of
 // lane quadrant e % 4: + bias, ReLU, bf16 pairs written to columns
@@ -101,11 +118,10 @@ __device__ __forceinline__ void hidden_layer(uint32_t tmem, uint32_t dcol, uint3
         const int n0 = 128 * h + 32 * j;
         uint32_t w[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const float2 b = *reinterpret_cast<const float2*>(bias + n0 + 2 * i);
-            const __nv_bfloat162 p = __floats2bfloat162_rn(fmaxf(__uint_as_float(cur[2 * i]) + b.x, 0.f),
-                                                           fmaxf(__uint_as_float(cur[2 * i + 1]) + b.y, 0.f));
-            w[i] = *reinterpret_cast<const uint32_t*>(&p);
+        for (int i = 0; i < 8; ++i) {
+            const float4 b = *reinterpret_cast<const float4*>(bias + n0 + 4 * i);
+            w[2 * i] = bias_relu_bf16x2(cur[4 * i], cur[4 * i + 1], b.x, b.y);
+            w[2 * i + 1] = bias_relu_bf16x2(cur[4 * i + 2], cur[4 * i + 3], b.z, b.w);
         }
         tc::tmem_st16(tmem + lanes + ocol + uint32_t(128 * h + 16 * j), w);
         tc::tmem_wait_st();

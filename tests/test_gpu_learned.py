@@ -216,10 +216,13 @@ def _with_output_bias(net, bias):
 
 @pytest.mark.parametrize("model,rng_mode,bias", [("L4_M8", "philox", 0.0), ("L3_M2", "mt19937", 0.0),
                                                  ("L4_M3", "philox", 0.0), ("L3_M1", "mt19937", 0.0),
-                                                 ("ring_S5_M4", "philox", 1.5), ("L5_M32", "philox", -0.7)])
+                                                 ("ring_S5_M4", "philox", 1.5), ("L5_M32", "philox", -0.7),
+                                                 ("ring_S5_M4_J30", "mt19937", 0.0)])
 def test_learned_pass_replays_on_the_oracle(ising, model, rng_mode, bias):
+    # ring_S5_M4_J30: couplings up to 90, beyond the byte-lane bound
+    # (sum_j 2 |J| <= 127 per site) of the neighbour sums: the slice-by-slice path
     if model.startswith("ring"):
-        g = _ring_model()
+        g = _ring_model(jscale=30 if model.endswith("J30") else 1)
     else:
         L, M = (int(x[1:]) for x in model.split("_"))
         g = W.layered_graph(L, M, 5)
@@ -301,11 +304,12 @@ def test_sweeps_stay_bit_exact_after_learned_passes(ising):
 
 
 # ------------------------------------------- exactness of the MH correction
-def _ring_model(S=5, M=4, jtau=2, seed=4):
-    """S sites on a ring plus one chord, M slices in a Trotter ring."""
+def _ring_model(S=5, M=4, jtau=2, seed=4, jscale=1):
+    """S sites on a ring plus one chord, M slices in a Trotter ring; the
+    spatial couplings multiplied by jscale."""
     rng = np.random.default_rng(seed)
-    spatial = {(q, (q + 1) % S): int(rng.choice([-3, -2, -1, 1, 2, 3])) for q in range(S)}
-    spatial[(0, 2)] = int(rng.choice([-2, 2]))
+    spatial = {(q, (q + 1) % S): jscale * int(rng.choice([-3, -2, -1, 1, 2, 3])) for q in range(S)}
+    spatial[(0, 2)] = jscale * int(rng.choice([-2, 2]))
     hs = rng.integers(-2, 3, size=S)
     edges = {}
     for t in range(M):
