@@ -251,7 +251,7 @@ struct MlpFusedArgs {
     const void* X;
     const void *W1t, *W2t, *W3t;
     const float *b1, *b2, *b3;  // [256], [256], [32]
-    float* L;                   // [tiles * 128][32] logits
+    float* L;                   // [tiles][32][128] logits, each tile stored column by column
     int tiles;
     int* err;
 };

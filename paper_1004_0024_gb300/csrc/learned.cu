@@ -194,7 +194,7 @@ struct LearnedArgs {
     int sp_simd;        // every site has sum_j 2 |J_qj| <= 127 (byte-lane phi)
     int* phi;          // [rows][32]
     bf16* X;           // [rows_pad][64]
-    const float* L;    // [rows_pad][32]
+    const float* L;    // [rows_pad / 128][32][128]: logit t of row i at (i / 128, t, i % 128)
     uint32_t seed, inst, pass;
     uint32_t *old_bits, *prop_bits;
     uint32_t* acc_word;  // [rows] the acceptance word of each row (Philox word 32)
@@ -389,33 +389,19 @@ __device__ __forceinline__ int column_term(uint32_t bits, int t, int M, int phi,
     return e;
 }
 
-// c = ceil(p 2^32) for an FP32 p in [0, 1], in integer arithmetic: with
-// p = m 2^(x - 23) (m the 24-bit significand), p 2^32 = m 2^(x + 9).
-__device__ __forceinline__ unsigned long long ceil_p32(float p)
+// c_t = ceil(p_t 2^32) of slice t's logit, p_t = 1 / (1 + exp(-l)) in FP32,
+// as an FP32 value: p 2^32 is exact (a power-of-two scale) and so is its
+// ceiling (every integer below 2^24 is a float, and above 2^24 p 2^32 is
+// already an integer), so c is the integer ceil(p 2^32) exactly, at most 2^32
+__device__ __forceinline__ float proposal_c(float l)
 {
-    const uint32_t b = __float_as_uint(p);
-    if ((b & 0x7FFFFFFFu) == 0u)
-        return 0ull;
-    const int ex = int((b >> 23) & 0xFFu);
-    const unsigned long long m = (b & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
-    const int sh = (ex ? ex : 1) - 127 - 23 + 32;
-    if (sh >= 0)
-        return m << sh;
-    const int k = -sh;
-    return k >= 40 ? 1ull : (m + (1ull << k) - 1ull) >> k;
+    return ceilf(1.f / (1.f + expf(-l)) * 4294967296.f);
 }
 
-// c_t = ceil(p_t 2^32) of slice t's logit, p_t = 1 / (1 + exp(-l)) in FP32
-__device__ __forceinline__ unsigned long long proposal_c(float l)
+// u < c for a 32-bit word u and an integer-valued c in [0, 2^32]
+__device__ __forceinline__ bool word_below(uint32_t u, float c)
 {
-    return ceil_p32(1.f / (1.f + expf(-l)));
-}
-
-// FP32 value (round to nearest) of an integer c in [0, 2^32], converted from
-// 32 bits: a conversion from a 64-bit integer would occupy the FP64 pipe
-__device__ __forceinline__ float c_to_float(unsigned long long c)
-{
-    return (c >> 32) ? 4294967296.f : float(uint32_t(c));
+    return c >= 4294967296.f || u < uint32_t(c);
 }
 
 // One MH column move per group of 8 lanes (kMhLanes): lane g of the group
@@ -451,7 +437,7 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
         const int r = row / a.ncols, q = a.sites[row - r * a.ncols];
         const int M = a.M, S = a.S;
         const uint32_t old = a.old_bits[row];
-        const float* Lr = a.L + size_t(row) * kOut;
+        const float* Lr = a.L + size_t(row >> 7) * (128 * kOut) + (row & 127);  // logit t at Lr[128 t]
         const int jt = a.jtau[a.pos[q]];
         const bool live = 4 * g < M;
         uint32_t prop = 0u;
@@ -459,18 +445,20 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
         if (live) {
             const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(g)), a.seed,
                                           uint32_t(r));
-            const float4 l4 = *reinterpret_cast<const float4*>(Lr + 4 * g);
             const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
-            const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+            float lv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                lv[u] = Lr[size_t(4 * g + u) * 128];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int t = 4 * g + u;
                 if (t < M) {
-                    const unsigned long long c1 = proposal_c(lv[u]);
-                    const bool up = (unsigned long long)wv[u] < c1;
+                    const float c1 = proposal_c(lv[u]);
+                    const bool up = word_below(wv[u], c1);
                     prop |= uint32_t(up) << t;
                     if (up != bool((old >> t) & 1u)) {  // FP32 log of this bit's ratio
-                        const float cp = c_to_float(c1), cm = c_to_float(4294967296ull - c1);
+                        const float cp = c1, cm = 4294967296.f - c1;  // cm: 2^32 - c rounded once
                         const float term = logf(up ? cm / cp : cp / cm);
                         lq += term;
                         mag += fabsf(term);
@@ -523,7 +511,7 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
                 int en = 0, ed = 0, n = 0;
                 for (uint32_t ch = old ^ prop; ch; ch &= ch - 1u) {
                     const int b = __ffs(ch) - 1;
-                    const double cp = double(proposal_c(Lr[b])), cm = 4294967296.0 - cp;
+                    const double cp = double(proposal_c(Lr[size_t(b) * 128])), cm = 4294967296.0 - cp;
                     const bool ob = (old >> b) & 1u;
                     num *= ob ? cp : cm;
                     den *= ob ? cm : cp;
@@ -1258,14 +1246,14 @@ int32_t ising_mlp_forward(ising_mlp_t m, int32_t B, const float* X, float* L)
             std::memcpy(xt.data() + size_t(b >> 7) * 16384 + tiled_offset(128, b & 127, c), &x[size_t(b) * kIn + c], 2);
     LCK(cudaMemcpyAsync(m->PX, xt.data(), xt.size(), cudaMemcpyHostToDevice, st));
     LCK(forward_fused(m, st, rows_pad, m->PX, m->PL));
-    std::vector<float> l(size_t(B) * kOut);
+    std::vector<float> l(size_t(rows_pad) * kOut);  // tiles stored column by column
     LCK(cudaMemcpyAsync(l.data(), m->PL, sizeof(float) * l.size(), cudaMemcpyDeviceToHost, st));
     int32_t rc = check_err(m, st);
     if (rc)
         return rc;
     for (int b = 0; b < B; ++b)
         for (int t = 0; t < m->M; ++t)
-            L[size_t(b) * m->M + t] = l[size_t(b) * kOut + t];
+            L[size_t(b) * m->M + t] = l[size_t(b >> 7) * (128 * kOut) + size_t(t) * 128 + (b & 127)];
     return ISING_OK;
 }
 
@@ -1432,12 +1420,20 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
                 return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
             };
             LCK(d2h(trace->phi ? trace->phi + done * kOut : nullptr, m->Pphi, sizeof(int) * size_t(rows) * kOut));
-            LCK(d2h(trace->logits ? trace->logits + done * kOut : nullptr, m->PL,
-                    sizeof(float) * size_t(rows) * kOut));
+            std::vector<float> lt;  // logits, tiles stored column by column
+            if (trace->logits) {
+                lt.resize(size_t(rows_pad) * kOut);
+                LCK(cudaMemcpyAsync(lt.data(), m->PL, sizeof(float) * lt.size(), cudaMemcpyDeviceToHost, st));
+            }
             LCK(d2h(trace->old_bits ? trace->old_bits + done : nullptr, m->Pold, sizeof(uint32_t) * rows));
             LCK(d2h(trace->prop_bits ? trace->prop_bits + done : nullptr, m->Pprop, sizeof(uint32_t) * rows));
             LCK(d2h(trace->accepted ? trace->accepted + done : nullptr, m->Pacc, size_t(rows)));
             LCK(cudaStreamSynchronize(st));
+            if (trace->logits)
+                for (int i = 0; i < rows; ++i)
+                    for (int t = 0; t < kOut; ++t)
+                        trace->logits[(done + i) * kOut + t] =
+                            lt[size_t(i >> 7) * (128 * kOut) + size_t(t) * 128 + (i & 127)];
             for (int i = 0; i < rows; ++i) {
                 const int r = i / ncols;
                 if (trace->replica)

@@ -2,26 +2,27 @@
 // tcgen05 kernel: logits = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for tiles of
 // 128 rows, bf16 operands, FP32 accumulation in tensor memory.
 //
-// One CTA per SM, persistent over tiles, nine warps.  Warp 8 is the producer:
-// it issues the 1-D bulk copies (W1, W2 and W3 once: all three stay resident
-// in shared memory; X tiles double-buffered) and the MMAs.  Warps 0-7 run the
-// epilogues.  Epilogue warp e reads the TMEM lanes of quadrant e % 4 (rows
-// 32 (e % 4) .. +31) and the half h = e / 4 of the accumulator's columns,
-// 32 columns at a time: + bias, ReLU, bf16 pairs, stored back into TMEM in
-// columns of its own half that it has already read (the hidden activation
-// is packed two per 32-bit column).  The next layer takes that activation as
+// One CTA per SM, persistent over tiles, seventeen warps.  Warp 16 is the
+// producer: it issues the 1-D bulk copies (W1, W2 and W3 once: all three stay
+// resident in shared memory; X tiles double-buffered) and the MMAs.  Warps
+// 0-15 run the epilogues.  Epilogue warp e reads the TMEM lanes of quadrant
+// e % 4 (rows 32 (e % 4) .. +31) and the part k = e / 4 (64 columns) of the
+// accumulator, 32 columns at a time: + bias, ReLU, bf16 pairs, stored back
+// into TMEM in columns of its own part (the hidden activation is packed two
+// per 32-bit column).  The next layer takes that activation as
 // its A operand straight from TMEM, so H1 and H2 never leave tensor memory.
-// Each 32-column step of all eight warps is signalled on its own mbarrier
+// Each 32-column step of all epilogue warps is signalled on its own mbarrier
 // and the next layer's MMAs on that K range start while the warps convert
 // the next step.
 //
 // TMEM (512 columns): layer 1 accumulates in 0..255 and H1 is packed in
-// place into 0..63 and 128..191; layer 2 accumulates in 256..511 and H2 is
-// packed into the columns of layer 1 that are no longer used, 64..127 and
-// 192..255; layer 3 accumulates in 256..287, which the first step of layer
-// 2's epilogue has read.  Layer 1 of the next tile (columns 0..255) is
-// issued right after layer 3 of this one; layer 2 of the next tile waits for
-// the first step of its own epilogue, which follows the reads of layer 3.
+// place into the first 32 columns of each 64-column part (columns the part's
+// warp has read); layer 2 accumulates in 256..511 and H2 is packed in the
+// same way; layer 3 accumulates in 288..319, the second half of part 0 of
+// layer 2, once the epilogue of layer 2 is complete.  Layer 1 of the next
+// tile (columns 0..255) is issued right after layer 2 of this one, so it runs
+// while the warps convert layer 2; layer 2 of the next tile waits for the
+// first step of its own epilogue, which follows the reads of layer 3.
 //
 // Every wait is bounded.  A role whose wait gives up raises the error flag
 // and an abort flag the other roles poll; the producer then drains its
@@ -44,12 +45,17 @@ constexpr int kOffW3 = kOffW1 + kW1;
 constexpr int kOffW2 = kOffW3 + 4 * kW3Chunk;
 constexpr int kOffX = kOffW2 + 4 * kW2Chunk;
 constexpr int kSmem = kOffX + 2 * kXTile;  // 212992 bytes
-constexpr int kEpiWarps = 8;               // two per TMEM lane quadrant
+constexpr int kEpiWarps = 16;              // four per TMEM lane quadrant
 constexpr int kThreads = 32 * (kEpiWarps + 1);  // + 1 producer warp
-constexpr uint32_t kD1 = 0, kH1 = 0, kH2 = 64, kD2 = 256, kD3 = 256;  // TMEM column bases
+constexpr int kParts = kEpiWarps / 4;      // column parts of a 256-column accumulator
+constexpr int kPartCols = 256 / kParts;    // columns of one part (64)
+constexpr int kSteps = kPartCols / 32;     // 32-column epilogue steps per part (2)
+// TMEM column bases: H1 and H2 packed in place at the start of each part of
+// D1 and D2; D3 in the second half of part 0 of D2 (read by its last step)
+constexpr uint32_t kD1 = 0, kH1 = 0, kD2 = 256, kH2 = 256, kD3 = 256 + kPartCols / 2;
 
 struct Bars {
-    uint64_t w, x[2], m1, m2, m3, h1[4], h2[4];
+    uint64_t w, x[2], m1, m2, m3, h1[kSteps], h2[kSteps];
 };
 
 // Bounded wait that also gives up when another role has aborted.
@@ -97,25 +103,25 @@ __device__ __forceinline__ uint32_t bias_relu_bf16x2(uint32_t v0, uint32_t v1, f
     return r;
 }
 
-// Epilogue of a hidden layer by epilogue warp e, in four steps j: the
-// accumulator's columns dcol + 128 h + 32 j .. +31 (h = e / 4) of the rows of
-// lane quadrant e % 4: + bias, ReLU, bf16 pairs written to columns
-// ocol + 128 h + 16 j .. +15 (K elements 128 h + 32 j .. +31 of the next
-// layer), then an arrival on hbar[j].  For layer 1 ocol = dcol: the output
-// goes into columns this warp has already read.  The load of step j + 1 is
-// in flight while step j is converted and stored.
+// Epilogue of a hidden layer by epilogue warp e, in kSteps steps j: the
+// accumulator's columns dcol + kPartCols k + 32 j .. +31 (part k = e / 4) of
+// the rows of lane quadrant e % 4: + bias, ReLU, bf16 pairs written to
+// columns ocol + kPartCols k + 16 j .. +15 (K elements kPartCols k + 32 j ..
+// +31 of the next layer), then an arrival on hbar[j].  With ocol = dcol the
+// output goes into columns this warp has already read.  The load of step
+// j + 1 is in flight while step j is converted and stored.
 __device__ __forceinline__ void hidden_layer(uint32_t tmem, uint32_t dcol, uint32_t ocol, int e,
                                              const float* bias, uint64_t* hbar)
 {
     const uint32_t lanes = uint32_t(32 * (e & 3)) << 16;
-    const int h = e >> 2;
+    const int k = e >> 2;
     uint32_t ra[32], rb[32];
-    tc::tmem_ld32_async(tmem + lanes + dcol + uint32_t(128 * h), ra);
+    tc::tmem_ld32_async(tmem + lanes + dcol + uint32_t(kPartCols * k), ra);
     auto step = [&](int j, uint32_t (&cur)[32], uint32_t (&nxt)[32]) {
         tc::tmem_wait_ld(cur);
-        if (j < 3)
-            tc::tmem_ld32_async(tmem + lanes + dcol + uint32_t(128 * h + 32 * (j + 1)), nxt);
-        const int n0 = 128 * h + 32 * j;
+        if (j + 1 < kSteps)
+            tc::tmem_ld32_async(tmem + lanes + dcol + uint32_t(kPartCols * k + 32 * (j + 1)), nxt);
+        const int n0 = kPartCols * k + 32 * j;
         uint32_t w[16];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -123,16 +129,19 @@ __device__ __forceinline__ void hidden_layer(uint32_t tmem, uint32_t dcol, uint3
             w[2 * i] = bias_relu_bf16x2(cur[4 * i], cur[4 * i + 1], b.x, b.y);
             w[2 * i + 1] = bias_relu_bf16x2(cur[4 * i + 2], cur[4 * i + 3], b.z, b.w);
         }
-        tc::tmem_st16(tmem + lanes + ocol + uint32_t(128 * h + 16 * j), w);
+        tc::tmem_st16(tmem + lanes + ocol + uint32_t(kPartCols * k + 16 * j), w);
         tc::tmem_wait_st();
         // the step's TMEM reads and writes are done before the arrival
         tc::fence_before_sync();
         mbar_arrive(&hbar[j]);
     };
-    step(0, ra, rb);
-    step(1, rb, ra);
-    step(2, ra, rb);
-    step(3, rb, ra);
+#pragma unroll
+    for (int j = 0; j < kSteps; ++j) {
+        if (j & 1)
+            step(j, rb, ra);
+        else
+            step(j, ra, rb);
+    }
 }
 
 // Byte address of K elements k0 .. k0+15 of a weight matrix stored as K
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
         mbar_init(&bars.m3, 1);
         for (int b = 0; b < 2; ++b)
             mbar_init(&bars.x[b], 1);
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < kSteps; ++c) {
             mbar_init(&bars.h1[c], 32 * kEpiWarps);
             mbar_init(&bars.h2[c], 32 * kEpiWarps);
         }
@@ -213,19 +222,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                                  kk > 0 ? 1u : 0u);
                 commit(&bars.m1, ph_m1);
             };
-            // the next layer on the K elements of epilogue step c: 32c .. +31
-            // (first half of the columns) and 128 + 32c .. +31 (second half),
-            // A packed in TMEM at hcol + 128 h + 16 c
+            // the next layer on the K elements of epilogue step c:
+            // kPartCols k + 32 c .. +31 of every part k, A packed in TMEM at
+            // hcol + kPartCols k + 16 c
             auto mma_step = [&](uint32_t dcol, uint32_t hcol, uint32_t wbase, int chunk_bytes, uint32_t idesc,
                                 int c) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
+                for (int k = 0; k < kParts; ++k)
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
-                        const int k0 = 128 * h + 32 * c + 16 * s;
-                        tc::mma_bf16_tmem_a(tmem + dcol, tmem + hcol + uint32_t(128 * h + 16 * c + 8 * s),
+                        const int k0 = kPartCols * k + 32 * c + 16 * s;
+                        tc::mma_bf16_tmem_a(tmem + dcol, tmem + hcol + uint32_t(kPartCols * k + 16 * c + 8 * s),
                                             tc::smem_desc(weight_k(wbase, chunk_bytes, k0)), idesc,
-                                            (c == 0 && h == 0 && s == 0) ? 0u : 1u);
+                                            (c == 0 && k == 0 && s == 0) ? 0u : 1u);
                     }
             };
             mbar_expect_tx(&bars.w, kW1 + 4 * kW3Chunk + 4 * kW2Chunk);
@@ -250,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                 if (it + 2 < n_it)
                     load_x(it + 2);
                 // layer 2, step by step as the epilogue of layer 1 delivers H1
-                for (int c = 0; c < 4 && ok; ++c) {
+                for (int c = 0; c < kSteps && ok; ++c) {
                     if (!(ok = wait_phase(&bars.h1[c], par, abort)))
                         break;
                     tc::fence_after_sync();
@@ -259,17 +268,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                 if (!ok)
                     break;
                 commit(&bars.m2, ph_m2);
-                // layer 3, step by step as the epilogue of layer 2 delivers H2;
-                // it accumulates in columns 256..287, read by the first step
-                for (int c = 0; c < 4 && ok; ++c) {
-                    if (!(ok = wait_phase(&bars.h2[c], par, abort)))
-                        break;
-                    tc::fence_after_sync();
-                    mma_step(kD3, kH2, w3, kW3Chunk, IDESC32, c);
-                }
-                if (!ok)
-                    break;
-                commit(&bars.m3, ph_m3);
                 // layer 1 of the next tile: columns 0..255 hold only this
                 // tile's H1, read by the layer-2 MMAs issued before
                 if (it + 1 < n_it) {
@@ -279,6 +277,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                     tc::fence_after_sync();
                     mma1(it + 1);
                 }
+                // layer 3 once the epilogue of layer 2 has packed all of H2
+                // (its last step has read the columns of D3)
+                for (int c = 0; c < kSteps && ok; ++c)
+                    ok = wait_phase(&bars.h2[c], par, abort);
+                if (!ok)
+                    break;
+                tc::fence_after_sync();
+                for (int c = 0; c < kSteps; ++c)
+                    mma_step(kD3, kH2, w3, kW3Chunk, IDESC32, c);
+                commit(&bars.m3, ph_m3);
             }
             if (!ok) {
                 fail();
@@ -316,19 +324,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fused_kernel(const MlpFusedAr
                 break;
             }
             tc::fence_after_sync();
-            if (warp < 4) {  // the logits: one quadrant of rows per warp
-                float v[32];
-                tc::tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + kD3, v);
+            {  // the logits: warp e takes columns 8 (e / 4) .. +7 of its quadrant's
+               // rows; the tile is stored column by column, so each store of
+               // the warp writes 32 consecutive rows (128 bytes)
+                const int quad = warp & 3, n0 = 8 * (warp >> 2);
+                float v[8];
+                tc::tmem_ld8(tmem + (uint32_t(32 * quad) << 16) + kD3 + uint32_t(n0), v);
                 const size_t tile = size_t(blockIdx.x) + size_t(it) * G;
-                float* out = a.L + (tile * 128 + size_t(32 * warp + lane)) * 32;
+                float* out = a.L + tile * (128 * 32) + size_t(n0) * 128 + size_t(32 * quad + lane);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    reinterpret_cast<float4*>(out)[i] =
-                        make_float4(v[4 * i] + sb3[4 * i], v[4 * i + 1] + sb3[4 * i + 1],
-                                    v[4 * i + 2] + sb3[4 * i + 2], v[4 * i + 3] + sb3[4 * i + 3]);
+                    out[size_t(i) * 128] = v[i] + sb3[n0 + i];
             }
             // the D3 reads are done before the next tile's first arrival,
-            // which layer 2 of that tile (overwriting 256..287) waits for
+            // which layer 2 of that tile (overwriting D3) waits for
             tc::fence_before_sync();
         }
     }
