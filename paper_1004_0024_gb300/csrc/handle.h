@@ -59,6 +59,7 @@ struct ising_s {
     // register-resident kernel (M <= 32, tables in shared memory)
     bool use_fast = false, use_lean = false, persistent_ok = false, fast_off = false, lean_off = false;
     bool use_track = false, track_on = false;
+    bool lean_small = false;  // lean kernel, small-block instantiation (kernel variant 3)
     // track schedule: columns (positions) in time order, track k =
     // track_col[track_off_v[k] .. track_off_v[k+1])
     std::vector<int> track_off_v, track_col;

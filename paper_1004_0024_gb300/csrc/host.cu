@@ -385,7 +385,7 @@ SweepArgs base_args(ising_s* g);
 
 // The register-resident kernel keeps up to 8 columns per thread; it needs
 // M <= 32, the slice tables in shared memory and spatial degree <= 255.
-int kernel_variant(const ising_s* g) { return g->use_track ? 2 : (g->use_lean ? 1 : 0); }
+int kernel_variant(const ising_s* g) { return g->use_track ? 2 : (g->use_lean ? (g->lean_small ? 3 : 1) : 0); }
 
 // The lean kernel's model limits (one replica per block; the block size is
 // checked when the launch is chosen).
@@ -409,6 +409,7 @@ void choose_fast(ising_s* g)
 {
     g->use_fast = false;
     g->use_lean = false;
+    g->lean_small = false;
     g->use_track = false;
     g->persistent_ok = false;
     if (g->M > 32 || !g->tables_smem || g->max_sp_deg > 255 || g->fast_off)
@@ -442,7 +443,10 @@ void choose_fast(ising_s* g)
             cmax = 1;
         }
     }
-    const int variant = g->use_track ? 2 : (g->use_lean ? 1 : 0);
+    // two columns per thread in blocks of at most 128 threads: the small-block
+    // lean instantiation (eight resident blocks per SM)
+    g->lean_small = g->use_lean && cmax == 2 && g->T <= kLeanSmallThreads;
+    const int variant = kernel_variant(g);
     SweepArgs a = base_args(g);
     const size_t smem = fast_smem_bytes(a, g->field_bits, variant, g->T);
     if (smem == size_t(-1))

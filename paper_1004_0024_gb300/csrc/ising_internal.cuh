@@ -265,12 +265,16 @@ __host__ __device__ __forceinline__ size_t tiled_offset(int rows, int row, int k
            size_t(row & 7) * 16 + size_t(k & 7) * 2;
 }
 
+// Largest block of the small-block lean instantiation (kernel variant 3: two
+// columns per thread, eight resident blocks per SM).
+constexpr int kLeanSmallThreads = 128;
+
 // Everything needed to launch a handle's register-resident sweep kernel.
 struct FusedLaunch {
     SweepArgs args;
     int field_bits, cmax, threads, blocks, R, rng;
     size_t smem_plain, smem_fused;
-    int variant;  // 0 fast, 1 lean, 2 track
+    int variant;  // 0 fast, 1 lean, 2 track, 3 lean with small blocks
     cudaStream_t stream;
 };
 

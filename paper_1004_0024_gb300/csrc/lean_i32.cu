@@ -2,8 +2,9 @@
 #include "lean_impl.cuh"
 
 namespace isg {
-void* lean_kernel_i32(int rng, int cmax, bool batch)
+void* lean_kernel_i32(int rng, int cmax, bool batch, bool small)
 {
-    return rng == 0 ? lean_detail::pick_lean<int32_t, 0>(cmax, batch) : lean_detail::pick_lean<int32_t, 1>(cmax, batch);
+    return rng == 0 ? lean_detail::pick_lean<int32_t, 0>(cmax, batch, small)
+                    : lean_detail::pick_lean<int32_t, 1>(cmax, batch, small);
 }
 }  // namespace isg

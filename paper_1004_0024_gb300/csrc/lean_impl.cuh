@@ -50,6 +50,22 @@ __host__ __device__ constexpr int lean_max_threads(int cmax)
 // registers each): a 256-replica ladder then fits on the GPU at once
 __host__ __device__ constexpr int lean_min_blocks(int cmax) { return cmax == 4 ? 2 : 1; }
 
+// The small-block instantiation (two columns per thread, at most
+// kLeanSmallThreads = 128 threads) for ladders of many small replicas, where
+// residency rather than the length of one level bounds the throughput:
+// twelve resident blocks per SM with MT19937 words (at most 42 registers a
+// thread; 1.17e11 attempts/s on 4096 spins x 65536 replicas against 1.11e11
+// with eight), eight with Philox (at most 64 registers: the ten rounds spill
+// at twelve, 1.08e11 against 1.22e11).
+__host__ __device__ constexpr int lean_bound_threads(int cmax, bool small)
+{
+    return small ? kLeanSmallThreads : lean_max_threads(cmax);
+}
+__host__ __device__ constexpr int lean_bound_blocks(int cmax, bool small, int rng)
+{
+    return small ? (rng == 0 ? 12 : 8) : lean_min_blocks(cmax);
+}
+
 // Body of one block: `blk` is the replica (block) index within its instance
 // and `nblk` the instance's number of blocks (the grid size for one instance).
 template <typename FT, int RNG, int CMAX>
@@ -353,16 +369,17 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     }
 }
 
-template <typename FT, int RNG, int CMAX>
-__global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX)) lean_kernel(const SweepArgs a)
+template <typename FT, int RNG, int CMAX, bool SMALL>
+__global__ void __launch_bounds__(lean_bound_threads(CMAX, SMALL), lean_bound_blocks(CMAX, SMALL, RNG))
+    lean_kernel(const SweepArgs a)
 {
     lean_body<FT, RNG, CMAX>(a, int(blockIdx.x), int(gridDim.x));
 }
 
 // Batched launch over many instances: each block copies its instance's
 // arguments into shared memory (so that every later read is a shared load).
-template <typename FT, int RNG, int CMAX>
-__global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
+template <typename FT, int RNG, int CMAX, bool SMALL>
+__global__ void __launch_bounds__(lean_bound_threads(CMAX, SMALL), lean_bound_blocks(CMAX, SMALL, RNG))
     lean_batch_kernel(const SweepArgs* __restrict__ args, const BatchItem* __restrict__ items)
 {
     __shared__ SweepArgs sa;
@@ -374,22 +391,26 @@ __global__ void __launch_bounds__(lean_max_threads(CMAX), lean_min_blocks(CMAX))
 }
 
 template <typename FT, int RNG>
-void* pick_lean(int cmax, bool batch = false)
+void* pick_lean(int cmax, bool batch = false, bool small = false)
 {
+    if (small)  // two columns per thread only
+        return cmax != 2 ? nullptr
+                         : (batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 2, true>)
+                                  : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2, true>));
     switch (cmax) {
-    case 1: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 1>)
-                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 1>);
-    case 2: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 2>)
-                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2>);
-    case 4: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 4>)
-                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 4>);
+    case 1: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 1, false>)
+                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 1, false>);
+    case 2: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 2, false>)
+                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2, false>);
+    case 4: return batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 4, false>)
+                   : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 4, false>);
     default: return nullptr;
     }
 }
 
 }  // namespace lean_detail
 
-void* lean_kernel_i16(int rng, int cmax, bool batch = false);
-void* lean_kernel_i32(int rng, int cmax, bool batch = false);
+void* lean_kernel_i16(int rng, int cmax, bool batch = false, bool small = false);
+void* lean_kernel_i32(int rng, int cmax, bool batch = false, bool small = false);
 
 }  // namespace isg
