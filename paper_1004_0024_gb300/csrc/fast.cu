@@ -11,9 +11,9 @@ void* pick(int field_bits, int rng, int cmax, int variant = 0, bool batch = fals
 {
     if (variant == 2)
         return field_bits == 16 ? track_kernel_i16(rng, batch) : track_kernel_i32(rng, batch);
-    if (variant == 1 || variant == 3)  // 3: the small-block lean instantiation
-        return field_bits == 16 ? lean_kernel_i16(rng, cmax, batch, variant == 3)
-                                : lean_kernel_i32(rng, cmax, batch, variant == 3);
+    if (variant == 1 || variant == 3 || variant == 4)  // 3: small blocks, 4: long columns
+        return field_bits == 16 ? lean_kernel_i16(rng, cmax, batch, variant == 3, variant == 4)
+                                : lean_kernel_i32(rng, cmax, batch, variant == 3, variant == 4);
     return field_bits == 16 ? fast_kernel_i16(rng, cmax, batch) : fast_kernel_i32(rng, cmax, batch);
 }
 
@@ -39,7 +39,7 @@ cudaError_t fast_set_smem_limits()
         return e;
     size_t lim = size_t(optin);
     for (int batch : {0, 1})
-    for (int variant : {0, 1, 2, 3})
+    for (int variant : {0, 1, 2, 3, 4})
         for (int fb : {16, 32})
             for (int rng : {0, 1})
                 for (int cm : {1, 2, 4, 8}) {

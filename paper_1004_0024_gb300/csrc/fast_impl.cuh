@@ -33,7 +33,7 @@ namespace isg {
 namespace fast_detail {
 
 struct FastLayout {
-    uint32_t nbr_off, nbr, jtau, pos, site, fsp, thr, eacc, slot, temp, total;
+    uint32_t nbr_off, nbr, jtau, pos, site, fsp, thr, eacc, colw, slot, temp, total;
 };
 
 __host__ __device__ inline FastLayout fast_layout(const SweepArgs& a, int fbytes)
@@ -52,6 +52,10 @@ __host__ __device__ inline FastLayout fast_layout(const SweepArgs& a, int fbytes
     L.fsp = o;     o += r16(uint32_t(fbytes) * a.N * a.G);
     L.thr = o;     o += r16(4u * a.G * a.K);
     L.eacc = o;    o += r16(4u * a.G);
+    // long columns (M > 32, lean kernel only): M / 32 words per column
+    L.colw = o;
+    if (a.M > 32)
+        o += r16(4u * uint32_t(a.S) * uint32_t(a.M / 32));
     if (a.swap_every > 0) {
         L.slot = o; o += r16(4u * a.R);
         L.temp = o; o += r16(4u * a.R);

@@ -60,6 +60,7 @@ struct ising_s {
     bool use_fast = false, use_lean = false, persistent_ok = false, fast_off = false, lean_off = false;
     bool use_track = false, track_on = false;
     bool lean_small = false;  // lean kernel, small-block instantiation (kernel variant 3)
+    bool lean_long = false;   // lean kernel, long columns: M > 32 (kernel variant 4)
     // track schedule: columns (positions) in time order, track k =
     // track_col[track_off_v[k] .. track_off_v[k+1])
     std::vector<int> track_off_v, track_col;

@@ -385,13 +385,20 @@ SweepArgs base_args(ising_s* g);
 
 // The register-resident kernel keeps up to 8 columns per thread; it needs
 // M <= 32, the slice tables in shared memory and spatial degree <= 255.
-int kernel_variant(const ising_s* g) { return g->use_track ? 2 : (g->use_lean ? (g->lean_small ? 3 : 1) : 0); }
+int kernel_variant(const ising_s* g)
+{
+    return g->use_track ? 2 : (g->use_lean ? (g->lean_long ? 4 : (g->lean_small ? 3 : 1)) : 0);
+}
+
+// slice counts of the lean kernel: a power of two from 4 to 32 (the column in
+// one register), or a multiple of 32 up to 1024 (long columns, M / 32 words)
+bool lean_slices(int M) { return M == 4 || M == 8 || M == 16 || M == 32 || (M % 32 == 0 && M <= 1024); }
 
 // The lean kernel's model limits (one replica per block; the block size is
 // checked when the launch is chosen).
 bool lean_eligible(const ising_s* g)
 {
-    return (g->M == 4 || g->M == 8 || g->M == 16 || g->M == 32) && g->max_sp_deg <= 6 && g->max_sp_J <= 63 &&
+    return lean_slices(g->M) && g->max_sp_deg <= 6 && g->max_sp_J <= 63 &&
            g->G_req <= 1 && !g->lean_off && !g->fast_off;
 }
 
@@ -410,9 +417,12 @@ void choose_fast(ising_s* g)
     g->use_fast = false;
     g->use_lean = false;
     g->lean_small = false;
+    g->lean_long = false;
     g->use_track = false;
     g->persistent_ok = false;
-    if (g->M > 32 || !g->tables_smem || g->max_sp_deg > 255 || g->fast_off)
+    // M > 32: only the lean kernel's long-column instantiation (M a multiple of 32)
+    const bool long_cols = g->M > 32;
+    if ((long_cols && !lean_slices(g->M)) || !g->tables_smem || g->max_sp_deg > 255 || g->fast_off)
         return;
     const long long C = ((long long)g->S * g->G + g->T - 1) / g->T;
     int cmax = 0;
@@ -425,14 +435,17 @@ void choose_fast(ising_s* g)
         return;
     // lean variant: one replica per block, power-of-two M >= 4, small degree
     // and couplings, at most 4 columns per thread within its register budget
-    g->use_lean = g->G == 1 && (g->M == 4 || g->M == 8 || g->M == 16 || g->M == 32) &&
-                  g->max_sp_deg <= 6 && g->max_sp_J <= 63 && cmax <= 4 &&
+    g->use_lean = g->G == 1 && lean_slices(g->M) && g->max_sp_deg <= 6 && g->max_sp_J <= 63 &&
+                  cmax <= (long_cols ? 2 : 4) &&
                   g->T <= (cmax <= 1 ? 1024 : (cmax == 2 ? 512 : 256)) && !g->lean_off &&
                   (g->rng == ISING_RNG_MT19937 || (g->ntracks >= 1 && g->ntracks <= g->T));
+    if (long_cols && !g->use_lean)
+        return;  // the register-resident fast kernel holds a column in one word
+    g->lean_long = long_cols;
     // track variant: the lean kernel's limits with the columns walked as
     // tracks, one thread per track (when the block size is left automatic)
     const int T_track = ((g->ntracks + 31) / 32) * 32;
-    if (g->G == 1 && track_eligible(g)) {
+    if (g->G == 1 && !long_cols && track_eligible(g)) {
         SweepArgs t = base_args(g);
         t.G = 1;
         const size_t sm = fast_smem_bytes(t, g->field_bits, 2, T_track);
@@ -445,7 +458,7 @@ void choose_fast(ising_s* g)
     }
     // two columns per thread in blocks of at most 128 threads: the small-block
     // lean instantiation (eight resident blocks per SM)
-    g->lean_small = g->use_lean && cmax == 2 && g->T <= kLeanSmallThreads;
+    g->lean_small = g->use_lean && !long_cols && cmax == 2 && g->T <= kLeanSmallThreads;
     const int variant = kernel_variant(g);
     SweepArgs a = base_args(g);
     const size_t smem = fast_smem_bytes(a, g->field_bits, variant, g->T);

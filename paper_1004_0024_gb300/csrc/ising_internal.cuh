@@ -274,7 +274,7 @@ struct FusedLaunch {
     SweepArgs args;
     int field_bits, cmax, threads, blocks, R, rng;
     size_t smem_plain, smem_fused;
-    int variant;  // 0 fast, 1 lean, 2 track, 3 lean with small blocks
+    int variant;  // 0 fast, 1 lean, 2 track, 3 lean with small blocks, 4 lean with long columns
     cudaStream_t stream;
 };
 

@@ -1,5 +1,6 @@
 // Lean register-resident wavefront sweep for the layered models of the
-// paper's QMC setting: one replica per block, M in {4, 8, 16, 32} slices,
+// paper's QMC setting: one replica per block, M in {4, 8, 16, 32} slices (or,
+// as the LONG instantiation, any multiple of 32 up to 1024: see below),
 // spatial degree <= 6 and |J| <= 63.  Same schedule, state and fused-PT
 // protocol as fast_impl.cuh (level(q, t) = lev0(q) + t; spatial fields in
 // shared memory with atomic neighbour updates; column bits and random-word
@@ -26,6 +27,12 @@
 //    most one busy column per level).
 //  * With at most 32 tabulated thresholds, lane k of every warp holds T[k] and
 //    the lookup of T[k] is a warp shuffle in a converged section.
+//  * LONG (M = 32 KW, KW >= 2): the column lives as KW words in shared
+//    memory; a thread holds the word of its busy slice and the words before
+//    and after it (ring order), so s_{t-1}, s_t, s_{t+1} are register bits.
+//    When the slice leaves a word, the word is stored and the next-but-one is
+//    loaded, 32 levels before it is needed; the words of slices 0 and M - 1
+//    are stored before the other end of the ring reads them.
 #pragma once
 #include <climits>
 
@@ -68,7 +75,7 @@ __host__ __device__ constexpr int lean_bound_blocks(int cmax, bool small, int rn
 
 // Body of one block: `blk` is the replica (block) index within its instance
 // and `nblk` the instance's number of blocks (the grid size for one instance).
-template <typename FT, int RNG, int CMAX>
+template <typename FT, int RNG, int CMAX, bool LONG>
 __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, const int nblk)
 {
     constexpr bool kI16 = sizeof(FT) == 2;
@@ -86,6 +93,8 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     const int* site = reinterpret_cast<const int*>(smem + L.site);
     void* fsp = smem + L.fsp;
     unsigned* fsw = reinterpret_cast<unsigned*>(smem + L.fsp);
+    uint32_t* colw = reinterpret_cast<uint32_t*>(smem + L.colw);  // LONG: [S][M / 32] column words
+    const int KW = M >> 5;                                          // LONG: words per column
     uint32_t* thr_s = reinterpret_cast<uint32_t*>(smem + L.thr);
     int* eacc = reinterpret_cast<int*>(smem + L.eacc);
     int* slot_s = reinterpret_cast<int*>(smem + L.slot);
@@ -141,7 +150,10 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     // ---- owned columns
     const uint32_t rep = (M == 32) ? 1u : (M == 16 ? 0x00010001u : (M == 8 ? 0x01010101u : 0x11111111u));
     int lv[CMAX], jd[CMAX], fb[CMAX];
-    uint32_t bits[CMAX];
+    uint32_t bits[CMAX];  // M <= 32: the column, replicated with period M
+    // LONG: the words k - 1, k, k + 1 (mod M / 32) around the word k of the
+    // column's busy slice; a word is stored to `colw` when the slice leaves it
+    uint32_t cwP[CMAX], cwW[CMAX], cwN[CMAX];
     uint32_t nb[CMAX][kMaxDeg];
     uint4 ba[CMAX];  // Philox: the current word block of each column
     unsigned char* stage = smem + L.nbr_off;  // MT19937: [S][2 blocks][16 B]
@@ -152,6 +164,7 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
         jd[c] = 0;
         fb[c] = 0;
         bits[c] = 0u;
+        cwP[c] = cwW[c] = cwN[c] = 0u;
         ba[c] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int e = 0; e < kMaxDeg; ++e)
@@ -174,10 +187,19 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                 }
             }
             const int8_t* sp = a.spins + size_t(r) * N + site[p];
-            uint32_t b = 0u;
-            for (int t = 0; t < M; ++t)
-                b |= (sp[size_t(t) * S] > 0 ? 1u : 0u) << t;
-            bits[c] = b * rep;  // replicate the column with period M
+            if constexpr (LONG) {
+                for (int w = 0; w < KW; ++w) {
+                    uint32_t b = 0u;
+                    for (int i = 0; i < 32; ++i)
+                        b |= (sp[size_t(32 * w + i) * S] > 0 ? 1u : 0u) << i;
+                    colw[p * KW + w] = b;
+                }
+            } else {
+                uint32_t b = 0u;
+                for (int t = 0; t < M; ++t)
+                    b |= (sp[size_t(t) * S] > 0 ? 1u : 0u) << t;
+                bits[c] = b * rep;  // replicate the column with period M
+            }
         }
     }
     __syncthreads();  // tables consumed: with MT19937 their region becomes `stage`
@@ -202,6 +224,11 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
         for (int c = 0; c < CMAX; ++c) {
             if (lv[c] < INT_MAX / 2) {
                 const int p = tid + c * T;
+                if constexpr (LONG) {  // slice 0 lies in word 0; slice M - 1 in the last word
+                    cwP[c] = colw[p * KW + KW - 1];
+                    cwW[c] = colw[p * KW];
+                    cwN[c] = colw[p * KW + 1];
+                }
                 if (RNG == 0) {
                     const uint32_t* src = wsw + (size_t(r) * S + p) * a.Mp;
                     cp_async16(stage + p * 32, src);
@@ -230,7 +257,16 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                     const uint32_t u = (RNG == 0)
                         ? *reinterpret_cast<const uint32_t*>(stage + p * 32 + odd * 16 + (t & 3) * 4)
                         : pick4(ba[c], t & 3);
-                    const uint32_t w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
+                    // bits 0, 1, 2 = s_{t-1}, s_t, s_{t+1} (ring wrap included)
+                    uint32_t w3;
+                    if constexpr (LONG) {
+                        const int tb = t & 31;
+                        const uint32_t sm1 = tb ? (cwW[c] >> (tb - 1)) : (cwP[c] >> 31);
+                        const uint32_t sp1 = tb < 31 ? (cwW[c] >> (tb + 1)) : cwN[c];
+                        w3 = (sm1 & 1u) | (((cwW[c] >> tb) & 1u) << 1) | ((sp1 & 1u) << 2);
+                    } else {
+                        w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
+                    }
                     const int s = 2 * int((w3 >> 1) & 1u) - 1;
                     const int ft = (jd[c] >> 8) * (2 * int((w3 & 1u) + ((w3 >> 2) & 1u)) - 2);
                     const int k = s * (fs + ft);
@@ -240,7 +276,10 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                     else
                         tk = (k > 0 && k < K) ? thr_s[k] : 0u;
                     if (act && ((k <= 0) || (k < K && u < tk))) {
-                        bits[c] ^= rep << t;
+                        if constexpr (LONG)
+                            cwW[c] ^= 1u << (t & 31);
+                        else
+                            bits[c] ^= rep << t;
                         dE += 2 * k;
                         const int tw = kI16 ? (t >> 1) : t;
                         const int sh = kI16 ? ((t & 1) << 4) : 0;
@@ -249,6 +288,18 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                             const uint32_t v = nb[c][e];
                             const int d = -s * int(int8_t(v & 0xFFu));
                             atomicAdd(fsw + (v >> 8) + tw, unsigned(d) << sh);
+                        }
+                    }
+                    if constexpr (LONG) {
+                        if (act && (t & 31) == 31) {  // the slice leaves word k: store it, rotate
+                            const int k = t >> 5;
+                            colw[p * KW + k] = cwW[c];
+                            if (k + 1 < KW) {
+                                cwP[c] = cwW[c];
+                                cwW[c] = cwN[c];
+                                const int k2 = k + 2 < KW ? k + 2 : k + 2 - KW;
+                                cwN[c] = colw[p * KW + k2];
+                            }
                         }
                     }
                     if (RNG == 0) {
@@ -344,7 +395,15 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
             FT* fg = static_cast<FT*>(a.fields) + size_t(r) * N + q;
             const int jt = jd[c] >> 8;
             for (int t = 0; t < M; ++t) {
-                const uint32_t w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
+                uint32_t w3;
+                if constexpr (LONG) {
+                    const int tm = t == 0 ? M - 1 : t - 1, tp = t + 1 == M ? 0 : t + 1;
+                    w3 = ((colw[p * KW + (tm >> 5)] >> (tm & 31)) & 1u) |
+                         (((colw[p * KW + (t >> 5)] >> (t & 31)) & 1u) << 1) |
+                         (((colw[p * KW + (tp >> 5)] >> (tp & 31)) & 1u) << 2);
+                } else {
+                    w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
+                }
                 sp[size_t(t) * S] = ((w3 >> 1) & 1u) ? int8_t(1) : int8_t(-1);
                 fg[size_t(t) * S] =
                     FT(Fsp<FT>::ld(fsp, fb[c] + t) + jt * (2 * int((w3 & 1u) + ((w3 >> 2) & 1u)) - 2));
@@ -369,16 +428,16 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     }
 }
 
-template <typename FT, int RNG, int CMAX, bool SMALL>
+template <typename FT, int RNG, int CMAX, bool SMALL, bool LONG = false>
 __global__ void __launch_bounds__(lean_bound_threads(CMAX, SMALL), lean_bound_blocks(CMAX, SMALL, RNG))
     lean_kernel(const SweepArgs a)
 {
-    lean_body<FT, RNG, CMAX>(a, int(blockIdx.x), int(gridDim.x));
+    lean_body<FT, RNG, CMAX, LONG>(a, int(blockIdx.x), int(gridDim.x));
 }
 
 // Batched launch over many instances: each block copies its instance's
 // arguments into shared memory (so that every later read is a shared load).
-template <typename FT, int RNG, int CMAX, bool SMALL>
+template <typename FT, int RNG, int CMAX, bool SMALL, bool LONG = false>
 __global__ void __launch_bounds__(lean_bound_threads(CMAX, SMALL), lean_bound_blocks(CMAX, SMALL, RNG))
     lean_batch_kernel(const SweepArgs* __restrict__ args, const BatchItem* __restrict__ items)
 {
@@ -387,12 +446,18 @@ __global__ void __launch_bounds__(lean_bound_threads(CMAX, SMALL), lean_bound_bl
     if (threadIdx.x == 0)
         sa = args[it.inst];
     __syncthreads();
-    lean_body<FT, RNG, CMAX>(sa, it.block, sa.inst_blocks);
+    lean_body<FT, RNG, CMAX, LONG>(sa, it.block, sa.inst_blocks);
 }
 
 template <typename FT, int RNG>
-void* pick_lean(int cmax, bool batch = false, bool small = false)
+void* pick_lean(int cmax, bool batch = false, bool small = false, bool longc = false)
 {
+    if (longc)  // M a multiple of 32 above 32: one or two columns per thread
+        return cmax == 1 ? (batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 1, false, true>)
+                                  : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 1, false, true>))
+             : cmax == 2 ? (batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 2, false, true>)
+                                  : reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2, false, true>))
+                         : nullptr;
     if (small)  // two columns per thread only
         return cmax != 2 ? nullptr
                          : (batch ? reinterpret_cast<void*>(&lean_batch_kernel<FT, RNG, 2, true>)
@@ -410,7 +475,7 @@ void* pick_lean(int cmax, bool batch = false, bool small = false)
 
 }  // namespace lean_detail
 
-void* lean_kernel_i16(int rng, int cmax, bool batch = false, bool small = false);
-void* lean_kernel_i32(int rng, int cmax, bool batch = false, bool small = false);
+void* lean_kernel_i16(int rng, int cmax, bool batch = false, bool small = false, bool longc = false);
+void* lean_kernel_i32(int rng, int cmax, bool batch = false, bool small = false, bool longc = false);
 
 }  // namespace isg
