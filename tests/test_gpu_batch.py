@@ -24,10 +24,11 @@ def ising():
 
 
 def _mixed_instances():
-    """Layered models of several slice counts and sizes, an unstructured graph
-    and a 64-slice model (generic kernel), with ragged replica counts."""
+    """Layered models of several slice counts and sizes, an unstructured graph,
+    a 64-slice model (the lean kernel's long columns) and a 33-slice model
+    (generic kernel), with ragged replica counts."""
     specs = [(8, 16, 8), (8, 32, 13), (9, 16, 32), (10, 16, 20), (12, 8, 5), (16, 16, 9),
-             (3, 4, 3), (4, 5, 7), (3, 64, 4), (11, 32, 24), (8, 16, 1), (6, 16, 40)]
+             (3, 4, 3), (4, 5, 7), (3, 64, 4), (11, 32, 24), (8, 16, 1), (6, 16, 40), (3, 33, 5)]
     out = []
     for k, (L, M, R) in enumerate(specs):
         g = W.layered_graph(L, M, graph_seed=700 + k)
