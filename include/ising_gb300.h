@@ -453,8 +453,15 @@ int32_t ising_mlp_destroy(ising_mlp_t m);
 int32_t ising_set_alloc_cap(uint64_t bytes);
 int32_t ising_selftest_wait(int32_t kind, void* stream);
 
-/* Release all device memory of the handle (NULL is ignored). */
+/* Release all device memory of the handle (NULL is ignored).  MT19937 word
+ * buffers of 256 MB or more are not returned to the driver: up to two of
+ * them are kept (after a device synchronisation) for the next handle whose
+ * buffer fits, which then skips the allocation. */
 int32_t ising_destroy(ising_t h);
+
+/* Frees the word buffers kept by ising_destroy (process-wide; always
+ * ISING_OK).  An allocation that fails frees them and retries by itself. */
+int32_t ising_release_cached_memory(void);
 
 #ifdef __cplusplus
 }

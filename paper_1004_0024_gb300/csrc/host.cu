@@ -16,6 +16,8 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <utility>
 #include <tuple>
 #include <vector>
@@ -89,14 +91,105 @@ void dfree(T*& p)
     p = nullptr;
 }
 
+// Large blocks (the MT19937 word buffers, gigabytes) are not returned to the
+// driver when a handle lets them go: freeing and re-mapping them costs
+// milliseconds per handle.  Up to kBigKeep freed blocks wait here, after a
+// device synchronisation (so no kernel of the old owner still touches them),
+// for an allocation of at most their size that needs no more than 5/4 of
+// it; ising_release_cached_memory frees them, and so does an allocation
+// that fails.  Their contents are undefined (no zero fill).
+constexpr size_t kBigBlock = size_t(256) << 20;
+constexpr size_t kBigKeep = 2;
+std::mutex g_big_mu;
+std::multimap<size_t, void*> g_big_free;       // size -> block
+std::unordered_map<void*, size_t> g_big_live;  // block -> size
+
+void big_release_all()
+{
+    std::lock_guard<std::mutex> lk(g_big_mu);
+    for (auto& kv : g_big_free)
+        cudaFree(kv.second);
+    g_big_free.clear();
+}
+
+template <typename T>
+int32_t big_alloc(T** p, size_t count)
+{
+    const size_t bytes = std::max<size_t>(16, ((count * sizeof(T)) + 15) & ~size_t(15));
+    *p = nullptr;
+    if (!alloc_allowed(bytes))
+        return fail(ISING_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes exceeds the cap");
+    if (bytes >= kBigBlock) {
+        std::lock_guard<std::mutex> lk(g_big_mu);
+        auto it = g_big_free.lower_bound(bytes);
+        if (it != g_big_free.end() && it->first - bytes <= bytes / 4) {
+            *p = static_cast<T*>(it->second);
+            g_big_live[it->second] = it->first;
+            g_big_free.erase(it);
+            return ISING_OK;
+        }
+    }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e == cudaErrorMemoryAllocation) {  // give the cached blocks back and retry once
+        cudaGetLastError();
+        big_release_all();
+        e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    }
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    if (bytes >= kBigBlock) {
+        std::lock_guard<std::mutex> lk(g_big_mu);
+        g_big_live[*p] = bytes;
+    }
+    return ISING_OK;
+}
+
+template <typename T>
+void big_free(T*& p)
+{
+    if (!p)
+        return;
+    void* v = p;
+    p = nullptr;
+    std::lock_guard<std::mutex> lk(g_big_mu);
+    auto it = g_big_live.find(v);
+    if (it == g_big_live.end()) {
+        cudaFree(v);
+        return;
+    }
+    const size_t bytes = it->second;
+    g_big_live.erase(it);
+    if (g_big_free.size() < kBigKeep && cudaDeviceSynchronize() == cudaSuccess) {
+        g_big_free.emplace(bytes, v);
+        return;
+    }
+    cudaFree(v);
+}
+
 template <typename T>
 int32_t upload(T** d, const std::vector<T>& h)
 {
-    int32_t rc = dalloc(d, h.size());
-    if (rc)
-        return rc;
+    // no fill of what the copy overwrites: only the 16-byte rounding tail is
+    // zeroed; the synchronous copy on the legacy stream follows the fill, so
+    // both are complete on return
+    size_t bytes = ((h.size() * sizeof(T)) + 15) & ~size_t(15);
+    if (bytes == 0)
+        bytes = 16;
+    *d = nullptr;
+    if (!alloc_allowed(bytes))
+        return fail(ISING_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes exceeds the cap");
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(d), bytes);
+    if (e != cudaSuccess) {
+        *d = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    const size_t data = h.size() * sizeof(T);
+    if (bytes > data)
+        CK(cudaMemset(reinterpret_cast<unsigned char*>(*d) + data, 0, bytes - data));
     if (!h.empty())
-        CK(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(*d, h.data(), data, cudaMemcpyHostToDevice));
     return ISING_OK;
 }
 
@@ -176,7 +269,7 @@ void ising_s::free_replicas()
     dfree(d_swlen);
     dfree(d_betas);
     dfree(d_betas32);
-    dfree(d_wbuf);
+    big_free(d_wbuf);
     dfree(d_swbuf);
     dfree(d_Epub);
     dfree(d_gridbar);
@@ -225,10 +318,10 @@ int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
     for (int i = 0; i < n; ++i)
         if (row_ptr[i + 1] < row_ptr[i])
             return fail(ISING_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
+    // every row's (column, J) entries sorted in one flat array
     const long long nnz = row_ptr[n];
-    std::vector<std::pair<int, int>> row;
+    std::vector<std::pair<int, int>> ent(size_t(std::max<long long>(nnz, 0)));
     for (int i = 0; i < n; ++i) {
-        row.clear();
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
             if (col[e] < 0 || col[e] >= n)
                 return fail(ISING_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
@@ -236,28 +329,22 @@ int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
                 return fail(ISING_ERR_SELF_LOOP_OR_DUP, "self loop at spin " + std::to_string(i));
             if (J[e] > 32767 || J[e] < -32767)
                 return fail(ISING_ERR_INVALID_ARG, "|J| must be <= 32767");
-            row.emplace_back(col[e], J[e]);
+            ent[size_t(e)] = std::make_pair(col[e], J[e]);
         }
-        std::sort(row.begin(), row.end());
-        for (size_t k = 1; k < row.size(); ++k)
-            if (row[k].first == row[k - 1].first)
+        std::sort(ent.begin() + row_ptr[i], ent.begin() + row_ptr[i + 1]);
+        for (int e = row_ptr[i] + 1; e < row_ptr[i + 1]; ++e)
+            if (ent[size_t(e)].first == ent[size_t(e) - 1].first)
                 return fail(ISING_ERR_SELF_LOOP_OR_DUP, "repeated neighbour in row " + std::to_string(i));
     }
     // symmetry: every (i, j, J) needs (j, i, J)
-    std::vector<std::vector<std::pair<int, int>>> rows(n);
-    for (int i = 0; i < n; ++i) {
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-            rows[i].emplace_back(col[e], J[e]);
-        std::sort(rows[i].begin(), rows[i].end());
-    }
-    (void)nnz;
     for (int i = 0; i < n; ++i)
-        for (auto& cj : rows[i]) {
-            auto& rj = rows[cj.first];
-            auto it = std::lower_bound(rj.begin(), rj.end(), std::make_pair(i, INT32_MIN));
-            if (it == rj.end() || it->first != i || it->second != cj.second)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int j = ent[size_t(e)].first;
+            const auto b = ent.begin() + row_ptr[j], en = ent.begin() + row_ptr[j + 1];
+            const auto it = std::lower_bound(b, en, std::make_pair(i, INT32_MIN));
+            if (it == en || it->first != i || it->second != ent[size_t(e)].second)
                 return fail(ISING_ERR_ASYMMETRIC_J,
-                            "J(" + std::to_string(i) + "," + std::to_string(cj.first) + ") has no equal transpose");
+                            "J(" + std::to_string(i) + "," + std::to_string(j) + ") has no equal transpose");
         }
     return ISING_OK;
 }
@@ -270,12 +357,13 @@ int32_t extract_slices(ising_s* g)
     const int n = g->n, M = g->M, S = g->S;
     std::vector<std::vector<std::pair<int, int>>> sp(S);
     std::vector<int> jt(S, 0);
+    std::vector<std::pair<int, int>> spat;  // scratch: the spatial entries of one spin
     for (int t = 0; t < M; ++t) {
         for (int q = 0; q < S; ++q) {
             const int i = t * S + q;
             if (g->h[i] != g->h[q])
                 return fail(ISING_ERR_INVALID_ARG, "declared slices differ in h at spin " + std::to_string(i));
-            std::vector<std::pair<int, int>> spat;
+            spat.clear();
             int ntrot = 0, jtrot = 0;
             bool jt_ok = true;
             const int tm = (t + M - 1) % M, tp = (t + 1) % M;
@@ -684,8 +772,9 @@ int32_t ensure_buffers(ising_s* g, long long cap_sweeps, long long cap_passes)
     if (g->rng != ISING_RNG_MT19937)
         return ISING_OK;
     if (cap_sweeps > g->wbuf_cap) {
-        dfree(g->d_wbuf);
-        int32_t rc = dalloc(&g->d_wbuf, size_t(cap_sweeps) * g->R * g->S * g->Mp);
+        big_free(g->d_wbuf);
+        // fully written by the generator before any sweep reads it: no zero fill
+        int32_t rc = big_alloc(&g->d_wbuf, size_t(cap_sweeps) * g->R * g->S * g->Mp);
         if (rc)
             return rc;
         g->wbuf_cap = cap_sweeps;
@@ -888,6 +977,12 @@ int32_t ising_set_alloc_cap(uint64_t bytes)
     return ISING_OK;
 }
 
+int32_t ising_release_cached_memory(void)
+{
+    big_release_all();
+    return ISING_OK;
+}
+
 int32_t ising_create(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* J,
                      const int32_t* h, int32_t n_slices, uint32_t flags, ising_t* out)
 {
@@ -1031,7 +1126,50 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
     std::vector<int> swlen(std::max(R - 1, 1), 1);
     std::vector<uint32_t> swthr;
     const long long dmax = 2 * g->ebound + 1;
-    for (int k = 0; k + 1 < R; ++k) {
+    // S_k(d) is zero once 2^32 exp(-db d) < 1, i.e. beyond d = 32 ln 2 / db
+    // (+1 for the rounding of the FP64 expression).  When these bounds keep
+    // the tables within 2^28 entries, each pair's table is written in
+    // parallel at an offset given by the bounds, with the same expression and
+    // stopping rule as the serial loop below (a few unused entries may sit
+    // between two tables); otherwise the serial loop builds them and refuses
+    // PT if they would not fit.
+    std::vector<long long> swcap(std::max(R - 1, 1), 0);
+    long long bound = 0;
+    for (int k = 0; k + 1 < R && bound <= (1LL << 28); ++k) {
+        swcap[k] = 1 + std::min<long long>(dmax - 1, (long long)(22.18070977791825 / (betas[k + 1] - betas[k])) + 2);
+        bound += swcap[k];
+    }
+    int k_serial = 0;  // first pair left to the serial loop
+    if (R > 2 && bound <= (1LL << 28)) {
+        const int npairs = R - 1;
+        swthr.assign(size_t(bound), 0u);
+        for (int k = 1; k < npairs; ++k)
+            swoff[k] = swoff[k - 1] + swcap[k - 1];
+        const int nthr = int(std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+        std::atomic<int> next{0};
+        auto work = [&]() {
+            for (int k; (k = next.fetch_add(1)) < npairs;) {
+                const double db = betas[k + 1] - betas[k];
+                uint32_t* v = swthr.data() + swoff[k];  // v[0] = 0: d = 0 never uses the table
+                long long d = 1;
+                for (; d < dmax && d < swcap[k]; ++d) {
+                    const double x = std::floor(std::ldexp(std::exp(-db * double(d)), 32));
+                    if (x == 0.0)
+                        break;
+                    v[d] = uint32_t(x);
+                }
+                swlen[k] = int(d);
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthr; ++t)
+            pool.emplace_back(work);
+        work();
+        for (auto& th : pool)
+            th.join();
+        k_serial = npairs;
+    }
+    for (int k = k_serial; k + 1 < R; ++k) {
         const double db = betas[k + 1] - betas[k];
         swoff[k] = (long long)swthr.size();
         swthr.push_back(0u);

@@ -130,6 +130,7 @@ _SIGS = {
     "ising_mlp_get_stats": ([_vp, ctypes.POINTER(MlpStats)], ctypes.c_int32),
     "ising_read_observables": ([_vp, _i64p, _i64p], ctypes.c_int32),
     "ising_set_alloc_cap": ([ctypes.c_uint64], ctypes.c_int32),
+    "ising_release_cached_memory": ([], ctypes.c_int32),
     "ising_selftest_wait": ([ctypes.c_int32, _vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -265,6 +266,11 @@ def ising_get_stats(h) -> dict:
 def ising_set_alloc_cap(nbytes):
     """Cap every later device allocation of the library at `nbytes` (0: none)."""
     _check(_lib.ising_set_alloc_cap(int(nbytes)))
+
+
+def ising_release_cached_memory():
+    """Free the MT19937 word buffers that destroyed handles left for reuse."""
+    _check(_lib.ising_release_cached_memory())
 
 
 def ising_selftest_wait(kind, stream=None):
