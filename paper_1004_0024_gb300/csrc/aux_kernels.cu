@@ -1,4 +1,5 @@
 // Random-number streams, state initialisation and the parallel-tempering pass.
+#include <algorithm>
 #include "ising_internal.cuh"
 
 namespace isg {
@@ -203,6 +204,14 @@ __device__ __forceinline__ void pt_body(const PtArgs& a)
         a.counters[1] = p + 1ull;
 }
 
+// int16 -> int32 widening of n fields (ising_read_state copies the result)
+__global__ void __launch_bounds__(256) widen_i16_kernel(const int16_t* __restrict__ src, int* __restrict__ dst,
+                                                        long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = int(src[i]);
+}
+
 __global__ void __launch_bounds__(1024) pt_kernel(const PtArgs a) { pt_body(a); }
 
 // Batched: block b runs one PT pass of instance b.
@@ -258,6 +267,15 @@ cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed
     const long long total = (long long)R * N;
     const int blocks = int(min((total + 255) / 256, 65535LL));
     philox_init_kernel<<<blocks, 256, 0, st>>>(spins, R, N, S, seed, inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen_i16(const int16_t* src, int* dst, long long n, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    widen_i16_kernel<<<int(blocks), 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,8 @@ struct ising_s {
     uint32_t* d_colbits = nullptr;  // [R][S] bit t = (spin (t, q) > 0), kept during a learned pass
     int sp_simd = 0;                // every site has sum_j 2 |J_qj| <= 127 over its spatial neighbours
     long long* d_obs = nullptr;  // [R] per-slot magnetisation (ising_read_observables)
+    int* d_widen = nullptr;      // int32 scratch of ising_read_state (int16 fields), widen_cap entries
+    size_t widen_cap = 0;
     // graph
     int n = 0, M = 1, S = 0, W = 1, Mp = 4, D0 = 0, D = 0, max_sp_deg = 0, max_sp_J = 0;
     long long kmax = 0, ebound = 0;

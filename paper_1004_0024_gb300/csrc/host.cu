@@ -249,6 +249,8 @@ void ising_s::drop_graphs()
 void ising_s::free_replicas()
 {
     dfree(d_obs);
+    dfree(d_widen);
+    widen_cap = 0;
     drop_graphs();
     dfree(d_spins);
     if (d_fields)
@@ -1348,13 +1350,26 @@ int32_t ising_read_state(ising_t g, int8_t* spins, int32_t* fields, int64_t* ene
     const size_t RN = size_t(g->R) * g->n;
     if (spins)
         CK(cudaMemcpyAsync(spins, g->d_spins, RN, cudaMemcpyDeviceToHost, g->stream));
-    std::vector<int16_t> f16;
     if (fields) {
         if (g->field_bits == 32) {
             CK(cudaMemcpyAsync(fields, g->d_fields, RN * 4, cudaMemcpyDeviceToHost, g->stream));
         } else {
-            f16.resize(RN);
-            CK(cudaMemcpyAsync(f16.data(), g->d_fields, RN * 2, cudaMemcpyDeviceToHost, g->stream));
+            // widened on the device in chunks of at most 16 Mi fields (64 MB of
+            // scratch), each copied straight into the caller's buffer
+            const size_t chunk = std::min<size_t>(RN, size_t(1) << 24);
+            if (g->widen_cap < chunk) {
+                dfree(g->d_widen);
+                g->widen_cap = 0;
+                if ((rc = dalloc(&g->d_widen, chunk)))
+                    return rc;
+                g->widen_cap = chunk;
+            }
+            const int16_t* src = static_cast<const int16_t*>(g->d_fields);
+            for (size_t o = 0; o < RN; o += chunk) {
+                const size_t m = std::min(chunk, RN - o);
+                CK(launch_widen_i16(src + o, g->d_widen, (long long)m, g->stream));
+                CK(cudaMemcpyAsync(fields + o, g->d_widen, m * 4, cudaMemcpyDeviceToHost, g->stream));
+            }
         }
     }
     std::vector<int> e32(g->R);
@@ -1365,9 +1380,6 @@ int32_t ising_read_state(ising_t g, int8_t* spins, int32_t* fields, int64_t* ene
     unsigned long long cnt[2] = {0, 0};
     CK(cudaMemcpyAsync(cnt, g->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
-    if (fields && g->field_bits == 16)
-        for (size_t i = 0; i < RN; ++i)
-            fields[i] = f16[i];
     if (energy)
         for (int r = 0; r < g->R; ++r)
             energy[r] = e32[r];

@@ -310,6 +310,7 @@ cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st);
 cudaError_t mt_gen_set_smem_limit();
 cudaError_t launch_philox_init(int8_t* spins, int R, int N, int S, uint32_t seed, uint32_t inst,
                                cudaStream_t st);
+cudaError_t launch_widen_i16(const int16_t* src, int* dst, long long n, cudaStream_t st);
 cudaError_t launch_state_init(const int8_t* spins, void* fields, int field_bits, int* E, int R,
                               int N, const int* row_ptr, const int* col, const int* J,
                               const int* h, cudaStream_t st);
