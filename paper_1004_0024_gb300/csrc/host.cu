@@ -320,34 +320,78 @@ int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
     for (int i = 0; i < n; ++i)
         if (row_ptr[i + 1] < row_ptr[i])
             return fail(ISING_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
-    // every row's (column, J) entries sorted in one flat array
+    // every row's (column, J) entries sorted in one flat array; rows are
+    // checked in parallel chunks, and of each phase the error of the lowest
+    // row is reported (the one a row-by-row pass would meet first)
     const long long nnz = row_ptr[n];
     std::vector<std::pair<int, int>> ent(size_t(std::max<long long>(nnz, 0)));
-    for (int i = 0; i < n; ++i) {
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            if (col[e] < 0 || col[e] >= n)
-                return fail(ISING_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
-            if (col[e] == i)
-                return fail(ISING_ERR_SELF_LOOP_OR_DUP, "self loop at spin " + std::to_string(i));
-            if (J[e] > 32767 || J[e] < -32767)
-                return fail(ISING_ERR_INVALID_ARG, "|J| must be <= 32767");
-            ent[size_t(e)] = std::make_pair(col[e], J[e]);
+    struct RowErr {
+        int row = INT32_MAX, code = ISING_OK;
+        std::string msg;
+    };
+    auto run_rows = [&](auto&& check) -> RowErr {
+        const int nthr = n >= 8192 ? int(std::max(1u, std::min(16u, std::thread::hardware_concurrency()))) : 1;
+        std::vector<RowErr> errs(static_cast<size_t>(nthr));
+        auto part = [&](int t) {
+            const int i0 = int((long long)n * t / nthr), i1 = int((long long)n * (t + 1) / nthr);
+            for (int i = i0; i < i1; ++i)
+                if (check(i, errs[size_t(t)]))
+                    return;
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthr; ++t)
+            pool.emplace_back(part, t);
+        part(0);
+        for (auto& th : pool)
+            th.join();
+        RowErr best;
+        for (auto& e : errs)
+            if (e.code != ISING_OK && e.row < best.row)
+                best = e;
+        return best;
+    };
+    RowErr err = run_rows([&](int i, RowErr& e) {
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            if (col[k] < 0 || col[k] >= n) {
+                e = {i, ISING_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i)};
+                return true;
+            }
+            if (col[k] == i) {
+                e = {i, ISING_ERR_SELF_LOOP_OR_DUP, "self loop at spin " + std::to_string(i)};
+                return true;
+            }
+            if (J[k] > 32767 || J[k] < -32767) {
+                e = {i, ISING_ERR_INVALID_ARG, "|J| must be <= 32767"};
+                return true;
+            }
+            ent[size_t(k)] = std::make_pair(col[k], J[k]);
         }
         std::sort(ent.begin() + row_ptr[i], ent.begin() + row_ptr[i + 1]);
-        for (int e = row_ptr[i] + 1; e < row_ptr[i + 1]; ++e)
-            if (ent[size_t(e)].first == ent[size_t(e) - 1].first)
-                return fail(ISING_ERR_SELF_LOOP_OR_DUP, "repeated neighbour in row " + std::to_string(i));
-    }
+        for (int k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k)
+            if (ent[size_t(k)].first == ent[size_t(k) - 1].first) {
+                e = {i, ISING_ERR_SELF_LOOP_OR_DUP, "repeated neighbour in row " + std::to_string(i)};
+                return true;
+            }
+        return false;
+    });
+    if (err.code != ISING_OK)
+        return fail(err.code, err.msg);
     // symmetry: every (i, j, J) needs (j, i, J)
-    for (int i = 0; i < n; ++i)
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int j = ent[size_t(e)].first;
+    err = run_rows([&](int i, RowErr& e) {
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const int j = ent[size_t(k)].first;
             const auto b = ent.begin() + row_ptr[j], en = ent.begin() + row_ptr[j + 1];
             const auto it = std::lower_bound(b, en, std::make_pair(i, INT32_MIN));
-            if (it == en || it->first != i || it->second != ent[size_t(e)].second)
-                return fail(ISING_ERR_ASYMMETRIC_J,
-                            "J(" + std::to_string(i) + "," + std::to_string(j) + ") has no equal transpose");
+            if (it == en || it->first != i || it->second != ent[size_t(k)].second) {
+                e = {i, ISING_ERR_ASYMMETRIC_J,
+                     "J(" + std::to_string(i) + "," + std::to_string(j) + ") has no equal transpose"};
+                return true;
+            }
         }
+        return false;
+    });
+    if (err.code != ISING_OK)
+        return fail(err.code, err.msg);
     return ISING_OK;
 }
 

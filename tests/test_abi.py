@@ -70,3 +70,32 @@ def test_host_validation_errors(lib, case, code):
         lib.ising_create(g.n, rp, col, J, g.h, n_slices)
     assert ei.value.name == code
     assert lib.ising_last_error()
+
+
+@pytest.mark.parametrize("faults,code,where", [
+    ({"self": 9000, "range": 200}, "INVALID_ARG", "row 200"),
+    ({"range": 9000, "self": 200}, "SELF_LOOP_OR_DUP", "spin 200"),
+    ({"asym": 150, "dup": 9100}, "SELF_LOOP_OR_DUP", "row 9100"),
+    ({"asym": 9500}, "ASYMMETRIC_J", "J(9499,9500)"),  # first seen from row 9499
+])
+def test_host_validation_of_large_graphs_reports_the_first_row(lib, faults, code, where):
+    """A ring of 12000 spins (rows checked in parallel chunks): of several
+    faults, the error reported is the one a row-by-row check meets first
+    (index faults in any row before asymmetry, then the lowest row)."""
+    n = 12000
+    g = _graph({(i, (i + 1) % n): 1 + (i % 3) for i in range(n)}, n)
+    rp, col, J = g.row_ptr.copy(), g.col.copy(), g.J.copy()
+    for kind, row in faults.items():
+        e = rp[row]
+        if kind == "self":
+            col[e] = row
+        elif kind == "range":
+            col[e] = n + 5
+        elif kind == "dup":
+            col[e + 1] = col[e]
+        elif kind == "asym":
+            J[e] = J[e] + 1
+    with pytest.raises(lib.IsingError) as ei:
+        lib.ising_create(g.n, rp, col, J, g.h, 1)
+    assert ei.value.name == code
+    assert where in lib.ising_last_error(), lib.ising_last_error()
