@@ -30,7 +30,7 @@ constexpr int kGenGroupMaxS = 4096;  // slice sizes up to this use the staged pa
 
 __device__ __forceinline__ void mt_gen_body(const MtGenArgs& a, const int stream)
 {
-    extern __shared__ __align__(16) uint32_t gbuf[];  // [4][S] staged words
+    extern __shared__ __align__(16) uint32_t gbuf[];  // [4][S] staged words, then [S] site positions
     __shared__ uint32_t ring[kMtRing];
     const bool swap = a.do_swap && stream == a.R;
     uint32_t* gring = a.ring + size_t(stream) * kMtRing;
@@ -81,27 +81,37 @@ __device__ __forceinline__ void mt_gen_body(const MtGenArgs& a, const int stream
         }
     } else {
         const int S = a.S, M = a.M;
+        uint32_t* spos = gbuf + 4 * S;  // [S] the column position of each site, staged once
+        for (int q = threadIdx.x; q < S; q += blockDim.x)
+            spos[q] = uint32_t(a.pos_of_site[q]);
+        __syncthreads();
         const long long sweeps = nwords / a.N;
-        long long k0 = 0;  // stream offset of the current group
+        // ring slots need only the low bits of the stream position: 32-bit
+        // arithmetic (w & 1023 of a 64-bit w equals that of its low word)
+        uint32_t wl = uint32_t(w0);
         for (long long c = 0; c < sweeps; ++c) {
             uint32_t* wsw = a.wbuf + size_t(c) * a.wbuf_sweep_stride + size_t(stream) * S * a.Mp;
             for (int t0 = 0; t0 < M; t0 += 4) {
                 const int group = min(4, M - t0) * S;
                 for (int base = 0; base < group; base += kMtStep) {
-                    const int cnt = min(kMtStep, group - base);
-                    if (int(threadIdx.x) < cnt) {
+                    if (int(threadIdx.x) < min(kMtStep, group - base)) {
                         const int kk = base + threadIdx.x;
-                        gbuf[kk] = mt_step_word(ring, w0 + (unsigned long long)(k0 + kk));
+                        const uint32_t w = wl + uint32_t(kk);
+                        const uint32_t x = mt_recur(ring[(w - 624u) & (kMtRing - 1)],
+                                                    ring[(w - 623u) & (kMtRing - 1)],
+                                                    ring[(w - 227u) & (kMtRing - 1)]);
+                        ring[w & (kMtRing - 1)] = x;
+                        gbuf[kk] = mt_temper(x);
                     }
                     __syncthreads();
                 }
                 // flush: column q gets words of slices t0..t0+3 as one 16-byte store
                 for (int q = threadIdx.x; q < S; q += blockDim.x) {
                     const uint4 v = make_uint4(gbuf[q], gbuf[S + q], gbuf[2 * S + q], gbuf[3 * S + q]);
-                    *reinterpret_cast<uint4*>(wsw + size_t(a.pos_of_site[q]) * a.Mp + t0) = v;
+                    *reinterpret_cast<uint4*>(wsw + size_t(spos[q]) * a.Mp + t0) = v;
                 }
                 __syncthreads();
-                k0 += group;
+                wl += uint32_t(group);
             }
         }
     }
@@ -229,8 +239,9 @@ __global__ void __launch_bounds__(1024) pt_batch_kernel(const PtArgs* __restrict
 cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st)
 {
     // staged slices: 4 x S words (the kernel reads gbuf[2S + q], gbuf[3S + q]
-    // even for a final group of fewer than 4 slices, so all 4S are allocated)
-    const size_t smem = (a.mode == 0 && a.S <= kGenGroupMaxS) ? 16u * a.S : 0u;
+    // even for a final group of fewer than 4 slices, so all 4S are allocated),
+    // then the S site positions
+    const size_t smem = (a.mode == 0 && a.S <= kGenGroupMaxS) ? 20u * a.S : 0u;
     mt_gen_kernel<<<blocks, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -238,17 +249,17 @@ cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st)
 cudaError_t mt_gen_set_smem_limit()
 {
     cudaError_t e = cudaFuncSetAttribute(mt_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         16 * kGenGroupMaxS);
+                                         20 * kGenGroupMaxS);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mt_gen_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 16 * kGenGroupMaxS);
+                                 20 * kGenGroupMaxS);
     return e;
 }
 
 cudaError_t launch_mt_gen_batch(const MtGenArgs* args, const BatchItem* items, int n_items,
                                 int max_S, cudaStream_t st)
 {
-    const size_t smem = (max_S <= kGenGroupMaxS) ? 16u * size_t(max_S) : 0u;
+    const size_t smem = (max_S <= kGenGroupMaxS) ? 20u * size_t(max_S) : 0u;
     mt_gen_batch_kernel<<<n_items, 256, smem, st>>>(args, items);
     return cudaGetLastError();
 }
