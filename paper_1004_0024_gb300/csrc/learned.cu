@@ -193,7 +193,7 @@ struct LearnedArgs {
     uint32_t* colbits;  // [R][S] column bits: bit t = (spin (t, q) > 0)
     int sp_simd;        // every site has sum_j 2 |J_qj| <= 127 (byte-lane phi)
     int* phi;          // [rows][32]
-    bf16* X;           // [rows_pad][64]
+    bf16* X;           // rows_pad x 64 inputs, in tiles of 128 rows in the operand layout
     const float* L;    // [rows_pad / 128][32][128]: logit t of row i at (i / 128, t, i % 128)
     uint32_t seed, inst, pass;
     uint32_t *old_bits, *prop_bits;
@@ -205,7 +205,6 @@ struct LearnedArgs {
     int fp64_only;                // decide every move by the FP64 product
     void* fields;                 // [R][N] local fields, int16 or int32
     int field_bits;
-    int* err;
 };
 
 // phi_t = h_i + sum over spatial neighbours j (same slice) of J s_j, i = t S + q
@@ -1057,7 +1056,6 @@ LearnedArgs learned_args(ising_s* g, ising_mlp_s* m)
     a.n_exact = m->n_acc + 1;
     a.fields = g->d_fields;
     a.field_bits = g->field_bits;
-    a.err = m->err;
     a.n_changed = m->n_acc + 2;
     return a;
 }
