@@ -187,10 +187,13 @@ typedef struct {
     int32_t field_bits, rng_mode, kmax;
     int32_t fast_kernel;   /* 0 generic kernel, 1 register-resident kernel,
                               2 its lean variant (one replica per block,
-                              M in {4,8,16,32}, degree <= 6, |J| <= 63),
+                              M in {4,8,16,32} or a multiple of 32 up to
+                              1024, degree <= 6, |J| <= 63; blocks of at
+                              most 128 threads with two columns per thread
+                              use a build for more resident blocks per SM),
                               3 the track-scheduled variant (lean's limits,
-                              one thread per track of columns; opt-in with
-                              ISING_LAUNCH_TRACK) */
+                              M <= 32, one thread per track of columns;
+                              opt-in with ISING_LAUNCH_TRACK) */
 } ising_info_t;
 int32_t ising_get_info(ising_t h, ising_info_t* out);
 
