@@ -95,3 +95,52 @@ def test_column_move_leaves_conditional_boltzmann_stationary():
     # detailed balance, term by term
     F = pi[:, None] * P
     assert np.abs(F - F.T).max() < 1e-12
+
+
+def _ceil_p32_exact(bits):
+    """ceil(p 2^32) of FP32 p in [0, 1] from the bit pattern, exact integer
+    arithmetic: p = m 2^(e - 150) (m the 24-bit significand, e the biased
+    exponent; e = 0 for subnormals with exponent 1 - 127 - 23)."""
+    bits = bits.astype(np.uint64)
+    e = (bits >> np.uint64(23)) & np.uint64(0xFF)
+    m = (bits & np.uint64(0x7FFFFF)) | np.where(e > 0, np.uint64(0x800000), np.uint64(0))
+    sh = np.where(e > 0, e.astype(np.int64), 1) - 150 + 32  # p 2^32 = m 2^sh
+    out = np.zeros(bits.shape, dtype=np.uint64)
+    pos = sh >= 0
+    out[pos] = m[pos] << sh[pos].astype(np.uint64)
+    neg = ~pos & (m > 0)
+    k = (-sh[neg]).astype(np.uint64)
+    big = k >= np.uint64(40)
+    kk = np.minimum(k, np.uint64(39))
+    out[neg] = np.where(big, np.uint64(1), (m[neg] + (np.uint64(1) << kk) - np.uint64(1)) >> kk)
+    return out
+
+
+def test_fp32_ceiling_of_proposal_thresholds_is_exact():
+    """The learned-proposal kernel forms c = ceil(p 2^32) as ceilf(p * 2^32)
+    in FP32 and decides u < c with a 32-bit compare (c = 2^32: always): for a
+    strided sample of every FP32 p in [0, 1] (and the edge cases) this equals
+    the integer ceiling, and u = c - 1 is below c while u = c is not."""
+    one = np.float32(1.0).view(np.uint32)
+    sample = np.arange(0, int(one) + 1, 97, dtype=np.uint32)
+    edges = np.array([0, 1, 2, 0x007FFFFF, 0x00800000, 0x2F800000, 0x2F800001, 0x2F7FFFFF,
+                      0x3F7FFFFF, int(one)], dtype=np.uint32)
+    bits = np.unique(np.concatenate([sample, edges]))
+    p = bits.view(np.float32)
+    with np.errstate(over="ignore"):
+        cf = np.ceil(p * np.float32(2.0 ** 32))  # FP32 throughout
+    ci = _ceil_p32_exact(bits)
+    assert np.array_equal(cf.astype(np.float64), ci.astype(np.float64))
+
+    def word_below(u, c):  # the kernel's test u < c for an FP32 integer c <= 2^32
+        full = c >= np.float32(2.0 ** 32)
+        return full | (u < np.where(full, np.float32(0), c).astype(np.uint32))
+
+    mid = (ci > 0) & (ci < np.uint64(1 << 32))
+    c, cx = cf[mid], ci[mid]
+    assert np.all(word_below((cx - np.uint64(1)).astype(np.uint32), c))   # u = c - 1: drawn +1
+    assert not np.any(word_below(cx.astype(np.uint32), c))                # u = c: not drawn
+    top = ci == np.uint64(1 << 32)                                        # p = 1: always +1
+    assert top.any() and np.all(word_below(np.full(top.sum(), 0xFFFFFFFF, np.uint32), cf[top]))
+    zero = ci == 0                                                        # p = 0: never
+    assert zero.any() and not np.any(word_below(np.zeros(zero.sum(), np.uint32), cf[zero]))
