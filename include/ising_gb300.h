@@ -114,6 +114,30 @@ int32_t ising_set_stream(ising_t h, void* cuda_stream);
  * Re-initialising an initialised handle discards its replicas.
  * Errors: INVALID_ARG, FIELD_OVERFLOW, UNSUPPORTED, OOM, CUDA.
  */
+/*
+ * Acceptance mode of the flip thresholds (section 2.4 of the paper), used by
+ * the next ising_replicas_init of the handle (a property of the handle, not
+ * of checkpoints):
+ *   ISING_ACCEPT_EXACT     T_beta(k) = floor(2^32 exp(-2 beta k)) in FP64 (default);
+ *   ISING_ACCEPT_FAST      exp replaced by the paper's fast approximation:
+ *                          2 ln^2 2 F(round(2^23 x log2 e) + 127 2^23), F(i) the
+ *                          FP32 value with the bits of i (a linear interpolation
+ *                          of 2^y between integer y, mean relative error 0),
+ *                          0 below x = -126 ln 2;
+ *   ISING_ACCEPT_ACCURATE  (2 ln^2 2 F(round(2^25 x log2 e) + 127 2^23))^(1/4),
+ *                          relative error within (-0.01, 0.005), 0 below
+ *                          x = -31.5 ln 2.
+ * Both approximations are evaluated in FP32 steps (x = -2 beta k rounded
+ * from FP64, round-half-even to the integer, the fourth root as two correctly
+ * rounded square roots), then T = floor(2^32 min(1, e)), at most 2^32 - 1.
+ * They bias the stationary distribution (by the approximation's error); the
+ * swap thresholds stay exact.  Errors: INVALID_ARG (NULL handle, unknown mode).
+ */
+#define ISING_ACCEPT_EXACT 0
+#define ISING_ACCEPT_FAST 1
+#define ISING_ACCEPT_ACCURATE 2
+int32_t ising_set_acceptance(ising_t h, int32_t mode);
+
 int32_t ising_replicas_init(ising_t h, int32_t R, const double* betas, uint32_t seed,
                             int32_t rng_mode, int32_t field_bits);
 

@@ -60,6 +60,12 @@ def _load():
         lib.orc_flip_threshold.restype = ctypes.c_uint32
         lib.orc_swap_threshold.argtypes = [ctypes.c_double, ctypes.c_int64]
         lib.orc_swap_threshold.restype = ctypes.c_uint32
+        lib.orc_exp_approx.argtypes = [ctypes.c_float, ctypes.c_int32]
+        lib.orc_exp_approx.restype = ctypes.c_float
+        lib.orc_flip_threshold_mode.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int32]
+        lib.orc_flip_threshold_mode.restype = ctypes.c_uint32
+        lib.orc_sim_set_acceptance.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        lib.orc_sim_set_acceptance.restype = None
         lib.orc_fields.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i8p, _i64p]
         lib.orc_energy.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i8p]
         lib.orc_energy.restype = ctypes.c_int64
@@ -114,6 +120,19 @@ def flip_threshold(beta: float, k: int) -> int:
     return int(_load().orc_flip_threshold(beta, k))
 
 
+ACCEPT_MODES = {"exact": 0, "fast": 1, "accurate": 2}
+
+
+def exp_approx(x: float, accurate: bool = False) -> float:
+    """The paper's fast (or accurate) approximation of e^x (section 2.4)."""
+    return float(_load().orc_exp_approx(x, 1 if accurate else 0))
+
+
+def flip_threshold_mode(beta: float, k: int, mode: str = "exact") -> int:
+    """floor(2^32 min(1, e(-2 beta k))) with the mode's exponential."""
+    return int(_load().orc_flip_threshold_mode(beta, k, ACCEPT_MODES[mode]))
+
+
 def swap_threshold(dbeta: float, d: int) -> int:
     """floor(2^32 exp(-dbeta d)), d >= 1."""
     return int(_load().orc_swap_threshold(dbeta, d))
@@ -149,7 +168,7 @@ class Sim:
     """
 
     def __init__(self, g, betas, seed: int, rng: str = "mt19937", instance: int = 0,
-                 threads: int = 0):
+                 threads: int = 0, accept: str = "exact"):
         lib = _load()
         self._lib = lib
         self.n = int(g.n)
@@ -170,6 +189,8 @@ class Sim:
                                      _ptr(self.betas, _f64p), ctypes.c_uint32(seed & 0xFFFFFFFF),
                                      ctypes.c_uint32(instance & 0xFFFFFFFF), mode, threads)
         self.threads = int(lib.orc_sim_threads(self._h))
+        if accept != "exact":
+            lib.orc_sim_set_acceptance(self._h, ACCEPT_MODES[accept])
 
     def sweep(self, n: int = 1):
         self._lib.orc_sim_sweep(self._h, n)

@@ -160,6 +160,58 @@ uint32_t orc_flip_threshold(double beta, int64_t k)
     return (uint32_t)floor(ldexp(p, 32));
 }
 
+/* The paper's approximations of e^x (section 2.4, Figure 7, Appendix), as an
+ * optional acceptance mode.  Both read a 32-bit integer i as the float with
+ * the same bits, F(i) = (1 + frac(y)) 2^floor(y) for i = 2^23 (y + 127): a
+ * linear interpolation of 2^y between integer y.
+ *   fast:     e^x ~ 2 ln^2 2 F(round(2^23 x log2 e) + 127 * 2^23), the factor
+ *             making the mean relative error zero; 0 below x = -126 ln 2.
+ *   accurate: e^x ~ (2 ln^2 2 F(round(2^25 x log2 e) + 127 * 2^23))^(1/4)
+ *             (F then interpolates 2^(4y), exact at four times the points);
+ *             0 below x = -31.5 ln 2.
+ * Readings: every step in FP32 (x rounded from FP64, products rounded to
+ * nearest, the integer by round-half-even), and the fourth root taken
+ * exactly (two correctly rounded square roots) where the paper uses an
+ * approximate reciprocal square root, whose result is implementation
+ * defined. */
+static float orc_float_of_bits(uint32_t b)
+{
+    float f;
+    memcpy(&f, &b, sizeof f);
+    return f;
+}
+
+float orc_exp_approx(float x, int32_t accurate)
+{
+    const double ln2 = 0.69314718055994530942, log2e = 1.44269504088896340736;
+    const float scale = (float)(2.0 * ln2 * ln2);
+    if (!accurate) {
+        if (x < (float)(-126.0 * ln2))
+            return 0.0f;
+        const float a = x * (float)(8388608.0 * log2e);
+        const int32_t n = (int32_t)lrintf(a);
+        return orc_float_of_bits((uint32_t)(n + 0x3F800000)) * scale;
+    }
+    if (x < (float)(-31.5 * ln2))
+        return 0.0f;
+    const float a = x * (float)(33554432.0 * log2e);
+    const int32_t n = (int32_t)lrintf(a);
+    const float g = orc_float_of_bits((uint32_t)(n + 0x3F800000)) * scale;
+    return sqrtf(sqrtf(g));
+}
+
+/* Flip threshold of acceptance mode `mode` (0 exact, 1 fast, 2 accurate):
+ * floor(2^32 min(1, e(-2 beta k))), e the mode's exponential; an estimate of
+ * 1 or more becomes 2^32 - 1 (the table holds 32 bits). */
+uint32_t orc_flip_threshold_mode(double beta, int64_t k, int32_t mode)
+{
+    if (mode == 0)
+        return orc_flip_threshold(beta, k);
+    const float p = orc_exp_approx((float)(-2.0 * beta * (double)k), mode == 2);
+    const double t = floor(ldexp((double)p, 32));
+    return t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+}
+
 /* S(d) = floor(2^32 exp(-dbeta d)) for d >= 1, dbeta = beta_{k+1} - beta_k. */
 uint32_t orc_swap_threshold(double dbeta, int64_t d)
 {
@@ -446,6 +498,15 @@ void orc_sim_read(const orc_sim* m, int8_t* spins, int64_t* fields, int64_t* ene
 }
 
 int32_t orc_sim_threads(const orc_sim* m) { return m->threads; }
+
+/* Rebuild the flip thresholds of every temperature in acceptance mode `mode`
+ * (0 exact, 1 fast, 2 accurate exponential of section 2.4). */
+void orc_sim_set_acceptance(orc_sim* m, int32_t mode)
+{
+    for (int32_t k = 0; k < m->R; k++)
+        for (int64_t x = 1; x <= m->kmax; x++)
+            m->thr[k][x] = orc_flip_threshold_mode(m->beta[k], x, mode);
+}
 
 void orc_sim_destroy(orc_sim* m)
 {

@@ -61,6 +61,7 @@ struct ising_s {
     // register-resident kernel (M <= 32, tables in shared memory)
     bool use_fast = false, use_lean = false, persistent_ok = false, fast_off = false, lean_off = false;
     bool use_track = false, track_on = false;
+    int accept_mode = 0;      // ISING_ACCEPT_* of the flip thresholds (next replicas_init)
     bool lean_small = false;  // lean kernel, small-block instantiation (kernel variant 3)
     bool lean_long = false;   // lean kernel, long columns: M > 32 (kernel variant 4)
     // track schedule: columns (positions) in time order, track k =

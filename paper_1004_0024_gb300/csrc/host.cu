@@ -1113,8 +1113,48 @@ int32_t ising_set_stream(ising_t g, void* s)
     return ISING_OK;
 }
 
+// The approximate exponentials of the paper's section 2.4 in FP32 steps: the
+// integer n (round half even) plus 127 * 2^23, read as a float, interpolates
+// 2^y linearly between integer y; fast: n = round(2^23 x log2 e), scaled by
+// 2 ln^2 2; accurate: n = round(2^25 x log2 e) (2^(4y)), scaled, then the
+// fourth root as two correctly rounded square roots.
+static float approx_exp(float x, bool accurate)
+{
+    const double ln2 = 0.69314718055994530942, log2e = 1.44269504088896340736;
+    const float two_ln2_sq = float(2.0 * ln2 * ln2);
+    if (x < float((accurate ? -31.5 : -126.0) * ln2))
+        return 0.0f;
+    const float a = x * float((accurate ? 33554432.0 : 8388608.0) * log2e);
+    const uint32_t bits = uint32_t(int32_t(std::lrint(a)) + 0x3F800000);
+    float f;
+    std::memcpy(&f, &bits, sizeof f);
+    const float e = f * two_ln2_sq;
+    return accurate ? std::sqrt(std::sqrt(e)) : e;
+}
+
+// T_beta(k) = floor(2^32 min(1, exp(-2 beta k))) in the acceptance mode,
+// at most 2^32 - 1
+static uint32_t flip_threshold(double beta, long long k, int mode)
+{
+    if (mode == ISING_ACCEPT_EXACT)
+        return uint32_t(std::floor(std::ldexp(std::exp(-2.0 * beta * double(k)), 32)));
+    const float e = approx_exp(float(-2.0 * beta * double(k)), mode == ISING_ACCEPT_ACCURATE);
+    const double t = std::floor(std::ldexp(double(e), 32));
+    return t >= 4294967295.0 ? 0xFFFFFFFFu : uint32_t(t);
+}
+
 static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uint32_t seed,
                                   int32_t rng_mode, int32_t field_bits, uint32_t inst);
+
+int32_t ising_set_acceptance(ising_t g, int32_t mode)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (mode != ISING_ACCEPT_EXACT && mode != ISING_ACCEPT_FAST && mode != ISING_ACCEPT_ACCURATE)
+        return fail(ISING_ERR_INVALID_ARG, "unknown acceptance mode");
+    g->accept_mode = mode;
+    return ISING_OK;
+}
 
 int32_t ising_replicas_init(ising_t g, int32_t R, const double* betas, uint32_t seed,
                             int32_t rng_mode, int32_t field_bits)
@@ -1154,10 +1194,12 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
     g->betas.assign(betas, betas + R);
     g->maxpairs = R / 2;
 
-    // flip thresholds T_beta(k) = floor(2^32 exp(-2 beta k)), FP64; k >= K -> 0
+    // flip thresholds T_beta(k) = floor(2^32 exp(-2 beta k)), FP64 (or the
+    // approximate exponential of the handle's acceptance mode); k >= K -> 0
+    const int amode = g->accept_mode;
     long long kz = g->kmax + 1;
     for (long long k = 1; k <= g->kmax; ++k)
-        if (std::floor(std::ldexp(std::exp(-2.0 * betas[0] * double(k)), 32)) == 0.0) {
+        if (flip_threshold(betas[0], k, amode) == 0u) {
             kz = k;
             break;
         }
@@ -1165,8 +1207,7 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
     std::vector<uint32_t> thr(size_t(R) * g->K, 0u);
     for (int t = 0; t < R; ++t)
         for (int k = 1; k < g->K; ++k)
-            thr[size_t(t) * g->K + k] =
-                uint32_t(std::floor(std::ldexp(std::exp(-2.0 * betas[t] * double(k)), 32)));
+            thr[size_t(t) * g->K + k] = flip_threshold(betas[t], k, amode);
     // swap thresholds S_k(d) = floor(2^32 exp(-(b_{k+1}-b_k) d)) for 1 <= d < len_k
     std::vector<long long> swoff(std::max(R - 1, 1), 0);
     std::vector<int> swlen(std::max(R - 1, 1), 1);

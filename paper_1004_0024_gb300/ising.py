@@ -131,6 +131,7 @@ _SIGS = {
     "ising_read_observables": ([_vp, _i64p, _i64p], ctypes.c_int32),
     "ising_set_alloc_cap": ([ctypes.c_uint64], ctypes.c_int32),
     "ising_release_cached_memory": ([], ctypes.c_int32),
+    "ising_set_acceptance": ([_vp, ctypes.c_int32], ctypes.c_int32),
     "ising_selftest_wait": ([ctypes.c_int32, _vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -268,6 +269,9 @@ def ising_set_alloc_cap(nbytes):
     _check(_lib.ising_set_alloc_cap(int(nbytes)))
 
 
+ACCEPT_MODES = {"exact": 0, "fast": 1, "accurate": 2}  # ISING_ACCEPT_*
+
+
 def ising_release_cached_memory():
     """Free the MT19937 word buffers that destroyed handles left for reuse."""
     _check(_lib.ising_release_cached_memory())
@@ -291,12 +295,15 @@ class Ising:
     ``paper_1004_0024_gb300.workloads.Graph``).
     """
 
-    def __init__(self, graph, betas=None, seed=5489, rng="mt19937", field_bits=32, stream=None):
+    def __init__(self, graph, betas=None, seed=5489, rng="mt19937", field_bits=32, stream=None,
+                 accept="exact"):
         self.n = int(graph.n)
         self.h = ising_create(graph.n, graph.row_ptr, graph.col, graph.J, graph.h,
                               getattr(graph, "n_slices", 1))
         if stream is not None:
             ising_set_stream(self.h, stream)
+        if accept != "exact":
+            self.set_acceptance(accept)
         self.R = 0
         if betas is not None:
             self.replicas_init(betas, seed, rng, field_bits)
@@ -305,6 +312,11 @@ class Ising:
         betas = np.asarray(betas, dtype=np.float64)
         ising_replicas_init(self.h, betas.size, betas, seed, rng, field_bits)
         self.R = int(betas.size)
+
+    def set_acceptance(self, mode):
+        """Flip thresholds from the exact exponential ("exact") or the paper's
+        fast / accurate approximation, for the next replicas_init."""
+        _check(_lib.ising_set_acceptance(self.h, ACCEPT_MODES[mode]))
 
     def set_stream(self, stream):
         ising_set_stream(self.h, stream)

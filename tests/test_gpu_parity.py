@@ -300,3 +300,22 @@ def test_long_columns(ising, L, M, fb, rng):
     dev.run(7, 1)
     ref.run(7, 1)
     assert_same(dev, ref)
+
+
+@pytest.mark.parametrize("accept", ["fast", "accurate"])
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_approximate_exp_acceptance_modes(ising, accept, rng):
+    """Flip thresholds built with the paper's fast or accurate exponential
+    (section 2.4): sweeps and PT passes bit-exact against the oracle in the
+    same mode, and different from the exact mode's chain."""
+    g = W.layered_graph(5, 8, graph_seed=31, j_tau=3)
+    betas = W.geometric_betas(12, 0.1, 3.0)
+    dev = ising.Ising(g, betas, seed=99, rng=rng, field_bits=16, accept=accept)
+    ref = oracle.Sim(g, betas, seed=99, rng=rng, accept=accept)
+    dev.run(15, 1)
+    ref.run(15, 1)
+    assert_same(dev, ref)
+    exact = oracle.Sim(g, betas, seed=99, rng=rng)
+    exact.run(15, 1)
+    assert not np.array_equal(exact.read()["spins"], dev.read_state()["spins"])
+    dev.close()

@@ -380,3 +380,53 @@ def test_oracle_invariants_on_layered_config():
         assert oracle.energy(g, st["spins"][r]) == st["energy"][r]
     assert sorted(st["temp_of_slot"].tolist()) == list(range(c["R"]))
     assert st["sweeps"] == 40 and st["passes"] == 40
+
+
+# ---------------------------------------------- exp approximations (section 2.4)
+def _exp_approx_grid(lo, hi, n, accurate):
+    ys = np.linspace(lo, hi, n, endpoint=False)
+    xs = ys * np.log(2.0)
+    approx = np.array([oracle.exp_approx(float(x), accurate) for x in xs])
+    exact = np.exp(xs.astype(np.float32).astype(np.float64))
+    return ys, approx, exact
+
+
+def test_fast_exp_approximation_has_the_papers_error_figures():
+    """Unscaled, the fast approximation interpolates 2^y linearly between
+    integer y (exact there) with mean relative error (2 ln^2 2)^-1 - 1 =
+    0.0407 (Appendix); the 2 ln^2 2 factor brings the mean to zero."""
+    scale = 2.0 * np.log(2.0) ** 2
+    for n in range(-20, 1):
+        assert oracle.exp_approx(n * np.log(2.0)) / np.float32(scale) == pytest.approx(2.0 ** n, rel=1e-6)
+    ys, approx, exact = _exp_approx_grid(-6.0, 0.0, 24000, False)
+    rel_unscaled = approx / np.float32(scale) / exact - 1.0
+    assert abs(rel_unscaled.mean() - (1.0 / scale - 1.0)) < 5e-4
+    assert abs(1.0 / scale - 1.0 - 0.0407) < 1e-4
+    assert abs((approx / exact - 1.0).mean()) < 5e-4
+    assert oracle.exp_approx(-127.0 * np.log(2.0)) == 0.0  # below -126 ln 2
+
+
+def test_accurate_exp_approximation_stays_in_the_papers_band():
+    """The accurate approximation (2^(4y) interpolated, fourth root taken
+    exactly) has relative error within (-0.01, 0.005) over its range
+    -31.5 <= y < 0, and is 0 below it (Appendix, Figure 17)."""
+    ys, approx, exact = _exp_approx_grid(-31.5, 0.0, 20000, True)
+    rel = approx / exact - 1.0
+    assert rel.min() > -0.01 and rel.max() < 0.005, (rel.min(), rel.max())
+    assert oracle.exp_approx(-32.0 * np.log(2.0), True) == 0.0
+
+
+@pytest.mark.parametrize("mode", ["fast", "accurate"])
+def test_approximate_flip_thresholds_are_monotone_and_close(mode):
+    """Thresholds built with an approximate exponential decrease with k, and
+    stay within the approximation's error of the exact ones."""
+    band = 0.045 if mode == "fast" else 0.011
+    for beta in (0.1, 0.7, 2.5):
+        prev = 2 ** 32
+        for k in range(1, 60):
+            t = oracle.flip_threshold_mode(beta, k, mode)
+            assert t <= prev
+            prev = t
+            ex = oracle.flip_threshold(beta, k)
+            if ex > 1 << 12:
+                assert abs(t / ex - 1.0) < band, (beta, k, t, ex)
