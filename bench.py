@@ -105,6 +105,24 @@ def max_over_ranks(ms, world):
     return float(t.item())
 
 
+def sum_over_ranks(x, world):
+    """Sum of a per-rank number over the default process group."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(items, rank, world):
+    """Instance sharding of a batch: rank r of N takes items r, r + N, r + 2N,
+    ... (instances are independent: no exchange between ranks)."""
+    return list(items)[rank::world]
+
+
 def whole_job_value(world, per_step, steps, max_ms):
     """All ranks' attempts over the slowest rank's time (weak scaling)."""
     return world * per_step * steps / (max_ms * 1e-3)
@@ -485,13 +503,24 @@ def learned_passes_only(n):
 def run_batch(args):
     """The ragged batch: 4096 instances (spin counts log-uniform in
     2^11..2^15, 8..64 replicas), autotuned, one step = ising_batch_run(100, 1)
-    (a recorded CUDA graph of batched sweep and PT launches), Philox words."""
+    (a recorded CUDA graph of batched sweep and PT launches), Philox words.
+    Under torchrun the instances are sharded over the ranks (rank r takes
+    instances r, r + N, ...; numbered within its own batch): the total work is
+    fixed ("scaling": "strong"), the value is every rank's attempts over the
+    slowest rank's time."""
     import torch
+    import torch.distributed as dist
 
     from paper_1004_0024_gb300 import ising
     from paper_1004_0024_gb300 import workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     t0 = time.perf_counter()
-    built = [W.build_instance(d) for d in W.ragged_instances(4096)]
+    built = [W.build_instance(d) for d in shard(W.ragged_instances(4096), rank, world)]
     inst = [(x["graph"], x["betas"], x["seed"]) for x in built]
     stream = torch.cuda.current_stream()
     b = ising.Batch(inst, rng="philox", field_bits=16, stream=stream.cuda_stream)
@@ -503,6 +532,8 @@ def run_batch(args):
         b.run(sweeps, 1)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -512,28 +543,39 @@ def run_batch(args):
         b.run(sweeps, 1)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = sampler.stop()
-    ms = sum(a.elapsed_time(e) for a, e in ev)
-    value = per_step * args.steps / (ms * 1e-3)
-    resident = sum(b.info(i)["resident"] for i in range(len(inst)))
+    ms = max_over_ranks(sum(a.elapsed_time(e) for a, e in ev), world)
+    total_per_step = sum_over_ranks(per_step, world)
+    value = total_per_step * args.steps / (ms * 1e-3)
+    resident = int(sum_over_ranks(sum(b.info(i)["resident"] for i in range(len(inst))), world))
     deg = sum(float(x["graph"].row_ptr[-1]) for x in built) / sum(x["graph"].n for x in built)
     ops = 20 + 6 + 3 * deg
     peak, mhz = int_peak_tops(clocks)
+    b.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
     line = {"metric": "spin-flip attempts/sec vs roofline; ESS/sec learned proposal vs plain sweep",
-            "value": value, "unit": "attempts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
             "dtype": "int8 spins/int16 fields/uint32 RNG", "data": "synthetic (seeded ragged layered models)",
             "config": {"workload": f"4096 ragged instances (2^11..2^15 spins, 8..64 replicas), {sweeps} sweeps + PT each",
-                       "rng": "philox", "attempts_per_step": per_step, "resident_instances": resident,
+                       "rng": "philox", "attempts_per_step": total_per_step, "resident_instances": resident,
                        "setup_seconds": setup_s, "l2": "flushed (512 MB write) between timed steps",
-                       "parallelism": "replicas-only x1"},
+                       "parallelism": f"instances sharded x{world}" if world > 1 else "replicas-only x1"},
             "clocks": clocks,
-            "roofline": {"bound": "alu", "achieved": value * ops / 1e12, "peak": peak, "unit": "Tops/s (int32)",
-                         "frac": value * ops / 1e12 / peak, "traffic": None, "ops_per_attempt": ops,
+            "roofline": {"bound": "alu", "achieved": value / world * ops / 1e12, "peak": peak, "unit": "Tops/s (int32)",
+                         "frac": value / world * ops / 1e12 / peak, "traffic": None, "ops_per_attempt": ops,
+                         "per": "one GPU (the job's value divided by the ranks)",
                          "peak_basis": f"152 SM x 128 lanes x {mhz:.0f} MHz sampled SM clock (derived, not measured)",
                          "timed": "whole graph replay (every kernel of the step)"}}
-    b.close()
     print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
