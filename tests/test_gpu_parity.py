@@ -319,3 +319,25 @@ def test_approximate_exp_acceptance_modes(ising, accept, rng):
     exact.run(15, 1)
     assert not np.array_equal(exact.read()["spins"], dev.read_state()["spins"])
     dev.close()
+
+
+def test_reused_word_buffer_gives_the_same_chain(ising):
+    """MT19937 word buffers of 256 MB or more (here 10 sweeps of the 32x32x32
+    x 256 model, 335 MB) are kept by ising_destroy for the next handle and are
+    not zero-filled: a run on the reused buffer equals the same run on a fresh
+    one; ising_release_cached_memory empties the cache."""
+    c = W.config1()
+
+    def run_once():
+        sim = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng="mt19937", field_bits=16)
+        sim.run(10, 1)
+        st = sim.read_state()
+        sim.close()
+        return st
+
+    ising.ising_release_cached_memory()
+    first = run_once()   # allocates the buffer, then leaves it in the cache
+    second = run_once()  # takes it from the cache
+    for key in ("spins", "fields", "energy", "temp_of_slot"):
+        assert np.array_equal(first[key], second[key]), key
+    ising.ising_release_cached_memory()
