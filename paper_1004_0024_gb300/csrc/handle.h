@@ -22,6 +22,7 @@ struct ising_s {
     int* d_sp_off = nullptr;  // [S+1] spatial neighbour list of each site
     int2* d_sp_nbr = nullptr; // (site, J) entries
     uint32_t* d_colbits = nullptr;  // [R][S] bit t = (spin (t, q) > 0), kept during a learned pass
+    size_t colbits_cap = 0;         // entries of d_colbits (R * S of the replicas it was sized for)
     int sp_simd = 0;                // every site has sum_j 2 |J_qj| <= 127 over its spatial neighbours
     long long* d_obs = nullptr;  // [R] per-slot magnetisation (ising_read_observables)
     int* d_widen = nullptr;      // int32 scratch of ising_read_state (int16 fields), widen_cap entries

@@ -251,6 +251,8 @@ void ising_s::free_replicas()
     dfree(d_obs);
     dfree(d_widen);
     widen_cap = 0;
+    dfree(d_colbits);  // sized for these replicas (learned passes)
+    colbits_cap = 0;
     drop_graphs();
     dfree(d_spins);
     if (d_fields)

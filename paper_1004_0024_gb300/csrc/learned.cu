@@ -1010,9 +1010,10 @@ int32_t build_colours(ising_s* g)
         e = zalloc(&g->d_sp_nbr, sp_nbr.size());
     if (e == cudaSuccess && !sp_nbr.empty())
         e = cudaMemcpy(g->d_sp_nbr, sp_nbr.data(), sp_nbr.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = zalloc(&g->d_colbits, size_t(g->R) * S);
     if (e != cudaSuccess) {
+        zfree(g->d_colour_sites);
+        zfree(g->d_sp_off);
+        zfree(g->d_sp_nbr);
         g->colour_off.clear();
         return cuda_err(e, "colour classes");
     }
@@ -1371,6 +1372,13 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
     int32_t rc = build_colours(h);
     if (rc)
         return rc;
+    // column bits of the replicas (their lifetime: ising_replicas_init frees them)
+    if (h->colbits_cap < size_t(total)) {
+        zfree(h->d_colbits);
+        h->colbits_cap = 0;
+        LCK(zalloc(&h->d_colbits, size_t(total)));
+        h->colbits_cap = size_t(total);
+    }
     cudaStream_t st = h->stream;
     long long maxrows = 0;
     for (size_t c = 0; c + 1 < h->colour_off.size(); ++c)

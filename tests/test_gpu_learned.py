@@ -416,3 +416,24 @@ def test_fp32_screen_gives_the_fp64_decisions(ising):
     assert np.array_equal(a0, a1)
     for key in ("spins", "energy", "fields", "temp_of_slot"):
         assert np.array_equal(s0[key], s1[key]), key
+
+
+def test_learned_pass_after_reinit_with_more_replicas(ising):
+    """The column bits of a learned pass belong to the replicas: after
+    ising_replicas_init with four times as many replicas, a pass still leaves
+    every replica's fields and energy those of its spins."""
+    g = W.layered_graph(4, 8, 5)
+    sim = ising.Ising(g, W.geometric_betas(4, 0.1, 3.0), seed=3, rng="philox")
+    net = ising.Mlp(8, seed=5)
+    sim.run(3, 1)
+    net.learned_pass(sim)
+    sim.replicas_init(W.geometric_betas(16, 0.1, 3.0), seed=4, rng="philox")
+    sim.run(3, 1)
+    stats = net.learned_pass(sim)
+    assert stats["proposed"] == 16 * (g.n // 8)
+    st = sim.read_state()
+    for r in range(16):
+        assert st["energy"][r] == oracle.energy(g, st["spins"][r])
+        assert np.array_equal(st["fields"][r], oracle.fields(g, st["spins"][r]))
+    net.close()
+    sim.close()
