@@ -82,6 +82,18 @@ def _load():
         lib.orc_sim_threads.restype = ctypes.c_int32
         lib.orc_sim_destroy.argtypes = [ctypes.c_void_p]
         lib.orc_sim_set_spins.argtypes = [ctypes.c_void_p, ctypes.c_int32, _i8p]
+        lib.orc_exp_det.argtypes = [ctypes.c_double]
+        lib.orc_exp_det.restype = ctypes.c_double
+        lib.orc_trotter_flip_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_int64, ctypes.c_int64]
+        lib.orc_trotter_flip_threshold.restype = ctypes.c_uint32
+        lib.orc_trotter_swap_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_int64, ctypes.c_int64]
+        lib.orc_trotter_swap_threshold.restype = ctypes.c_uint32
+        lib.orc_sim_set_trotter.argtypes = [ctypes.c_void_p, _f64p]
+        lib.orc_sim_set_trotter.restype = None
+        lib.orc_sim_read_trotter.argtypes = [ctypes.c_void_p, _i64p]
+        lib.orc_sim_read_trotter.restype = None
         if hasattr(lib, "orc_mlp_forward"):
             _bind_mlp(lib)
         _lib = lib
@@ -136,6 +148,21 @@ def flip_threshold_mode(beta: float, k: int, mode: str = "exact") -> int:
 def swap_threshold(dbeta: float, d: int) -> int:
     """floor(2^32 exp(-dbeta d)), d >= 1."""
     return int(_load().orc_swap_threshold(dbeta, d))
+
+
+def exp_det(x: float) -> float:
+    """Deterministic e^x (Cody-Waite reduction, degree-13 Taylor, unfused FP64)."""
+    return float(_load().orc_exp_det(x))
+
+
+def trotter_flip_threshold(beta: float, K: float, ks: int, kt: int) -> int:
+    """Split couplings: floor(2^32 exp(-z)), z = 2 (beta ks + K kt) > 0."""
+    return int(_load().orc_trotter_flip_threshold(beta, K, ks, kt))
+
+
+def trotter_swap_threshold(dbeta: float, dK: float, dE: int, dC: int) -> int:
+    """Split couplings: floor(2^32 exp_det(-z)), z = dbeta dE + dK dC > 0."""
+    return int(_load().orc_trotter_swap_threshold(dbeta, dK, dE, dC))
 
 
 # ----------------------------------------------------------- graph helpers
@@ -213,6 +240,19 @@ class Sim:
                                _ptr(temp, _i32p), _ptr(counters, _u64p), _ptr(acc, _u64p))
         return dict(spins=spins, fields=fields_, energy=E, temp_of_slot=temp,
                     sweeps=int(counters[0]), passes=int(counters[1]), swap_acc=acc[:max(R - 1, 0)])
+
+    def set_trotter(self, K):
+        """Split couplings: temperature k weights exp(-beta_k E_space - K_k C);
+        fields and energies become the spatial ones (rebuilt from the spins)."""
+        self._K = _c(K, np.float64)
+        assert self._K.size == self.R
+        self._lib.orc_sim_set_trotter(self._h, _ptr(self._K, _f64p))
+
+    def read_trotter(self) -> np.ndarray:
+        """C = -sum over Trotter pairs of s s', per slot (split couplings)."""
+        out = np.empty(self.R, dtype=np.int64)
+        self._lib.orc_sim_read_trotter(self._h, _ptr(out, _i64p))
+        return out
 
     def set_spins(self, spins: np.ndarray):
         """Set every slot's spins ([R, n] or [n] broadcast); fields/energy recomputed."""

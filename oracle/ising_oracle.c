@@ -46,6 +46,14 @@
  *     -1.  For MT19937 the init words are the first N outputs of the replica's
  *     stream, and sweep c uses outputs N(1+c) .. N(2+c)-1.  Slot r starts at
  *     temperature index r.
+ *   - Split couplings (optional, orc_sim_set_trotter): the layered model of
+ *     section 4 comes from a Trotter decomposition whose inter-slice coupling
+ *     depends on the temperature.  Reading: temperature k weights a state by
+ *     exp(-beta_k E_space - K_k C), E_space the cost function over the
+ *     in-slice edges and C = -sum over the inter-slice (Trotter) pairs of
+ *     s s'; a flip has z = 2 s (beta f_space + K tau), tau the sum of the
+ *     spin's Trotter neighbours, and a swap z = dbeta dE + dK dC; each is
+ *     accepted iff z <= 0 or u < floor(2^32 e^-z) (held to 2^32 - 1).
  *
  * Replicas are independent between PT passes, so sweeps of different
  * replicas run on a pthread pool (one replica chunk per thread); the order of
@@ -219,6 +227,95 @@ uint32_t orc_swap_threshold(double dbeta, int64_t d)
     return (uint32_t)floor(ldexp(p, 32));
 }
 
+/* A deterministic exponential for the split-coupling PT rule below, whose
+ * argument z = dbeta dE + dK dC is real-valued and too varied to tabulate on
+ * the host: the same FP64 operations, in the same order and without fused
+ * multiply-adds, give the same bits on any IEEE machine.
+ *   Cody & Waite's reduction (Software Manual for the Elementary Functions,
+ *   1980): x = n ln 2 + r with n = round-half-even(x / ln 2) and ln 2 split
+ *   into a head of 32 significant bits (so n * head is exact) and a tail;
+ *   |r| <= ln(2)/2 up to rounding.
+ *   e^r by its Taylor series to degree 13 (truncation below r^14 / 14! <
+ *   4e-18), Horner order, coefficients 1/k! rounded to nearest.
+ *   e^x = e^r 2^n, exact while the result stays normal; x < -708 returns 0
+ *   (every threshold built from it is 0 long before that).
+ * Constants: head = ln 2 truncated to 32 significant bits, tail = ln 2 - head
+ * rounded to FP64, 1/ln 2 rounded to FP64. */
+double orc_exp_det(double x)
+{
+    static const double inv_ln2 = 0x1.71547652b82fep+0;
+    static const double ln2_hi = 0x1.62e42fee00000p-1;
+    static const double ln2_lo = 0x1.a39ef35793c76p-33;
+    static const double inv_fact[14] = {
+        0x1p+0, 0x1p+0, 0x1p-1, 0x1.5555555555555p-3, 0x1.5555555555555p-5,
+        0x1.1111111111111p-7, 0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13,
+        0x1.a01a01a01a01ap-16, 0x1.71de3a556c734p-19, 0x1.27e4fb7789f5cp-22,
+        0x1.ae64567f544e4p-26, 0x1.1eed8eff8d898p-29, 0x1.6124613a86d09p-33};
+    if (x < -708.0)
+        return 0.0;
+    if (x > 709.0)
+        return INFINITY;
+    /* volatile keeps every product and sum rounded on its own (no contraction) */
+    volatile double t = x * inv_ln2;
+    const double n = nearbyint(t);
+    volatile double a = n * ln2_hi;
+    volatile double b = n * ln2_lo;
+    volatile double r = (x - a) - b;
+    volatile double p = inv_fact[13];
+    for (int k = 12; k >= 0; k--) {
+        volatile double pr = p * r;
+        p = pr + inv_fact[k];
+    }
+    return ldexp(p, (int)n);
+}
+
+/* A 32-bit acceptance threshold: floor(2^32 p) for a probability p, held to
+ * 2^32 - 1 when p rounds to 1 (the word u < threshold test then rejects only
+ * u = 2^32 - 1). */
+static uint32_t orc_threshold_of(double p)
+{
+    const double t = floor(ldexp(p, 32));
+    return t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+}
+
+/* The exponents of the split-coupling rules, each product rounded on its own:
+ * a flip of spin s has z = 2 (beta k_s + K k_tau), k_s = s f_space and
+ * k_tau = s tau; a swap of the states at temperatures k, k+1 has
+ * z = dbeta dE + dK dC, dE and dC the lower-temperature state's energy and
+ * Trotter sum minus the upper one's.  Either is accepted iff z <= 0 or the
+ * word u < threshold(z). */
+static double flip_z(double beta, double K, int64_t ks, int64_t kt)
+{
+    volatile double a = beta * (double)ks;
+    volatile double b = K * (double)kt;
+    return 2.0 * (a + b);
+}
+
+static double swap_z(double dbeta, double dK, int64_t dE, int64_t dC)
+{
+    volatile double a = dbeta * (double)dE;
+    volatile double b = dK * (double)dC;
+    return a + b;
+}
+
+/* Flip threshold with split couplings: floor(2^32 exp(-z)) with libm's exp
+ * (the FP64 expression a host-built table uses).  Only meaningful for
+ * z > 0; z <= 0 flips unconditionally and returns 2^32 - 1 here. */
+uint32_t orc_trotter_flip_threshold(double beta, double K, int64_t ks, int64_t kt)
+{
+    const double z = flip_z(beta, K, ks, kt);
+    return z <= 0.0 ? 0xFFFFFFFFu : orc_threshold_of(exp(-z));
+}
+
+/* Swap threshold with split couplings: floor(2^32 e^-z) with the
+ * deterministic exponential.  Only meaningful for z > 0; z <= 0 always swaps
+ * and returns 2^32 - 1 here. */
+uint32_t orc_trotter_swap_threshold(double dbeta, double dK, int64_t dE, int64_t dC)
+{
+    const double z = swap_z(dbeta, dK, dE, dC);
+    return z <= 0.0 ? 0xFFFFFFFFu : orc_threshold_of(orc_exp_det(-z));
+}
+
 /* ----------------------------------------------------- energy and fields */
 /* f_i = h_i + sum_j J_ij s_j (the quantity Figure 6 keeps up to date). */
 void orc_fields(int32_t n, const int32_t* row_ptr, const int32_t* col,
@@ -271,7 +368,82 @@ typedef struct {
     uint64_t* swap_acc;    /* [R-1] */
     uint64_t sweeps, passes;
     int32_t threads;
+    /* split couplings (orc_sim_set_trotter): 0 = off */
+    int32_t split;
+    double* K;             /* [R] Trotter coupling per temperature index */
+    int64_t* C;            /* [R] -sum over Trotter pairs of s s' */
 } orc_sim;
+
+/* ------------------------------------------- split space / Trotter parts */
+/* With split couplings an edge (i, j) is a Trotter edge when i and j lie in
+ * different slices (i / S != j / S) and a spatial edge otherwise.  The
+ * spatial part keeps the graph's J; the Trotter part counts every pair with
+ * unit weight and the per-temperature coupling K_k instead of J. */
+static int same_slice(const orc_sim* m, int32_t i, int32_t j)
+{
+    return i / m->slice == j / m->slice;
+}
+
+/* f_i = h_i + sum over spatial neighbours of J_ij s_j. */
+static void split_fields(const orc_sim* m, const int8_t* s, int64_t* f)
+{
+    for (int32_t i = 0; i < m->n; i++) {
+        int64_t acc = m->h[i];
+        for (int32_t e = m->row_ptr[i]; e < m->row_ptr[i + 1]; e++)
+            if (same_slice(m, i, m->col[e]))
+                acc += (int64_t)m->J[e] * (int64_t)s[m->col[e]];
+        f[i] = acc;
+    }
+}
+
+/* E_space = -sum_i h_i s_i - sum over spatial pairs J s s' (each pair once). */
+static int64_t split_energy(const orc_sim* m, const int8_t* s)
+{
+    int64_t e = 0;
+    for (int32_t i = 0; i < m->n; i++) {
+        e -= (int64_t)m->h[i] * s[i];
+        for (int32_t k = m->row_ptr[i]; k < m->row_ptr[i + 1]; k++)
+            if (m->col[k] > i && same_slice(m, i, m->col[k]))
+                e -= (int64_t)m->J[k] * s[i] * s[m->col[k]];
+    }
+    return e;
+}
+
+/* C = -sum over Trotter pairs of s s' (each pair once). */
+static int64_t split_trotter_sum(const orc_sim* m, const int8_t* s)
+{
+    int64_t c = 0;
+    for (int32_t i = 0; i < m->n; i++)
+        for (int32_t k = m->row_ptr[i]; k < m->row_ptr[i + 1]; k++)
+            if (m->col[k] > i && !same_slice(m, i, m->col[k]))
+                c -= (int64_t)s[i] * s[m->col[k]];
+    return c;
+}
+
+/* tau_i = sum over Trotter neighbours of s_j. */
+static int64_t split_tau(const orc_sim* m, const int8_t* s, int32_t i)
+{
+    int64_t t = 0;
+    for (int32_t e = m->row_ptr[i]; e < m->row_ptr[i + 1]; e++)
+        if (!same_slice(m, i, m->col[e]))
+            t += s[m->col[e]];
+    return t;
+}
+
+/* Fields, energy (and Trotter sum) of slot r from its spins. */
+static void refresh_replica(orc_sim* m, int32_t r)
+{
+    const int8_t* s = m->s + (int64_t)r * m->n;
+    int64_t* f = m->f + (int64_t)r * m->n;
+    if (m->split) {
+        split_fields(m, s, f);
+        m->E[r] = split_energy(m, s);
+        m->C[r] = split_trotter_sum(m, s);
+    } else {
+        orc_fields(m->n, m->row_ptr, m->col, m->J, m->h, s, f);
+        m->E[r] = orc_energy(m->n, m->row_ptr, m->col, m->J, m->h, s);
+    }
+}
 
 static uint32_t init_word(orc_sim* m, int32_t r, int32_t i)
 {
@@ -291,8 +463,10 @@ static void sweep_replica_block(orc_sim* m, int32_t r, uint64_t c0, int64_t nswe
     int8_t* s = m->s + (int64_t)r * m->n;
     int64_t* f = m->f + (int64_t)r * m->n;
     const uint32_t* T = m->thr[m->temp_of_slot[r]];
+    const double beta = m->beta[m->temp_of_slot[r]];
+    const double K = m->split ? m->K[m->temp_of_slot[r]] : 0.0;
     for (int64_t c = 0; c < nsweeps; c++) {
-        int64_t dE = 0;
+        int64_t dE = 0, dC = 0;
         uint32_t sweep_id = (uint32_t)(c0 + (uint64_t)c);
         for (int32_t i = 0; i < m->n; i++) {
             uint32_t u;
@@ -304,16 +478,29 @@ static void sweep_replica_block(orc_sim* m, int32_t r, uint64_t c0, int64_t nswe
                                 sweep_id, m->inst, 0u, t & 3);
             }
             int64_t k = (int64_t)s[i] * f[i];
-            int accept = (k <= 0) || (u < T[k]);
+            int64_t kt = 0;
+            int accept;
+            if (m->split) {
+                /* split couplings: z = 2 s (beta f_space + K tau) */
+                kt = (int64_t)s[i] * split_tau(m, s, i);
+                const double z = flip_z(beta, K, k, kt);
+                accept = (z <= 0.0) || (u < orc_threshold_of(exp(-z)));
+            } else {
+                accept = (k <= 0) || (u < T[k]);
+            }
             if (accept) {
                 int64_t two_s = 2 * (int64_t)s[i];
                 for (int32_t e = m->row_ptr[i]; e < m->row_ptr[i + 1]; e++)
-                    f[m->col[e]] -= two_s * m->J[e];
+                    if (!m->split || same_slice(m, i, m->col[e]))
+                        f[m->col[e]] -= two_s * m->J[e];
                 s[i] = (int8_t)(-s[i]);
                 dE += 2 * k;
+                dC += 2 * kt;
             }
         }
         m->E[r] += dE;
+        if (m->split)
+            m->C[r] += dC;
     }
 }
 
@@ -375,7 +562,14 @@ void orc_sim_pt(orc_sim* m)
         }
         int32_t a = m->slot_of_temp[k], b = m->slot_of_temp[k + 1];
         int64_t d = m->E[a] - m->E[b];
-        int accept = (d <= 0) || (u < orc_swap_threshold(m->beta[k + 1] - m->beta[k], d));
+        int accept;
+        if (m->split) {
+            const double z = swap_z(m->beta[k + 1] - m->beta[k], m->K[k + 1] - m->K[k], d,
+                                    m->C[a] - m->C[b]);
+            accept = (z <= 0.0) || (u < orc_threshold_of(orc_exp_det(-z)));
+        } else {
+            accept = (d <= 0) || (u < orc_swap_threshold(m->beta[k + 1] - m->beta[k], d));
+        }
         if (accept) {
             m->slot_of_temp[k] = b;
             m->slot_of_temp[k + 1] = a;
@@ -464,8 +658,7 @@ orc_sim* orc_sim_create(int32_t n, const int32_t* row_ptr, const int32_t* col,
         int8_t* s = m->s + (int64_t)r * n;
         for (int32_t i = 0; i < n; i++)
             s[i] = (init_word(m, r, i) >> 31) ? (int8_t)1 : (int8_t)-1;
-        orc_fields(n, m->row_ptr, m->col, m->J, m->h, s, m->f + (int64_t)r * n);
-        m->E[r] = orc_energy(n, m->row_ptr, m->col, m->J, m->h, s);
+        refresh_replica(m, r);
         m->temp_of_slot[r] = r;
         m->slot_of_temp[r] = r;
     }
@@ -527,6 +720,8 @@ void orc_sim_destroy(orc_sim* m)
     free(m->slot_of_temp);
     free(m->swap_acc);
     free(m->mt);
+    free(m->K);
+    free(m->C);
     free(m);
 }
 
@@ -536,6 +731,30 @@ void orc_sim_set_spins(orc_sim* m, int32_t r, const int8_t* spins)
 {
     int8_t* s = m->s + (int64_t)r * m->n;
     memcpy(s, spins, (size_t)m->n);
-    orc_fields(m->n, m->row_ptr, m->col, m->J, m->h, s, m->f + (int64_t)r * m->n);
-    m->E[r] = orc_energy(m->n, m->row_ptr, m->col, m->J, m->h, s);
+    refresh_replica(m, r);
+}
+
+/* Switch to split couplings (space and Trotter parts weighted apart): the
+ * state at temperature index k then follows exp(-beta_k E_space - K_k C),
+ * C = -sum over Trotter pairs of s s'.  Fields become spatial only and the
+ * energy the spatial energy; both are rebuilt from the current spins.  The
+ * flip rule uses libm's exp (as a host-built table would), the swap rule the
+ * deterministic orc_exp_det.  K holds R values, by temperature index. */
+void orc_sim_set_trotter(orc_sim* m, const double* K)
+{
+    if (!m->K)
+        m->K = (double*)malloc(sizeof(double) * m->R);
+    if (!m->C)
+        m->C = (int64_t*)calloc(m->R, sizeof(int64_t));
+    memcpy(m->K, K, sizeof(double) * m->R);
+    m->split = 1;
+    for (int32_t r = 0; r < m->R; r++)
+        refresh_replica(m, r);
+}
+
+/* Trotter sums C of every slot (split couplings only; zeros otherwise). */
+void orc_sim_read_trotter(const orc_sim* m, int64_t* C)
+{
+    for (int32_t r = 0; r < m->R; r++)
+        C[r] = m->split ? m->C[r] : 0;
 }
