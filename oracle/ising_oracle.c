@@ -52,8 +52,10 @@
  *     exp(-beta_k E_space - K_k C), E_space the cost function over the
  *     in-slice edges and C = -sum over the inter-slice (Trotter) pairs of
  *     s s'; a flip has z = 2 s (beta f_space + K tau), tau the sum of the
- *     spin's Trotter neighbours, and a swap z = dbeta dE + dK dC; each is
- *     accepted iff z <= 0 or u < floor(2^32 e^-z) (held to 2^32 - 1).
+ *     spin's Trotter neighbours, and a swap z = dbeta dE + dK dC.  Each has
+ *     the threshold T = min(floor(2^32 e^-z), 2^32 - 1), T = 2^32 - 1 for
+ *     z <= 0, and is accepted iff T = 2^32 - 1 or u < T (so that one 32-bit
+ *     table entry holds the whole decision).
  *
  * Replicas are independent between PT passes, so sweeps of different
  * replicas run on a pthread pool (one replica chunk per thread); the order of
@@ -270,8 +272,7 @@ double orc_exp_det(double x)
 }
 
 /* A 32-bit acceptance threshold: floor(2^32 p) for a probability p, held to
- * 2^32 - 1 when p rounds to 1 (the word u < threshold test then rejects only
- * u = 2^32 - 1). */
+ * 2^32 - 1 when p rounds to 1 (or more). */
 static uint32_t orc_threshold_of(double p)
 {
     const double t = floor(ldexp(p, 32));
@@ -282,8 +283,7 @@ static uint32_t orc_threshold_of(double p)
  * a flip of spin s has z = 2 (beta k_s + K k_tau), k_s = s f_space and
  * k_tau = s tau; a swap of the states at temperatures k, k+1 has
  * z = dbeta dE + dK dC, dE and dC the lower-temperature state's energy and
- * Trotter sum minus the upper one's.  Either is accepted iff z <= 0 or the
- * word u < threshold(z). */
+ * Trotter sum minus the upper one's. */
 static double flip_z(double beta, double K, int64_t ks, int64_t kt)
 {
     volatile double a = beta * (double)ks;
@@ -299,8 +299,9 @@ static double swap_z(double dbeta, double dK, int64_t dE, int64_t dC)
 }
 
 /* Flip threshold with split couplings: floor(2^32 exp(-z)) with libm's exp
- * (the FP64 expression a host-built table uses).  Only meaningful for
- * z > 0; z <= 0 flips unconditionally and returns 2^32 - 1 here. */
+ * (the FP64 expression a host-built table uses), held to 2^32 - 1, and
+ * 2^32 - 1 for z <= 0.  The flip is taken iff the threshold is 2^32 - 1 or
+ * the word u is below it. */
 uint32_t orc_trotter_flip_threshold(double beta, double K, int64_t ks, int64_t kt)
 {
     const double z = flip_z(beta, K, ks, kt);
@@ -308,8 +309,8 @@ uint32_t orc_trotter_flip_threshold(double beta, double K, int64_t ks, int64_t k
 }
 
 /* Swap threshold with split couplings: floor(2^32 e^-z) with the
- * deterministic exponential.  Only meaningful for z > 0; z <= 0 always swaps
- * and returns 2^32 - 1 here. */
+ * deterministic exponential, held to 2^32 - 1, and 2^32 - 1 for z <= 0; the
+ * swap is taken iff the threshold is 2^32 - 1 or the word u is below it. */
 uint32_t orc_trotter_swap_threshold(double dbeta, double dK, int64_t dE, int64_t dC)
 {
     const double z = swap_z(dbeta, dK, dE, dC);
@@ -483,8 +484,8 @@ static void sweep_replica_block(orc_sim* m, int32_t r, uint64_t c0, int64_t nswe
             if (m->split) {
                 /* split couplings: z = 2 s (beta f_space + K tau) */
                 kt = (int64_t)s[i] * split_tau(m, s, i);
-                const double z = flip_z(beta, K, k, kt);
-                accept = (z <= 0.0) || (u < orc_threshold_of(exp(-z)));
+                const uint32_t thr = orc_trotter_flip_threshold(beta, K, k, kt);
+                accept = (thr == 0xFFFFFFFFu) || (u < thr);
             } else {
                 accept = (k <= 0) || (u < T[k]);
             }
@@ -564,9 +565,9 @@ void orc_sim_pt(orc_sim* m)
         int64_t d = m->E[a] - m->E[b];
         int accept;
         if (m->split) {
-            const double z = swap_z(m->beta[k + 1] - m->beta[k], m->K[k + 1] - m->K[k], d,
-                                    m->C[a] - m->C[b]);
-            accept = (z <= 0.0) || (u < orc_threshold_of(orc_exp_det(-z)));
+            const uint32_t thr = orc_trotter_swap_threshold(m->beta[k + 1] - m->beta[k],
+                                                            m->K[k + 1] - m->K[k], d, m->C[a] - m->C[b]);
+            accept = (thr == 0xFFFFFFFFu) || (u < thr);
         } else {
             accept = (d <= 0) || (u < orc_swap_threshold(m->beta[k + 1] - m->beta[k], d));
         }

@@ -69,11 +69,19 @@ def _threshold(p):
     return min(math.floor(math.ldexp(p, 32)), TOP)
 
 
+def _accept_prob(z, expfn):
+    """Probability of the rule: T = 2^32 - 1 for z <= 0, else
+    min(floor(2^32 e^-z), 2^32 - 1); T = 2^32 - 1 accepts every word, any
+    other T accepts the T words below it."""
+    t = TOP if z <= 0 else _threshold(expfn(-z))
+    return 1.0 if t == TOP else t / 2**32
+
+
 def _split_sweep_matrix(g, beta, K, order, sign=1):
     """One sweep as the product of single-spin kernels under split couplings:
-    z = 2 (beta s f_space + K s tau), accepted with probability 1 for z <= 0,
-    else min(floor(2^32 e^-z), 2^32 - 1) / 2^32.  ``sign = -1`` flips the
-    Trotter term (a wrong rule the histogram test must reject)."""
+    z = 2 (beta s f_space + K s tau) and the acceptance of ``_accept_prob``
+    with libm's exp.  ``sign = -1`` flips the Trotter term (a wrong rule the
+    histogram test must reject)."""
     n, S = g.n, g.slice_size
     X = _states(n)
     P = np.eye(2**n)
@@ -87,7 +95,7 @@ def _split_sweep_matrix(g, beta, K, order, sign=1):
             ks = int(s[i]) * (int(g.h[i]) + int(np.dot(Jn[spatial], s[nb[spatial]])))
             kt = sign * int(s[i]) * int(s[nb[~spatial]].sum())
             z = 2.0 * (beta * ks + K * kt)
-            a = 1.0 if z <= 0 else _threshold(math.exp(-z)) / 2**32
+            a = _accept_prob(z, math.exp)
             Ki[x, x ^ (1 << i)] += a
             Ki[x, x] += 1 - a
         P = P @ Ki
@@ -267,7 +275,7 @@ def test_split_pt_joint_chain_is_stationary():
         for x in range(ns):
             for y in range(ns):
                 z = (b1 - b0) * int(E[x] - E[y]) + ((K1 - K0) * int(C[x] - C[y]) if with_c else 0.0)
-                a = 1.0 if z <= 0 else _threshold(oracle.exp_det(-z)) / 2**32
+                a = _accept_prob(z, oracle.exp_det)
                 Q[x * ns + y, y * ns + x] += a
                 Q[x * ns + y, x * ns + y] += 1 - a
         return Q
