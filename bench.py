@@ -12,6 +12,7 @@ with a parallel-tempering pass after every sweep.  Synthetic seeded inputs
     python bench.py --impl reference     # the CPU oracle on the host cores
     python bench.py --workload cfg3      # 4096 spins x 65536 replicas, 500 sweeps, no PT
     python bench.py --workload paper     # the paper's 96 x 256-layer x 115-model shape, 30000 sweeps
+    python bench.py --workload cfg1-trotter  # cfg1 with temperature-dependent Trotter couplings
     python bench.py --learned-passes 3   # a short learned-proposal case for profilers
 
 The default line also carries `learned`: the ESS/s study of the learned
@@ -44,6 +45,8 @@ WORKLOAD_NAMES = {
     "cfg3": "16x16 lattice x 16 Trotter slices (4096 spins), 65536 replicas, betas 0.1-3.0 geometric, 500 sweeps, no PT",
     "paper": "the paper's shape: 256 Trotter layers x 96 spins (8x12 lattice, 24576 spins), 115 models at betas "
              "0.1-3.0 geometric, 30000 sweeps, no PT",
+    "cfg1-trotter": "32x32 lattice x 32 Trotter slices (32768 spins), 256 replicas, betas 0.05-5.0 geometric, "
+                    "split couplings K_k = (1/2) ln coth(beta_k 2 / 32), 200 sweeps + PT each",
 }
 # The paper's figures for its own workload shape (30000 sweeps x 115 models x
 # 24576 spins), derived from section 4 / Figure 13: other hardware, context only
@@ -63,10 +66,11 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposal study (ESS/s against the plain sweep)")
-    ap.add_argument("--workload", choices=["cfg1", "cfg3", "batch", "paper"], default="cfg1",
+    ap.add_argument("--workload", choices=["cfg1", "cfg3", "batch", "paper", "cfg1-trotter"], default="cfg1",
                     help="cfg1: the headline 32768-spin x 256-replica model; cfg3: 4096 spins x 65536 replicas; "
                          "batch: 4096 ragged instances, 100 sweeps + PT per step in one CUDA graph; "
-                         "paper: the paper's 96 x 256-layer x 115-model shape")
+                         "paper: the paper's 96 x 256-layer x 115-model shape; "
+                         "cfg1-trotter: cfg1 with temperature-dependent Trotter couplings (ising_set_trotter)")
     ap.add_argument("--launch-flags", type=int, default=-1,
                     help="ising_set_launch flags for the handle (-1: the library's choice)")
     ap.add_argument("--sweeps", type=int, default=0,
@@ -78,7 +82,8 @@ def parse_args():
 
 def workload(name="cfg1"):
     from paper_1004_0024_gb300 import workloads as W
-    return {"cfg1": W.config1, "cfg3": W.config3, "paper": W.config_paper}[name]()
+    return {"cfg1": W.config1, "cfg3": W.config3, "paper": W.config_paper,
+            "cfg1-trotter": W.config1_trotter}[name]()
 
 
 def attempts_per_step(c):
@@ -205,6 +210,8 @@ def run_ours(args):
                       stream=stream.cuda_stream)
     if args.launch_flags >= 0:
         sim.set_launch(0, 0, args.launch_flags)
+    if "K" in c:
+        sim.set_trotter(c["K"])
     info = sim.info()
     for _ in range(args.warmup):
         sim.run(sweeps, swap_every)
@@ -414,6 +421,8 @@ def cpu_baseline(c, rng, seconds):
     if c["R"] > 512:  # a bounded sample: the first 512 replicas (no PT in this workload)
         c = dict(c, R=512, betas=c["betas"][:512])
     sim = oracle.Sim(c["graph"], c["betas"], seed=c["seed"], rng=rng)
+    if "K" in c:
+        sim.set_trotter(c["K"][:c["R"]])
     t0 = time.perf_counter()
     sw = 1 if c["swap_every"] else 0
     sim.run(4, sw)

@@ -187,6 +187,45 @@ int32_t ising_read_state(ising_t h, int8_t* spins, int32_t* fields, int64_t* ene
 /* accepted[R-1]: accepted swaps of pair (k, k+1) so far (host, synchronises). */
 int32_t ising_read_swap_stats(ising_t h, uint64_t* accepted);
 
+/*
+ * ising_set_trotter -- split couplings.  The layered models of section 4 of
+ * the paper come from a Trotter decomposition whose inter-slice coupling
+ * depends on the temperature; the paper's original loop keeps the spatial
+ * and Trotter parts of the field apart (sections 2.1 and 2.2, Figures 2 and
+ * 3).  After this call the
+ * state at temperature index k follows exp(-beta_k E_space - K[k] C):
+ *   E_space  the cost function over the in-slice edges (h included),
+ *   C        -sum over the Trotter (inter-slice) pairs of s s', every pair
+ *            with unit weight (the graph's Trotter J values are ignored).
+ * A flip of spin s has z = 2 (beta k_s + K k_tau), k_s = s f_space and
+ * k_tau = s (s_{t-1} + s_{t+1}); a swap of the states at k, k+1 has
+ * z = (beta_{k+1} - beta_k) dE + (K[k+1] - K[k]) dC, dE and dC the state at
+ * k's E_space and C minus the state at k+1's.  Each product is rounded to
+ * FP64 on its own; the threshold is T = min(floor(2^32 e^-z), 2^32 - 1), and
+ * 2^32 - 1 for z <= 0; the move is taken iff T = 2^32 - 1 or the word u < T.
+ * Flips look T up in a table built on the host with the C library's exp;
+ * swaps evaluate e^-z on the device with a fixed FP64 exponential (Cody and
+ * Waite's reduction, degree-13 Taylor polynomial, no fused operations).
+ *   K  [R] host array by temperature index, finite (copied).
+ * The current spins are kept; fields become the spatial ones and the
+ * energies E_space (as ising_read_state reports them from then on), and C is
+ * computed.  Words are drawn exactly as without split couplings.  Split
+ * couplings last until the next ising_replicas_init.  Requires declared
+ * slices with a Trotter ring (M >= 3) and the lean kernel (M in {4, 8, 16,
+ * 32} or a multiple of 32 up to 1024, spatial degree <= 6, |J| <= 63, one
+ * replica per block); not with checkpoints, learned passes or
+ * ising_run_noalloc.  Errors: INVALID_ARG (NULL argument, non-finite K, set
+ * twice), NOT_INITIALISED, UNSUPPORTED (model or launch configuration without
+ * the lean kernel, acceptance mode other than EXACT, a flip table above 8192
+ * entries per temperature), OOM, CUDA.
+ */
+int32_t ising_set_trotter(ising_t h, const double* K);
+
+/* C[R] (int64, by slot): -sum over Trotter pairs of s s' of each slot's
+ * state under split couplings, zeros without them.  Synchronises.
+ * Errors: INVALID_ARG, NOT_INITIALISED, TIMEOUT, CUDA. */
+int32_t ising_read_trotter(ising_t h, int64_t* C);
+
 /* Energy and magnetisation m = sum_i s_i of the replica holding each
  * temperature index k (arrays [R], either may be NULL).  Synchronises. */
 int32_t ising_read_observables(ising_t h, int64_t* energy_by_temp, int64_t* magnetisation_by_temp);

@@ -1,6 +1,7 @@
 // Random-number streams, state initialisation and the parallel-tempering pass.
 #include <algorithm>
 #include "ising_internal.cuh"
+#include "split_math.cuh"
 
 namespace isg {
 namespace {
@@ -181,6 +182,50 @@ __global__ void __launch_bounds__(256) state_init_kernel(const int8_t* spins, FT
         E[r] = int(-red[0] / 2);
 }
 
+// Split couplings: f_i = h_i + sum over spatial j of J_ij s_j (j in the slice
+// of i), E = -1/2 sum_i s_i (f_i + h_i) (each spatial edge once) and
+// C = -1/2 sum_i s_i tau_i, tau_i the sum of the Trotter neighbours' spins
+// (each Trotter pair once).
+template <typename FT>
+__global__ void __launch_bounds__(256) split_state_init_kernel(const int8_t* spins, FT* fields, int* E,
+                                                               int* C, int N, int S, const int* row_ptr,
+                                                               const int* col, const int* J,
+                                                               const int* h)
+{
+    __shared__ long long red_e[256], red_c[256];
+    const int r = blockIdx.x;
+    const int8_t* s = spins + size_t(r) * N;
+    long long acc_e = 0, acc_c = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int ti = i / S;
+        int f = h[i], tau = 0;
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int j = col[e];
+            if (j / S == ti)
+                f += J[e] * int(s[j]);
+            else
+                tau += int(s[j]);
+        }
+        fields[size_t(r) * N + i] = FT(f);
+        acc_e += (long long)s[i] * (f + h[i]);
+        acc_c += (long long)s[i] * tau;
+    }
+    red_e[threadIdx.x] = acc_e;
+    red_c[threadIdx.x] = acc_c;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red_e[threadIdx.x] += red_e[threadIdx.x + w];
+            red_c[threadIdx.x] += red_c[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        E[r] = int(-red_e[0] / 2);
+        C[r] = int(-red_c[0] / 2);
+    }
+}
+
 // -------------------------------------------------------- PT pass
 // Pass p tries pairs (k, k+1), k = 2j + (p & 1).  Pairs of one pass are
 // disjoint, so each thread decides and applies its own pairs.
@@ -200,7 +245,14 @@ __device__ __forceinline__ void pt_body(const PtArgs& a)
             const uint4 ctr = make_uint4(uint32_t(j) >> 2, uint32_t(p), a.inst, 1u);
             u = pick4(philox4x32_10(ctr, a.seed, 0xFFFFFFFFu), j & 3);
         }
-        const bool acc = (d <= 0) || (d < a.swlen[k] && u < a.swthr[a.swoff[k] + d]);
+        bool acc;
+        if (a.split) {
+            const long long dc = (long long)a.C[sa] - (long long)a.C[sb];
+            const uint32_t th = split_detail::swap_threshold(a.dbeta[k], a.dK[k], d, dc);
+            acc = th == 0xFFFFFFFFu || u < th;
+        } else {
+            acc = (d <= 0) || (d < a.swlen[k] && u < a.swthr[a.swoff[k] + d]);
+        }
         if (acc) {
             a.slot_of_temp[k] = sb;
             a.slot_of_temp[k + 1] = sa;
@@ -300,6 +352,19 @@ cudaError_t launch_state_init(const int8_t* spins, void* fields, int field_bits,
     else
         state_init_kernel<int32_t><<<R, 256, 0, st>>>(spins, static_cast<int32_t*>(fields), E, N,
                                                        row_ptr, col, J, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_state_init(const int8_t* spins, void* fields, int field_bits, int* E, int* C,
+                                    int R, int N, int S, const int* row_ptr, const int* col,
+                                    const int* J, const int* h, cudaStream_t st)
+{
+    if (field_bits == 16)
+        split_state_init_kernel<int16_t><<<R, 256, 0, st>>>(spins, static_cast<int16_t*>(fields), E, C, N,
+                                                             S, row_ptr, col, J, h);
+    else
+        split_state_init_kernel<int32_t><<<R, 256, 0, st>>>(spins, static_cast<int32_t*>(fields), E, C, N,
+                                                             S, row_ptr, col, J, h);
     return cudaGetLastError();
 }
 

@@ -7,8 +7,13 @@
 namespace isg {
 namespace {
 
-void* pick(int field_bits, int rng, int cmax, int variant = 0, bool batch = false)
+void* pick(int field_bits, int rng, int cmax, int variant = 0, bool batch = false, bool split = false)
 {
+    if (split)  // lean variants only, single-instance launches only
+        return (batch || !(variant == 1 || variant == 3 || variant == 4))
+                   ? nullptr
+                   : (field_bits == 16 ? lean_split_kernel_i16(rng, cmax, variant == 3, variant == 4)
+                                       : lean_split_kernel_i32(rng, cmax, variant == 3, variant == 4));
     if (variant == 2)
         return field_bits == 16 ? track_kernel_i16(rng, batch) : track_kernel_i32(rng, batch);
     if (variant == 1 || variant == 3 || variant == 4)  // 3: small blocks, 4: long columns
@@ -38,14 +43,14 @@ cudaError_t fast_set_smem_limits()
     if (e != cudaSuccess)
         return e;
     size_t lim = size_t(optin);
-    for (int batch : {0, 1})
+    for (int batch : {0, 1, 2})  // 2: the split-coupling instantiations
     for (int variant : {0, 1, 2, 3, 4})
         for (int fb : {16, 32})
             for (int rng : {0, 1})
                 for (int cm : {1, 2, 4, 8}) {
                     if (variant == 2 && cm != 1)
                         continue;
-                    void* fn = pick(fb, rng, cm, variant, batch != 0);
+                    void* fn = pick(fb, rng, cm, variant, batch == 1, batch == 2);
                     if (!fn)
                         continue;
                     cudaFuncAttributes fa;
@@ -63,16 +68,18 @@ cudaError_t fast_set_smem_limits()
 }
 
 cudaError_t fast_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
-                                   int* out, int variant)
+                                   int* out, int variant, bool split)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, pick(field_bits, rng, cmax, variant),
-                                                         threads, smem);
+    void* fn = pick(field_bits, rng, cmax, variant, false, split);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, threads, smem);
 }
 
 cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
                         size_t smem, bool cooperative, cudaStream_t st, int variant)
 {
-    void* fn = pick(field_bits, a.rng, cmax, variant);
+    void* fn = pick(field_bits, a.rng, cmax, variant, false, a.split != 0);
     if (!fn)
         return cudaErrorInvalidValue;
     SweepArgs copy = a;

@@ -54,6 +54,13 @@ struct ising_s {
     uint32_t *d_wbuf = nullptr, *d_swbuf = nullptr;
     int* d_Epub = nullptr;
     unsigned* d_gridbar = nullptr;
+    // split couplings (ising_set_trotter; cleared by ising_replicas_init)
+    bool split = false;
+    int split_ks = 0;                  // k_space in [-split_ks, split_ks]
+    std::vector<double> trotter_K;     // [R] by temperature index
+    int* d_C = nullptr;                // [R] -sum over Trotter pairs of s s'
+    int* d_Cpub = nullptr;             // [2][R]
+    double *d_dbeta = nullptr, *d_dK = nullptr;  // [R-1]
     long long wbuf_cap = 0, swbuf_cap = 0;  // sweeps / passes
     long long word_budget = 8LL << 30;     // bytes of pre-generated MT19937 words
     // launch configuration

@@ -277,6 +277,13 @@ void ising_s::free_replicas()
     dfree(d_swbuf);
     dfree(d_Epub);
     dfree(d_gridbar);
+    dfree(d_C);
+    dfree(d_Cpub);
+    dfree(d_dbeta);
+    dfree(d_dK);
+    split = false;
+    split_ks = 0;
+    trotter_K.clear();
     wbuf_cap = swbuf_cap = 0;
     inited = false;
 }
@@ -577,11 +584,13 @@ void choose_fast(ising_s* g)
                   (g->rng == ISING_RNG_MT19937 || (g->ntracks >= 1 && g->ntracks <= g->T));
     if (long_cols && !g->use_lean)
         return;  // the register-resident fast kernel holds a column in one word
+    if (g->split && !g->use_lean)
+        return;  // split couplings: the lean kernel only
     g->lean_long = long_cols;
     // track variant: the lean kernel's limits with the columns walked as
     // tracks, one thread per track (when the block size is left automatic)
     const int T_track = ((g->ntracks + 31) / 32) * 32;
-    if (g->G == 1 && !long_cols && track_eligible(g)) {
+    if (g->G == 1 && !long_cols && !g->split && track_eligible(g)) {
         SweepArgs t = base_args(g);
         t.G = 1;
         const size_t sm = fast_smem_bytes(t, g->field_bits, 2, T_track);
@@ -608,8 +617,8 @@ void choose_fast(ising_s* g)
     if (!g_coop || !g->allow_persistent || g->smem_fused == size_t(-1) || g->R > 16384)
         return;
     int per_sm = 0;
-    if (fast_max_blocks_per_sm(g->field_bits, cmax, g->rng, g->T, g->smem_fused, &per_sm, variant) !=
-        cudaSuccess)
+    if (fast_max_blocks_per_sm(g->field_bits, cmax, g->rng, g->T, g->smem_fused, &per_sm, variant,
+                               g->split) != cudaSuccess)
         return;
     g->persistent_ok = (long long)per_sm * g_num_sms >= g->blocks;
 }
@@ -670,6 +679,12 @@ SweepArgs base_args(ising_s* g)
     // busy columns of a level form a contiguous range of positions no longer
     // than ntracks (the widest level); a thread's columns are T positions apart
     a.one_active = (g->ntracks >= 1 && g->ntracks <= g->T) ? 1 : 0;
+    a.split = g->split ? 1 : 0;
+    a.split_ks = g->split_ks;
+    a.C = g->d_C;
+    a.C_pub = g->d_Cpub;
+    a.dbeta = g->d_dbeta;
+    a.dK = g->d_dK;
     return a;
 }
 
@@ -897,6 +912,10 @@ PtArgs pt_args(ising_s* g, const Op& op)
     a.swbuf = g->d_swbuf;
     a.maxpairs = g->maxpairs;
     a.pass_rel = op.offset;
+    a.split = g->split ? 1 : 0;
+    a.C = g->d_C;
+    a.dbeta = g->d_dbeta;
+    a.dK = g->d_dK;
     return a;
 }
 
@@ -986,6 +1005,8 @@ int32_t isg_fused_launch(ising_t g, isg::FusedLaunch* out)
     if (!g->use_fast || !g->persistent_ok)
         return fail(ISING_ERR_UNSUPPORTED,
                     "this model/ladder has no persistent fused launch (replicas do not all fit on the GPU)");
+    if (g->split)
+        return fail(ISING_ERR_UNSUPPORTED, "split couplings run through ising_run / ising_sweep only");
     out->args = base_args(g);
     out->field_bits = g->field_bits;
     out->cmax = g->fast_cmax;
@@ -1353,6 +1374,8 @@ static int32_t run_ops(ising_t g, long long n, int swap_every, bool use_graph)
         return fail(ISING_ERR_INVALID_ARG, "NULL handle");
     if (!g->inited)
         return fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    if (g->split && !(g->use_fast && g->use_lean))
+        return fail(ISING_ERR_UNSUPPORTED, "split couplings need the lean kernel (this launch configuration has none)");
     const long long cap = (n > 0) ? words_cap(g, n) : 1;
     int32_t rc = ensure_buffers(g, cap, cap);
     if (rc)
@@ -1408,7 +1431,7 @@ int32_t ising_sweep(ising_t g, int64_t n)
 
 int32_t ising_pt_swap(ising_t g)
 {
-    if (g && g->inited && !g->pt_ok)
+    if (g && g->inited && !g->pt_ok && !g->split)
         return fail(ISING_ERR_UNSUPPORTED, "PT swap tables exceed 2^28 entries for this ladder: sweeps only");
     return run_ops(g, 0, -1, false);
 }
@@ -1419,7 +1442,7 @@ int32_t ising_run(ising_t g, int64_t n, int32_t swap_every)
         return fail(ISING_ERR_INVALID_ARG, "n must be >= 0");
     if (n == 0)
         return (g && g->inited) ? ISING_OK : fail(ISING_ERR_NOT_INITIALISED, "not initialised");
-    if (g && g->inited && swap_every > 0 && swap_every <= n && !g->pt_ok)
+    if (g && g->inited && swap_every > 0 && swap_every <= n && !g->pt_ok && !g->split)
         return fail(ISING_ERR_UNSUPPORTED, "PT swap tables exceed 2^28 entries for this ladder: sweeps only");
     return run_ops(g, n, swap_every > 0 ? swap_every : 0, true);
 }
@@ -1477,6 +1500,132 @@ int32_t ising_read_state(ising_t g, int8_t* spins, int32_t* fields, int64_t* ene
     return ISING_OK;
 }
 
+// Split-coupling flip threshold of temperature beta with Trotter coupling K:
+// z = 2 (beta k_s + K k_tau), each product rounded on its own (volatile keeps
+// the host compiler from fusing them); T = min(floor(2^32 e^-z), 2^32 - 1),
+// 2^32 - 1 for z <= 0 (that value accepts every word).
+static uint32_t split_flip_threshold(double beta, double K, int ks, int kt)
+{
+    volatile double a = beta * double(ks);
+    volatile double b = K * double(kt);
+    const double z = 2.0 * (a + b);
+    if (z <= 0.0)
+        return 0xFFFFFFFFu;
+    const double t = std::floor(std::ldexp(std::exp(-z), 32));
+    return t >= 4294967295.0 ? 0xFFFFFFFFu : uint32_t(t);
+}
+
+int32_t ising_set_trotter(ising_t g, const double* K)
+{
+    if (!g || !K)
+        return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    const int R = g->R;
+    for (int k = 0; k < R; ++k)
+        if (!std::isfinite(K[k]))
+            return fail(ISING_ERR_INVALID_ARG, "Trotter couplings must be finite");
+    if (g->split)
+        return fail(ISING_ERR_INVALID_ARG, "split couplings are already set: call ising_replicas_init first");
+    if (g->accept_mode != ISING_ACCEPT_EXACT)
+        return fail(ISING_ERR_UNSUPPORTED, "split couplings use the exact exponential (ISING_ACCEPT_EXACT)");
+    if (g->M < 3 || g->S < 1)
+        return fail(ISING_ERR_UNSUPPORTED, "split couplings need declared slices with a Trotter ring (M >= 3)");
+    // k_space bound: max_i |h_i| + sum over spatial j of |J_ij| (slices are identical)
+    long long ks = 0;
+    for (int q = 0; q < g->S; ++q) {
+        long long b = std::llabs((long long)g->h[q]);
+        for (int e = g->row_ptr[q]; e < g->row_ptr[q + 1]; ++e)
+            if (g->col[e] < g->S)
+                b += std::llabs((long long)g->J[e]);
+        ks = std::max(ks, b);
+    }
+    const long long Ks = 3 * (2 * ks + 1);
+    if (Ks > 8192)
+        return fail(ISING_ERR_UNSUPPORTED, "split-coupling flip table exceeds 8192 entries per temperature");
+    std::vector<uint32_t> thr(size_t(R) * size_t(Ks));
+    for (int t = 0; t < R; ++t)
+        for (long long k = -ks; k <= ks; ++k)
+            for (int j = 0; j < 3; ++j)
+                thr[size_t(t) * Ks + size_t(k + ks) * 3 + j] =
+                    split_flip_threshold(g->betas[t], K[t], int(k), 2 * j - 2);
+    std::vector<double> dbeta(std::max(R - 1, 1), 0.0), dK(std::max(R - 1, 1), 0.0);
+    for (int k = 0; k + 1 < R; ++k) {
+        dbeta[k] = g->betas[k + 1] - g->betas[k];
+        dK[k] = K[k + 1] - K[k];
+    }
+    // nothing queued may still read the plain tables or fields
+    CK(cudaStreamSynchronize(g->stream));
+    uint32_t* d_thr = nullptr;
+    int *d_C = nullptr, *d_Cpub = nullptr;
+    double *d_db = nullptr, *d_dk = nullptr;
+    int32_t rc;
+    if ((rc = upload(&d_thr, thr)) || (rc = dalloc(&d_C, R)) || (rc = dalloc(&d_Cpub, 2 * size_t(R))) ||
+        (rc = upload(&d_db, dbeta)) || (rc = upload(&d_dk, dK))) {
+        dfree(d_thr);
+        dfree(d_C);
+        dfree(d_Cpub);
+        dfree(d_db);
+        dfree(d_dk);
+        return rc;
+    }
+    const int K_plain = g->K;
+    uint32_t* thr_plain = g->d_thr;
+    g->split = true;
+    g->split_ks = int(ks);
+    g->K = int(Ks);
+    g->d_thr = d_thr;
+    g->drop_graphs();
+    rc = choose_launch(g);
+    if (rc || !(g->use_fast && g->use_lean)) {
+        // no lean launch for this model or configuration: back to plain couplings
+        g->split = false;
+        g->split_ks = 0;
+        g->K = K_plain;
+        g->d_thr = thr_plain;
+        dfree(d_thr);
+        dfree(d_C);
+        dfree(d_Cpub);
+        dfree(d_db);
+        dfree(d_dk);
+        const int32_t rc2 = choose_launch(g);
+        if (rc2)
+            return rc2;
+        return fail(ISING_ERR_UNSUPPORTED, "split couplings need the lean kernel, which this model or launch "
+                                           "configuration does not allow");
+    }
+    dfree(thr_plain);
+    g->d_C = d_C;
+    g->d_Cpub = d_Cpub;
+    g->d_dbeta = d_db;
+    g->d_dK = d_dk;
+    g->trotter_K.assign(K, K + R);
+    CK(launch_split_state_init(g->d_spins, g->d_fields, g->field_bits, g->d_E, g->d_C, R, g->n, g->S,
+                               g->d_row_ptr, g->d_col, g->d_J, g->d_h, g->stream));
+    return ISING_OK;
+}
+
+int32_t ising_read_trotter(ising_t g, int64_t* C)
+{
+    if (!g || !C)
+        return fail(ISING_ERR_INVALID_ARG, "NULL argument");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    if (!g->split) {
+        std::fill(C, C + g->R, int64_t(0));
+        return ISING_OK;
+    }
+    int32_t rc = check_device_error(g);
+    if (rc)
+        return rc;
+    std::vector<int> c32(g->R);
+    CK(cudaMemcpyAsync(c32.data(), g->d_C, sizeof(int) * g->R, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    for (int r = 0; r < g->R; ++r)
+        C[r] = c32[r];
+    return ISING_OK;
+}
+
 int32_t ising_read_swap_stats(ising_t g, uint64_t* accepted)
 {
     if (!g || !accepted)
@@ -1515,6 +1664,8 @@ int32_t ising_save(ising_t g, void* buf, size_t cap, size_t* size)
         return fail(ISING_ERR_INVALID_ARG, "NULL argument");
     if (!g->inited)
         return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    if (g->split)
+        return fail(ISING_ERR_UNSUPPORTED, "checkpoints of split-coupling state are not supported");
     const size_t need = blob_size(g);
     *size = need;
     if (!buf)
@@ -1555,6 +1706,8 @@ int32_t ising_load(ising_t g, const void* buf, size_t size)
         return fail(ISING_ERR_INVALID_ARG, "NULL argument");
     if (!g->inited)
         return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
+    if (g->split)
+        return fail(ISING_ERR_UNSUPPORTED, "checkpoints of split-coupling state are not supported");
     if (size != blob_size(g))
         return fail(ISING_ERR_INVALID_ARG, "blob size does not match this handle");
     const char* p = static_cast<const char*>(buf);

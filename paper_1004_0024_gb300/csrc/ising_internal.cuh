@@ -83,6 +83,17 @@ struct SweepArgs {
     // lean kernel: at most one owned column of a thread is busy per level
     // (no level has more busy columns than the block has threads)
     int one_active;
+    // split couplings (ising_set_trotter; lean kernel only): the fields are
+    // spatial, E the spatial energy, C = -sum over Trotter pairs of s s', and
+    // the flip table of temperature k has K = 3 (2 split_ks + 1) entries, entry
+    // (k_s + split_ks) * 3 + k_tau / 2 + 1 for k_s = s f_space in
+    // [-split_ks, split_ks] and k_tau = s (s_{t-1} + s_{t+1}) in {-2, 0, 2}
+    int split;
+    int split_ks;
+    int* C;                // [R]
+    int* C_pub;            // [2][R] Trotter sums published for the PT pass
+    const double* dbeta;   // [R-1] beta_{k+1} - beta_k
+    const double* dK;      // [R-1] K_{k+1} - K_k
 };
 
 // One block of a batched launch: instance index and block index within it.
@@ -105,6 +116,11 @@ struct PtArgs {
     const uint32_t* swbuf;     // MT swap words [pass][maxpairs]
     int maxpairs;
     int pass_rel;              // pass index inside swbuf
+    // split couplings: z = dbeta dE + dK dC with the deterministic exponential
+    int split;
+    const int* C;              // [R]
+    const double* dbeta;       // [R-1]
+    const double* dK;          // [R-1]
 };
 
 struct MtGenArgs {
@@ -302,8 +318,10 @@ cudaError_t launch_fast_batch(const SweepArgs* args, const BatchItem* items, int
 cudaError_t launch_pt_batch(const PtArgs* args, int n_inst, int max_R, cudaStream_t st);
 cudaError_t launch_mt_gen_batch(const MtGenArgs* args, const BatchItem* items, int n_items,
                                 int max_S, cudaStream_t st);
+// split: the split-coupling instantiation of the lean kernel (variants 1, 3, 4
+// only; launch_fast takes it from a.split)
 cudaError_t fast_max_blocks_per_sm(int field_bits, int cmax, int rng, int threads, size_t smem,
-                                   int* out, int variant = 0);
+                                   int* out, int variant = 0, bool split = false);
 cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int threads, int blocks,
                         size_t smem, bool cooperative, cudaStream_t st, int variant = 0);
 cudaError_t launch_mt_gen(const MtGenArgs& a, int blocks, cudaStream_t st);
@@ -314,5 +332,11 @@ cudaError_t launch_widen_i16(const int16_t* src, int* dst, long long n, cudaStre
 cudaError_t launch_state_init(const int8_t* spins, void* fields, int field_bits, int* E, int R,
                               int N, const int* row_ptr, const int* col, const int* J,
                               const int* h, cudaStream_t st);
+// Split couplings: spatial fields, spatial energy and Trotter sum C of every
+// replica from its spins (an edge is spatial when both ends lie in one slice
+// of S spins).
+cudaError_t launch_split_state_init(const int8_t* spins, void* fields, int field_bits, int* E, int* C,
+                                    int R, int N, int S, const int* row_ptr, const int* col,
+                                    const int* J, const int* h, cudaStream_t st);
 
 }  // namespace isg

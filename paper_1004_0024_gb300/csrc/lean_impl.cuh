@@ -33,10 +33,17 @@
 //    When the slice leaves a word, the word is stored and the next-but-one is
 //    loaded, 32 levels before it is needed; the words of slices 0 and M - 1
 //    are stored before the other end of the ring reads them.
+//  * SPLIT (split couplings, ising_set_trotter): the global fields are the
+//    spatial ones, the Trotter coupling of the graph is ignored, and a flip
+//    looks up the temperature's table at (k_s, k_tau), k_s = s f_space and
+//    k_tau = s (s_{t-1} + s_{t+1}); the block accumulates the spatial energy
+//    and the Trotter sum C apart, and the fused PT pass evaluates
+//    z = dbeta dE + dK dC with the deterministic exponential (split_math.cuh).
 #pragma once
 #include <climits>
 
 #include "fast_impl.cuh"
+#include "split_math.cuh"
 
 namespace isg {
 namespace lean_detail {
@@ -68,14 +75,14 @@ __host__ __device__ constexpr int lean_bound_threads(int cmax, bool small)
 {
     return small ? kLeanSmallThreads : lean_max_threads(cmax);
 }
-__host__ __device__ constexpr int lean_bound_blocks(int cmax, bool small, int rng)
+__host__ __device__ constexpr int lean_bound_blocks(int cmax, bool small, int rng, bool split = false)
 {
-    return small ? (rng == 0 ? 12 : 8) : lean_min_blocks(cmax);
+    return small ? (rng == 0 && !split ? 12 : 8) : lean_min_blocks(cmax);
 }
 
 // Body of one block: `blk` is the replica (block) index within its instance
 // and `nblk` the instance's number of blocks (the grid size for one instance).
-template <typename FT, int RNG, int CMAX, bool LONG>
+template <typename FT, int RNG, int CMAX, bool LONG, bool SPLIT = false>
 __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, const int nblk)
 {
     constexpr bool kI16 = sizeof(FT) == 2;
@@ -115,8 +122,11 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
         bulk_g2s(smem + L.pos, a.pos, b2, bar);
         bulk_g2s(smem + L.site, a.site, b2, bar);
     }
-    if (tid == 0)
+    if (tid == 0) {
         eacc[0] = 0;
+        if constexpr (SPLIT)
+            eacc[1] = 0;  // the region holds 16 bytes even for one replica
+    }
     if (fused)
         for (int i = tid; i < R; i += T) {
             slot_s[i] = a.slot_of_temp[i];
@@ -137,7 +147,8 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
         for (int i = tid; i < N; i += T) {
             const int t = i / S, q = i - t * S, p = pos[q];
             const int tm = (t == 0) ? M - 1 : t - 1, tp = (t == M - 1) ? 0 : t + 1;
-            const int ft = jtau[p] * (int(sp[tm * S + q]) + int(sp[tp * S + q]));
+            // SPLIT: the global fields already hold the spatial part only
+            const int ft = SPLIT ? 0 : jtau[p] * (int(sp[tm * S + q]) + int(sp[tp * S + q]));
             Fsp<FT>::st(fsp, p * M + t, int(fg[i]) - ft);
         }
     }
@@ -172,7 +183,7 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
         if (p < S) {
             lv[c] = a.lev0[p];
             const int e0 = nbr_off[p], deg = nbr_off[p + 1] - e0;
-            jd[c] = (jtau[p] << 8) | deg;
+            jd[c] = ((SPLIT ? 0 : jtau[p]) << 8) | deg;  // SPLIT: no Trotter part in the field
             fb[c] = p * M;
             const uint32_t own = kI16 ? uint32_t(p * M / 2) : uint32_t(p * M);
 #pragma unroll
@@ -206,12 +217,13 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
 
     const unsigned long long sweep0 = a.counters[0];
     const unsigned FULL = 0xFFFFFFFFu;
-    const bool shfl_thr = K <= 32;
+    const bool shfl_thr = !SPLIT && K <= 32;
     uint32_t thr_lane = (shfl_thr && (tid & 31) < K) ? thr_s[tid & 31] : 0u;
     const unsigned long long pass0 = a.counters[1];
     const int nrb = (M + 3) >> 2;  // random-word blocks per column
     int npass = 0;
     int dE = 0;
+    int dC = 0;  // SPLIT: change of the Trotter sum C
     // Philox block in progress: one per thread, as a thread has at most one busy
     // column per level (the host sizes the block to the widest level)
     uint4 pc = make_uint4(0u, 0u, 0u, 0u);
@@ -271,16 +283,30 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                     const int ft = (jd[c] >> 8) * (2 * int((w3 & 1u) + ((w3 >> 2) & 1u)) - 2);
                     const int k = s * (fs + ft);
                     uint32_t tk;
-                    if (shfl_thr)
-                        tk = __shfl_sync(FULL, thr_lane, (k > 0 && k < K) ? k : 0);
-                    else
-                        tk = (k > 0 && k < K) ? thr_s[k] : 0u;
-                    if (act && ((k <= 0) || (k < K && u < tk))) {
+                    bool take;
+                    int kt = 0;
+                    if constexpr (SPLIT) {
+                        // k = k_s (ft = 0); entry (k_s + KS) * 3 + k_tau / 2 + 1, held inside
+                        // the table for the idle lanes of the converged section
+                        kt = s * (2 * int((w3 & 1u) + ((w3 >> 2) & 1u)) - 2);
+                        const int idx = min(max((k + a.split_ks) * 3 + (kt >> 1) + 1, 0), K - 1);
+                        tk = thr_s[idx];
+                        take = act && (tk == 0xFFFFFFFFu || u < tk);
+                    } else {
+                        if (shfl_thr)
+                            tk = __shfl_sync(FULL, thr_lane, (k > 0 && k < K) ? k : 0);
+                        else
+                            tk = (k > 0 && k < K) ? thr_s[k] : 0u;
+                        take = act && ((k <= 0) || (k < K && u < tk));
+                    }
+                    if (take) {
                         if constexpr (LONG)
                             cwW[c] ^= 1u << (t & 31);
                         else
                             bits[c] ^= rep << t;
                         dE += 2 * k;
+                        if constexpr (SPLIT)
+                            dC += 2 * kt;
                         const int tw = kI16 ? (t >> 1) : t;
                         const int sh = kI16 ? ((t & 1) << 4) : 0;
 #pragma unroll
@@ -335,13 +361,25 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
             if (dE != 0)
                 atomicAdd(&eacc[0], dE);
             dE = 0;
+            if constexpr (SPLIT) {
+                if (dC != 0)
+                    atomicAdd(&eacc[1], dC);
+                dC = 0;
+            }
             __syncthreads();
             int* Ep = a.E_pub + size_t(npass & 1) * R;
+            int* Cp = SPLIT ? a.C_pub + size_t(npass & 1) * R : nullptr;
             if (tid == 0) {
                 const int e = a.E[r] + eacc[0];
                 a.E[r] = e;
                 Ep[r] = e;
                 eacc[0] = 0;
+                if constexpr (SPLIT) {
+                    const int cs = a.C[r] + eacc[1];
+                    a.C[r] = cs;
+                    Cp[r] = cs;
+                    eacc[1] = 0;
+                }
             }
             if (nblk == 1)  // a one-block instance has nobody else to wait for
                 __syncthreads();
@@ -361,7 +399,15 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
                     else
                         u = pick4(philox4x32_10(make_uint4(uint32_t(j) >> 2, uint32_t(p), a.inst, 1u),
                                                 a.seed, 0xFFFFFFFFu), j & 3);
-                    if ((d <= 0) || (d < a.swlen[k] && u < a.swthr[a.swoff[k] + d])) {
+                    bool take;
+                    if constexpr (SPLIT) {
+                        const long long dc = (long long)__ldcg(Cp + sa) - (long long)__ldcg(Cp + sb);
+                        const uint32_t th = split_detail::swap_threshold(a.dbeta[k], a.dK[k], d, dc);
+                        take = th == 0xFFFFFFFFu || u < th;
+                    } else {
+                        take = (d <= 0) || (d < a.swlen[k] && u < a.swthr[a.swoff[k] + d]);
+                    }
+                    if (take) {
                         slot_s[k] = sb;
                         slot_s[k + 1] = sa;
                         temp_s[sa] = k + 1;
@@ -383,9 +429,15 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     // ---- energies and write-back of the owned columns
     if (dE != 0)
         atomicAdd(&eacc[0], dE);
+    if constexpr (SPLIT)
+        if (dC != 0)
+            atomicAdd(&eacc[1], dC);
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0) {
         a.E[r] += eacc[0];
+        if constexpr (SPLIT)
+            a.C[r] += eacc[1];
+    }
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
         if (lv[c] < INT_MAX / 2) {
@@ -428,11 +480,11 @@ __device__ __forceinline__ void lean_body(const SweepArgs& a, const int blk, con
     }
 }
 
-template <typename FT, int RNG, int CMAX, bool SMALL, bool LONG = false>
-__global__ void __launch_bounds__(lean_bound_threads(CMAX, SMALL), lean_bound_blocks(CMAX, SMALL, RNG))
+template <typename FT, int RNG, int CMAX, bool SMALL, bool LONG = false, bool SPLIT = false>
+__global__ void __launch_bounds__(lean_bound_threads(CMAX, SMALL), lean_bound_blocks(CMAX, SMALL, RNG, SPLIT))
     lean_kernel(const SweepArgs a)
 {
-    lean_body<FT, RNG, CMAX, LONG>(a, int(blockIdx.x), int(gridDim.x));
+    lean_body<FT, RNG, CMAX, LONG, SPLIT>(a, int(blockIdx.x), int(gridDim.x));
 }
 
 // Batched launch over many instances: each block copies its instance's
@@ -473,9 +525,30 @@ void* pick_lean(int cmax, bool batch = false, bool small = false, bool longc = f
     }
 }
 
+// The split-coupling instantiations (single-instance launches only).
+template <typename FT, int RNG>
+void* pick_lean_split(int cmax, bool small, bool longc)
+{
+    if (longc)
+        return cmax == 1 ? reinterpret_cast<void*>(&lean_kernel<FT, RNG, 1, false, true, true>)
+             : cmax == 2 ? reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2, false, true, true>)
+                         : nullptr;
+    if (small)
+        return cmax == 2 ? reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2, true, false, true>) : nullptr;
+    switch (cmax) {
+    case 1: return reinterpret_cast<void*>(&lean_kernel<FT, RNG, 1, false, false, true>);
+    case 2: return reinterpret_cast<void*>(&lean_kernel<FT, RNG, 2, false, false, true>);
+    case 4: return reinterpret_cast<void*>(&lean_kernel<FT, RNG, 4, false, false, true>);
+    default: return nullptr;
+    }
+}
+
 }  // namespace lean_detail
 
 void* lean_kernel_i16(int rng, int cmax, bool batch = false, bool small = false, bool longc = false);
 void* lean_kernel_i32(int rng, int cmax, bool batch = false, bool small = false, bool longc = false);
+// split couplings (lean_split_i16.cu, lean_split_i32.cu)
+void* lean_split_kernel_i16(int rng, int cmax, bool small, bool longc);
+void* lean_split_kernel_i32(int rng, int cmax, bool small, bool longc);
 
 }  // namespace isg

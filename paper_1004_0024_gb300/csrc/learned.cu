@@ -1295,6 +1295,8 @@ int32_t ising_mlp_collect(ising_mlp_t m, ising_t h)
         return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
     if (!h->inited)
         return isg_fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    if (h->split)
+        return isg_fail(ISING_ERR_UNSUPPORTED, "learned column moves use the plain Trotter coupling, not split couplings");
     if (h->M != m->M)
         return isg_fail(ISING_ERR_INVALID_ARG, "the handle's slice count differs from the network's");
     const long long rows = (long long)h->R * h->S;
@@ -1362,6 +1364,8 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
         return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
     if (!h->inited)
         return isg_fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    if (h->split)
+        return isg_fail(ISING_ERR_UNSUPPORTED, "learned column moves use the plain Trotter coupling, not split couplings");
     if (h->M != m->M)
         return isg_fail(ISING_ERR_INVALID_ARG, "the handle's slice count differs from the network's");
     const long long total = (long long)h->R * h->S;

@@ -132,6 +132,8 @@ _SIGS = {
     "ising_set_alloc_cap": ([ctypes.c_uint64], ctypes.c_int32),
     "ising_release_cached_memory": ([], ctypes.c_int32),
     "ising_set_acceptance": ([_vp, ctypes.c_int32], ctypes.c_int32),
+    "ising_set_trotter": ([_vp, _f64p], ctypes.c_int32),
+    "ising_read_trotter": ([_vp, _i64p], ctypes.c_int32),
     "ising_selftest_wait": ([ctypes.c_int32, _vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -222,6 +224,17 @@ def ising_read_swap_stats(h, R):
     acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
     _check(_lib.ising_read_swap_stats(h, _p(acc, _u64p)))
     return acc[:max(R - 1, 0)]
+
+
+def ising_set_trotter(h, K):
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    _check(_lib.ising_set_trotter(h, _p(K, _f64p)))
+
+
+def ising_read_trotter(h, R):
+    C = np.empty(R, dtype=np.int64)
+    _check(_lib.ising_read_trotter(h, _p(C, _i64p)))
+    return C
 
 
 def ising_save(h) -> bytes:
@@ -317,6 +330,18 @@ class Ising:
         """Flip thresholds from the exact exponential ("exact") or the paper's
         fast / accurate approximation, for the next replicas_init."""
         _check(_lib.ising_set_acceptance(self.h, ACCEPT_MODES[mode]))
+
+    def set_trotter(self, K):
+        """Split couplings: temperature k weights exp(-beta_k E_space - K[k] C);
+        fields and energies become the spatial ones."""
+        K = np.asarray(K, dtype=np.float64)
+        if K.shape != (self.R,):
+            raise ValueError("K needs one value per temperature index")
+        ising_set_trotter(self.h, K)
+
+    def read_trotter(self):
+        """C = -sum over Trotter pairs of s s', per slot (zeros without split couplings)."""
+        return ising_read_trotter(self.h, self.R)
 
     def set_stream(self, stream):
         ising_set_stream(self.h, stream)

@@ -181,6 +181,24 @@ def config1():
                 swap_every=1)
 
 
+def trotter_couplings(betas, gamma: float, M: int) -> np.ndarray:
+    """K_k = (1/2) ln coth(beta_k Gamma / M): the inter-slice coupling of M
+    Trotter slices of a transverse field Gamma at inverse temperature beta_k
+    (the standard Suzuki-Trotter mapping; it falls as beta rises)."""
+    b = np.asarray(betas, dtype=np.float64)
+    return 0.5 * np.log(1.0 / np.tanh(b * gamma / M))
+
+
+def config1_trotter(gamma: float = 2.0):
+    """The 32x32 x 32-slice, 256-replica system with split couplings:
+    temperature k weights exp(-beta_k E_space - K_k C), K_k from a transverse
+    field Gamma = 2 over the 32 slices (K from 2.88 at beta 0.05 to 0.60 at
+    beta 5.0)."""
+    c = config1()
+    return dict(c, name="cfg1_trotter_L32_M32_R256", K=trotter_couplings(c["betas"], gamma, 32),
+                gamma=gamma)
+
+
 def config3(R: int = 65536):
     """16x16 lattice x M=16 (4096 spins), 65536 replicas, betas 0.1..3.0, int16 fields."""
     return dict(name=f"cfg3_L16_M16_R{R}", graph=layered_graph(16, 16, 1), R=R,

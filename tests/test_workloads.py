@@ -83,3 +83,14 @@ def test_ragged_batch_distribution():
     assert 12.3 < lg.mean() < 13.4
     # reproducible: the same seed gives the same batch
     assert W.ragged_instances(4096) == d
+
+
+def test_split_coupling_workload():
+    """cfg1 with K_k = (1/2) ln coth(beta_k Gamma / M), Gamma = 2, M = 32:
+    positive, falling as beta rises, from 2.88 at beta 0.05 to 0.60 at 5.0."""
+    c = W.config1_trotter()
+    K = c["K"]
+    assert K.shape == (256,) and np.all(np.diff(K) < 0) and np.all(K > 0)
+    assert K[0] == pytest.approx(2.8842, abs=1e-3) and K[-1] == pytest.approx(0.5975, abs=1e-3)
+    # the mapping's defining identity: tanh(K) = exp(-2 beta Gamma / M)
+    assert np.allclose(np.tanh(K), np.exp(-2.0 * c["betas"] * 2.0 / 32))
