@@ -226,6 +226,24 @@ int32_t ising_set_trotter(ising_t h, const double* K);
  * Errors: INVALID_ARG, NOT_INITIALISED, TIMEOUT, CUDA. */
 int32_t ising_read_trotter(ising_t h, int64_t* C);
 
+/*
+ * Host-side pieces of split couplings (no device needed; for tests and
+ * tools):
+ *   ising_split_flip_table  the flip tables ising_set_trotter builds: for
+ *       temperature t (0 <= t < R) and k_s in [-ks, ks], k_tau in {-2, 0, 2},
+ *       out[t * 3 (2 ks + 1) + (k_s + ks) * 3 + k_tau / 2 + 1] = T of
+ *       z = 2 (betas[t] k_s + K[t] k_tau) (caller's buffer of R * 3 (2 ks + 1)
+ *       uint32).  Errors: INVALID_ARG (R < 1, ks outside [0, 1364], NULL).
+ *   ising_split_exp  the fixed FP64 exponential the device evaluates for
+ *       swaps (the same source compiled for the host): e^x within about one
+ *       ulp, 0 below -708.
+ *   ising_split_swap_threshold  T of z = dbeta dE + dK dC as the device
+ *       computes it (2^32 - 1 for z <= 0).
+ */
+int32_t ising_split_flip_table(int32_t R, const double* betas, const double* K, int32_t ks, uint32_t* out);
+double ising_split_exp(double x);
+uint32_t ising_split_swap_threshold(double dbeta, double dK, int64_t dE, int64_t dC);
+
 /* Energy and magnetisation m = sum_i s_i of the replica holding each
  * temperature index k (arrays [R], either may be NULL).  Synchronises. */
 int32_t ising_read_observables(ising_t h, int64_t* energy_by_temp, int64_t* magnetisation_by_temp);

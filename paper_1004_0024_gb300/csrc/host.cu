@@ -24,6 +24,7 @@
 
 #include "ising_gb300.h"
 #include "ising_internal.cuh"
+#include "split_math.cuh"
 
 using namespace isg;
 
@@ -1515,6 +1516,32 @@ static uint32_t split_flip_threshold(double beta, double K, int ks, int kt)
     return t >= 4294967295.0 ? 0xFFFFFFFFu : uint32_t(t);
 }
 
+// Flip tables of R temperatures: entry (k_s + ks) * 3 + k_tau / 2 + 1 of
+// temperature t (stride 3 (2 ks + 1)) for k_s in [-ks, ks], k_tau in {-2, 0, 2}.
+static void split_flip_table(const double* betas, const double* K, int R, int ks, uint32_t* out)
+{
+    const size_t Ks = size_t(3) * size_t(2 * ks + 1);
+    for (int t = 0; t < R; ++t)
+        for (int k = -ks; k <= ks; ++k)
+            for (int j = 0; j < 3; ++j)
+                out[size_t(t) * Ks + size_t(k + ks) * 3 + j] = split_flip_threshold(betas[t], K[t], k, 2 * j - 2);
+}
+
+int32_t ising_split_flip_table(int32_t R, const double* betas, const double* K, int32_t ks, uint32_t* out)
+{
+    if (R < 1 || !betas || !K || !out || ks < 0 || ks > 1364)
+        return fail(ISING_ERR_INVALID_ARG, "R >= 1, 0 <= ks <= 1364 and non-NULL arrays required");
+    split_flip_table(betas, K, R, ks, out);
+    return ISING_OK;
+}
+
+double ising_split_exp(double x) { return isg::split_detail::exp_det(x); }
+
+uint32_t ising_split_swap_threshold(double dbeta, double dK, int64_t dE, int64_t dC)
+{
+    return isg::split_detail::swap_threshold(dbeta, dK, (long long)dE, (long long)dC);
+}
+
 int32_t ising_set_trotter(ising_t g, const double* K)
 {
     if (!g || !K)
@@ -1544,11 +1571,7 @@ int32_t ising_set_trotter(ising_t g, const double* K)
     if (Ks > 8192)
         return fail(ISING_ERR_UNSUPPORTED, "split-coupling flip table exceeds 8192 entries per temperature");
     std::vector<uint32_t> thr(size_t(R) * size_t(Ks));
-    for (int t = 0; t < R; ++t)
-        for (long long k = -ks; k <= ks; ++k)
-            for (int j = 0; j < 3; ++j)
-                thr[size_t(t) * Ks + size_t(k + ks) * 3 + j] =
-                    split_flip_threshold(g->betas[t], K[t], int(k), 2 * j - 2);
+    split_flip_table(g->betas.data(), K, R, int(ks), thr.data());
     std::vector<double> dbeta(std::max(R - 1, 1), 0.0), dK(std::max(R - 1, 1), 0.0);
     for (int k = 0; k + 1 < R; ++k) {
         dbeta[k] = g->betas[k + 1] - g->betas[k];

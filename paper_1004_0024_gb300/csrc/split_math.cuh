@@ -17,13 +17,60 @@
 //     coefficients 1/k! rounded to FP64;
 //   * e^x = e^r 2^n, an exact scaling while the result is normal; x < -708
 //     gives 0 (every threshold is 0 long before that).
+// The functions also compile for the host (volatile temporaries instead of the
+// intrinsics), where ising_split_exp exposes them for tests.
 #pragma once
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 namespace isg {
 namespace split_detail {
 
-__device__ __forceinline__ double exp_det(double x)
+__host__ __device__ __forceinline__ double mul_rn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    volatile double r = a * b;
+    return r;
+#endif
+}
+
+__host__ __device__ __forceinline__ double add_rn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(a, b);
+#else
+    volatile double r = a + b;
+    return r;
+#endif
+}
+
+__host__ __device__ __forceinline__ double sub_rn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(a, b);
+#else
+    volatile double r = a - b;
+    return r;
+#endif
+}
+
+// 2^n for n in [-1022, 1023]: the biased exponent n + 1023 in bits 52..62
+__host__ __device__ __forceinline__ double pow2i(int n)
+{
+    const long long bits = (long long)(n + 1023) << 52;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(bits);
+#else
+    double d;
+    std::memcpy(&d, &bits, sizeof d);
+    return d;
+#endif
+}
+
+__host__ __device__ __forceinline__ double exp_det(double x)
 {
     // ln 2 = kLn2Hi + kLn2Lo: the head holds the first 32 significant bits
     constexpr double kInvLn2 = 0x1.71547652b82fep+0;
@@ -31,8 +78,10 @@ __device__ __forceinline__ double exp_det(double x)
     constexpr double kLn2Lo = 0x1.a39ef35793c76p-33;
     if (x < -708.0)
         return 0.0;
-    const double n = rint(__dmul_rn(x, kInvLn2));
-    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(n, kLn2Hi)), __dmul_rn(n, kLn2Lo));
+    if (x > 709.0)
+        return INFINITY;
+    const double n = rint(mul_rn(x, kInvLn2));
+    const double r = sub_rn(sub_rn(x, mul_rn(n, kLn2Hi)), mul_rn(n, kLn2Lo));
     // 1/k!, k = 13 down to 0
     constexpr double c[14] = {0x1.6124613a86d09p-33, 0x1.1eed8eff8d898p-29, 0x1.ae64567f544e4p-26,
                               0x1.27e4fb7789f5cp-22, 0x1.71de3a556c734p-19, 0x1.a01a01a01a01ap-16,
@@ -42,23 +91,22 @@ __device__ __forceinline__ double exp_det(double x)
     double p = c[0];
 #pragma unroll
     for (int k = 1; k < 14; ++k)
-        p = __dadd_rn(__dmul_rn(p, r), c[k]);
-    // 2^n for n in [-1021, 1023]: the biased exponent n + 1023 in bits 52..62
-    const long long bexp = (long long)(int(n) + 1023) << 52;
-    return __dmul_rn(p, __longlong_as_double(bexp));
+        p = add_rn(mul_rn(p, r), c[k]);
+    return mul_rn(p, pow2i(int(n)));  // n in [-1021, 1023]
 }
 
 // T = min(floor(2^32 p), 2^32 - 1) for a probability estimate p >= 0
-__device__ __forceinline__ uint32_t threshold_of(double p)
+__host__ __device__ __forceinline__ uint32_t threshold_of(double p)
 {
-    const double t = floor(__dmul_rn(p, 4294967296.0));
+    const double t = floor(mul_rn(p, 4294967296.0));
     return t >= 4294967295.0 ? 0xFFFFFFFFu : uint32_t(t);
 }
 
 // Swap threshold of pair (k, k+1); 2^32 - 1 means the swap is certain.
-__device__ __forceinline__ uint32_t swap_threshold(double dbeta, double dK, long long dE, long long dC)
+__host__ __device__ __forceinline__ uint32_t swap_threshold(double dbeta, double dK, long long dE,
+                                                            long long dC)
 {
-    const double z = __dadd_rn(__dmul_rn(dbeta, double(dE)), __dmul_rn(dK, double(dC)));
+    const double z = add_rn(mul_rn(dbeta, double(dE)), mul_rn(dK, double(dC)));
     if (z <= 0.0)
         return 0xFFFFFFFFu;
     return threshold_of(exp_det(-z));

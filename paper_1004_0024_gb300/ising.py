@@ -134,6 +134,10 @@ _SIGS = {
     "ising_set_acceptance": ([_vp, ctypes.c_int32], ctypes.c_int32),
     "ising_set_trotter": ([_vp, _f64p], ctypes.c_int32),
     "ising_read_trotter": ([_vp, _i64p], ctypes.c_int32),
+    "ising_split_flip_table": ([ctypes.c_int32, _f64p, _f64p, ctypes.c_int32, _u32p], ctypes.c_int32),
+    "ising_split_exp": ([ctypes.c_double], ctypes.c_double),
+    "ising_split_swap_threshold": ([ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64],
+                                   ctypes.c_uint32),
     "ising_selftest_wait": ([ctypes.c_int32, _vp], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -235,6 +239,24 @@ def ising_read_trotter(h, R):
     C = np.empty(R, dtype=np.int64)
     _check(_lib.ising_read_trotter(h, _p(C, _i64p)))
     return C
+
+
+def split_flip_table(betas, K, ks: int) -> np.ndarray:
+    """The flip tables ising_set_trotter builds, as [R][2 ks + 1][3] (k_s, k_tau / 2 + 1)."""
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    out = np.empty((betas.size, 2 * ks + 1, 3), dtype=np.uint32)
+    _check(_lib.ising_split_flip_table(betas.size, _p(betas, _f64p), _p(K, _f64p), ks, _p(out, _u32p)))
+    return out
+
+
+def split_exp(x: float) -> float:
+    """The device's fixed FP64 exponential of the split-coupling swap rule (host build)."""
+    return float(_lib.ising_split_exp(float(x)))
+
+
+def split_swap_threshold(dbeta: float, dK: float, dE: int, dC: int) -> int:
+    return int(_lib.ising_split_swap_threshold(dbeta, dK, int(dE), int(dC)))
 
 
 def ising_save(h) -> bytes:

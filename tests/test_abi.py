@@ -99,3 +99,39 @@ def test_host_validation_of_large_graphs_reports_the_first_row(lib, faults, code
         lib.ising_create(g.n, rp, col, J, g.h, 1)
     assert ei.value.name == code
     assert where in lib.ising_last_error(), lib.ising_last_error()
+
+
+# ------------------------------------------ split couplings, host side
+def test_split_flip_table_matches_the_oracle(lib):
+    """The tables ising_set_trotter uploads, entry by entry against the
+    oracle's split flip rule (k_s in [-ks, ks], k_tau in {-2, 0, 2})."""
+    import oracle
+    from paper_1004_0024_gb300 import workloads as W
+    betas = W.geometric_betas(16, 0.05, 5.0)
+    K = W.trotter_couplings(betas, 2.0, 32)
+    ks = 20
+    tab = lib.split_flip_table(betas, K, ks)
+    for t in range(betas.size):
+        for k in range(-ks, ks + 1):
+            for j, kt in enumerate((-2, 0, 2)):
+                assert tab[t, k + ks, j] == oracle.trotter_flip_threshold(betas[t], K[t], k, kt), (t, k, kt)
+    with pytest.raises(lib.IsingError):
+        lib.split_flip_table(betas, K, 1365)
+
+
+def test_split_device_exponential_matches_the_oracle(lib):
+    """The swap rule's fixed FP64 exponential, compiled from the device source
+    for the host, equals the oracle's on 200000 arguments, and so do the swap
+    thresholds built from it."""
+    import oracle
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([rng.uniform(-708, 0, 120000), rng.uniform(-1, 0, 60000),
+                         -np.logspace(-18, 2.85, 20000), [0.0, -708.5, -745.0]])
+    got = np.array([lib.split_exp(x) for x in xs.tolist()])
+    want = np.array([oracle.exp_det(x) for x in xs.tolist()])
+    assert np.array_equal(got, want)
+    for dbeta, dK in [(0.02, -0.1), (0.3, 0.05), (1e-3, -2.0), (0.0123, 0.77)]:
+        for dE in range(-50, 400, 13):
+            for dC in range(-40, 41, 5):
+                assert lib.split_swap_threshold(dbeta, dK, dE, dC) == \
+                    oracle.trotter_swap_threshold(dbeta, dK, dE, dC), (dbeta, dK, dE, dC)
