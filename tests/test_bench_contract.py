@@ -35,3 +35,27 @@ def test_hbm_roofline_of_streamed_words():
     assert r["bound"] == "hbm" and r["bytes_per_attempt"] == pytest.approx(bpa)
     assert r["achieved"] == pytest.approx(attempts * bpa / 1.0 / 1e9)
     assert r["peak"] == pytest.approx(float(peak)) and r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_cpu_baseline_uses_the_workloads_split_couplings(monkeypatch):
+    """The oracle leg times the same chain the GPU runs: with split couplings
+    (cfg1-trotter) it sets the workload's K; a bounded sample of a small
+    layered model runs in a fraction of a second here."""
+    import numpy as np
+
+    import oracle
+    seen = []
+    orig = oracle.Sim.set_trotter
+
+    def spy(self, K):
+        seen.append(np.asarray(K).copy())
+        return orig(self, K)
+
+    monkeypatch.setattr(oracle.Sim, "set_trotter", spy)
+    c = dict(W.config0(), R=4, betas=W.geometric_betas(4, 0.1, 3.0))
+    c["K"] = W.trotter_couplings(c["betas"], 2.0, 16)
+    r = bench.cpu_baseline(c, "philox", 0.05)
+    assert len(seen) == 1 and np.array_equal(seen[0], c["K"])
+    assert r["kind"] == "oracle" and r["unit"] == "attempts/s" and r["value"] > 0
+    assert bench.workload("cfg1-trotter")["K"].shape == (256,)
+    assert "split couplings" in bench.WORKLOAD_NAMES["cfg1-trotter"]
