@@ -89,7 +89,9 @@ __host__ __device__ __forceinline__ double exp_det(double x)
                               0x1.5555555555555p-5,  0x1.5555555555555p-3,  0x1p-1,
                               0x1p+0,                0x1p+0};
     double p = c[0];
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
     for (int k = 1; k < 14; ++k)
         p = add_rn(mul_rn(p, r), c[k]);
     return mul_rn(p, pow2i(int(n)));  // n in [-1021, 1023]
