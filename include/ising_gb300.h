@@ -213,8 +213,7 @@ int32_t ising_read_swap_stats(ising_t h, uint64_t* accepted);
  * couplings last until the next ising_replicas_init.  Requires declared
  * slices with a Trotter ring (M >= 3) and the lean kernel (M in {4, 8, 16,
  * 32} or a multiple of 32 up to 1024, spatial degree <= 6, |J| <= 63, one
- * replica per block); not with checkpoints, learned passes or
- * ising_run_noalloc.  Errors: INVALID_ARG (NULL argument, non-finite K, set
+ * replica per block); not with learned passes or ising_run_noalloc.  Errors: INVALID_ARG (NULL argument, non-finite K, set
  * twice), NOT_INITIALISED, UNSUPPORTED (model or launch configuration without
  * the lean kernel, acceptance mode other than EXACT, a flip table above 8192
  * entries per temperature), OOM, CUDA.
@@ -251,11 +250,17 @@ int32_t ising_read_observables(ising_t h, int64_t* energy_by_temp, int64_t* magn
 
 /*
  * ising_save / ising_load -- checkpoint blob of the full replica state (spins,
- * fields, energies, labels, RNG states and positions, counters).  save: pass
- * buf = NULL to query the size in *size; otherwise cap >= *size.  load: the
- * handle must be initialised with the same n, R and modes.  Running k sweeps,
- * saving, loading into another handle and running m more gives the same
- * result as k + m straight sweeps.  Errors: NOT_INITIALISED, INVALID_ARG.
+ * fields, energies, labels, MT19937 rings and positions, the generator key
+ * {seed, instance}, counters, the count of learned passes; with split
+ * couplings also K and the Trotter sums).  save: pass buf = NULL to query the
+ * size in *size; otherwise cap >= *size.  load: the handle must be
+ * initialised with the same n, R and modes (its seed may differ: the blob's
+ * key replaces it); a blob with split couplings sets
+ * them on a handle without them (ising_set_trotter) and needs the same K on a
+ * handle with them; a blob without them is refused by a handle with them.
+ * Running k sweeps, saving, loading into another handle and running m more
+ * gives the same result as k + m straight sweeps.  Errors: NOT_INITIALISED,
+ * INVALID_ARG, and those of ising_set_trotter.
  */
 int32_t ising_save(ising_t h, void* buf, size_t cap, size_t* size);
 int32_t ising_load(ising_t h, const void* buf, size_t size);

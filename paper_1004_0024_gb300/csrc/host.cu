@@ -1670,7 +1670,12 @@ struct BlobHeader {
 };
 constexpr uint32_t kMagic = 0x31475349u;  // "ISG1"
 
-size_t blob_size(ising_s* g)
+// Version 2: the state, then the generator key {seed, instance} (what Philox
+// words depend on; MT19937 streams are in the rings) and the count of learned
+// passes (their Philox counter), then with split couplings (bit 0 of `pad`)
+// K [R] (FP64) and C [R] (int32).  Version 1 (read only) has neither the key
+// nor split couplings.
+size_t blob_size_v1(const ising_s* g)
 {
     const size_t RN = size_t(g->R) * g->n;
     size_t s = sizeof(BlobHeader) + RN + RN * (g->field_bits / 8) + 4 * size_t(g->R) * 3 +
@@ -1679,6 +1684,13 @@ size_t blob_size(ising_s* g)
         s += 4 * size_t(g->R + 1) * kMtRing + 8 * size_t(g->R + 1);
     return s;
 }
+
+size_t blob_size_for(const ising_s* g, bool split)
+{
+    return blob_size_v1(g) + 16 + (split ? 12 * size_t(g->R) : 0);
+}
+
+size_t blob_size(ising_s* g) { return blob_size_for(g, g->split); }
 }  // namespace
 
 int32_t ising_save(ising_t g, void* buf, size_t cap, size_t* size)
@@ -1687,8 +1699,6 @@ int32_t ising_save(ising_t g, void* buf, size_t cap, size_t* size)
         return fail(ISING_ERR_INVALID_ARG, "NULL argument");
     if (!g->inited)
         return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
-    if (g->split)
-        return fail(ISING_ERR_UNSUPPORTED, "checkpoints of split-coupling state are not supported");
     const size_t need = blob_size(g);
     *size = need;
     if (!buf)
@@ -1699,7 +1709,7 @@ int32_t ising_save(ising_t g, void* buf, size_t cap, size_t* size)
     if (rc)
         return rc;
     char* p = static_cast<char*>(buf);
-    BlobHeader hd{kMagic, 1u, g->n, g->R, g->field_bits, g->rng, g->M, 0};
+    BlobHeader hd{kMagic, 2u, g->n, g->R, g->field_bits, g->rng, g->M, g->split ? 1 : 0};
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
     const size_t RN = size_t(g->R) * g->n;
@@ -1719,6 +1729,17 @@ int32_t ising_save(ising_t g, void* buf, size_t cap, size_t* size)
         CK(d2h(g->d_mtring, 4 * size_t(g->R + 1) * kMtRing));
         CK(d2h(g->d_mtpos, 8 * size_t(g->R + 1)));
     }
+    const uint32_t key[2] = {g->seed, g->inst};
+    std::memcpy(p, key, sizeof key);
+    p += sizeof key;
+    const unsigned long long lp = g->learned_passes;
+    std::memcpy(p, &lp, sizeof lp);
+    p += sizeof lp;
+    if (g->split) {
+        std::memcpy(p, g->trotter_K.data(), 8 * size_t(g->R));
+        p += 8 * size_t(g->R);
+        CK(d2h(g->d_C, 4 * size_t(g->R)));
+    }
     CK(cudaStreamSynchronize(g->stream));
     return ISING_OK;
 }
@@ -1729,17 +1750,34 @@ int32_t ising_load(ising_t g, const void* buf, size_t size)
         return fail(ISING_ERR_INVALID_ARG, "NULL argument");
     if (!g->inited)
         return fail(ISING_ERR_NOT_INITIALISED, "not initialised");
-    if (g->split)
-        return fail(ISING_ERR_UNSUPPORTED, "checkpoints of split-coupling state are not supported");
-    if (size != blob_size(g))
-        return fail(ISING_ERR_INVALID_ARG, "blob size does not match this handle");
+    if (size < sizeof(BlobHeader))
+        return fail(ISING_ERR_INVALID_ARG, "blob too small");
     const char* p = static_cast<const char*>(buf);
     BlobHeader hd;
     std::memcpy(&hd, p, sizeof hd);
     p += sizeof hd;
-    if (hd.magic != kMagic || hd.n != g->n || hd.R != g->R || hd.field_bits != g->field_bits ||
-        hd.rng != g->rng || hd.M != g->M)
+    if (hd.magic != kMagic || (hd.version != 1u && hd.version != 2u))
+        return fail(ISING_ERR_INVALID_ARG, "not a checkpoint blob of this library");
+    const bool bsplit = hd.version == 2u && (hd.pad & 1);
+    if (size != (hd.version == 1u ? blob_size_v1(g) : blob_size_for(g, bsplit)))
+        return fail(ISING_ERR_INVALID_ARG, "blob size does not match this handle");
+    if (hd.n != g->n || hd.R != g->R || hd.field_bits != g->field_bits || hd.rng != g->rng || hd.M != g->M)
         return fail(ISING_ERR_INVALID_ARG, "blob was saved from a different configuration");
+    if (bsplit) {
+        // the couplings first: a plain handle takes the blob's split couplings
+        std::vector<double> Kb(g->R);
+        std::memcpy(Kb.data(), static_cast<const char*>(buf) + blob_size_v1(g) + 16, 8 * size_t(g->R));
+        if (g->split) {
+            if (std::memcmp(Kb.data(), g->trotter_K.data(), 8 * size_t(g->R)) != 0)
+                return fail(ISING_ERR_INVALID_ARG, "blob was saved with other Trotter couplings");
+        } else {
+            const int32_t rc = ising_set_trotter(g, Kb.data());
+            if (rc)
+                return rc;
+        }
+    } else if (g->split) {
+        return fail(ISING_ERR_INVALID_ARG, "blob holds plain couplings; this handle has split couplings");
+    }
     const size_t RN = size_t(g->R) * g->n;
     auto h2d = [&](void* d, size_t bytes) -> cudaError_t {
         cudaError_t e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, g->stream);
@@ -1756,6 +1794,22 @@ int32_t ising_load(ising_t g, const void* buf, size_t size)
     if (g->rng == ISING_RNG_MT19937) {
         CK(h2d(g->d_mtring, 4 * size_t(g->R + 1) * kMtRing));
         CK(h2d(g->d_mtpos, 8 * size_t(g->R + 1)));
+    }
+    if (hd.version >= 2u) {
+        uint32_t key[2];
+        std::memcpy(key, p, sizeof key);
+        p += sizeof key;
+        g->seed = key[0];  // Philox words of later sweeps follow the saved key
+        g->inst = key[1];
+        unsigned long long lp;
+        std::memcpy(&lp, p, sizeof lp);
+        p += sizeof lp;
+        g->learned_passes = lp;
+        g->drop_graphs();  // recorded launches hold the old key
+    }
+    if (bsplit) {
+        p += 8 * size_t(g->R);  // K, applied above
+        CK(h2d(g->d_C, 4 * size_t(g->R)));
     }
     CK(cudaStreamSynchronize(g->stream));
     return ISING_OK;

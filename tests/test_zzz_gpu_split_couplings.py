@@ -146,9 +146,55 @@ def test_split_reproduces_the_plain_chain_where_the_rules_coincide(ising, rng):
     assert np.array_equal(plain.swap_stats(), split.swap_stats())
 
 
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_split_checkpoint_resume_is_bit_exact(ising, rng):
+    """Save after 7 sweeps, load into a fresh handle without split couplings
+    (the blob sets them), run 5 more on both: identical to each other and to
+    the oracle; a plain blob is refused by a handle with split couplings."""
+    g = W.layered_graph(6, 8, graph_seed=40)
+    betas = W.geometric_betas(10, 0.1, 2.5)
+    K = trotter_K(betas, 2.0, 8)
+    dev, ref = split_pair(ising, g, betas, K, 17, rng, 16)
+    dev.run(7, 1)
+    ref.run(7, 1)
+    blob = dev.save()
+    other = ising.Ising(g, betas, seed=999, rng=rng, field_bits=16)
+    other.load(blob)
+    for h in (dev, other):
+        h.run(5, 1)
+    ref.run(5, 1)
+    assert_same(dev, ref, "resumed run")
+    assert_same(other, ref, "loaded handle")
+    plain = ising.Ising(g, betas, seed=17, rng=rng, field_bits=16)
+    with pytest.raises(ising.IsingError) as e:
+        dev.load(plain.save())
+    assert e.value.name == "INVALID_ARG"
+    for h in (dev, other, plain):
+        h.close()
+
+
+def test_philox_checkpoint_carries_the_generator_key(ising):
+    """Philox words depend on (seed, instance): a blob loaded into a handle
+    initialised with another seed continues the saved chain (plain couplings)."""
+    c = W.config0()
+    a = ising.Ising(c["graph"], c["betas"], seed=11, rng="philox", field_bits=16)
+    a.run(9, 1)
+    b = ising.Ising(c["graph"], c["betas"], seed=999, rng="philox", field_bits=16)
+    b.load(a.save())
+    a.run(6, 1)
+    b.run(6, 1)
+    ref = oracle.Sim(c["graph"], c["betas"], seed=11, rng="philox", threads=4)
+    ref.run(15, 1)
+    for h in (a, b):
+        d, r = h.read_state(), ref.read()
+        for key in ("spins", "fields", "energy", "temp_of_slot"):
+            assert np.array_equal(d[key], r[key]), key
+        h.close()
+
+
 def test_split_refusals(ising):
-    """Models without the lean kernel, a second call, checkpoints and the
-    allocation-free run are refused; without split couplings C reads 0."""
+    """Models without the lean kernel, a second call and the allocation-free
+    run are refused; without split couplings C reads 0."""
     g = W.random_graph(12, 20, seed=1)
     dev = ising.Ising(g, [0.3, 0.6], seed=1)
     with pytest.raises(ising.IsingError) as e:
@@ -163,9 +209,6 @@ def test_split_refusals(ising):
     with pytest.raises(ising.IsingError) as e:
         dev.set_trotter(trotter_K(c["betas"], 2.0, 16))
     assert e.value.name == "INVALID_ARG"
-    with pytest.raises(ising.IsingError) as e:
-        dev.save()
-    assert e.value.name == "UNSUPPORTED"
     with pytest.raises(ising.IsingError) as e:
         ising.ising_run_noalloc(dev.h, 2, 1)
     assert e.value.name == "UNSUPPORTED"
