@@ -59,3 +59,16 @@ def test_cpu_baseline_uses_the_workloads_split_couplings(monkeypatch):
     assert r["kind"] == "oracle" and r["unit"] == "attempts/s" and r["value"] > 0
     assert bench.workload("cfg1-trotter")["K"].shape == (256,)
     assert "split couplings" in bench.WORKLOAD_NAMES["cfg1-trotter"]
+
+
+def test_throttled_or_clock_locked_runs_are_remeasured():
+    """Rejected: hw / thermal slowdown, or an SM clock well below its maximum
+    with no reason active; kept: the power cap, full clocks, no samples."""
+    base = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_rejected(base)
+    assert not bench.clocks_rejected(None)
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(base, reasons=[r]))
+    assert not bench.clocks_rejected(dict(base, sm_mhz=1500.0, reasons=["sw_power_cap"]))
+    assert bench.clocks_rejected(dict(base, sm_mhz=1100.0))
+    assert bench.any_rank(True, 1) and not bench.any_rank(False, 1)
