@@ -419,6 +419,13 @@ class Ising:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
 
 # ------------------------------------------------------------------- batches
 class Batch:
@@ -497,6 +504,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
 
 # ------------------------------------------------------ learned column proposal
@@ -616,3 +630,10 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
