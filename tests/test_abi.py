@@ -135,3 +135,18 @@ def test_split_device_exponential_matches_the_oracle(lib):
             for dC in range(-40, 41, 5):
                 assert lib.split_swap_threshold(dbeta, dK, dE, dC) == \
                     oracle.trotter_swap_threshold(dbeta, dK, dE, dC), (dbeta, dK, dE, dC)
+
+
+def test_header_is_plain_c():
+    """The boundary header compiles as ISO C11 (no C++ or CUDA types leak
+    into the ABI) and as C++17."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    hdr = os.path.join(HEADER_DIR, "ising_gb300.h")
+    for lang, std in (("c", "-std=c11"), ("c++", "-std=c++17")):
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
