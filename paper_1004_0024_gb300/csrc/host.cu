@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -22,6 +23,7 @@
 #include <tuple>
 #include <vector>
 
+#include "host_pool.h"
 #include "ising_gb300.h"
 #include "ising_internal.cuh"
 #include "split_math.cuh"
@@ -323,7 +325,10 @@ void ising_s::free_all()
 namespace {
 
 // ---------------------------------------------------------- validation
-int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* J)
+// Also returns, for a valid model, kmax = max_i |h_i| + sum_j |J_ij| and
+// ebound = sum_i |h_i| + sum over pairs of |J_ij| (computed in the same pass).
+int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, const int32_t* J,
+                     const int32_t* h, long long* kmax, long long* ebound)
 {
     if (row_ptr[0] != 0)
         return fail(ISING_ERR_INVALID_ARG, "row_ptr[0] must be 0");
@@ -334,33 +339,36 @@ int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
     // checked in parallel chunks, and of each phase the error of the lowest
     // row is reported (the one a row-by-row pass would meet first)
     const long long nnz = row_ptr[n];
-    std::vector<std::pair<int, int>> ent(size_t(std::max<long long>(nnz, 0)));
+    std::vector<std::pair<int, int>> ent_mem(size_t(std::max<long long>(nnz, 1)));
+    std::pair<int, int>* const ent = ent_mem.data();
     struct RowErr {
         int row = INT32_MAX, code = ISING_OK;
         std::string msg;
     };
+    const int nthr = n >= 8192 ? host_threads() : 1;
+    // per-thread partial sums, one cache line each
+    struct alignas(64) Part {
+        long long km = 0, eb = 0, up = 0, low = 0;
+        bool bad = false;
+    };
+    std::vector<Part> part(static_cast<size_t>(nthr));
     auto run_rows = [&](auto&& check) -> RowErr {
-        const int nthr = n >= 8192 ? int(std::max(1u, std::min(16u, std::thread::hardware_concurrency()))) : 1;
         std::vector<RowErr> errs(static_cast<size_t>(nthr));
-        auto part = [&](int t) {
+        host_parallel(nthr, [&](int t) {
             const int i0 = int((long long)n * t / nthr), i1 = int((long long)n * (t + 1) / nthr);
             for (int i = i0; i < i1; ++i)
-                if (check(i, errs[size_t(t)]))
+                if (check(i, t, errs[size_t(t)]))
                     return;
-        };
-        std::vector<std::thread> pool;
-        for (int t = 1; t < nthr; ++t)
-            pool.emplace_back(part, t);
-        part(0);
-        for (auto& th : pool)
-            th.join();
+        });
         RowErr best;
         for (auto& e : errs)
             if (e.code != ISING_OK && e.row < best.row)
                 best = e;
         return best;
     };
-    RowErr err = run_rows([&](int i, RowErr& e) {
+    RowErr err = run_rows([&](int i, int t, RowErr& e) {
+        long long b = std::llabs((long long)h[i]);
+        long long eb = b;
         for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
             if (col[k] < 0 || col[k] >= n) {
                 e = {i, ISING_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i)};
@@ -375,33 +383,84 @@ int32_t validate_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
                 return true;
             }
             ent[size_t(k)] = std::make_pair(col[k], J[k]);
+            b += std::llabs((long long)J[k]);
+            if (col[k] > i)
+                eb += std::llabs((long long)J[k]);
         }
-        std::sort(ent.begin() + row_ptr[i], ent.begin() + row_ptr[i + 1]);
+        std::sort(ent + row_ptr[i], ent + row_ptr[i + 1]);
         for (int k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k)
             if (ent[size_t(k)].first == ent[size_t(k) - 1].first) {
                 e = {i, ISING_ERR_SELF_LOOP_OR_DUP, "repeated neighbour in row " + std::to_string(i)};
                 return true;
             }
+        Part& pt = part[size_t(t)];
+        pt.km = std::max(pt.km, b);
+        pt.eb += eb;
         return false;
     });
     if (err.code != ISING_OK)
         return fail(err.code, err.msg);
-    // symmetry: every (i, j, J) needs (j, i, J)
-    err = run_rows([&](int i, RowErr& e) {
-        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-            const int j = ent[size_t(k)].first;
-            const auto b = ent.begin() + row_ptr[j], en = ent.begin() + row_ptr[j + 1];
-            const auto it = std::lower_bound(b, en, std::make_pair(i, INT32_MIN));
-            if (it == en || it->first != i || it->second != ent[size_t(k)].second) {
-                e = {i, ISING_ERR_ASYMMETRIC_J,
-                     "J(" + std::to_string(i) + "," + std::to_string(j) + ") has no equal transpose"};
-                return true;
+    // symmetry, fast test: every entry above the diagonal, (i, j, J) with
+    // j > i, has its transpose (j, i, J), and there are as many entries below
+    // the diagonal as above.  The transpose map is then one to one from the
+    // upper entries onto the lower ones, so J is symmetric.
+    auto has_transpose = [&](int i, int k) {
+        const int j = ent[size_t(k)].first;
+        const auto b = ent + row_ptr[j], en = ent + row_ptr[j + 1];
+        const auto it = std::lower_bound(b, en, std::make_pair(i, INT32_MIN));
+        return it != en && it->first == i && it->second == ent[size_t(k)].second;
+    };
+    host_parallel(nthr, [&](int t) {
+        const int i0 = int((long long)n * t / nthr), i1 = int((long long)n * (t + 1) / nthr);
+        long long up = 0, low = 0;
+        bool bad = false;
+        for (int i = i0; i < i1 && !bad; ++i)
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                if (ent[size_t(k)].first < i) {
+                    ++low;
+                    continue;
+                }
+                ++up;
+                if (!has_transpose(i, k)) {
+                    bad = true;
+                    break;
+                }
             }
-        }
-        return false;
+        part[size_t(t)].up = up;
+        part[size_t(t)].low = low;
+        part[size_t(t)].bad = bad;
     });
-    if (err.code != ISING_OK)
-        return fail(err.code, err.msg);
+    long long nup = 0, nlow = 0;
+    bool any_bad = false;
+    for (const Part& pt : part) {
+        nup += pt.up;
+        nlow += pt.low;
+        any_bad |= pt.bad;
+    }
+    if (any_bad || nup != nlow) {
+        // the error a row-by-row check of every entry meets first
+        err = run_rows([&](int i, int, RowErr& e) {
+            for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+                if (!has_transpose(i, k)) {
+                    e = {i, ISING_ERR_ASYMMETRIC_J, "J(" + std::to_string(i) + "," +
+                                                        std::to_string(ent[size_t(k)].first) +
+                                                        ") has no equal transpose"};
+                    return true;
+                }
+            return false;
+        });
+        return fail(err.code != ISING_OK ? err.code : ISING_ERR_ASYMMETRIC_J,
+                    err.code != ISING_OK ? err.msg : std::string("J is not symmetric"));
+    }
+    long long km = 0, eb = 0;
+    for (const Part& pt : part) {
+        km = std::max(km, pt.km);
+        eb += pt.eb;
+    }
+    if (kmax)
+        *kmax = km;
+    if (ebound)
+        *ebound = eb;
     return ISING_OK;
 }
 
@@ -413,44 +472,82 @@ int32_t extract_slices(ising_s* g)
     const int n = g->n, M = g->M, S = g->S;
     std::vector<std::vector<std::pair<int, int>>> sp(S);
     std::vector<int> jt(S, 0);
-    std::vector<std::pair<int, int>> spat;  // scratch: the spatial entries of one spin
-    for (int t = 0; t < M; ++t) {
-        for (int q = 0; q < S; ++q) {
-            const int i = t * S + q;
-            if (g->h[i] != g->h[q])
-                return fail(ISING_ERR_INVALID_ARG, "declared slices differ in h at spin " + std::to_string(i));
-            spat.clear();
-            int ntrot = 0, jtrot = 0;
-            bool jt_ok = true;
-            const int tm = (t + M - 1) % M, tp = (t + 1) % M;
-            for (int e = g->row_ptr[i]; e < g->row_ptr[i + 1]; ++e) {
-                const int c = g->col[e];
-                const int tc = c / S, qc = c - tc * S;
-                if (tc == t) {
-                    spat.emplace_back(qc, g->J[e]);
-                } else if (qc == q && M >= 2 && (tc == tm || tc == tp)) {
-                    if (ntrot > 0 && g->J[e] != jtrot)
-                        jt_ok = false;
-                    jtrot = g->J[e];
-                    ++ntrot;
-                } else {
-                    return fail(ISING_ERR_INVALID_ARG,
-                                "spin " + std::to_string(i) + " has a coupling that is neither spatial nor Trotter");
-                }
-            }
-            const int want = (M >= 3) ? 2 : (M == 2 ? 1 : 0);
-            if (ntrot != want || !jt_ok)
-                return fail(ISING_ERR_INVALID_ARG,
-                            "spin " + std::to_string(i) + " lacks the Trotter ring couplings of the declared slices");
-            std::sort(spat.begin(), spat.end());
-            if (t == 0) {
-                sp[q] = spat;
-                jt[q] = jtrot;
-            } else if (spat != sp[q] || jtrot != jt[q]) {
-                return fail(ISING_ERR_INVALID_ARG, "declared slices are not identical at spin " + std::to_string(i));
+    // Spin i = t S + q: h equal to slice 0's, every coupling spatial (same
+    // slice) or Trotter (same site, adjacent slice), the ring's Trotter
+    // couplings present and equal, and (t > 0) the sorted spatial entries and
+    // Trotter coupling equal to site q's in slice 0.  Slice 0 is checked
+    // first, then the others against it, each phase in parallel chunks; of a
+    // phase the error of the lowest spin is reported (the one a spin-by-spin
+    // pass meets first).  Errors are raised on the calling thread.
+    struct SpinErr {
+        int i = INT32_MAX;
+        std::string msg;
+    };
+    const int nthr = n >= 8192 ? host_threads() : 1;
+    std::vector<SpinErr> errs(static_cast<size_t>(nthr));
+    auto check = [&](int i, std::vector<std::pair<int, int>>& spat, SpinErr& e) -> bool {
+        const int t = i / S, q = i - t * S;
+        if (g->h[i] != g->h[q]) {
+            e = {i, "declared slices differ in h at spin " + std::to_string(i)};
+            return false;
+        }
+        spat.clear();
+        int ntrot = 0, jtrot = 0;
+        bool jt_ok = true;
+        const int tm = (t + M - 1) % M, tp = (t + 1) % M;
+        for (int k = g->row_ptr[i]; k < g->row_ptr[i + 1]; ++k) {
+            const int c = g->col[k];
+            const int tc = c / S, qc = c - tc * S;
+            if (tc == t) {
+                spat.emplace_back(qc, g->J[k]);
+            } else if (qc == q && M >= 2 && (tc == tm || tc == tp)) {
+                if (ntrot > 0 && g->J[k] != jtrot)
+                    jt_ok = false;
+                jtrot = g->J[k];
+                ++ntrot;
+            } else {
+                e = {i, "spin " + std::to_string(i) + " has a coupling that is neither spatial nor Trotter"};
+                return false;
             }
         }
-    }
+        const int want = (M >= 3) ? 2 : (M == 2 ? 1 : 0);
+        if (ntrot != want || !jt_ok) {
+            e = {i, "spin " + std::to_string(i) + " lacks the Trotter ring couplings of the declared slices"};
+            return false;
+        }
+        if (!std::is_sorted(spat.begin(), spat.end()))
+            std::sort(spat.begin(), spat.end());
+        if (t == 0) {
+            sp[q] = spat;
+            jt[q] = jtrot;
+        } else if (spat != sp[q] || jtrot != jt[q]) {
+            e = {i, "declared slices are not identical at spin " + std::to_string(i)};
+            return false;
+        }
+        return true;
+    };
+    auto phase = [&](int lo, int hi) -> int32_t {
+        for (auto& e : errs)
+            e = SpinErr{};
+        host_parallel(nthr, [&](int p) {
+            std::vector<std::pair<int, int>> spat;
+            const int i0 = lo + int((long long)(hi - lo) * p / nthr);
+            const int i1 = lo + int((long long)(hi - lo) * (p + 1) / nthr);
+            for (int i = i0; i < i1; ++i)
+                if (!check(i, spat, errs[size_t(p)]))
+                    return;
+        });
+        const SpinErr* best = nullptr;
+        for (const auto& e : errs)
+            if (e.i != INT32_MAX && (!best || e.i < best->i))
+                best = &e;
+        return best ? fail(ISING_ERR_INVALID_ARG, best->msg) : ISING_OK;
+    };
+    int32_t rc = phase(0, S);
+    if (!rc && n > S)
+        rc = phase(S, n);
+    if (rc)
+        return rc;
     (void)n;
     // slice wavefront levels: lev0(q) = 1 + max lev0(q') over spatial q' < q
     std::vector<int> lev(S, 0);
@@ -1067,7 +1164,8 @@ int32_t ising_create(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
         return fail(ISING_ERR_INVALID_ARG, "n_slices must be >= 1 and divide n");
     if (flags != 0)
         return fail(ISING_ERR_INVALID_ARG, "flags must be 0");
-    int32_t rc = validate_csr(n, row_ptr, col, J);
+    long long km = 0, eb = 0;
+    int32_t rc = validate_csr(n, row_ptr, col, J, h, &km, &eb);
     if (rc)
         return rc;
 
@@ -1090,17 +1188,6 @@ int32_t ising_create(int32_t n, const int32_t* row_ptr, const int32_t* col, cons
     if (rc) {
         delete g;
         return rc;
-    }
-    long long eb = 0, km = 0;
-    for (int i = 0; i < n; ++i) {
-        long long b = std::llabs((long long)h[i]);
-        eb += std::llabs((long long)h[i]);
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            b += std::llabs((long long)J[e]);
-            if (col[e] > i)
-                eb += std::llabs((long long)J[e]);
-        }
-        km = std::max(km, b);
     }
     g->kmax = km;
     g->ebound = eb;
@@ -1256,9 +1343,10 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
         swthr.assign(size_t(bound), 0u);
         for (int k = 1; k < npairs; ++k)
             swoff[k] = swoff[k - 1] + swcap[k - 1];
-        const int nthr = int(std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+        // pairs taken from a shared counter (their tables differ in length)
+        const int nthr = std::min(host_threads(), npairs);
         std::atomic<int> next{0};
-        auto work = [&]() {
+        host_parallel(nthr, [&](int) {
             for (int k; (k = next.fetch_add(1)) < npairs;) {
                 const double db = betas[k + 1] - betas[k];
                 uint32_t* v = swthr.data() + swoff[k];  // v[0] = 0: d = 0 never uses the table
@@ -1271,13 +1359,7 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
                 }
                 swlen[k] = int(d);
             }
-        };
-        std::vector<std::thread> pool;
-        for (int t = 1; t < nthr; ++t)
-            pool.emplace_back(work);
-        work();
-        for (auto& th : pool)
-            th.join();
+        });
         k_serial = npairs;
     }
     for (int k = k_serial; k + 1 < R; ++k) {
@@ -1521,10 +1603,14 @@ static uint32_t split_flip_threshold(double beta, double K, int ks, int kt)
 static void split_flip_table(const double* betas, const double* K, int R, int ks, uint32_t* out)
 {
     const size_t Ks = size_t(3) * size_t(2 * ks + 1);
-    for (int t = 0; t < R; ++t)
-        for (int k = -ks; k <= ks; ++k)
-            for (int j = 0; j < 3; ++j)
-                out[size_t(t) * Ks + size_t(k + ks) * 3 + j] = split_flip_threshold(betas[t], K[t], k, 2 * j - 2);
+    const int nthr = (double(R) * double(Ks) >= 65536.0) ? std::min(host_threads(), R) : 1;
+    isg::host_parallel(nthr, [&](int p) {
+        for (int t = p; t < R; t += nthr)
+            for (int k = -ks; k <= ks; ++k)
+                for (int j = 0; j < 3; ++j)
+                    out[size_t(t) * Ks + size_t(k + ks) * 3 + j] =
+                        split_flip_threshold(betas[t], K[t], k, 2 * j - 2);
+    });
 }
 
 int32_t ising_split_flip_table(int32_t R, const double* betas, const double* K, int32_t ks, uint32_t* out)

@@ -150,3 +150,78 @@ def test_header_is_plain_c():
         r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang, hdr],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def _layered_with_fault(L, M, spin_offset):
+    """A layered model whose slice t = 3 differs from slice 0 in h at one
+    site: ising_create must reject it at spin 3 S + spin_offset."""
+    from paper_1004_0024_gb300 import workloads as W
+    g = W.layered_graph(L, M, graph_seed=7)
+    S = g.n // M
+    h = g.h.copy()
+    h[3 * S + spin_offset] += 1
+    return g, h, 3 * S + spin_offset
+
+
+def test_host_worker_threads_serve_concurrent_callers(lib):
+    """The library's host loops share one set of worker threads: eight Python
+    threads creating models (rejected in slice extraction, which runs on the
+    workers) and building flip tables at once all get their own, correct
+    answers."""
+    import threading
+    import oracle
+    from paper_1004_0024_gb300 import workloads as W
+    betas = W.geometric_betas(1024, 0.05, 5.0)
+    K = W.trotter_couplings(betas, 2.0, 32)
+    want = lib.split_flip_table(betas, K, 20)
+    assert want[517, 21, 2] == oracle.trotter_flip_threshold(betas[517], K[517], 1, 2)
+    cases = [_layered_with_fault(32, 16, off) for off in (5, 77, 300, 901)]
+    errors = []
+
+    def worker(k):
+        try:
+            for rep in range(6):
+                g, h, spin = cases[(k + rep) % len(cases)]
+                with pytest.raises(lib.IsingError) as e:
+                    lib.ising_create(g.n, g.row_ptr, g.col, g.J, h, g.n_slices)
+                assert f"declared slices differ in h at spin {spin}" in str(e.value), str(e.value)
+                assert np.array_equal(lib.split_flip_table(betas, K, 20), want)
+        except BaseException as exc:  # reported on the main thread
+            errors.append(repr(exc))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=120)
+    assert not any(t.is_alive() for t in threads), "a host loop did not return"
+    assert not errors, errors
+
+
+def _forked_table(q):
+    from paper_1004_0024_gb300 import ising
+    from paper_1004_0024_gb300 import workloads as W
+    betas = W.geometric_betas(1024, 0.05, 5.0)
+    K = W.trotter_couplings(betas, 2.0, 32)
+    q.put(ising.split_flip_table(betas, K, 20).sum(dtype=np.uint64))
+
+
+def test_host_loops_work_in_a_forked_child(lib):
+    """A child forked after the parent's worker threads exist has none of
+    them: its host loops run on fresh threads instead of waiting forever."""
+    import multiprocessing as mp
+    from paper_1004_0024_gb300 import workloads as W
+    betas = W.geometric_betas(1024, 0.05, 5.0)
+    K = W.trotter_couplings(betas, 2.0, 32)
+    want = lib.split_flip_table(betas, K, 20).sum(dtype=np.uint64)  # parent's workers now exist
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    p = ctx.Process(target=_forked_table, args=(q,))
+    p.start()
+    p.join(timeout=60)
+    if p.is_alive():
+        p.kill()
+        p.join()
+        pytest.fail("host loop in the forked child did not return")
+    assert p.exitcode == 0
+    assert q.get(timeout=5) == want
