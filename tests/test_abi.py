@@ -206,6 +206,7 @@ def _forked_table(q):
     q.put(ising.split_flip_table(betas, K, 20).sum(dtype=np.uint64))
 
 
+@pytest.mark.filterwarnings("ignore:This process .* is multi-threaded:DeprecationWarning")
 def test_host_loops_work_in_a_forked_child(lib):
     """A child forked after the parent's worker threads exist has none of
     them: its host loops run on fresh threads instead of waiting forever."""
