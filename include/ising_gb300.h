@@ -548,8 +548,12 @@ int32_t ising_selftest_wait(int32_t kind, void* stream);
  * buffer fits, which then skips the allocation. */
 int32_t ising_destroy(ising_t h);
 
-/* Frees the word buffers kept by ising_destroy (process-wide; always
- * ISING_OK).  An allocation that fails frees them and retries by itself. */
+/* Frees the word buffers kept by ising_destroy and the host copies of the
+ * swap-threshold tables kept for the last two ladders (at most 2^24 entries
+ * each; ising_replicas_init reuses them for a ladder with the same betas and
+ * energy bound instead of evaluating its exponentials again).  Process-wide;
+ * always ISING_OK.  An allocation that fails frees the word buffers and
+ * retries by itself. */
 int32_t ising_release_cached_memory(void);
 
 #ifdef __cplusplus

@@ -1134,6 +1134,132 @@ int32_t isg_device_setup()
 }
 
 // ====================================================================== ABI
+namespace {
+
+// Swap thresholds S_k(d) = floor(2^32 exp(-(b_{k+1}-b_k) d)) for 1 <= d < len_k
+// of every pair k of a ladder, flattened (pair k's table starts at off[k]).
+struct SwapTables {
+    std::vector<uint32_t> thr;
+    std::vector<long long> off;
+    std::vector<int> len;
+    bool pt_ok = true;  // false when the tables would exceed 2^28 entries
+};
+
+std::shared_ptr<const SwapTables> build_swap_tables(const double* betas, int R, long long dmax)
+{
+    auto out = std::make_shared<SwapTables>();
+    std::vector<long long>& swoff = out->off;
+    std::vector<int>& swlen = out->len;
+    std::vector<uint32_t>& swthr = out->thr;
+    swoff.assign(std::max(R - 1, 1), 0);
+    swlen.assign(std::max(R - 1, 1), 1);
+    // S_k(d) is zero once 2^32 exp(-db d) < 1, i.e. beyond d = 32 ln 2 / db
+    // (+1 for the rounding of the FP64 expression).  When these bounds keep
+    // the tables within 2^28 entries, each pair's table is written in
+    // parallel at an offset given by the bounds, with the same expression and
+    // stopping rule as the serial loop below (a few unused entries may sit
+    // between two tables); otherwise the serial loop builds them and refuses
+    // PT if they would not fit.
+    std::vector<long long> swcap(std::max(R - 1, 1), 0);
+    long long bound = 0;
+    for (int k = 0; k + 1 < R && bound <= (1LL << 28); ++k) {
+        swcap[k] = 1 + std::min<long long>(dmax - 1, (long long)(22.18070977791825 / (betas[k + 1] - betas[k])) + 2);
+        bound += swcap[k];
+    }
+    int k_serial = 0;  // first pair left to the serial loop
+    if (R > 2 && bound <= (1LL << 28)) {
+        const int npairs = R - 1;
+        swthr.assign(size_t(bound), 0u);
+        for (int k = 1; k < npairs; ++k)
+            swoff[k] = swoff[k - 1] + swcap[k - 1];
+        // pairs taken from a shared counter (their tables differ in length)
+        const int nthr = std::min(host_threads(), npairs);
+        std::atomic<int> next{0};
+        host_parallel(nthr, [&](int) {
+            for (int k; (k = next.fetch_add(1)) < npairs;) {
+                const double db = betas[k + 1] - betas[k];
+                uint32_t* v = swthr.data() + swoff[k];  // v[0] = 0: d = 0 never uses the table
+                long long d = 1;
+                for (; d < dmax && d < swcap[k]; ++d) {
+                    const double x = std::floor(std::ldexp(std::exp(-db * double(d)), 32));
+                    if (x == 0.0)
+                        break;
+                    v[d] = uint32_t(x);
+                }
+                swlen[k] = int(d);
+            }
+        });
+        k_serial = npairs;
+    }
+    for (int k = k_serial; k + 1 < R; ++k) {
+        const double db = betas[k + 1] - betas[k];
+        swoff[k] = (long long)swthr.size();
+        swthr.push_back(0u);
+        long long d = 1;
+        for (; d < dmax; ++d) {
+            const double v = std::floor(std::ldexp(std::exp(-db * double(d)), 32));
+            if (v == 0.0)
+                break;
+            swthr.push_back(uint32_t(v));
+            if (swthr.size() > (size_t(1) << 28))
+                break;
+        }
+        swlen[k] = int(d);
+        if (swthr.size() > (size_t(1) << 28)) {
+            // a long, finely spaced ladder: the FP64 tables would exceed 2^28
+            // entries; sweeps stay available, PT passes are refused
+            out->pt_ok = false;
+            swthr.assign(1, 0u);
+            std::fill(swoff.begin(), swoff.end(), 0LL);
+            std::fill(swlen.begin(), swlen.end(), 1);
+            break;
+        }
+    }
+    return out;
+}
+
+// The tables of the last few ladders (exact betas and bound): handles made
+// again and again for the same ladder (a bench loop, a restart, many
+// instances of one problem) reuse them instead of evaluating up to millions
+// of exponentials each time.  At most kSwapCacheKeep ladders of at most
+// 2^24 entries are kept; ising_release_cached_memory empties the cache.
+constexpr size_t kSwapCacheKeep = 2;
+std::mutex g_swap_mu;
+std::vector<std::pair<std::pair<std::vector<double>, long long>, std::shared_ptr<const SwapTables>>> g_swap_cache;
+
+std::shared_ptr<const SwapTables> swap_tables(const double* betas, int R, long long dmax)
+{
+    std::pair<std::vector<double>, long long> key(std::vector<double>(betas, betas + R), dmax);
+    {
+        std::lock_guard<std::mutex> lk(g_swap_mu);
+        for (size_t i = 0; i < g_swap_cache.size(); ++i)
+            if (g_swap_cache[i].first.second == dmax &&
+                std::memcmp(g_swap_cache[i].first.first.data(), betas, sizeof(double) * size_t(R)) == 0 &&
+                g_swap_cache[i].first.first.size() == size_t(R)) {
+                auto hit = g_swap_cache[i];
+                g_swap_cache.erase(g_swap_cache.begin() + long(i));
+                g_swap_cache.push_back(hit);  // most recent last
+                return hit.second;
+            }
+    }
+    std::shared_ptr<const SwapTables> t = build_swap_tables(betas, R, dmax);
+    if (t->thr.size() <= (size_t(1) << 24)) {
+        std::lock_guard<std::mutex> lk(g_swap_mu);
+        if (g_swap_cache.size() >= kSwapCacheKeep)
+            g_swap_cache.erase(g_swap_cache.begin());
+        g_swap_cache.emplace_back(std::move(key), t);
+    }
+    return t;
+}
+
+void swap_cache_clear()
+{
+    std::lock_guard<std::mutex> lk(g_swap_mu);
+    g_swap_cache.clear();
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* ising_last_error(void) { return g_err.c_str(); }
@@ -1147,6 +1273,7 @@ int32_t ising_set_alloc_cap(uint64_t bytes)
 int32_t ising_release_cached_memory(void)
 {
     big_release_all();
+    swap_cache_clear();
     return ISING_OK;
 }
 
@@ -1319,73 +1446,12 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
     for (int t = 0; t < R; ++t)
         for (int k = 1; k < g->K; ++k)
             thr[size_t(t) * g->K + k] = flip_threshold(betas[t], k, amode);
-    // swap thresholds S_k(d) = floor(2^32 exp(-(b_{k+1}-b_k) d)) for 1 <= d < len_k
-    std::vector<long long> swoff(std::max(R - 1, 1), 0);
-    std::vector<int> swlen(std::max(R - 1, 1), 1);
-    std::vector<uint32_t> swthr;
-    const long long dmax = 2 * g->ebound + 1;
-    // S_k(d) is zero once 2^32 exp(-db d) < 1, i.e. beyond d = 32 ln 2 / db
-    // (+1 for the rounding of the FP64 expression).  When these bounds keep
-    // the tables within 2^28 entries, each pair's table is written in
-    // parallel at an offset given by the bounds, with the same expression and
-    // stopping rule as the serial loop below (a few unused entries may sit
-    // between two tables); otherwise the serial loop builds them and refuses
-    // PT if they would not fit.
-    std::vector<long long> swcap(std::max(R - 1, 1), 0);
-    long long bound = 0;
-    for (int k = 0; k + 1 < R && bound <= (1LL << 28); ++k) {
-        swcap[k] = 1 + std::min<long long>(dmax - 1, (long long)(22.18070977791825 / (betas[k + 1] - betas[k])) + 2);
-        bound += swcap[k];
-    }
-    int k_serial = 0;  // first pair left to the serial loop
-    if (R > 2 && bound <= (1LL << 28)) {
-        const int npairs = R - 1;
-        swthr.assign(size_t(bound), 0u);
-        for (int k = 1; k < npairs; ++k)
-            swoff[k] = swoff[k - 1] + swcap[k - 1];
-        // pairs taken from a shared counter (their tables differ in length)
-        const int nthr = std::min(host_threads(), npairs);
-        std::atomic<int> next{0};
-        host_parallel(nthr, [&](int) {
-            for (int k; (k = next.fetch_add(1)) < npairs;) {
-                const double db = betas[k + 1] - betas[k];
-                uint32_t* v = swthr.data() + swoff[k];  // v[0] = 0: d = 0 never uses the table
-                long long d = 1;
-                for (; d < dmax && d < swcap[k]; ++d) {
-                    const double x = std::floor(std::ldexp(std::exp(-db * double(d)), 32));
-                    if (x == 0.0)
-                        break;
-                    v[d] = uint32_t(x);
-                }
-                swlen[k] = int(d);
-            }
-        });
-        k_serial = npairs;
-    }
-    for (int k = k_serial; k + 1 < R; ++k) {
-        const double db = betas[k + 1] - betas[k];
-        swoff[k] = (long long)swthr.size();
-        swthr.push_back(0u);
-        long long d = 1;
-        for (; d < dmax; ++d) {
-            const double v = std::floor(std::ldexp(std::exp(-db * double(d)), 32));
-            if (v == 0.0)
-                break;
-            swthr.push_back(uint32_t(v));
-            if (swthr.size() > (size_t(1) << 28))
-                break;
-        }
-        swlen[k] = int(d);
-        if (swthr.size() > (size_t(1) << 28)) {
-            // a long, finely spaced ladder: the FP64 tables would exceed 2^28
-            // entries; sweeps stay available, PT passes are refused
-            g->pt_ok = false;
-            swthr.assign(1, 0u);
-            std::fill(swoff.begin(), swoff.end(), 0LL);
-            std::fill(swlen.begin(), swlen.end(), 1);
-            break;
-        }
-    }
+    // swap thresholds of the ladder (shared with earlier handles of the same ladder)
+    const std::shared_ptr<const SwapTables> swt = swap_tables(betas, R, 2 * g->ebound + 1);
+    g->pt_ok = swt->pt_ok;
+    const std::vector<uint32_t>& swthr = swt->thr;
+    const std::vector<long long>& swoff = swt->off;
+    const std::vector<int>& swlen = swt->len;
     int32_t rc;
     const size_t RN = size_t(R) * g->n;
     if ((rc = dalloc(&g->d_spins, RN)))
