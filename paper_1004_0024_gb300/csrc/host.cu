@@ -1482,8 +1482,11 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
     if (rng_mode == ISING_RNG_MT19937) {
         std::vector<uint32_t> ring(size_t(R + 1) * kMtRing);
         std::vector<unsigned long long> pos(R + 1, 624ull);
-        for (int r = 0; r <= R; ++r)
-            mt_seed_ring(seed + uint32_t(r), ring.data() + size_t(r) * kMtRing);
+        const int nthr = R >= 64 ? std::min(host_threads(), R + 1) : 1;
+        host_parallel(nthr, [&](int p) {
+            for (int r = p; r <= R; r += nthr)
+                mt_seed_ring(seed + uint32_t(r), ring.data() + size_t(r) * kMtRing);
+        });
         if ((rc = upload(&g->d_mtring, ring)) || (rc = upload(&g->d_mtpos, pos))) {
             g->free_replicas();
             return rc;
