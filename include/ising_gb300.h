@@ -240,6 +240,19 @@ int32_t ising_read_trotter(ising_t h, int64_t* C);
  *       computes it (2^32 - 1 for z <= 0).
  */
 int32_t ising_split_flip_table(int32_t R, const double* betas, const double* K, int32_t ks, uint32_t* out);
+
+/*
+ * ising_swap_thresholds -- the PT swap tables ising_replicas_init builds
+ * (host only, for tests and tools): for pair k (0 <= k < R-1) and
+ * 1 <= d < len[k], thr[off[k] + d] = floor(2^32 exp(-(betas[k+1]-betas[k]) d))
+ * in FP64, len[k] the first d with a zero threshold or dmax (the energy
+ * bound 2 (sum |h| + sum |J|) + 1 of the model); thr[off[k]] is unused.
+ * *pt_ok = 0 when the tables would exceed 2^28 entries (PT is then refused).
+ * off [R-1], len [R-1], pt_ok may be NULL; thr may be NULL to query
+ * *n_entries, else it holds cap >= *n_entries values.  Errors: INVALID_ARG.
+ */
+int32_t ising_swap_thresholds(int32_t R, const double* betas, int64_t dmax, uint32_t* thr, int64_t cap,
+                              int64_t* off, int32_t* len, int64_t* n_entries, int32_t* pt_ok);
 double ising_split_exp(double x);
 uint32_t ising_split_swap_threshold(double dbeta, double dK, int64_t dE, int64_t dC);
 

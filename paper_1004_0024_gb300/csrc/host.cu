@@ -1160,6 +1160,22 @@ std::shared_ptr<const SwapTables> build_swap_tables(const double* betas, int R, 
     // stopping rule as the serial loop below (a few unused entries may sit
     // between two tables); otherwise the serial loop builds them and refuses
     // PT if they would not fit.
+    // The tables hold sum_k len_k entries, and len_k >= min(dmax, 32 ln 2 / db - 2)
+    // (below that d, 2^32 exp(-db d) >= exp(2 db) > 1 even after rounding).  When
+    // that lower bound passes 2^28 PT is refused without evaluating anything:
+    // the same tables the serial loop below ends with.
+    {
+        long long lower = 0;
+        for (int k = 0; k + 1 < R && lower <= (1LL << 28); ++k) {
+            const double est = 22.18070977791825 / (betas[k + 1] - betas[k]) - 2.0;
+            lower += std::min<long long>(dmax, est > 1.0 ? (long long)std::min(est, 1e18) : 1LL);
+        }
+        if (lower > (1LL << 28)) {
+            out->pt_ok = false;
+            swthr.assign(1, 0u);
+            return out;
+        }
+    }
     std::vector<long long> swcap(std::max(R - 1, 1), 0);
     long long bound = 0;
     for (int k = 0; k + 1 < R && bound <= (1LL << 28); ++k) {
@@ -1691,6 +1707,32 @@ int32_t ising_split_flip_table(int32_t R, const double* betas, const double* K, 
 }
 
 double ising_split_exp(double x) { return isg::split_detail::exp_det(x); }
+
+int32_t ising_swap_thresholds(int32_t R, const double* betas, int64_t dmax, uint32_t* thr, int64_t cap,
+                              int64_t* off, int32_t* len, int64_t* n_entries, int32_t* pt_ok)
+{
+    if (R < 1 || !betas || dmax < 1 || !n_entries)
+        return fail(ISING_ERR_INVALID_ARG, "R >= 1, dmax >= 1, betas and n_entries required");
+    for (int k = 1; k < R; ++k)
+        if (!(betas[k] > betas[k - 1]))
+            return fail(ISING_ERR_INVALID_ARG, "betas must be strictly ascending");
+    const std::shared_ptr<const SwapTables> t = build_swap_tables(betas, R, (long long)dmax);
+    *n_entries = (int64_t)t->thr.size();
+    if (pt_ok)
+        *pt_ok = t->pt_ok ? 1 : 0;
+    if (off)
+        for (int k = 0; k + 1 < R; ++k)
+            off[k] = t->off[size_t(k)];
+    if (len)
+        for (int k = 0; k + 1 < R; ++k)
+            len[k] = t->len[size_t(k)];
+    if (thr) {
+        if (cap < (int64_t)t->thr.size())
+            return fail(ISING_ERR_INVALID_ARG, "thr holds fewer than n_entries values");
+        std::copy(t->thr.begin(), t->thr.end(), thr);
+    }
+    return ISING_OK;
+}
 
 uint32_t ising_split_swap_threshold(double dbeta, double dK, int64_t dE, int64_t dC)
 {

@@ -136,6 +136,8 @@ _SIGS = {
     "ising_read_trotter": ([_vp, _i64p], ctypes.c_int32),
     "ising_split_flip_table": ([ctypes.c_int32, _f64p, _f64p, ctypes.c_int32, _u32p], ctypes.c_int32),
     "ising_split_exp": ([ctypes.c_double], ctypes.c_double),
+    "ising_swap_thresholds": ([ctypes.c_int32, _f64p, ctypes.c_int64, _u32p, ctypes.c_int64, _i64p, _i32p,
+                               _i64p, _i32p], ctypes.c_int32),
     "ising_split_swap_threshold": ([ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64],
                                    ctypes.c_uint32),
     "ising_selftest_wait": ([ctypes.c_int32, _vp], ctypes.c_int32),
@@ -248,6 +250,23 @@ def split_flip_table(betas, K, ks: int) -> np.ndarray:
     out = np.empty((betas.size, 2 * ks + 1, 3), dtype=np.uint32)
     _check(_lib.ising_split_flip_table(betas.size, _p(betas, _f64p), _p(K, _f64p), ks, _p(out, _u32p)))
     return out
+
+
+def swap_thresholds(betas, dmax: int):
+    """The PT swap tables of a ladder as ising_replicas_init builds them:
+    (thr, off, len, pt_ok), pair k's S_k(d) = thr[off[k] + d] for 1 <= d < len[k]."""
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    R = betas.size
+    n = ctypes.c_int64(0)
+    ok = ctypes.c_int32(0)
+    off = np.zeros(max(R - 1, 1), dtype=np.int64)
+    ln = np.zeros(max(R - 1, 1), dtype=np.int32)
+    _check(_lib.ising_swap_thresholds(R, _p(betas, _f64p), int(dmax), None, 0, _p(off, _i64p), _p(ln, _i32p),
+                                      ctypes.byref(n), ctypes.byref(ok)))
+    thr = np.zeros(max(n.value, 1), dtype=np.uint32)
+    _check(_lib.ising_swap_thresholds(R, _p(betas, _f64p), int(dmax), _p(thr, _u32p), thr.size, None, None,
+                                      ctypes.byref(n), None))
+    return thr[:n.value], off[:max(R - 1, 0)], ln[:max(R - 1, 0)], bool(ok.value)
 
 
 def split_exp(x: float) -> float:

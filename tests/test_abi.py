@@ -226,3 +226,32 @@ def test_host_loops_work_in_a_forked_child(lib):
         pytest.fail("host loop in the forked child did not return")
     assert p.exitcode == 0
     assert q.get(timeout=5) == want
+
+
+@pytest.mark.parametrize("R,lo,hi,dmax", [(32, 0.1, 3.0, 67789), (2, 0.4, 0.9, 5000), (9, 0.2, 2.0, 40)])
+def test_swap_tables_match_the_oracle(lib, R, lo, hi, dmax):
+    """The PT swap tables ising_replicas_init uploads, entry by entry against
+    the oracle's floor(2^32 exp(-dbeta d)), with each table ending at the
+    first zero threshold or at the energy bound dmax."""
+    import oracle
+    from paper_1004_0024_gb300 import workloads as W
+    betas = W.geometric_betas(R, lo, hi)
+    thr, off, ln, ok = lib.swap_thresholds(betas, dmax)
+    assert ok
+    for k in range(R - 1):
+        db = betas[k + 1] - betas[k]
+        L = int(ln[k])
+        got = thr[off[k] + 1: off[k] + L]
+        want = [oracle.swap_threshold(db, d) for d in range(1, L)]
+        assert np.array_equal(got, np.array(want, dtype=np.uint32)), k
+        assert L == dmax or oracle.swap_threshold(db, L) == 0
+        assert L == 1 or got[-1] > 0
+
+
+def test_swap_tables_beyond_2p28_entries_refuse_pt(lib):
+    """The 65536-temperature ladder of the many-replica workload needs far
+    more than 2^28 FP64 thresholds: PT is refused at once (one placeholder
+    entry), as ising_pt_swap then reports."""
+    from paper_1004_0024_gb300 import workloads as W
+    thr, off, ln, ok = lib.swap_thresholds(W.geometric_betas(65536, 0.1, 3.0), 60001)
+    assert not ok and thr.size == 1 and np.all(off == 0) and np.all(ln == 1)
