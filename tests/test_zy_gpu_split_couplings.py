@@ -6,8 +6,9 @@ PT swaps evaluate the deterministic exponential on the device.  Every check is
 element by element: spins, spatial fields, spatial energies, Trotter sums,
 labels, acceptance counts and counters.
 
-This file is collected after every other GPU file, so that a run stopping at
-its first failure has already run the rest.
+This file is collected after every other GPU file but the allocation-free run's
+(which comes last), so that a run stopping at its first failure has already run
+the rest.
 """
 from __future__ import annotations
 
