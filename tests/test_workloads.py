@@ -94,3 +94,36 @@ def test_split_coupling_workload():
     assert K[0] == pytest.approx(2.8842, abs=1e-3) and K[-1] == pytest.approx(0.5975, abs=1e-3)
     # the mapping's defining identity: tanh(K) = exp(-2 beta Gamma / M)
     assert np.allclose(np.tanh(K), np.exp(-2.0 * c["betas"] * 2.0 / 32))
+
+
+@pytest.mark.parametrize("L,Ly,seed", [(8, 8, 1), (32, 32, 1), (8, 12, 7), (16, 16, 3)])
+def test_matchings_are_disjoint_and_off_the_lattice(L, Ly, seed):
+    """The spatial edges beyond the periodic lattice come from two partial
+    matchings (section 1: degree 6-8 with the Trotter pair): none of them is a
+    lattice bond or a self loop, no site has more than two such partners (one
+    per matching), and each matching stops at a quarter of the sites in pairs."""
+    adj, Jd, h = W.spatial_model(L, seed, Ly)
+    S = L * Ly
+
+    def site(x, y):
+        return (y % Ly) * L + (x % L)
+
+    lattice = set()
+    for y in range(Ly):
+        for x in range(L):
+            a = site(x, y)
+            for b in (site(x + 1, y), site(x, y + 1)):
+                lattice.add((min(a, b), max(a, b)))
+    assert len(lattice) == 2 * S
+    edges = {(min(a, b), max(a, b)) for a in range(S) for b in adj[a]}
+    assert lattice <= edges and set(Jd) == edges
+    extra = edges - lattice
+    partners = np.zeros(S, dtype=np.int64)
+    for a, b in extra:
+        assert a != b
+        partners[a] += 1
+        partners[b] += 1
+    assert partners.max() <= 2
+    # each matching accepts floor(S / 4) pairs (about half of the sites covered)
+    assert len(extra) == 2 * (S // 4)
+    assert h.shape == (S,)
