@@ -1249,9 +1249,8 @@ std::shared_ptr<const SwapTables> swap_tables(const double* betas, int R, long l
     {
         std::lock_guard<std::mutex> lk(g_swap_mu);
         for (size_t i = 0; i < g_swap_cache.size(); ++i)
-            if (g_swap_cache[i].first.second == dmax &&
-                std::memcmp(g_swap_cache[i].first.first.data(), betas, sizeof(double) * size_t(R)) == 0 &&
-                g_swap_cache[i].first.first.size() == size_t(R)) {
+            if (g_swap_cache[i].first.second == dmax && g_swap_cache[i].first.first.size() == size_t(R) &&
+                std::memcmp(g_swap_cache[i].first.first.data(), betas, sizeof(double) * size_t(R)) == 0) {
                 auto hit = g_swap_cache[i];
                 g_swap_cache.erase(g_swap_cache.begin() + long(i));
                 g_swap_cache.push_back(hit);  // most recent last
