@@ -344,7 +344,9 @@ int32_t ising_get_stats(ising_t h, ising_stats_t* out);
  *   call), so calls whose kernels overlap on the GPU race: issue them on one
  *   stream, or otherwise order them.
  * Errors: NOT_INITIALISED, INVALID_ARG (n < 0, R > 16384), UNSUPPORTED (MT19937
- * mode, or no persistent launch for this handle), CUDA.
+ * mode, no persistent launch for this handle, split couplings set by
+ * ising_set_trotter, or swap_every > 0 on a ladder whose PT tables would exceed
+ * 2^28 entries), CUDA.
  */
 int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every);
 
