@@ -213,9 +213,10 @@ int32_t ising_read_swap_stats(ising_t h, uint64_t* accepted);
  * couplings last until the next ising_replicas_init.  Requires declared
  * slices with a Trotter ring (M >= 3) and the lean kernel (M in {4, 8, 16,
  * 32} or a multiple of 32 up to 1024, spatial degree <= 6, |J| <= 63, one
- * replica per block); not with learned passes or ising_run_noalloc.  Errors: INVALID_ARG (NULL argument, non-finite K, set
- * twice), NOT_INITIALISED, UNSUPPORTED (model or launch configuration without
- * the lean kernel, acceptance mode other than EXACT, a flip table above 8192
+ * replica per block); not with learned passes or ising_run_noalloc.
+ * Errors: INVALID_ARG (NULL argument, non-finite K, set twice),
+ * NOT_INITIALISED, UNSUPPORTED (model or launch configuration without the
+ * lean kernel, acceptance mode other than EXACT, a flip table above 8192
  * entries per temperature), OOM, CUDA.
  */
 int32_t ising_set_trotter(ising_t h, const double* K);
