@@ -73,3 +73,37 @@ def test_throttled_or_clock_locked_runs_are_remeasured():
     assert not bench.clocks_rejected(dict(base, sm_mhz=1500.0, reasons=["sw_power_cap"]))
     assert bench.clocks_rejected(dict(base, sm_mhz=1100.0))
     assert bench.any_rank(True, 1) and not bench.any_rank(False, 1)
+
+
+def test_clock_samples_and_the_remeasure_rule(tmp_path):
+    """nvidia-smi's CSV rows (no header, no units) give the median SM clock,
+    the maximum and the active throttle reasons; a timed region is measured
+    again after a hardware or thermal slowdown, or with the SM clock well
+    below its maximum and no reason given, but not for sw_power_cap alone."""
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1900, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2070, 1200.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc, s.path = Done(), str(path)
+    c = s.stop()
+    assert c == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not path.exists()
+    assert not bench.clocks_rejected(c)
+    assert not bench.clocks_rejected(None)
+    assert bench.clocks_rejected({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown"]})
+    assert bench.clocks_rejected({"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": ["sw_thermal_slowdown"]})
+    assert bench.clocks_rejected({"sm_mhz": 1200.0, "sm_max_mhz": 2070.0, "reasons": []})
+    assert not bench.clocks_rejected({"sm_mhz": 1200.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]})
