@@ -338,16 +338,23 @@ int32_t ising_get_stats(ising_t h, ising_stats_t* out);
  *   fit on the GPU at once (ising_get_info(...).persistent_ok == 1).
  *   Scratch (grid-barrier and block counters, energies exchanged for the PT
  *   passes) is one file-scope device array of 128 KB that every GPU loading
- *   the library holds until the process exits.  The first call on a device
- *   resolves that array's device address (cudaGetSymbolAddress); make that
- *   first call before any stream capture.  Every call shares the array and
- *   it keeps the last call's contents (the counters are cleared by each
- *   call), so calls whose kernels overlap on the GPU race: issue them on one
- *   stream, or otherwise order them.
- * Errors: NOT_INITIALISED, INVALID_ARG (n < 0, R > 16384), UNSUPPORTED (MT19937
- * mode, no persistent launch for this handle, split couplings set by
- * ising_set_trotter, or swap_every > 0 on a ladder whose PT tables would exceed
- * 2^28 entries), CUDA.
+ *   the library holds until the process exits.  ising_replicas_init resolves
+ *   that array's device address (cudaGetSymbolAddress) on the handle's
+ *   device, which also loads the device module holding it, so this call
+ *   itself loads and allocates nothing; if the device current at this call
+ *   has had no handle initialised on it, this call resolves the address
+ *   first (and may then load the module): make such a first call before any
+ *   stream capture and outside the allocation-free phase.  Every call shares
+ *   the array and it keeps the last call's contents (the counters are
+ *   cleared by each call), so calls whose kernels overlap on the GPU race:
+ *   issue them on one stream, or otherwise order them.
+ *   Each launch counts in ising_get_stats' launches and sweep_launches; no
+ *   profiling events are recorded (their creation is not allocation-free).
+ * Errors: NOT_INITIALISED, INVALID_ARG (n < 0, R > 16384, or swap_every >
+ * 2^30 with n >= swap_every: one PT group would exceed a launch), UNSUPPORTED
+ * (MT19937 mode, no persistent launch for this handle, split couplings set by
+ * ising_set_trotter, or 0 < swap_every <= n on a ladder whose PT tables would
+ * exceed 2^28 entries, the case ising_run refuses too), CUDA.
  */
 int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every);
 

@@ -101,3 +101,4 @@ int32_t isg_device_setup();  // once per process: kernel attributes, SM count
 int isg_num_sms();           // SMs of the current device (after isg_device_setup)
 bool isg_pt_ok(const ising_s* g);
 bool isg_alloc_allowed(size_t bytes);  // the cap of ising_set_alloc_cap
+int32_t isg_noalloc_prepare();  // noalloc.cu: resolve the static scratch on the current device

@@ -1127,6 +1127,12 @@ bool isg_alloc_allowed(size_t bytes) { return alloc_allowed(bytes); }
 
 bool isg_pt_ok(const ising_s* g) { return g->pt_ok; }
 
+void isg_count_launches(ising_t g, long long all, long long sweeps)
+{
+    g->n_launches += all;
+    g->n_sweep_launches += sweeps;
+}
+
 int32_t isg_device_setup()
 {
     const cudaError_t e = device_setup();
@@ -1531,6 +1537,12 @@ static int32_t replicas_init_impl(ising_t g, int32_t R, const double* betas, uin
     }
     CK(launch_state_init(g->d_spins, g->d_fields, field_bits, g->d_E, R, g->n, g->d_row_ptr,
                          g->d_col, g->d_J, g->d_h, g->stream));
+    // ising_run_noalloc's scratch: its device address is resolved (and its
+    // module loaded) here, so that the allocation-free run loads nothing
+    if ((rc = isg_noalloc_prepare())) {
+        g->free_replicas();
+        return rc;
+    }
     g->inited = true;
     return ISING_OK;
 }

@@ -16,6 +16,7 @@
 
 int32_t isg_fused_launch(ising_t g, isg::FusedLaunch* out);
 int32_t isg_fail(int32_t code, const char* msg);
+void isg_count_launches(ising_t g, long long all, long long sweeps);
 
 namespace {
 
@@ -30,7 +31,11 @@ std::mutex g_mu;
 unsigned int* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, resolved once
-// per device (with that device current).
+// per device (with that device current).  The library is built from separate
+// device modules, and under lazy module loading the module holding the array
+// is loaded -- its 128 KB placed on the device -- by the first
+// cudaGetSymbolAddress; isg_noalloc_prepare makes that happen while a handle
+// is initialised, so that ising_run_noalloc itself finds the address cached.
 int32_t scratch_for_current_device(unsigned int** out)
 {
     int dev = 0;
@@ -53,10 +58,22 @@ int32_t scratch_for_current_device(unsigned int** out)
 
 }  // namespace
 
+// Called by ising_replicas_init with the handle's device current.
+int32_t isg_noalloc_prepare()
+{
+    unsigned int* p = nullptr;
+    return scratch_for_current_device(&p);
+}
+
 extern "C" int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every)
 {
     if (n < 0)
         return isg_fail(ISING_ERR_INVALID_ARG, "n must be >= 0");
+    // a launch runs whole groups of swap_every sweeps and at most 2^30 sweeps
+    if (swap_every > (1 << 30) && n >= swap_every)
+        return isg_fail(ISING_ERR_INVALID_ARG,
+                        "ising_run_noalloc: swap_every > 2^30 with n >= swap_every (a PT group longer than "
+                        "one launch)");
     ising_info_t info;
     int32_t rc = ising_get_info(h, &info);
     if (rc)
@@ -70,7 +87,7 @@ extern "C" int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every)
     if (info.replicas > kNoAllocMaxReplicas)
         return isg_fail(ISING_ERR_INVALID_ARG,
                         "ising_run_noalloc supports at most 16384 replicas (static scratch size)");
-    if (swap_every > 0 && !isg_pt_ok(h))
+    if (swap_every > 0 && swap_every <= n && !isg_pt_ok(h))
         return isg_fail(ISING_ERR_UNSUPPORTED, "PT swap tables exceed 2^28 entries for this ladder: sweeps only");
     isg::FusedLaunch fl;
     if ((rc = isg_fused_launch(h, &fl)))
@@ -115,6 +132,7 @@ extern "C" int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every)
         if (e != cudaSuccess)
             return isg_fail(e == cudaErrorCooperativeLaunchTooLarge ? ISING_ERR_UNSUPPORTED : ISING_ERR_CUDA,
                             cudaGetErrorString(e));
+        isg_count_launches(h, 1, 1);
         done += m;
     }
     return ISING_OK;

@@ -255,3 +255,16 @@ def test_swap_tables_beyond_2p28_entries_refuse_pt(lib):
     from paper_1004_0024_gb300 import workloads as W
     thr, off, ln, ok = lib.swap_thresholds(W.geometric_betas(65536, 0.1, 3.0), 60001)
     assert not ok and thr.size == 1 and np.all(off == 0) and np.all(ln == 1)
+
+
+def test_noalloc_refuses_a_pt_group_longer_than_a_launch(lib):
+    # an argument check taken before any handle or device work: a PT group of
+    # more than 2^30 sweeps cannot run in one launch (it used to loop forever)
+    with pytest.raises(lib.IsingError) as ei:
+        lib.ising_run_noalloc(None, (1 << 30) + 5, (1 << 30) + 1)
+    assert ei.value.name == "INVALID_ARG"
+    assert "2^30" in lib.ising_last_error()
+    # fewer sweeps than one group: no fused group, so the handle is checked next
+    with pytest.raises(lib.IsingError) as ei:
+        lib.ising_run_noalloc(None, 5, (1 << 30) + 1)
+    assert "2^30" not in lib.ising_last_error()
