@@ -279,6 +279,17 @@ int32_t ising_read_observables(ising_t h, int64_t* energy_by_temp, int64_t* magn
 int32_t ising_save(ising_t h, void* buf, size_t cap, size_t* size);
 int32_t ising_load(ising_t h, const void* buf, size_t size);
 
+/* ising_set_seed -- continue the current state with other random numbers
+ * (ISING_RNG_PHILOX only): the seed of every later Philox word (sweeps, PT
+ * passes, learned passes) becomes `seed`; spins, fields, energies, labels
+ * and counters are kept.  After ising_load this gives a second chain from a
+ * checkpoint that is statistically independent of the saved chain's
+ * continuation.  On a freshly initialised handle, the sweeps that follow are
+ * those of a handle initialised with `seed` whose initial spins were set to
+ * this handle's.  Errors: INVALID_ARG (NULL handle), NOT_INITIALISED,
+ * UNSUPPORTED (MT19937 mode: its streams are seeded by ising_replicas_init). */
+int32_t ising_set_seed(ising_t h, uint32_t seed);
+
 /* Layout facts of a handle (for tests and tuning reports). */
 typedef struct {
     int32_t n, slices, slice_size, levels, slice_depth, replicas;

@@ -2023,6 +2023,19 @@ int32_t ising_load(ising_t g, const void* buf, size_t size)
     return ISING_OK;
 }
 
+int32_t ising_set_seed(ising_t g, uint32_t seed)
+{
+    if (!g)
+        return fail(ISING_ERR_INVALID_ARG, "NULL handle");
+    if (!g->inited)
+        return fail(ISING_ERR_NOT_INITIALISED, "call ising_replicas_init first");
+    if (g->rng != ISING_RNG_PHILOX)
+        return fail(ISING_ERR_UNSUPPORTED, "ising_set_seed needs ISING_RNG_PHILOX");
+    g->seed = seed;
+    g->drop_graphs();  // recorded launches hold the old key
+    return ISING_OK;
+}
+
 int32_t ising_get_info(ising_t g, ising_info_t* o)
 {
     if (!g || !o)

@@ -58,23 +58,57 @@ def mean_and_se(x: np.ndarray) -> tuple[float, float]:
     return float(x.mean()), float(np.sqrt(2.0 * tau_int(x) * x.var() / x.size))
 
 
-def histogram_agreement(a: np.ndarray, b: np.ndarray, bins: int = 8) -> np.ndarray:
-    """z-scores of the bin fractions of two correlated series on shared edges
-    (the standard error of each fraction from its indicator's tau)."""
-    lo, hi = min(a.min(), b.min()), max(a.max(), b.max())
-    if lo == hi:
+N_BATCHES = 20  # batch means per series for the histogram standard errors
+
+
+def batch_mean_and_se(x: np.ndarray, n_batches: int = N_BATCHES) -> tuple[float, float]:
+    """Mean and its standard error from the spread of `n_batches` contiguous
+    batch means (valid when a batch is much longer than tau_int; the first
+    len(x) mod n_batches samples are dropped)."""
+    x = np.asarray(x, dtype=np.float64)
+    b = x.size // n_batches
+    if b < 1:
+        raise ValueError("fewer samples than batches")
+    bm = x[x.size - b * n_batches:].reshape(n_batches, b).mean(axis=1)
+    return float(bm.mean()), float(bm.std(ddof=1) / np.sqrt(n_batches))
+
+
+def histogram_agreement(a: np.ndarray, b: np.ndarray, bins: int = 8,
+                        n_batches: int = N_BATCHES) -> np.ndarray:
+    """z-scores of the bin fractions of two correlated series.  The edges are
+    quantiles of the pooled samples (so every bin holds a fair share of both
+    series; tied values of an integer observable merge bins); the standard
+    error of each fraction comes from batch means of its indicator series."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    pooled = np.concatenate([a, b])
+    if pooled.min() == pooled.max():
         return np.zeros(0)
-    edges = np.linspace(lo, hi + 1e-9 * max(1.0, abs(hi)), bins + 1)
+    inner = np.unique(np.quantile(pooled, np.arange(1, bins) / bins))
+    edges = np.concatenate([[-np.inf], inner, [np.inf]])
     z = []
-    for k in range(bins):
+    for k in range(edges.size - 1):
         ia = ((a >= edges[k]) & (a < edges[k + 1])).astype(np.float64)
         ib = ((b >= edges[k]) & (b < edges[k + 1])).astype(np.float64)
-        ma, sa = mean_and_se(ia)
-        mb, sb = mean_and_se(ib)
+        ma, sa = batch_mean_and_se(ia, n_batches)
+        mb, sb = batch_mean_and_se(ib, n_batches)
         s = np.hypot(sa, sb)
         if s > 0:
             z.append((ma - mb) / s)
     return np.asarray(z)
+
+
+def beyond_3se_law(bins: int, n_batches: int = N_BATCHES, q: float = 0.999) -> dict:
+    """What two chains of the same law give: each z above is approximately
+    Student-t with 2 (n_batches - 1) degrees of freedom (two batch-mean
+    standard errors of similar size), so |z| > 3 has probability p; of
+    `bins` such z-scores the count beyond 3 is about Binomial(bins, p)
+    (bins of one histogram are not independent, which widens the law a
+    little).  Returns p, the expected count and the q-quantile used as the
+    bound of the check."""
+    from scipy import stats
+    p = float(2.0 * stats.t.sf(3.0, 2 * (n_batches - 1)))
+    return {"p": p, "expected": p * bins, "bound": int(stats.binom.ppf(q, bins, p)), "quantile": q}
 
 
 def _observe(sim, step, n_steps):
@@ -106,15 +140,20 @@ def _seconds_per_step(sim, step, n_steps):
     return e0.elapsed_time(e1) / 1e3 / n_steps
 
 
-def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time: int = 200, ctrl=None):
+def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time: int = 200, ctrl=None,
+            ctrl_seed: int | None = None):
     """Plain chain (one sweep + PT per step) against the 1:1 chain (one sweep
     + PT, then one learned pass per step), both from the handle's current
-    state.  With ``ctrl`` (a second handle of the same configuration and
-    another seed) a second plain chain runs from the same state with other
-    random numbers: the spread between two correct chains calibrates the
-    comparison.  Returns per-temperature series, ESS and ESS/s of E and m,
-    and the learned acceptance and change rates."""
+    state.  With ``ctrl`` (a second handle of the same configuration, Philox
+    streams) a second plain chain runs from the same state with other random
+    numbers: after loading the shared state its seed is set to ``ctrl_seed``
+    (the loaded checkpoint carries the first chain's key), so the spread
+    between two correct chains calibrates the comparison.  Returns
+    per-temperature series, ESS and ESS/s of E and m, and the learned
+    acceptance and change rates."""
     blob = sim.save()
+    if ctrl is not None and ctrl_seed is None:
+        raise ValueError("a control chain needs its own seed")
 
     def plain():
         sim.run(1, swap_every)
@@ -130,12 +169,18 @@ def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time:
     if ctrl is not None:
         chains.append(("plain_ctrl", ctrl, plain_ctrl))
     out = {}
-    for name, h, step in chains:
+
+    def restart(name, h):
         h.load(blob)
+        if name == "plain_ctrl":
+            h.set_seed(ctrl_seed)
+
+    for name, h, step in chains:
+        restart(name, h)
         for _ in range(warm):
             step()
         sps = _seconds_per_step(h, step, n_time)
-        h.load(blob)
+        restart(name, h)
         t0 = time.perf_counter()
         E, m = _observe(h, step, n_steps)
         wall = time.perf_counter() - t0
@@ -201,8 +246,13 @@ def fast_mixing(res: dict, names, max_tau_frac: float = 1.0 / 500) -> np.ndarray
 def _hist_stats(res, a, b, temps):
     z = [histogram_agreement(res[a][o][:, k], res[b][o][:, k]) for o in ("E", "m") for k in np.nonzero(temps)[0]]
     z = np.concatenate(z) if z else np.zeros(0)
+    law = beyond_3se_law(int(z.size)) if z.size else None
     return {"bins": int(z.size), "beyond_3se": int((np.abs(z) > 3).sum()),
-            "max_abs_z": float(np.abs(z).max()) if z.size else None}
+            "max_abs_z": float(np.abs(z).max()) if z.size else None,
+            "z_rms": float(np.sqrt(np.mean(z * z))) if z.size else None,
+            "se": f"batch means ({N_BATCHES} batches per series), pooled-quantile bins",
+            "expected_beyond_3se": law["expected"] if law else None,
+            "bound_beyond_3se": law["bound"] if law else None}
 
 
 def summarize(res: dict, betas) -> dict:
@@ -265,7 +315,7 @@ def study(ising, W, burn: int, n_steps: int, epochs: int, records: int = 1 << 20
     t0 = time.perf_counter()
     losses = [net.train(1, 4096, 1e-3) for _ in range(epochs)]
     train_s = time.perf_counter() - t0
-    res = compare(sim, net, n_steps, ctrl=ctrl)
+    res = compare(sim, net, n_steps, ctrl=ctrl, ctrl_seed=c["seed"] + 7919)
     out = summarize(res, c["betas"])
     # the fused network kernel alone, timed with CUDA events around each launch
     net.set_profiling(True)

@@ -91,6 +91,7 @@ _SIGS = {
     "ising_read_swap_stats": ([_vp, _u64p], ctypes.c_int32),
     "ising_save": ([_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
     "ising_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int32),
+    "ising_set_seed": ([_vp, ctypes.c_uint32], ctypes.c_int32),
     "ising_get_info": ([_vp, ctypes.POINTER(IsingInfo)], ctypes.c_int32),
     "ising_set_launch": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
     "ising_run_noalloc": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int32),
@@ -291,6 +292,10 @@ def ising_load(h, blob: bytes):
     _check(_lib.ising_load(h, ctypes.cast(buf, _vp), len(blob)))
 
 
+def ising_set_seed(h, seed):
+    _check(_lib.ising_set_seed(h, int(seed) & 0xFFFFFFFF))
+
+
 def ising_get_info(h) -> dict:
     info = IsingInfo()
     _check(_lib.ising_get_info(h, ctypes.byref(info)))
@@ -414,6 +419,10 @@ class Ising:
 
     def load(self, blob: bytes):
         ising_load(self.h, blob)
+
+    def set_seed(self, seed):
+        """Philox: later random words use ``seed``; the state is kept."""
+        ising_set_seed(self.h, seed)
 
     def info(self) -> dict:
         return ising_get_info(self.h)

@@ -10,9 +10,13 @@ control.  The test checks, and prints, that
 * the trained network's proposals are accepted far more often than an
   untrained one's (the gain from training);
 * on the fast-mixing temperatures the learned chain's energy and
-  magnetisation histograms agree with the plain chain's about as well as an
-  independent plain chain does (the Metropolis-Hastings correction keeps the
-  Boltzmann law);
+  magnetisation histograms agree with the plain chain's within 3 standard
+  errors as often as two chains of one law do: batch-mean standard errors,
+  and a count of |z| > 3 bins no larger than the 0.999 quantile of its
+  binomial law; a second plain chain continuing the same state on its own
+  Philox seed passes the same bound and is not a replay of the first
+  (its largest |z| is not 0) -- the Metropolis-Hastings correction keeps the
+  Boltzmann law;
 * at the coldest quarter of the ladder, where the single-spin sweep is nearly
   frozen, the learned chain reaches lower energies than the plain chain in
   the same number of steps.
@@ -59,6 +63,8 @@ def test_trained_proposal_gain(mods):
     assert out["loss_first_last"][1] < 0.8 * out["loss_first_last"][0]
     h, hc = out["histograms_learned_vs_plain"], out["histograms_plain_vs_plain"]
     assert out["fast_mixing_temps"] >= 20 and h["bins"] > 100
-    assert h["beyond_3se"] <= max(2 * hc["beyond_3se"], 0.03 * h["bins"]), (h, hc)
+    assert hc["max_abs_z"] > 0.5, hc  # the control chain draws its own random numbers
+    assert hc["beyond_3se"] <= hc["bound_beyond_3se"], hc
+    assert h["beyond_3se"] <= h["bound_beyond_3se"], (h, hc)
     cq = out["coldest_quarter"]
     assert cq["mean_E_last_fifth_learned"] < cq["mean_E_last_fifth_plain"], cq

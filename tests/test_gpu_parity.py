@@ -199,6 +199,37 @@ def test_checkpoint_resume_is_bit_exact(ising):
     assert_same(b, ref)
 
 
+def test_set_seed_continues_with_the_new_seeds_random_numbers(ising):
+    # a fresh handle of seed 11 given seed 23: its chain is the oracle's chain
+    # of seed 23 started from the seed-11 handle's initial spins
+    c = W.config0()
+    dev = ising.Ising(c["graph"], c["betas"], seed=11, rng="philox", field_bits=32)
+    init = dev.read_state()["spins"]
+    dev.set_seed(23)
+    ref = oracle.Sim(c["graph"], c["betas"], seed=23, rng="philox")
+    ref.set_spins(init)
+    assert_same(dev, ref, "after set_seed")
+    dev.run(40, 1)
+    ref.run(40, 1)
+    assert_same(dev, ref, "40 sweeps after set_seed")
+    # after loading a checkpoint, the reseeded chain leaves the saved chain's path
+    blob = dev.save()
+    a = ising.Ising(c["graph"], c["betas"], seed=5, rng="philox", field_bits=32)
+    b = ising.Ising(c["graph"], c["betas"], seed=5, rng="philox", field_bits=32)
+    a.load(blob)
+    b.load(blob)
+    b.set_seed(77)
+    a.run(5, 1)
+    b.run(5, 1)
+    dev.run(5, 1)
+    assert np.array_equal(a.read_state()["spins"], dev.read_state()["spins"])
+    assert not np.array_equal(b.read_state()["spins"], dev.read_state()["spins"])
+    mt = ising.Ising(c["graph"], c["betas"], seed=5, rng="mt19937", field_bits=32)
+    with pytest.raises(ising.IsingError) as ei:
+        mt.set_seed(3)
+    assert ei.value.name == "UNSUPPORTED"
+
+
 def test_graph_replay_matches_fresh_launches(ising):
     """ising_run records a CUDA graph once and replays it; replays must advance
     the device-side counters and streams exactly like fresh launches."""
