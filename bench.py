@@ -64,6 +64,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads of the default line (cfg1 Philox, cfg3, cfg1-trotter, "
+                         "the paper's shape, the ragged batch)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposal study (ESS/s against the plain sweep)")
     ap.add_argument("--workload", choices=["cfg1", "cfg3", "batch", "paper", "cfg1-trotter"], default="cfg1",
@@ -199,6 +202,94 @@ def any_rank(flag, world):
 
 
 # ------------------------------------------------------------- our path
+def time_steps(sim, sweeps, swap_every, steps, flush, stream, dev_index, world):
+    """Time `steps` runs of ising_run(sweeps, swap_every) on the handle's
+    stream: CUDA events around each step, an L2 flush between steps (outside
+    the events), clocks sampled during the timed region, one re-measure when
+    the clocks show a slowdown or a locked clock.  Warm-up is the caller's."""
+    import torch
+    import torch.distributed as dist
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sim.set_profiling(True)
+    timed_passes, first_clocks = 0, None
+    while True:
+        st0 = sim.stats()
+        sampler = ClockSampler(dev_index)
+        sampler.start()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
+            ev[k][0].record(stream)
+            sim.run(sweeps, swap_every)
+            ev[k][1].record(stream)
+        barrier()
+        clocks = sampler.stop()
+        timed_passes += 1
+        if timed_passes == 1 and any_rank(clocks_rejected(clocks), world):
+            first_clocks = clocks  # throttled or clock-locked: measure once more
+            continue
+        break
+    st1 = sim.stats()
+    sim.set_profiling(False)
+    return {"step_ms": [a.elapsed_time(b) for a, b in ev], "clocks": clocks, "first_clocks": first_clocks,
+            "timed_passes": timed_passes, "kernel_ms": st1["kernel_ms"] - st0["kernel_ms"],
+            "sweep_launches": st1["timed_launches"] - st0["timed_launches"],
+            "launches": st1["launches"] - st0["launches"]}
+
+
+def workload_line(name, rng, steps, warmup, flush, stream, dev_index, sweeps=0):
+    """One extra workload of the default line (a single GPU): its own handle,
+    warm-up, timed steps, clocks and roofline."""
+    from paper_1004_0024_gb300 import ising
+    c = workload(name)
+    if sweeps > 0:
+        c = dict(c, sweeps=sweeps)
+    sim = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=c["field_bits"],
+                      stream=stream.cuda_stream)
+    if "K" in c:
+        sim.set_trotter(c["K"])
+    info = sim.info()
+    t_w = time.perf_counter()
+    for _ in range(warmup):
+        sim.run(c["sweeps"], c["swap_every"])
+    import torch
+    torch.cuda.synchronize()
+    warm_s = time.perf_counter() - t_w
+    t = time_steps(sim, c["sweeps"], c["swap_every"], steps, flush, stream, dev_index, 1)
+    sim.close()
+    per_step = attempts_per_step(c)
+    total_ms = sum(t["step_ms"])
+    out = {"workload": WORKLOAD_NAMES[name], "rng": rng, "field_bits": c["field_bits"],
+           "value": per_step * steps / (total_ms * 1e-3), "unit": "attempts/s",
+           "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup, "warmup_seconds": warm_s,
+           "sweeps_per_step": c["sweeps"], "attempts_per_step": per_step, "clocks": t["clocks"],
+           "gpu_launches": int(t["launches"]),
+           "kernel_variant": info["fast_kernel"], "levels": info["levels"],
+           "roofline": roofline(c, rng, per_step * steps, t["kernel_ms"], t["sweep_launches"], t["clocks"],
+                                info["fast_kernel"], name)}
+    if t["first_clocks"] is not None:
+        out["remeasured"] = {"first_clocks": t["first_clocks"]}
+    return out
+
+
+# the extra workloads of the default line: (key, workload, rng, steps,
+# warm-up steps, sweeps per step override)
+EXTRA_WORKLOADS = [
+    ("cfg1_philox", "cfg1", "philox", 5, 3, 0),
+    ("cfg3_mt19937", "cfg3", "mt19937", 2, 3, 0),
+    ("cfg3_philox", "cfg3", "philox", 2, 3, 0),
+    ("cfg1_trotter", "cfg1-trotter", "mt19937", 5, 3, 0),
+    ("paper_shape_3000_sweeps", "paper", "mt19937", 2, 3, 3000),
+]
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -234,40 +325,11 @@ def run_ours(args):
         sim.run(sweeps, swap_every)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
-    sim.set_profiling(True)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    timed_passes, first_clocks = 0, None
-    while True:
-        st0 = sim.stats()
-        sampler = ClockSampler(dev_index)
-        sampler.start()
-        barrier()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
-            ev[k][0].record(stream)
-            sim.run(sweeps, swap_every)
-            ev[k][1].record(stream)
-        barrier()
-        clocks = sampler.stop()
-        timed_passes += 1
-        if timed_passes == 1 and any_rank(clocks_rejected(clocks), world):
-            first_clocks = clocks  # throttled or clock-locked: measure once more
-            continue
-        break
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t = time_steps(sim, sweeps, swap_every, args.steps, flush, stream, dev_index, world)
+    clocks, first_clocks, timed_passes = t["clocks"], t["first_clocks"], t["timed_passes"]
+    step_ms = t["step_ms"]
     total_ms = sum(step_ms)
-    st1 = sim.stats()
-    kernel_ms = st1["kernel_ms"] - st0["kernel_ms"]
-    sweep_launches = st1["timed_launches"] - st0["timed_launches"]
-    launches = st1["launches"] - st0["launches"]
-    sim.set_profiling(False)
+    kernel_ms, sweep_launches, launches = t["kernel_ms"], t["sweep_launches"], t["launches"]
     max_ms = max_over_ranks(total_ms, world)
     value = whole_job_value(world, per_step, args.steps, max_ms)
 
@@ -323,6 +385,13 @@ def run_ours(args):
                                  "basis": "derived from the paper's section 4 and Figure 13 (other hardware)"}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(c, args.rng, args.cpu_seconds)
+    if world == 1 and not args.no_extra and args.workload == "cfg1" and args.sweeps == 0:
+        # the other workloads, each with its own handle, clocks and roofline
+        extra = {}
+        for key, name, rng, steps, warm, sw in EXTRA_WORKLOADS:
+            extra[key] = workload_line(name, rng, steps, warm, flush, stream, dev_index, sw)
+        extra["batch"] = measure_batch(2, 3, 100, 1, 0)
+        line["workloads"] = extra
     if world == 1 and not args.no_learned and args.workload == "cfg1":
         line["learned"] = learned_study()
     print(json.dumps(line), flush=True)
@@ -475,7 +544,7 @@ def learned_study():
     streams), plus the fused network kernel against the bf16 tensor peak."""
     from paper_1004_0024_gb300 import ess, ising
     from paper_1004_0024_gb300 import workloads as W
-    out = ess.study(ising, W, burn=20000, n_steps=4000, epochs=6)
+    out = ess.study(ising, W, burn=20000, n_steps=16000, epochs=6)
     peak = measured_peak("bf16_tflops")
     net = out.pop("network")
     out["network_roofline"] = {
@@ -541,25 +610,18 @@ def learned_passes_only(n):
     print(json.dumps({"learned_passes": n, "loss": loss, "accepted": [s["accepted"] for s in stats]}), flush=True)
 
 
-def run_batch(args):
+def measure_batch(steps, warmup, sweeps, world, rank):
     """The ragged batch: 4096 instances (spin counts log-uniform in
-    2^11..2^15, 8..64 replicas), autotuned, one step = ising_batch_run(100, 1)
-    (a recorded CUDA graph of batched sweep and PT launches), Philox words.
+    2^11..2^15, 8..64 replicas), autotuned, one step = ising_batch_run(sweeps,
+    1) (a recorded CUDA graph of batched sweep and PT launches), Philox words.
     Under torchrun the instances are sharded over the ranks (rank r takes
     instances r, r + N, ...; numbered within its own batch): the total work is
-    fixed ("scaling": "strong"), the value is every rank's attempts over the
-    slowest rank's time."""
+    fixed, the value is every rank's attempts over the slowest rank's time.
+    Returns the measurement on rank 0 (None elsewhere)."""
     import torch
-    import torch.distributed as dist
 
     from paper_1004_0024_gb300 import ising
     from paper_1004_0024_gb300 import workloads as W
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     t0 = time.perf_counter()
     built = [W.build_instance(d) for d in shard(W.ragged_instances(4096), rank, world)]
     inst = [(x["graph"], x["betas"], x["seed"]) for x in built]
@@ -567,21 +629,21 @@ def run_batch(args):
     b = ising.Batch(inst, rng="philox", field_bits=16, stream=stream.cuda_stream)
     b.autotune()
     setup_s = time.perf_counter() - t0
-    sweeps = args.sweeps if args.sweeps > 0 else 100
     per_step = sum(x["graph"].n * len(x["betas"]) for x in built) * sweeps
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run(sweeps, 1)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     first_clocks = None
     for timed_pass in range(2):
         sampler = ClockSampler(torch.cuda.current_device())
         sampler.start()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        for k in range(args.steps):
+              for _ in range(steps)]
+        for k in range(steps):
             flush.fill_(k & 0xFF)
             ev[k][0].record(stream)
             b.run(sweeps, 1)
@@ -596,33 +658,56 @@ def run_batch(args):
         break
     ms = max_over_ranks(sum(a.elapsed_time(e) for a, e in ev), world)
     total_per_step = sum_over_ranks(per_step, world)
-    value = total_per_step * args.steps / (ms * 1e-3)
+    value = total_per_step * steps / (ms * 1e-3)
     resident = int(sum_over_ranks(sum(b.info(i)["resident"] for i in range(len(inst))), world))
     deg = sum(float(x["graph"].row_ptr[-1]) for x in built) / sum(x["graph"].n for x in built)
     ops = 20 + 6 + 3 * deg
     peak, mhz = int_peak_tops(clocks)
     b.close()
     if rank != 0:
+        return None
+    out = {"workload": f"4096 ragged instances (2^11..2^15 spins, 8..64 replicas), {sweeps} sweeps + PT each",
+           "rng": "philox", "field_bits": 16, "value": value, "unit": "attempts/s", "ms_per_step": ms / steps,
+           "steps": steps, "warmup": warmup, "attempts_per_step": total_per_step,
+           "resident_instances": resident, "setup_seconds": setup_s, "clocks": clocks,
+           "roofline": {"bound": "alu", "achieved": value / world * ops / 1e12, "peak": peak,
+                        "unit": "Tops/s (int32)", "frac": value / world * ops / 1e12 / peak, "traffic": None,
+                        "ops_per_attempt": ops, "per": "one GPU (the job's value divided by the ranks)",
+                        "peak_basis": f"152 SM x 128 lanes x {mhz:.0f} MHz sampled SM clock (derived, not measured)",
+                        "timed": "whole graph replay (every kernel of the step)"}}
+    if first_clocks is not None:
+        out["remeasured"] = {"first_clocks": first_clocks, "why": "slowdown or locked clock in the first timed pass"}
+    return out
+
+
+def run_batch(args):
+    """bench.py --workload batch: the ragged batch as the line's workload."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    sweeps = args.sweeps if args.sweeps > 0 else 100
+    m = measure_batch(args.steps, args.warmup, sweeps, world, rank)
+    if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     line = {"metric": "spin-flip attempts/sec vs roofline; ESS/sec learned proposal vs plain sweep",
-            "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "value": m["value"], "unit": "attempts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": m["ms_per_step"], "higher_is_better": True,
             "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
             "dtype": "int8 spins/int16 fields/uint32 RNG", "data": "synthetic (seeded ragged layered models)",
-            "config": {"workload": f"4096 ragged instances (2^11..2^15 spins, 8..64 replicas), {sweeps} sweeps + PT each",
-                       "rng": "philox", "attempts_per_step": total_per_step, "resident_instances": resident,
-                       "setup_seconds": setup_s, "l2": "flushed (512 MB write) between timed steps",
+            "config": {"workload": m["workload"], "rng": "philox", "attempts_per_step": m["attempts_per_step"],
+                       "resident_instances": m["resident_instances"], "setup_seconds": m["setup_seconds"],
+                       "l2": "flushed (512 MB write) between timed steps",
                        "parallelism": f"instances sharded x{world}" if world > 1 else "replicas-only x1"},
-            "clocks": clocks,
-            "roofline": {"bound": "alu", "achieved": value / world * ops / 1e12, "peak": peak, "unit": "Tops/s (int32)",
-                         "frac": value / world * ops / 1e12 / peak, "traffic": None, "ops_per_attempt": ops,
-                         "per": "one GPU (the job's value divided by the ranks)",
-                         "peak_basis": f"152 SM x 128 lanes x {mhz:.0f} MHz sampled SM clock (derived, not measured)",
-                         "timed": "whole graph replay (every kernel of the step)"}}
-    if first_clocks is not None:
-        line["remeasured"] = {"first_clocks": first_clocks, "why": "slowdown or locked clock in the first timed pass"}
+            "clocks": m["clocks"], "roofline": m["roofline"]}
+    if "remeasured" in m:
+        line["remeasured"] = m["remeasured"]
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -304,7 +304,13 @@ typedef struct {
                               use a build for more resident blocks per SM),
                               3 the track-scheduled variant (lean's limits,
                               M <= 32, one thread per track of columns;
-                              opt-in with ISING_LAUNCH_TRACK) */
+                              opt-in with ISING_LAUNCH_TRACK),
+                              4 the packed variant (one replica per block of
+                              one to eight warps, the columns' busy windows
+                              packed into thread slots, fields gathered from
+                              the neighbours' spins at each visit; M in
+                              {8,16,32}, spatial degree <= 6, |J| <= 127,
+                              plain couplings; the default where it applies) */
 } ising_info_t;
 int32_t ising_get_info(ising_t h, ising_info_t* out);
 
@@ -313,6 +319,7 @@ int32_t ising_get_info(ising_t h, ising_info_t* out);
 #define ISING_LAUNCH_GENERIC 2    /* force the generic (shared-memory column) kernel */
 #define ISING_LAUNCH_NO_LEAN 4    /* do not use the lean register-resident variant */
 #define ISING_LAUNCH_TRACK 8      /* use the track-scheduled variant where it applies */
+#define ISING_LAUNCH_NO_PACKED 16 /* do not use the packed variant (the lean one instead) */
 
 /* Override the launch shape: replicas per block (0 = automatic, else a power
  * of two <= 32), threads per block (0 = automatic, else a multiple of 32 and

@@ -2,6 +2,7 @@
 #include <algorithm>
 
 #include "lean_impl.cuh"
+#include "packed_impl.cuh"
 #include "track_impl.cuh"
 
 namespace isg {
@@ -9,6 +10,8 @@ namespace {
 
 void* pick(int field_bits, int rng, int cmax, int variant = 0, bool batch = false, bool split = false)
 {
+    if (variant == 5)  // packed: single-instance, plain couplings; cmax = slot rounds per thread
+        return (batch || split) ? nullptr : packed_kernel_ptr(rng, cmax);
     if (split)  // lean variants only, single-instance launches only
         return (batch || !(variant == 1 || variant == 3 || variant == 4))
                    ? nullptr
@@ -29,8 +32,9 @@ size_t g_fast_max_dyn = 0;
 size_t fast_smem_bytes(const SweepArgs& a, int field_bits, int variant, int threads)
 {
     const int fb = field_bits == 16 ? 2 : 4;
-    const size_t b = variant == 2 ? track_detail::track_layout(a, fb, threads).total
-                                  : fast_detail::fast_layout(a, fb).total;
+    const size_t b = variant == 5   ? packed_smem_bytes(a, threads)
+                     : variant == 2 ? track_detail::track_layout(a, fb, threads).total
+                                    : fast_detail::fast_layout(a, fb).total;
     return (g_fast_max_dyn && b > g_fast_max_dyn) ? size_t(-1) : b;
 }
 
@@ -44,11 +48,12 @@ cudaError_t fast_set_smem_limits()
         return e;
     size_t lim = size_t(optin);
     for (int batch : {0, 1, 2})  // 2: the split-coupling instantiations
-    for (int variant : {0, 1, 2, 3, 4})
+    for (int variant : {0, 1, 2, 3, 4, 5})
         for (int fb : {16, 32})
             for (int rng : {0, 1})
-                for (int cm : {1, 2, 4, 8}) {
-                    if (variant == 2 && cm != 1)
+                for (int cm : {1, 2, 3, 4, 5, 8}) {
+                    if ((variant == 2 && cm != 1) || (variant == 5 && (batch != 0 || fb != 16)) ||
+                        (variant != 5 && (cm == 3 || cm == 5)))
                         continue;
                     void* fn = pick(fb, rng, cm, variant, batch == 1, batch == 2);
                     if (!fn)

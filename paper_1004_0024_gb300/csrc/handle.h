@@ -77,6 +77,16 @@ struct ising_s {
     std::vector<int> track_off_v, track_col;
     int ntracks = 0;
     int *d_track_off = nullptr, *d_track_col = nullptr;
+    // packed kernel (packed_impl.cuh, kernel variant 5): columns packed into
+    // slots whose busy windows do not overlap, slot k = slot_col[slot_off[k] ..
+    // slot_off[k+1]); the device table buffer d_pk (pk_bytes) holds the column
+    // descriptors, positions and slot lists
+    std::vector<int> slot_off_v, slot_col_v;
+    int nslots = 0;
+    int sp_bound = 0;  // max over sites of |h_q| + sum of |J| over its spatial neighbours
+    uint32_t* d_pk = nullptr;
+    uint32_t pk_bytes = 0;
+    bool use_packed = false, packed_off = false;
     int fast_cmax = 1;
     size_t fast_smem = 0, smem_fused = 0;
     int G_req = 0, T_req = 0, allow_persistent = 1;

@@ -240,6 +240,7 @@ void mt_seed_ring(uint32_t seed, uint32_t* ring)
 }  // namespace
 
 #include "handle.h"
+#include "packed_impl.cuh"
 
 
 void ising_s::drop_graphs()
@@ -315,6 +316,7 @@ void ising_s::free_all()
     dfree(d_colour_sites);
     dfree(d_track_off);
     dfree(d_track_col);
+    dfree(d_pk);
     dfree(d_sp_off);
     dfree(d_sp_nbr);
     dfree(d_colbits);
@@ -618,7 +620,90 @@ int32_t extract_slices(ising_s* g)
             g->track_off_v.push_back(int(g->track_col.size()));
         }
     }
+    // slots of the packed kernel: the same windows, each column (in lev0
+    // order) into the lowest-numbered slot free at its start, so that the busy
+    // slots of a level crowd the lowest numbers; a slot is free again at the
+    // first level divisible by 4 at or after its column's window (the kernel
+    // moves slots to their next column at those levels)
+    {
+        std::vector<std::vector<int>> sl;
+        std::vector<int> free_at;
+        for (int p = 0; p < S; ++p) {
+            const int start = g->lev0p[p];
+            size_t k = 0;
+            while (k < free_at.size() && free_at[k] > start)
+                ++k;
+            if (k == free_at.size()) {
+                sl.emplace_back();
+                free_at.push_back(0);
+            }
+            sl[k].push_back(p);
+            free_at[k] = (start + M + 3) & ~3;
+        }
+        g->nslots = int(sl.size());
+        g->slot_off_v.assign(1, 0);
+        g->slot_col_v.clear();
+        for (auto& v : sl) {
+            g->slot_col_v.insert(g->slot_col_v.end(), v.begin(), v.end());
+            g->slot_off_v.push_back(int(g->slot_col_v.size()));
+        }
+        g->sp_bound = 0;
+        for (int q = 0; q < S; ++q) {
+            int b = std::abs(g->h[q]);
+            for (auto& e : sp[q])
+                b += std::abs(e.second);
+            g->sp_bound = std::max(g->sp_bound, b);
+        }
+    }
     return ISING_OK;
+}
+
+// The packed kernel's table buffer: column descriptors [S][8] (lev0 | site <<
+// 16, jtau, six neighbour entries pos << 16 | (uint16) J, missing ones
+// padded with the column itself and J = 0), positions [S], slot offsets
+// [nslots + 1], slot columns [S], and per position the constant part of the
+// spatial field h_q - sum_j J_qj [S], each part padded to 16 bytes.  A
+// neighbour entry is pos << 16 | (uint8) J << 8 | (uint8) dlev with dlev =
+// lev0(p) - lev0(neighbour) clamped to [-128, 127].
+std::vector<uint32_t> packed_tables(const ising_s* g)
+{
+    using isg::packed_detail::kDescWords;
+    const int S = g->S;
+    auto pad4 = [](size_t n) { return (n + 3) & ~size_t(3); };
+    std::vector<uint32_t> pk(isg::packed_detail::packed_table_bytes(S, g->nslots) / 4, 0u);
+    for (int p = 0; p < S; ++p) {
+        uint32_t* d = pk.data() + size_t(p) * kDescWords;
+        d[0] = uint32_t(g->lev0p[p]) | (uint32_t(g->site[p]) << 16);
+        d[1] = uint32_t(g->jtau[p]);
+        const int e0 = g->nbr_off[p], deg = g->nbr_off[p + 1] - e0;
+        for (int e = 0; e < isg::packed_detail::kMaxDeg; ++e) {
+            if (e >= deg) {
+                d[2 + e] = uint32_t(p) << 16;
+                continue;
+            }
+            const uint32_t en = g->nbr[e0 + e];
+            const int pj = int(en >> 16), J = int(int16_t(en & 0xFFFFu));
+            const int dlev = std::max(-128, std::min(127, g->lev0p[p] - g->lev0p[pj]));
+            d[2 + e] = (uint32_t(pj) << 16) | ((uint32_t(J) & 0xFFu) << 8) | (uint32_t(dlev) & 0xFFu);
+        }
+    }
+    size_t o = size_t(S) * kDescWords;
+    for (int q = 0; q < S; ++q)
+        pk[o + q] = uint32_t(g->pos[q]);
+    o += pad4(S);
+    for (int k = 0; k <= g->nslots; ++k)
+        pk[o + k] = uint32_t(g->slot_off_v[k]);
+    o += pad4(size_t(g->nslots) + 1);
+    for (int i = 0; i < S; ++i)
+        pk[o + i] = uint32_t(g->slot_col_v[i]);
+    o += pad4(S);
+    for (int p = 0; p < S; ++p) {
+        long long c = g->h[g->site[p]];
+        for (int e = g->nbr_off[p]; e < g->nbr_off[p + 1]; ++e)
+            c -= int16_t(g->nbr[e] & 0xFFFFu);
+        pk[o + p] = uint32_t(int32_t(c));
+    }
+    return pk;
 }
 
 // --------------------------------------------------- launch configuration
@@ -628,7 +713,73 @@ SweepArgs base_args(ising_s* g);
 // M <= 32, the slice tables in shared memory and spatial degree <= 255.
 int kernel_variant(const ising_s* g)
 {
+    if (g->use_packed)
+        return 5;
     return g->use_track ? 2 : (g->use_lean ? (g->lean_long ? 4 : (g->lean_small ? 3 : 1)) : 0);
+}
+
+// The packed kernel's model limits: M in {8, 16, 32} (the column in one
+// register, whole 4-word blocks), spatial degree <= 6, |J| <= 127 (8 bits in
+// the descriptor), positions and levels in 16 bits, plain couplings, one
+// replica per block and no opt-out.
+bool packed_eligible(const ising_s* g)
+{
+    return (g->M == 8 || g->M == 16 || g->M == 32) && g->max_sp_deg <= 6 && g->max_sp_J <= 127 &&
+           g->S < 65536 && g->D0 < 65536 && g->nslots >= 1 && !g->split &&
+           g->G_req <= 1 && !g->packed_off && !g->lean_off && !g->fast_off && !g->track_on &&
+           (g->T_req == 0 || g->T_req == 32 || g->T_req == 64 || g->T_req == 128 || g->T_req == 256);
+}
+
+// Configure the packed kernel: threads per block (one to eight warps;
+// automatic: the fewest whole warps that give every slot its own thread, up
+// to eight), slot rounds per thread, shared memory and the persistent check.
+bool choose_packed(ising_s* g)
+{
+    if (!packed_eligible(g))
+        return false;
+    const int T = g->T_req > 0 ? g->T_req : std::min(256, ((g->nslots + 31) / 32) * 32);
+    const int rounds = (g->nslots + T - 1) / T;
+    if (T > 128 && rounds > 1)
+        return false;  // the instantiations with more than one round allow 128 threads
+    int rmax = 0;
+    for (int r : isg::kPackedRounds)
+        if (rounds <= r) {
+            rmax = r;
+            break;
+        }
+    if (rmax == 0)
+        return false;
+    if (!g->d_pk) {
+        const std::vector<uint32_t> pk = packed_tables(g);
+        if (upload(&g->d_pk, pk) != ISING_OK)
+            return false;
+        g->pk_bytes = uint32_t(pk.size() * 4);
+    }
+    SweepArgs a = base_args(g);
+    a.G = 1;
+    const size_t plain = packed_smem_bytes(a, T);
+    a.swap_every = 1;
+    const size_t fused = packed_smem_bytes(a, T);
+    const size_t lim = sweep_max_dynamic_smem() ? sweep_max_dynamic_smem() : 200 * 1024;
+    if (plain > lim)
+        return false;
+    g->use_packed = true;
+    g->use_fast = true;
+    g->G = 1;
+    g->T = T;
+    g->blocks = g->R;
+    g->fast_cmax = rmax;
+    g->fast_smem = plain;
+    g->smem_fused = fused;
+    g->smem = plain;
+    g->persistent_ok = false;
+    if (!g_coop || !g->allow_persistent || fused > lim || g->R > 16384)
+        return true;
+    int per_sm = 0;
+    if (fast_max_blocks_per_sm(g->field_bits, rmax, g->rng, T, fused, &per_sm, 5) != cudaSuccess)
+        return true;
+    g->persistent_ok = (long long)per_sm * g_num_sms >= g->blocks;
+    return true;
 }
 
 // slice counts of the lean kernel: a power of two from 4 to 32 (the column in
@@ -656,11 +807,14 @@ bool track_eligible(const ising_s* g)
 void choose_fast(ising_s* g)
 {
     g->use_fast = false;
+    g->use_packed = false;
     g->use_lean = false;
     g->lean_small = false;
     g->lean_long = false;
     g->use_track = false;
     g->persistent_ok = false;
+    if (choose_packed(g))
+        return;
     // M > 32: only the lean kernel's long-column instantiation (M a multiple of 32)
     const bool long_cols = g->M > 32;
     if ((long_cols && !lean_slices(g->M)) || !g->tables_smem || g->max_sp_deg > 255 || g->fast_off)
@@ -783,11 +937,26 @@ SweepArgs base_args(ising_s* g)
     a.C_pub = g->d_Cpub;
     a.dbeta = g->d_dbeta;
     a.dK = g->d_dK;
+    a.pk = g->d_pk;
+    a.pk_bytes = g->pk_bytes;
+    a.nslots = g->nslots;
+    a.field_bits = g->field_bits;
     return a;
 }
 
 int32_t choose_launch(ising_s* g)
 {
+    if (packed_eligible(g)) {
+        // the packed kernel sizes its own blocks (one replica per block)
+        g->G = 1;
+        g->tables_smem = 1;
+        g->thr_smem = 1;
+        g->stage_words = 0;
+        g->cmax = 1;
+        choose_fast(g);
+        if (g->use_packed)
+            return ISING_OK;
+    }
     const int sms = g_num_sms > 0 ? g_num_sms : 148;
     const size_t kMaxSmem = sweep_max_dynamic_smem() ? sweep_max_dynamic_smem() : 200 * 1024;
     const long long table_bytes = 4LL * (4 * g->S + 1) + 4LL * (long long)g->nbr.size();
@@ -2052,7 +2221,7 @@ int32_t ising_get_info(ising_t g, ising_info_t* o)
     o->blocks = g->blocks;
     o->smem_bytes = int(g->smem);
     o->persistent_ok = g->persistent_ok ? 1 : 0;
-    o->fast_kernel = g->use_fast ? (g->use_track ? 3 : (g->use_lean ? 2 : 1)) : 0;
+    o->fast_kernel = g->use_fast ? (g->use_packed ? 4 : (g->use_track ? 3 : (g->use_lean ? 2 : 1))) : 0;
     o->field_bits = g->field_bits;
     o->rng_mode = g->rng;
     o->kmax = int(std::min<long long>(g->kmax, INT32_MAX));
@@ -2073,6 +2242,7 @@ int32_t ising_set_launch(ising_t g, int32_t replicas_per_block, int32_t threads_
     g->fast_off = (launch_flags & ISING_LAUNCH_GENERIC) != 0;
     g->lean_off = (launch_flags & ISING_LAUNCH_NO_LEAN) != 0;
     g->track_on = (launch_flags & ISING_LAUNCH_TRACK) != 0;
+    g->packed_off = (launch_flags & ISING_LAUNCH_NO_PACKED) != 0;
     g->drop_graphs();
     if (g->inited)
         return choose_launch(g);
@@ -2428,9 +2598,11 @@ int32_t ising_batch_create(int32_t n_inst, const ising_instance_t* in, int32_t r
         ising_t g = nullptr;
         int32_t rc = ising_create(in[i].n, in[i].row_ptr, in[i].col, in[i].J, in[i].h, in[i].n_slices,
                                   0u, &g);
-        if (!rc)
+        if (!rc) {
+            g->packed_off = true;  // the packed kernel has no batched instantiation
             rc = replicas_init_impl(g, in[i].replicas, in[i].betas, in[i].seed, rng_mode, field_bits,
                                     uint32_t(i));
+        }
         if (rc) {
             const std::string msg = "instance " + std::to_string(i) + ": " + g_err;
             if (g)

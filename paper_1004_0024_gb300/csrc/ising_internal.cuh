@@ -94,6 +94,13 @@ struct SweepArgs {
     int* C_pub;            // [2][R] Trotter sums published for the PT pass
     const double* dbeta;   // [R-1] beta_{k+1} - beta_k
     const double* dK;      // [R-1] K_{k+1} - K_k
+    // packed kernel (packed_impl.cuh): the table buffer (column descriptors,
+    // positions, slot offsets, slot columns; pk_bytes long), the number of
+    // slots, and the global field width (16 or 32)
+    const uint32_t* pk;
+    uint32_t pk_bytes;
+    int nslots;
+    int field_bits;
 };
 
 // One block of a batched launch: instance index and block index within it.

@@ -1,0 +1,597 @@
+// Packed (slot-scheduled) wavefront sweep: one replica per block of one or a
+// few warps, the columns' busy windows packed by the host into thread slots.
+//
+// Schedule and exactness are those of the lean kernel (lean_impl.cuh): spin
+// (q, t) runs at level lev0(q) + t, a block barrier separates levels, and
+// the random words are fixed in advance, so any such order gives the chain
+// of the sequential sweep of Figure 1 bit for bit.  What changes is who does
+// the work of a level.  A column of M slices is busy during M consecutive
+// levels [lev0, lev0 + M); the host packs the columns, in order of lev0, into
+// "slots", each column into the lowest-numbered slot that is free at its
+// start, a slot's next column starting no earlier than the first level
+// divisible by 4 after the previous one's window (165 slots cover the 1024
+// columns of the 32 x 32 lattice; its widest level has 152 busy columns).
+// Thread `tid` of a block of T threads runs slots tid, tid + T, ... (RMAX of
+// them, unrolled as "rounds").
+//
+// Per level a thread only does the items of its busy slots: six neighbour
+// words, the random word, the decision, and on a flip one store of the
+// column word.  Everything else
+// happens every fourth level, at the same level for every thread (no
+// divergence): at a level l divisible by 4, before its items, a slot whose
+// column has ended moves on to its next column (descriptor from shared
+// memory); after the items, the word block of the slot that starts in levels
+// [l + 8, l + 12) is requested.
+//
+// Fields by gathering.  A visit computes the spatial field from the
+// neighbours' column bits, f_space = (h_q - sum_j J_qj) + sum_j 2 J_qj b_j(t),
+// with plain shared-memory loads of their column words, instead of keeping
+// every field and pushing the changes of a flip into the neighbours' fields:
+// on sm_103a a shared-memory reduction instruction costs about 40 cycles of
+// a warp's time (measured), six of them per visit, while six plain loads
+// issue back to back.  The values are the same by definition (f = h + sum J
+// s), so the chain is unchanged; the fields handed back through the ABI are
+// recomputed from the spins when the launch ends.  Shared memory then holds
+// only the column words of the replica (bit t of column q = spin (q, t) is
+// +1): the owner of a busy column keeps it in a register and stores it when
+// a spin flips; a neighbour reading the word at the same level reads a slice
+// other than the one being flipped (neighbours lie at different levels), so
+// it sees the value of the sequential sweep: updated for a lower-indexed
+// neighbour (visited at an earlier level), not yet for a higher-indexed one.
+// The Trotter part of the field, Jtau (s_{t-1} + s_{t+1}), comes from the
+// owner's register bits.
+//
+// Random words go through a ring of four 4-word blocks per slot in shared
+// memory, word w of ring entry j of slot sl at (4 j + w) NSP + sl (a lane's
+// word reads are conflict-free).  MT19937 words come from the pre-generated
+// word buffer by 4-byte cp.async copies (not waited for by the level
+// barrier), one commit group every fourth level; at a level divisible by 4
+// the thread waits until at most one group is pending, i.e. for the copies
+// requested 8 levels earlier.  Philox blocks are computed by the slot, the
+// ten rounds spread over four levels (3, 3, 3, 1), and stored after the
+// fourth.  A block is written after the last item that reads the ring entry
+// it replaces.
+//
+// Fused PT: as in the lean kernel (publish the energies, bounded grid
+// barrier, every block runs the same PT pass on its own copy of the labels).
+#pragma once
+#include <climits>
+
+#include "fast_impl.cuh"
+
+namespace isg {
+namespace packed_detail {
+
+using fast_detail::grid_sync;
+
+constexpr int kMaxDeg = 6;
+// descriptor words: [0] lev0 | site << 16, [1] jtau, [2..7] one per spatial
+// neighbour: pos << 16 | (uint8) J << 8 | (uint8) dlev, dlev = lev0(q) -
+// lev0(neighbour) clamped to [-128, 127] (missing neighbours: the column
+// itself with J = 0)
+constexpr int kDescWords = 8;
+
+struct PackedLayout {
+    uint32_t bar, desc, pos, soff, scol, cq, colw, stage, thr, eacc, slot, temp, total;
+};
+
+// Shared-memory layout; the table part (desc .. scol) is one bulk copy of the
+// handle's packed table buffer, whose parts are padded identically.
+__host__ __device__ inline PackedLayout packed_layout(const SweepArgs& a, int threads)
+{
+    PackedLayout L{};
+    uint32_t o = 0;
+    L.bar = o;   o += 16;
+    L.desc = o;  o += 4u * kDescWords * uint32_t(a.S);
+    L.pos = o;   o += r16(4u * uint32_t(a.S));
+    L.soff = o;  o += r16(4u * uint32_t(a.nslots + 1));
+    L.scol = o;  o += r16(4u * uint32_t(a.S));
+    L.cq = o;    o += r16(4u * uint32_t(a.S));
+    L.colw = o;  o += r16(4u * uint32_t(a.S));
+    L.stage = o;  // the word ring: 4 entries x 4 words x slots rounded up to whole rounds
+    o += 64u * uint32_t((a.nslots + threads - 1) / threads) * uint32_t(threads);
+    L.thr = o;   o += r16(4u * uint32_t(a.K));
+    L.eacc = o;  o += 16;
+    if (a.swap_every > 0) {
+        L.slot = o; o += r16(4u * uint32_t(a.R));
+        L.temp = o; o += r16(4u * uint32_t(a.R));
+    }
+    L.total = o;
+    return L;
+}
+
+// bytes of the table part (desc, pos, slot offsets, slot columns, the
+// constant c_p = h_q - sum_j J_qj of the column at each position)
+__host__ __device__ inline uint32_t packed_table_bytes(int S, int nslots)
+{
+    return 4u * kDescWords * uint32_t(S) + r16(4u * uint32_t(S)) + r16(4u * uint32_t(nslots + 1)) +
+           2u * r16(4u * uint32_t(S));
+}
+
+// 16-byte asynchronous copy without its own commit group.
+__device__ __forceinline__ void cp_async16_nc(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void philox_round(uint4& c, uint32_t& k0, uint32_t& k1)
+{
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+}
+
+template <int RNG, int RMAX>
+__device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, const int nblk)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_flag;
+    const int T = blockDim.x, tid = threadIdx.x;
+    const PackedLayout L = packed_layout(a, T);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+    const int S = a.S, M = a.M, N = a.N, K = a.K, R = a.R;
+    const int r = blk;  // one replica per block
+    const uint32_t* desc = reinterpret_cast<const uint32_t*>(smem + L.desc);
+    const int* pos = reinterpret_cast<const int*>(smem + L.pos);
+    const int* soff = reinterpret_cast<const int*>(smem + L.soff);
+    const int* scol = reinterpret_cast<const int*>(smem + L.scol);
+    const int* cqt = reinterpret_cast<const int*>(smem + L.cq);
+    uint32_t* colw = reinterpret_cast<uint32_t*>(smem + L.colw);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem + L.stage);
+    uint32_t* thr_s = reinterpret_cast<uint32_t*>(smem + L.thr);
+    int* eacc = reinterpret_cast<int*>(smem + L.eacc);
+    int* slot_s = reinterpret_cast<int*>(smem + L.slot);
+    int* temp_s = reinterpret_cast<int*>(smem + L.temp);
+    const bool fused = a.swap_every > 0;
+    const bool f16 = a.field_bits == 16;
+
+    // ---- tables (one bulk copy), labels
+    if (tid == 0)
+        mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(bar, a.pk_bytes);
+        bulk_g2s(smem + L.desc, a.pk, a.pk_bytes, bar);
+        eacc[0] = 0;
+    }
+    if (fused)
+        for (int i = tid; i < R; i += T) {
+            slot_s[i] = a.slot_of_temp[i];
+            temp_s[i] = a.temp_of_slot[i];
+        }
+    if (tid == 0)
+        s_flag = mbar_wait(bar, 0, kWaitPolls) ? 1 : 0;
+    __syncthreads();
+    if (!s_flag) {
+        if (tid == 0)
+            set_err(a.err, kErrTimeout);
+        return;
+    }
+    mbar_wait(bar, 0, kWaitPolls);
+
+    // ---- column bits from the spins (the fields follow from them)
+    const int8_t* spg = a.spins + size_t(r) * N;
+    for (int p = tid; p < S; p += T) {
+        const int q = int(desc[p * kDescWords] >> 16);
+        uint32_t b = 0u;
+        for (int t = 0; t < M; ++t)
+            b |= (spg[size_t(t) * S + q] > 0 ? 1u : 0u) << t;
+        colw[p] = b;
+    }
+    {
+        const int temp = fused ? temp_s[r] : a.temp_of_slot[r];
+        for (int k = tid; k < K; k += T)
+            thr_s[k] = a.thr[size_t(temp) * K + k];
+    }
+    __syncthreads();
+
+    const uint32_t rep = (M == 32) ? 1u : (M == 16 ? 0x00010001u : 0x01010101u);
+    const uint32_t cmask = (M == 32) ? 0xFFFFFFFFu : ((1u << M) - 1u);
+    const int nrb = M >> 2;  // word blocks per column
+    const unsigned FULL = 0xFFFFFFFFu;
+    const bool shfl_thr = K <= 32;
+    uint32_t thr_lane = (shfl_thr && (tid & 31) < K) ? thr_s[tid & 31] : 0u;
+    const unsigned long long sweep0 = a.counters[0];
+    const unsigned long long pass0 = a.counters[1];
+    const int NSP = ((a.nslots + T - 1) / T) * T;  // slots rounded up to whole rounds
+    const uint32_t colw_s = smem_u32(colw), stage_s = smem_u32(stage);
+    constexpr int kNone = INT_MAX / 2;
+    int npass = 0;
+    int dE = 0;
+
+    // per slot (round c): the current column (busy, or the next to become
+    // busy) and its successor in the slot's list
+    int lv[RMAX] = {}, kk[RMAX] = {}, ke[RMAX] = {}, pp[RMAX] = {}, qq[RMAX] = {}, jt2[RMAX] = {},
+        rs[RMAX] = {};
+    int pn[RMAX] = {}, qn[RMAX] = {}, ln[RMAX] = {};
+    int cq[RMAX];
+    uint32_t bits[RMAX], nw[RMAX][kMaxDeg];  // nw: shared address of each neighbour's column word
+    int nj[RMAX][kMaxDeg];                    // 2 J of each neighbour
+    int rq[RMAX];  // 4 * (ring entry of the column's block 0)
+    // Philox block in progress: counter, keys, ring entry, whether any
+    uint4 pc[RMAX];
+    uint32_t pk0[RMAX], pk1[RMAX];
+    int pring[RMAX];
+    bool pgo[RMAX];
+
+    // take up column p at level s (a multiple of 4, before the level's items)
+    auto load_col = [&](int c, int p, int s) {
+        const uint4 d0 = *reinterpret_cast<const uint4*>(desc + p * kDescWords);
+        const uint4 d1 = *reinterpret_cast<const uint4*>(desc + p * kDescWords + 4);
+        lv[c] = int(d0.x & 0xFFFFu);
+        qq[c] = int(d0.x >> 16);
+        jt2[c] = 2 * int(d0.y);
+        const uint32_t e6[kMaxDeg] = {d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+        (void)s;
+#pragma unroll
+        for (int e = 0; e < kMaxDeg; ++e) {
+            nw[c][e] = colw_s + 4u * (e6[e] >> 16);
+            nj[c][e] = 2 * int(int8_t((e6[e] >> 8) & 0xFFu));
+        }
+        pp[c] = p;
+        cq[c] = cqt[p];
+        bits[c] = colw[p] * rep;
+        rs[c] = (kk[c] * nrb) & 3;
+        rq[c] = 4 * rs[c];
+    };
+    auto set_next = [&](int c) {
+        pn[c] = kk[c] + 1 < ke[c] ? scol[kk[c] + 1] : -1;
+        const uint32_t d0 = pn[c] >= 0 ? desc[pn[c] * kDescWords] : 0u;
+        qn[c] = int(d0 >> 16);
+        ln[c] = pn[c] >= 0 ? int(d0 & 0xFFFFu) : kNone;
+    };
+    // slots restart at their first column (every column word is current:
+    // owners store theirs at each flip; after a sweep's last level barrier
+    // every thread sees them)
+    auto restart = [&](bool) {
+#pragma unroll
+        for (int c = 0; c < RMAX; ++c) {
+            const int sl = tid + c * T;
+            lv[c] = kNone;
+            kk[c] = ke[c] = 0;
+            pp[c] = qq[c] = jt2[c] = rs[c] = 0;
+            pn[c] = -1;
+            qn[c] = 0;
+            ln[c] = kNone;
+            cq[c] = 0;
+            bits[c] = 0u;
+            rq[c] = 0;
+#pragma unroll
+            for (int e = 0; e < kMaxDeg; ++e) {
+                nw[c][e] = colw_s;
+                nj[c][e] = 0;
+            }
+            pgo[c] = false;
+            pring[c] = 0;
+            if (sl < a.nslots) {
+                kk[c] = soff[sl];
+                ke[c] = soff[sl + 1];
+                if (kk[c] < ke[c]) {
+                    load_col(c, scol[kk[c]], 0);  // at a sweep's start no window has closed
+                    set_next(c);
+                }
+            }
+        }
+    };
+    // The block of round c's stream that starts in levels [l + 8, l + 12):
+    // of the current column, else of the next one (at most one of them).
+    auto candidate = [&](int c, int l, int& col, int& b, int& ring, int& site) -> bool {
+        const int b1 = (l + 8 - lv[c] + 3) >> 2;
+        if (lv[c] < kNone && b1 >= 0 && b1 < nrb) {
+            col = pp[c];
+            b = b1;
+            ring = (rs[c] + b1) & 3;
+            site = qq[c];
+            return true;
+        }
+        const int b2 = (l + 8 - ln[c] + 3) >> 2;
+        if (ln[c] < kNone && b2 >= 0 && b2 < nrb) {
+            col = pn[c];
+            b = b2;
+            ring = (rs[c] + nrb + b2) & 3;
+            site = qn[c];
+            return true;
+        }
+        return false;
+    };
+    // MT19937: 4-byte copies of the candidate block of every round into its ring entry
+    auto request_words = [&](const uint32_t* wsw, int l) {
+#pragma unroll
+        for (int c = 0; c < RMAX; ++c) {
+            int col = 0, b = 0, ring = 0, site = 0;
+            if (candidate(c, l, col, b, ring, site)) {
+                const uint32_t* src = wsw + (size_t(r) * S + col) * a.Mp + 4 * b;
+                const uint32_t dst = stage_s + 4u * uint32_t((4 * ring) * NSP + tid + c * T);
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * uint32_t(w * NSP)),
+                                 "l"(src + w)
+                                 : "memory");
+            }
+        }
+    };
+    // Philox: start (and with `full`, finish and store) the candidate blocks
+    auto philox_start = [&](uint32_t sid, int l, bool full) {
+#pragma unroll
+        for (int c = 0; c < RMAX; ++c) {
+            int col = 0, b = 0, ring = 0, site = 0;
+            pgo[c] = candidate(c, l, col, b, ring, site);
+            if (pgo[c]) {
+                pc[c] = make_uint4(uint32_t(b * S + site), sid, a.inst, 0u);
+                pk0[c] = a.seed;
+                pk1[c] = uint32_t(r);
+                pring[c] = ring;
+                for (int i = 0; i < (full ? 10 : 3); ++i)
+                    philox_round(pc[c], pk0[c], pk1[c]);
+                if (full) {
+                    uint32_t* st = stage + (4 * ring) * NSP + tid + c * T;
+                    st[0] = pc[c].x;
+                    st[NSP] = pc[c].y;
+                    st[2 * NSP] = pc[c].z;
+                    st[3 * NSP] = pc[c].w;
+                    pgo[c] = false;
+                }
+            }
+        }
+    };
+
+    restart(false);
+    for (int sw = 0; sw < a.nsweeps; ++sw) {
+        const uint32_t sid = uint32_t(sweep0 + sw);
+        const uint32_t* wsw = (RNG == 0) ? a.wbuf + size_t(sw) * a.wbuf_sweep_stride : nullptr;
+        // the blocks that start in levels [0, 8)
+        if (RNG == 0) {
+            if (sw == 0) {  // later sweeps: requested at the end of the previous one
+                request_words(wsw, -8);
+                request_words(wsw, -4);
+            }
+            cp_async_commit();
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        } else {
+            philox_start(sid, -8, true);
+            philox_start(sid, -4, true);
+        }
+        __syncthreads();
+
+        for (int l = 0; l < a.D; ++l) {
+            const int phase = l & 3;
+            if (phase == 0) {
+                if (RNG == 0)
+                    cp_async_wait_group<1>();  // the copies requested 8 levels ago have landed
+                // a slot takes up its next column at the last multiple of 4 before
+                // the column's start (the previous one has ended by then: the host
+                // packs a slot's next column at or after the first multiple of 4
+                // past the previous window)
+#pragma unroll
+                for (int c = 0; c < RMAX; ++c) {
+                    if (pn[c] >= 0 && (ln[c] & ~3) <= l) {
+                        ++kk[c];
+                        load_col(c, pn[c], l);
+                        set_next(c);
+                    }
+                }
+            }
+            // the items of the level: the rounds are independent (a neighbour of a
+            // busy spin is at another level), so all loads go first, then the
+            // fields and decisions, then the stores of the flipped columns
+            int tt[RMAX];
+            uint32_t uu[RMAX], wn[RMAX][kMaxDeg];
+            bool any = true;
+            if (RMAX == 1)  // one round: a warp without a busy slot skips the level's items
+                any = __any_sync(FULL, unsigned(l - lv[0]) < unsigned(M));
+            if (any) {
+#pragma unroll
+            for (int c = 0; c < RMAX; ++c) {
+                const int t0 = l - lv[c];
+                const bool act = unsigned(t0) < unsigned(M);
+                tt[c] = act ? t0 : -1;
+                const int t = act ? t0 : 0;
+#pragma unroll
+                for (int e = 0; e < kMaxDeg; ++e)
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(wn[c][e]) : "r"(nw[c][e]) : "memory");
+                // ring word (4 entry + w) for slice t: entry (rs + t / 4) & 3, word t & 3
+                uu[c] = stage[((rq[c] + t) & 15) * NSP + tid + c * T];
+            }
+#pragma unroll
+            for (int c = 0; c < RMAX; ++c) {
+                const bool act = tt[c] >= 0;
+                const int t = act ? tt[c] : 0;
+                int f = cq[c];
+#pragma unroll
+                for (int e = 0; e < kMaxDeg; ++e)
+                    f += int((wn[c][e] >> t) & 1u) * nj[c][e];
+                // bits 0, 1, 2 = s_{t-1}, s_t, s_{t+1} (ring wrap included)
+                const uint32_t w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
+                const int h = f + jt2[c] * (__popc(w3 & 5u) - 1);  // the local field
+                const int k = (w3 & 2u) ? h : -h;                  // s_t f
+                // T(k) by lane k for 0 < k < K, else T(0) = 0: flip iff k <= 0 or u < T(k)
+                uint32_t th;
+                if (shfl_thr)
+                    th = __shfl_sync(FULL, thr_lane, unsigned(k - 1) < unsigned(K - 1) ? k : 0);
+                else
+                    th = unsigned(k - 1) < unsigned(K - 1) ? thr_s[k] : 0u;
+                const bool take = act && (k <= 0 || uu[c] < th);
+                bits[c] ^= take ? (rep << t) : 0u;
+                dE += take ? 2 * k : 0;
+                asm volatile("{ .reg .pred p; setp.ne.b32 p, %2, 0; @p st.shared.u32 [%0], %1; }" ::"r"(
+                                 colw_s + 4u * uint32_t(pp[c])),
+                             "r"(bits[c] & cmask), "r"(take ? 1u : 0u)
+                             : "memory");
+            }
+            }  // any
+            // the word stream
+            if (RNG == 0) {
+                if (phase == 0) {
+                    request_words(wsw, l);
+                    cp_async_commit();
+                }
+            } else {
+                if (phase == 0) {
+                    philox_start(sid, l, false);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < RMAX; ++c) {
+                        if (pgo[c]) {
+#pragma unroll
+                            for (int i = 0; i < 3; ++i)
+                                if (phase < 3 || i == 0)
+                                    philox_round(pc[c], pk0[c], pk1[c]);
+                            if (phase == 3) {
+                                uint32_t* st = stage + (4 * pring[c]) * NSP + tid + c * T;
+                                st[0] = pc[c].x;
+                                st[NSP] = pc[c].y;
+                                st[2 * NSP] = pc[c].z;
+                                st[3 * NSP] = pc[c].w;
+                                pgo[c] = false;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // columns of the sweep's end stored, slots back at their first column;
+        // MT19937: the next sweep's first blocks requested, in flight during PT
+        restart(true);
+        if (RNG == 0 && sw + 1 < a.nsweeps) {
+            const uint32_t* wn = wsw + a.wbuf_sweep_stride;
+            request_words(wn, -8);
+            request_words(wn, -4);
+        }
+
+        if (fused && (sw + 1) % a.swap_every == 0) {
+            if (dE != 0)
+                atomicAdd(&eacc[0], dE);
+            dE = 0;
+            __syncthreads();
+            int* Ep = a.E_pub + size_t(npass & 1) * R;
+            if (tid == 0) {
+                const int e = a.E[r] + eacc[0];
+                a.E[r] = e;
+                Ep[r] = e;
+                eacc[0] = 0;
+            }
+            if (nblk == 1)
+                __syncthreads();
+            else if (!grid_sync(a.gridbar, unsigned(npass + 1) * unsigned(nblk), a.err, &s_flag))
+                return;
+            if (tid < 32) {
+                const unsigned long long p = pass0 + npass;
+                const int par = int(p & 1ull);
+                const int npairs = par ? (R - 1) / 2 : R / 2;
+                for (int j = tid; j < npairs; j += 32) {
+                    const int k = 2 * j + par;
+                    const int sa = slot_s[k], sb = slot_s[k + 1];
+                    const long long d = (long long)__ldcg(Ep + sa) - (long long)__ldcg(Ep + sb);
+                    uint32_t u;
+                    if (RNG == 0)
+                        u = a.swbuf[size_t(npass) * a.maxpairs + j];
+                    else
+                        u = pick4(philox4x32_10(make_uint4(uint32_t(j) >> 2, uint32_t(p), a.inst, 1u), a.seed,
+                                                0xFFFFFFFFu),
+                                  j & 3);
+                    const bool take = (d <= 0) || (d < a.swlen[k] && u < a.swthr[a.swoff[k] + d]);
+                    if (take) {
+                        slot_s[k] = sb;
+                        slot_s[k + 1] = sa;
+                        temp_s[sa] = k + 1;
+                        temp_s[sb] = k;
+                        if (blk == 0)
+                            a.swap_acc[k] += 1ull;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int k = tid; k < K; k += T)
+                thr_s[k] = a.thr[size_t(temp_s[r]) * K + k];
+            __syncthreads();
+            thr_lane = (shfl_thr && (tid & 31) < K) ? thr_s[tid & 31] : 0u;
+            ++npass;
+        }
+    }
+    if (RNG == 0)
+        asm volatile("cp.async.wait_all;" ::: "memory");
+
+    // ---- energies and write-back (coalesced over the spin index)
+    if (dE != 0)
+        atomicAdd(&eacc[0], dE);
+    __syncthreads();
+    if (tid == 0)
+        a.E[r] += eacc[0];
+    int8_t* spo = a.spins + size_t(r) * N;
+    for (int i = tid; i < N; i += T) {
+        const int t = i / S, q = i - t * S, p = pos[q];
+        const int tm = (t == 0) ? M - 1 : t - 1, tp = (t == M - 1) ? 0 : t + 1;
+        const uint32_t cb = colw[p];
+        const uint32_t* d = desc + p * kDescWords;
+        int f = cqt[p] + int(d[1]) * (2 * int(((cb >> tm) & 1u) + ((cb >> tp) & 1u)) - 2);
+        for (int e = 0; e < kMaxDeg; ++e)
+            f += 2 * int(int8_t((d[2 + e] >> 8) & 0xFFu)) * int((colw[d[2 + e] >> 16] >> t) & 1u);
+        spo[i] = ((cb >> t) & 1u) ? int8_t(1) : int8_t(-1);
+        if (f16)
+            static_cast<int16_t*>(a.fields)[size_t(r) * N + i] = int16_t(f);
+        else
+            static_cast<int*>(a.fields)[size_t(r) * N + i] = f;
+    }
+    if (fused && blk == 0)
+        for (int i = tid; i < R; i += T) {
+            a.slot_of_temp[i] = slot_s[i];
+            a.temp_of_slot_out[i] = temp_s[i];
+        }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done_blocks, 1u);
+        if (prev == unsigned(nblk) - 1u) {
+            a.counters[0] += (unsigned long long)a.nsweeps;
+            a.counters[1] += (unsigned long long)npass;
+            *a.done_blocks = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// Register budget: about 30 registers per slot round; blocks of up to 256
+// threads (one round) or 128 (more rounds).
+template <int RNG, int RMAX>
+__global__ void __launch_bounds__(RMAX == 1 ? 256 : 128, 1) packed_kernel(const SweepArgs a)
+{
+    packed_body<RNG, RMAX>(a, int(blockIdx.x), int(gridDim.x));
+}
+
+template <int RNG>
+void* pick_packed(int rmax)
+{
+    switch (rmax) {
+    case 1: return reinterpret_cast<void*>(&packed_kernel<RNG, 1>);
+    case 2: return reinterpret_cast<void*>(&packed_kernel<RNG, 2>);
+    case 3: return reinterpret_cast<void*>(&packed_kernel<RNG, 3>);
+    case 5: return reinterpret_cast<void*>(&packed_kernel<RNG, 5>);
+    case 8: return reinterpret_cast<void*>(&packed_kernel<RNG, 8>);
+    default: return nullptr;
+    }
+}
+
+}  // namespace packed_detail
+
+// slot rounds per thread with an instantiation, and the kernels (packed_mt.cu,
+// packed_philox.cu)
+constexpr int kPackedRounds[5] = {1, 2, 3, 5, 8};
+void* packed_kernel_mt(int rmax);
+void* packed_kernel_philox(int rmax);
+inline void* packed_kernel_ptr(int rng, int rmax)
+{
+    return rng == 0 ? packed_kernel_mt(rmax) : packed_kernel_philox(rmax);
+}
+size_t packed_smem_bytes(const SweepArgs& a, int threads);
+
+}  // namespace isg

@@ -1,0 +1,6 @@
+// Philox4x32-10 instantiations of the packed sweep kernel.
+#include "packed_impl.cuh"
+
+namespace isg {
+void* packed_kernel_philox(int rmax) { return packed_detail::pick_packed<1>(rmax); }
+}  // namespace isg

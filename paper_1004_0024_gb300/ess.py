@@ -228,9 +228,10 @@ def equilibrated(x: np.ndarray) -> bool:
     return abs(m1 - m2) < 3.0 * max(np.hypot(s1, s2), 1e-300)
 
 
-def fast_mixing(res: dict, names, max_tau_frac: float = 1.0 / 500) -> np.ndarray:
+def fast_mixing(res: dict, names, max_tau_frac: float = 1.0 / (100 * N_BATCHES)) -> np.ndarray:
     """Temperatures where E and m of every named chain pass the split-half
-    check with tau_int below max_tau_frac of the run."""
+    check with tau_int below max_tau_frac of the run (by default a hundredth
+    of one batch of the histogram standard errors)."""
     R = res["plain"]["E"].shape[1]
     n = res["plain"]["E"].shape[0]
     ok = np.ones(R, dtype=bool)
@@ -258,7 +259,7 @@ def _hist_stats(res, a, b, temps):
 def summarize(res: dict, betas) -> dict:
     """JSON-ready summary of ``compare``.  ESS/s ratios (learned / plain) are
     medians over the fast-mixing temperatures (split-half check passed, tau
-    below 1/500 of the run, for every chain); the histogram comparison is
+    below a hundredth of a batch, for every chain); the histogram comparison is
     made there too, for learned vs plain and, as calibration, for the second
     plain chain vs plain.  The coldest quarter, where the plain sweep barely
     moves on this time scale, is reported by the energies reached."""

@@ -306,6 +306,7 @@ LAUNCH_PERSISTENT = 1
 LAUNCH_GENERIC = 2
 LAUNCH_NO_LEAN = 4
 LAUNCH_TRACK = 8
+LAUNCH_NO_PACKED = 16
 
 
 def ising_set_launch(h, replicas_per_block=0, threads_per_block=0, launch_flags=LAUNCH_PERSISTENT):

@@ -11,7 +11,8 @@ control.  The test checks, and prints, that
   untrained one's (the gain from training);
 * on the fast-mixing temperatures the learned chain's energy and
   magnetisation histograms agree with the plain chain's within 3 standard
-  errors as often as two chains of one law do: batch-mean standard errors,
+  errors as often as two chains of one law do: batch-mean standard errors
+  (20 batches of 800 steps, tau_int below a hundredth of a batch),
   and a count of |z| > 3 bins no larger than the 0.999 quantile of its
   binomial law; a second plain chain continuing the same state on its own
   Philox seed passes the same bound and is not a replay of the first
@@ -55,7 +56,7 @@ def test_trained_proposal_gain(mods):
     raw.close()
     sim.close()
 
-    out = ess.study(ising, W, burn=20000, n_steps=4000, epochs=6)
+    out = ess.study(ising, W, burn=20000, n_steps=16000, epochs=6)
     out["untrained_accept_rate"] = untrained
     print(json.dumps(out, indent=1))
     assert out["accept_rate"] > 0.5 and out["accept_rate"] > 20 * untrained

@@ -134,13 +134,13 @@ def test_launch_shapes_give_identical_results(ising, G, T, flags):
 
 @pytest.mark.parametrize("rng", ["mt19937", "philox"])
 def test_config1_paths_agree(ising, rng):
-    """cfg1 through every kernel (track, lean, register-resident, generic),
-    persistent with fused PT (the bench path) or per-sweep launches:
-    identical to the oracle after 12 sweeps."""
+    """cfg1 through every kernel (track, packed, lean, register-resident,
+    generic), persistent with fused PT (the bench path) or per-sweep
+    launches: identical to the oracle after 12 sweeps."""
     c = W.config1()
     ref = oracle.Sim(c["graph"], c["betas"], seed=c["seed"], rng=rng)
     ref.run(12, 1)
-    for flags, kernel in ((9, 3), (8, 3), (1, 2), (0, 2), (5, 1), (4, 1), (2, 0)):
+    for flags, kernel in ((9, 3), (8, 3), (1, 4), (0, 4), (17, 2), (16, 2), (5, 1), (4, 1), (2, 0)):
         dev = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=16)
         dev.set_launch(0, 0, flags)
         info = dev.info()
@@ -372,3 +372,47 @@ def test_reused_word_buffer_gives_the_same_chain(ising):
     for key in ("spins", "fields", "energy", "temp_of_slot"):
         assert np.array_equal(first[key], second[key]), key
     ising.ising_release_cached_memory()
+
+
+@pytest.mark.parametrize("L,M,R,fb", [(8, 16, 32, 32), (6, 8, 9, 16), (5, 32, 5, 16), (12, 16, 40, 32),
+                                      (9, 8, 3, 32)])
+@pytest.mark.parametrize("T", [0, 32, 64, 128, 256])
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_packed_kernel_matches_oracle(ising, L, M, R, fb, T, rng):
+    """The packed (slot-scheduled) kernel on several lattices, slice counts,
+    ladders, field widths and block sizes (one, two or four warps; 0 =
+    automatic), persistent with PT fused and in per-sweep launches, and with
+    groups of sweeps between PT passes: bit-exact against the oracle."""
+    g = W.layered_graph(L, M, L * 7 + M)
+    betas = W.geometric_betas(R, 0.15, 2.8)
+    for flags in (1, 0):
+        ref = oracle.Sim(g, betas, seed=31 + L, rng=rng)
+        dev = ising.Ising(g, betas, seed=31 + L, rng=rng, field_bits=fb)
+        dev.set_launch(0, T, flags)
+        info = dev.info()
+        assert info["fast_kernel"] == 4, info
+        if T:
+            assert info["threads_per_block"] == T
+        for n, every in ((9, 1), (7, 3), (4, 0), (2, 1)):
+            dev.run(n, every)
+            ref.run(n, every)
+            assert_same(dev, ref, f"T {T} flags {flags} after ({n}, {every})")
+        dev.close()
+
+
+@pytest.mark.parametrize("rng", ["mt19937", "philox"])
+def test_packed_and_lean_kernels_agree_on_config1(ising, rng):
+    """The bench workload through the packed kernel (one and two warps per
+    replica) and the lean kernel: the same chain over 30 sweeps with PT."""
+    c = W.config1()
+    states = []
+    for T, flags in ((32, 1), (64, 1), (0, 17)):
+        dev = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=16)
+        dev.set_launch(0, T, flags)
+        assert dev.info()["fast_kernel"] == (2 if flags & 16 else 4)
+        dev.run(30, 1)
+        states.append(dev.read_state())
+        dev.close()
+    for st in states[1:]:
+        for key in ("spins", "fields", "energy", "temp_of_slot"):
+            assert np.array_equal(st[key], states[0][key]), key
