@@ -87,6 +87,8 @@ cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int thread
     void* fn = pick(field_bits, a.rng, cmax, variant, false, a.split != 0);
     if (!fn)
         return cudaErrorInvalidValue;
+    if (variant == 5)  // the packed kernel's blocks: its sweep threads and the generator warps
+        threads = a.sweep_threads + (a.rng == 0 ? 32 * a.gen : 0);
     SweepArgs copy = a;
     void* args[] = {&copy};
     if (cooperative)

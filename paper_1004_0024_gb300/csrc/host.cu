@@ -711,6 +711,11 @@ SweepArgs base_args(ising_s* g);
 
 // The register-resident kernel keeps up to 8 columns per thread; it needs
 // M <= 32, the slice tables in shared memory and spatial degree <= 255.
+// The packed kernel generates its MT19937 sweep words itself (an extra warp
+// per block, two-sweep word buffer); the separate generator then only makes
+// the swap stream's words.
+bool packed_gen(const ising_s* g) { return g->use_packed && g->rng == ISING_RNG_MT19937; }
+
 int kernel_variant(const ising_s* g)
 {
     if (g->use_packed)
@@ -730,14 +735,15 @@ bool packed_eligible(const ising_s* g)
            (g->T_req == 0 || g->T_req == 32 || g->T_req == 64 || g->T_req == 128 || g->T_req == 256);
 }
 
-// Configure the packed kernel: threads per block (one to eight warps;
-// automatic: the fewest whole warps that give every slot its own thread, up
-// to eight), slot rounds per thread, shared memory and the persistent check.
+// Configure the packed kernel: sweep threads per block (one to eight warps;
+// automatic: the fewest whole warps that give every slot its own thread, or
+// four warps of several rounds beyond 256 slots), slot rounds per thread,
+// two generator warps with MT19937, shared memory and the persistent check.
 bool choose_packed(ising_s* g)
 {
     if (!packed_eligible(g))
         return false;
-    const int T = g->T_req > 0 ? g->T_req : std::min(256, ((g->nslots + 31) / 32) * 32);
+    const int T = g->T_req > 0 ? g->T_req : (g->nslots <= 256 ? ((g->nslots + 31) / 32) * 32 : 128);
     const int rounds = (g->nslots + T - 1) / T;
     if (T > 128 && rounds > 1)
         return false;  // the instantiations with more than one round allow 128 threads
@@ -757,6 +763,7 @@ bool choose_packed(ising_s* g)
     }
     SweepArgs a = base_args(g);
     a.G = 1;
+    a.gen = g->rng == ISING_RNG_MT19937 ? kPackedGenWarps : 0;
     const size_t plain = packed_smem_bytes(a, T);
     a.swap_every = 1;
     const size_t fused = packed_smem_bytes(a, T);
@@ -776,7 +783,7 @@ bool choose_packed(ising_s* g)
     if (!g_coop || !g->allow_persistent || fused > lim || g->R > 16384)
         return true;
     int per_sm = 0;
-    if (fast_max_blocks_per_sm(g->field_bits, rmax, g->rng, T, fused, &per_sm, 5) != cudaSuccess)
+    if (fast_max_blocks_per_sm(g->field_bits, rmax, g->rng, T + 32 * a.gen, fused, &per_sm, 5) != cudaSuccess)
         return true;
     g->persistent_ok = (long long)per_sm * g_num_sms >= g->blocks;
     return true;
@@ -941,6 +948,10 @@ SweepArgs base_args(ising_s* g)
     a.pk_bytes = g->pk_bytes;
     a.nslots = g->nslots;
     a.field_bits = g->field_bits;
+    a.gen = packed_gen(g) ? kPackedGenWarps : 0;
+    a.mtring = g->d_mtring;
+    a.mtpos = g->d_mtpos;
+    a.sweep_threads = g->T;
     return a;
 }
 
@@ -1041,6 +1052,7 @@ std::vector<Op> plan(ising_s* g, long long n, int swap_every, long long cap)
 {
     std::vector<Op> ops;
     const bool mt = g->rng == ISING_RNG_MT19937;
+    const bool own = packed_gen(g);  // sweep words generated by the sweep kernel
     long long done = 0;
     if (n <= 0 && swap_every == -1) {
         // a lone PT pass
@@ -1056,12 +1068,12 @@ std::vector<Op> plan(ising_s* g, long long n, int swap_every, long long cap)
         while (n - done >= swap_every) {
             const long long m = std::min(per, ((n - done) / swap_every) * swap_every);
             if (mt)
-                ops.push_back({Op::GEN, int(m), int(m / swap_every), 0});
+                ops.push_back({Op::GEN, own ? 0 : int(m), int(m / swap_every), 0});
             ops.push_back({Op::FUSED, int(m), swap_every, 0});
             done += m;
         }
         if (done < n) {
-            if (mt)
+            if (mt && !own)
                 ops.push_back({Op::GEN, int(n - done), 0, 0});
             ops.push_back({Op::SWEEP, int(n - done), 0, 0});
         }
@@ -1082,8 +1094,8 @@ std::vector<Op> plan(ising_s* g, long long n, int swap_every, long long cap)
                 ++cp;
             }
         }
-        if (mt)
-            ops.push_back({Op::GEN, int(cs), cp, 0});
+        if (mt && (!own || cp > 0))
+            ops.push_back({Op::GEN, own ? 0 : int(cs), cp, 0});
         ops.insert(ops.end(), chunk.begin(), chunk.end());
     }
     return ops;
@@ -1093,6 +1105,9 @@ long long words_cap(ising_s* g, long long n)
 {
     if (g->rng != ISING_RNG_MT19937)
         return std::max<long long>(n, 1);
+    if (packed_gen(g))  // only the swap stream's words are made ahead: up to 256 MB of them
+        return std::max<long long>(
+            1, std::min<long long>(std::max<long long>(n, 1), (256LL << 20) / (4LL * std::max(g->maxpairs, 1))));
     const long long per_sweep = (long long)g->R * g->S * g->Mp * 4;
     return std::max<long long>(1, std::min<long long>(std::max<long long>(n, 1), g->word_budget / per_sweep));
 }
@@ -1101,6 +1116,8 @@ int32_t ensure_buffers(ising_s* g, long long cap_sweeps, long long cap_passes)
 {
     if (g->rng != ISING_RNG_MT19937)
         return ISING_OK;
+    if (packed_gen(g))
+        cap_sweeps = 2;  // the sweep kernel's two-sweep word buffer
     if (cap_sweeps > g->wbuf_cap) {
         big_free(g->d_wbuf);
         // fully written by the generator before any sweep reads it: no zero fill
@@ -1156,7 +1173,7 @@ SweepArgs sweep_args(ising_s* g, const Op& op)
         a.swap_every = op.passes;
         a.wbuf = g->d_wbuf;
     } else {
-        a.wbuf = g->d_wbuf ? g->d_wbuf + size_t(op.offset) * a.wbuf_sweep_stride : nullptr;
+        a.wbuf = (g->d_wbuf && !a.gen) ? g->d_wbuf + size_t(op.offset) * a.wbuf_sweep_stride : g->d_wbuf;
     }
     return a;
 }

@@ -101,6 +101,14 @@ struct SweepArgs {
     uint32_t pk_bytes;
     int nslots;
     int field_bits;
+    // packed kernel, MT19937: with gen > 0, gen extra warps of each block
+    // advance the replica's stream (ring [R + 1][kMtRing], positions) and
+    // write the next sweep's words into a two-sweep buffer (wbuf, parity of
+    // the sweep) while the block's sweep_threads threads run the current one
+    int gen;
+    uint32_t* mtring;
+    unsigned long long* mtpos;
+    int sweep_threads;
 };
 
 // One block of a batched launch: instance index and block index within it.

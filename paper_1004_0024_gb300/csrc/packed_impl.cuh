@@ -52,6 +52,16 @@
 // fourth.  A block is written after the last item that reads the ring entry
 // it replaces.
 //
+// MT19937 words are generated inside the kernel: after its T sweep threads a
+// block has `gen` more warps (two), which advance the replica's stream (its
+// ring of 1024 words in shared memory; 227 consecutive words of the stream
+// depend only on earlier ones and are computed in parallel) and write the
+// next sweep's words into a two-sweep buffer in global memory (in L2 for a
+// resident ladder), four slices at a time staged in shared memory and then
+// one 16-byte store per column.  The sweep threads synchronise levels with a
+// barrier of their own; block-wide barriers at the start and end of a sweep
+// hand a buffer half from the generator to the sweep threads and back.
+//
 // Fused PT: as in the lean kernel (publish the energies, bounded grid
 // barrier, every block runs the same PT pass on its own copy of the labels).
 #pragma once
@@ -65,6 +75,7 @@ namespace packed_detail {
 using fast_detail::grid_sync;
 
 constexpr int kMaxDeg = 6;
+constexpr int kGenWarps = 2;  // MT19937 generator warps per block
 // descriptor words: [0] lev0 | site << 16, [1] jtau, [2..7] one per spatial
 // neighbour: pos << 16 | (uint8) J << 8 | (uint8) dlev, dlev = lev0(q) -
 // lev0(neighbour) clamped to [-128, 127] (missing neighbours: the column
@@ -72,7 +83,7 @@ constexpr int kMaxDeg = 6;
 constexpr int kDescWords = 8;
 
 struct PackedLayout {
-    uint32_t bar, desc, pos, soff, scol, cq, colw, stage, thr, eacc, slot, temp, total;
+    uint32_t bar, desc, pos, soff, scol, cq, colw, stage, thr, eacc, slot, temp, gring, gstg, total;
 };
 
 // Shared-memory layout; the table part (desc .. scol) is one bulk copy of the
@@ -95,6 +106,10 @@ __host__ __device__ inline PackedLayout packed_layout(const SweepArgs& a, int th
     if (a.swap_every > 0) {
         L.slot = o; o += r16(4u * uint32_t(a.R));
         L.temp = o; o += r16(4u * uint32_t(a.R));
+    }
+    if (a.gen) {  // the generator warp's stream ring and four staged slices
+        L.gring = o; o += 4u * kMtRing;
+        L.gstg = o;  o += 16u * uint32_t(a.S);
     }
     L.total = o;
     return L;
@@ -134,7 +149,13 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_flag;
-    const int T = blockDim.x, tid = threadIdx.x;
+    // T sweep threads (threads 0 .. T-1), then with the MT19937 generator
+    // a.gen more warps (glane numbers their threads)
+    const int T = a.sweep_threads, NT = blockDim.x, tid = threadIdx.x;
+    const bool gen = RNG == 0 && a.gen != 0;
+    const bool is_gen = gen && tid >= T;
+    const int st = tid;
+    const int glane = tid - T, GL = NT - T;  // generator threads
     const PackedLayout L = packed_layout(a, T);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     const int S = a.S, M = a.M, N = a.N, K = a.K, R = a.R;
@@ -163,7 +184,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         eacc[0] = 0;
     }
     if (fused)
-        for (int i = tid; i < R; i += T) {
+        for (int i = tid; i < R; i += NT) {
             slot_s[i] = a.slot_of_temp[i];
             temp_s[i] = a.temp_of_slot[i];
         }
@@ -179,7 +200,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
 
     // ---- column bits from the spins (the fields follow from them)
     const int8_t* spg = a.spins + size_t(r) * N;
-    for (int p = tid; p < S; p += T) {
+    for (int p = tid; p < S; p += NT) {
         const int q = int(desc[p * kDescWords] >> 16);
         uint32_t b = 0u;
         for (int t = 0; t < M; ++t)
@@ -188,7 +209,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     }
     {
         const int temp = fused ? temp_s[r] : a.temp_of_slot[r];
-        for (int k = tid; k < K; k += T)
+        for (int k = tid; k < K; k += NT)
             thr_s[k] = a.thr[size_t(temp) * K + k];
     }
     __syncthreads();
@@ -254,7 +275,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     auto restart = [&](bool) {
 #pragma unroll
         for (int c = 0; c < RMAX; ++c) {
-            const int sl = tid + c * T;
+            const int sl = st + c * T;
             lv[c] = kNone;
             kk[c] = ke[c] = 0;
             pp[c] = qq[c] = jt2[c] = rs[c] = 0;
@@ -309,7 +330,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             int col = 0, b = 0, ring = 0, site = 0;
             if (candidate(c, l, col, b, ring, site)) {
                 const uint32_t* src = wsw + (size_t(r) * S + col) * a.Mp + 4 * b;
-                const uint32_t dst = stage_s + 4u * uint32_t((4 * ring) * NSP + tid + c * T);
+                const uint32_t dst = stage_s + 4u * uint32_t((4 * ring) * NSP + st + c * T);
 #pragma unroll
                 for (int w = 0; w < 4; ++w)
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * uint32_t(w * NSP)),
@@ -332,21 +353,86 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 for (int i = 0; i < (full ? 10 : 3); ++i)
                     philox_round(pc[c], pk0[c], pk1[c]);
                 if (full) {
-                    uint32_t* st = stage + (4 * ring) * NSP + tid + c * T;
-                    st[0] = pc[c].x;
-                    st[NSP] = pc[c].y;
-                    st[2 * NSP] = pc[c].z;
-                    st[3 * NSP] = pc[c].w;
+                    uint32_t* sp = stage + (4 * ring) * NSP + st + c * T;
+                    sp[0] = pc[c].x;
+                    sp[NSP] = pc[c].y;
+                    sp[2 * NSP] = pc[c].z;
+                    sp[3 * NSP] = pc[c].w;
                     pgo[c] = false;
                 }
             }
         }
     };
 
-    restart(false);
+    // ---- MT19937 generator warp
+    uint32_t* gring = reinterpret_cast<uint32_t*>(smem + L.gring);
+    uint32_t* gstg = reinterpret_cast<uint32_t*>(smem + L.gstg);
+    uint32_t gw = 0u;  // low word of the stream position (ring slots need only these bits)
+    // barrier of the generator warps (named barrier 2)
+    auto gen_sync = [&]() { asm volatile("bar.sync 2, %0;" ::"r"(GL) : "memory"); };
+    auto gen_sweep = [&](uint32_t* wdst) {
+        const int lane = glane;
+        for (int t0 = 0; t0 < M; t0 += 4) {
+            const int group = 4 * S;
+            for (int base = 0; base < group; base += kMtStep) {
+                const int cnt = min(kMtStep, group - base);
+                // the thread's (up to) 4 words of the step: their inputs first (all
+                // of them from earlier steps), then the recurrences, then the stores
+                constexpr int kPer = (kMtStep + 32 * kGenWarps - 1) / (32 * kGenWarps);
+                uint32_t xa[kPer], xb[kPer], xm[kPer];
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    const uint32_t w = gw + uint32_t(base + lane + GL * i);
+                    xa[i] = gring[(w - 624u) & (kMtRing - 1)];
+                    xb[i] = gring[(w - 623u) & (kMtRing - 1)];
+                    xm[i] = gring[(w - 227u) & (kMtRing - 1)];
+                }
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    const int j = lane + GL * i;
+                    if (j < cnt) {
+                        const uint32_t w = gw + uint32_t(base + j);
+                        const uint32_t x = mt_recur(xa[i], xb[i], xm[i]);
+                        gring[w & (kMtRing - 1)] = x;
+                        gstg[base + j] = mt_temper(x);
+                    }
+                }
+                gen_sync();
+            }
+            // column q gets the words of slices t0 .. t0 + 3 as one 16-byte store
+            for (int q = lane; q < S; q += GL)
+                *reinterpret_cast<uint4*>(wdst + (size_t(r) * S + pos[q]) * a.Mp + t0) =
+                    make_uint4(gstg[q], gstg[S + q], gstg[2 * S + q], gstg[3 * S + q]);
+            gen_sync();
+            gw += uint32_t(group);
+        }
+    };
+    // the half of the two-sweep buffer for sweep sw (the handle's own word buffer)
+    auto gen_buf = [&](int sw) { return const_cast<uint32_t*>(a.wbuf) + size_t(sw & 1) * a.wbuf_sweep_stride; };
+    if (is_gen) {
+        for (int i = glane; i < kMtRing; i += GL)
+            gring[i] = a.mtring[size_t(r) * kMtRing + i];
+        gw = uint32_t(a.mtpos[r]);
+        gen_sync();
+        if (a.nsweeps > 0)
+            gen_sweep(gen_buf(0));
+    }
+
+    if (!is_gen)
+        restart(false);
+    __syncthreads();  // the first sweep's words are ready
     for (int sw = 0; sw < a.nsweeps; ++sw) {
         const uint32_t sid = uint32_t(sweep0 + sw);
-        const uint32_t* wsw = (RNG == 0) ? a.wbuf + size_t(sw) * a.wbuf_sweep_stride : nullptr;
+        const uint32_t* wsw = (RNG == 0) ? (gen ? gen_buf(sw) : a.wbuf + size_t(sw) * a.wbuf_sweep_stride)
+                                         : nullptr;
+        if (is_gen) {
+            // the generator: the next sweep's words while this one runs, handed over
+            // at the sweep's end barrier
+            __syncthreads();
+            if (sw + 1 < a.nsweeps)
+                gen_sweep(gen_buf(sw + 1));
+            __syncthreads();
+        } else {
         // the blocks that start in levels [0, 8)
         if (RNG == 0) {
             if (sw == 0) {  // later sweeps: requested at the end of the previous one
@@ -359,7 +445,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             philox_start(sid, -8, true);
             philox_start(sid, -4, true);
         }
-        __syncthreads();
+        __syncthreads();  // sweep start (block-wide)
 
         for (int l = 0; l < a.D; ++l) {
             const int phase = l & 3;
@@ -398,16 +484,17 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 for (int e = 0; e < kMaxDeg; ++e)
                     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(wn[c][e]) : "r"(nw[c][e]) : "memory");
                 // ring word (4 entry + w) for slice t: entry (rs + t / 4) & 3, word t & 3
-                uu[c] = stage[((rq[c] + t) & 15) * NSP + tid + c * T];
+                uu[c] = stage[((rq[c] + t) & 15) * NSP + st + c * T];
             }
 #pragma unroll
             for (int c = 0; c < RMAX; ++c) {
                 const bool act = tt[c] >= 0;
                 const int t = act ? tt[c] : 0;
-                int f = cq[c];
+                int g6[kMaxDeg];
 #pragma unroll
                 for (int e = 0; e < kMaxDeg; ++e)
-                    f += int((wn[c][e] >> t) & 1u) * nj[c][e];
+                    g6[e] = int((wn[c][e] >> t) & 1u) * nj[c][e];
+                const int f = cq[c] + ((g6[0] + g6[1]) + (g6[2] + g6[3])) + (g6[4] + g6[5]);  // a tree
                 // bits 0, 1, 2 = s_{t-1}, s_t, s_{t+1} (ring wrap included)
                 const uint32_t w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
                 const int h = f + jt2[c] * (__popc(w3 & 5u) - 1);  // the local field
@@ -445,28 +532,31 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                                 if (phase < 3 || i == 0)
                                     philox_round(pc[c], pk0[c], pk1[c]);
                             if (phase == 3) {
-                                uint32_t* st = stage + (4 * pring[c]) * NSP + tid + c * T;
-                                st[0] = pc[c].x;
-                                st[NSP] = pc[c].y;
-                                st[2 * NSP] = pc[c].z;
-                                st[3 * NSP] = pc[c].w;
+                                uint32_t* sp = stage + (4 * pring[c]) * NSP + st + c * T;
+                                sp[0] = pc[c].x;
+                                sp[NSP] = pc[c].y;
+                                sp[2 * NSP] = pc[c].z;
+                                sp[3 * NSP] = pc[c].w;
                                 pgo[c] = false;
                             }
                         }
                     }
                 }
             }
-            __syncthreads();
+            // the level barrier of the sweep threads
+            asm volatile("bar.sync 1, %0;" ::"r"(T) : "memory");
         }
+        __syncthreads();  // sweep end (block-wide): the generator has the next sweep's words
 
-        // columns of the sweep's end stored, slots back at their first column;
-        // MT19937: the next sweep's first blocks requested, in flight during PT
+        // slots back at their first column; MT19937: the next sweep's first
+        // blocks requested, in flight during PT
         restart(true);
         if (RNG == 0 && sw + 1 < a.nsweeps) {
-            const uint32_t* wn = wsw + a.wbuf_sweep_stride;
+            const uint32_t* wn = gen ? gen_buf(sw + 1) : wsw + a.wbuf_sweep_stride;
             request_words(wn, -8);
             request_words(wn, -4);
         }
+        }  // sweep threads
 
         if (fused && (sw + 1) % a.swap_every == 0) {
             if (dE != 0)
@@ -511,7 +601,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 }
             }
             __syncthreads();
-            for (int k = tid; k < K; k += T)
+            for (int k = tid; k < K; k += NT)
                 thr_s[k] = a.thr[size_t(temp_s[r]) * K + k];
             __syncthreads();
             thr_lane = (shfl_thr && (tid & 31) < K) ? thr_s[tid & 31] : 0u;
@@ -520,6 +610,13 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     }
     if (RNG == 0)
         asm volatile("cp.async.wait_all;" ::: "memory");
+    if (is_gen) {  // the stream as it now stands
+        gen_sync();
+        for (int i = glane; i < kMtRing; i += GL)
+            a.mtring[size_t(r) * kMtRing + i] = gring[i];
+        if (glane == 0)
+            a.mtpos[r] += (unsigned long long)a.nsweeps * (unsigned long long)N;
+    }
 
     // ---- energies and write-back (coalesced over the spin index)
     if (dE != 0)
@@ -528,7 +625,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     if (tid == 0)
         a.E[r] += eacc[0];
     int8_t* spo = a.spins + size_t(r) * N;
-    for (int i = tid; i < N; i += T) {
+    for (int i = tid; i < N; i += NT) {
         const int t = i / S, q = i - t * S, p = pos[q];
         const int tm = (t == 0) ? M - 1 : t - 1, tp = (t == M - 1) ? 0 : t + 1;
         const uint32_t cb = colw[p];
@@ -543,7 +640,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             static_cast<int*>(a.fields)[size_t(r) * N + i] = f;
     }
     if (fused && blk == 0)
-        for (int i = tid; i < R; i += T) {
+        for (int i = tid; i < R; i += NT) {
             a.slot_of_temp[i] = slot_s[i];
             a.temp_of_slot_out[i] = temp_s[i];
         }
@@ -561,9 +658,10 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
 }
 
 // Register budget: about 30 registers per slot round; blocks of up to 256
-// threads (one round) or 128 (more rounds).
+// sweep threads (one round) or 128 (more rounds), plus the generator warps,
+// two resident blocks per SM.
 template <int RNG, int RMAX>
-__global__ void __launch_bounds__(RMAX == 1 ? 256 : 128, 1) packed_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(RMAX == 1 ? 256 + 64 : 128 + 64, 2) packed_kernel(const SweepArgs a)
 {
     packed_body<RNG, RMAX>(a, int(blockIdx.x), int(gridDim.x));
 }
@@ -586,6 +684,7 @@ void* pick_packed(int rmax)
 // slot rounds per thread with an instantiation, and the kernels (packed_mt.cu,
 // packed_philox.cu)
 constexpr int kPackedRounds[5] = {1, 2, 3, 5, 8};
+constexpr int kPackedGenWarps = packed_detail::kGenWarps;
 void* packed_kernel_mt(int rmax);
 void* packed_kernel_philox(int rmax);
 inline void* packed_kernel_ptr(int rng, int rmax)
