@@ -480,11 +480,12 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 const bool act = unsigned(t0) < unsigned(M);
                 tt[c] = act ? t0 : -1;
                 const int t = act ? t0 : 0;
+                // lanes without a busy slot all read word 0 (one broadcast, no conflicts)
 #pragma unroll
                 for (int e = 0; e < kMaxDeg; ++e)
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(wn[c][e]) : "r"(nw[c][e]) : "memory");
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(wn[c][e]) : "r"(act ? nw[c][e] : colw_s) : "memory");
                 // ring word (4 entry + w) for slice t: entry (rs + t / 4) & 3, word t & 3
-                uu[c] = stage[((rq[c] + t) & 15) * NSP + st + c * T];
+                uu[c] = stage[act ? ((rq[c] + t) & 15) * NSP + st + c * T : 0];
             }
 #pragma unroll
             for (int c = 0; c < RMAX; ++c) {
