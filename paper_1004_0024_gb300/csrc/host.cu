@@ -770,6 +770,18 @@ bool choose_packed(ising_s* g)
     const size_t lim = sweep_max_dynamic_smem() ? sweep_max_dynamic_smem() : 200 * 1024;
     if (plain > lim)
         return false;
+    // A ladder that cannot be resident at once is throughput-bound rather than
+    // bound by one replica's chain of levels; there the lean kernel's
+    // small-block build is faster (65536 replicas of 4096 spins: 1.18e11
+    // against 1.05e11 attempts/s), so the packed kernel is chosen
+    // automatically only for resident ladders.  The handle is changed only
+    // when the packed kernel is taken.
+    int per_sm = 0;
+    const bool occ = fused <= lim && fast_max_blocks_per_sm(g->field_bits, rmax, g->rng, T + 32 * a.gen, fused,
+                                                           &per_sm, 5) == cudaSuccess;
+    const bool resident = occ && (long long)per_sm * g_num_sms >= g->R;
+    if (!resident && g->T_req == 0)
+        return false;
     g->use_packed = true;
     g->use_fast = true;
     g->G = 1;
@@ -779,13 +791,7 @@ bool choose_packed(ising_s* g)
     g->fast_smem = plain;
     g->smem_fused = fused;
     g->smem = plain;
-    g->persistent_ok = false;
-    if (!g_coop || !g->allow_persistent || fused > lim || g->R > 16384)
-        return true;
-    int per_sm = 0;
-    if (fast_max_blocks_per_sm(g->field_bits, rmax, g->rng, T + 32 * a.gen, fused, &per_sm, 5) != cudaSuccess)
-        return true;
-    g->persistent_ok = (long long)per_sm * g_num_sms >= g->blocks;
+    g->persistent_ok = resident && g_coop && g->allow_persistent && g->R <= 16384;
     return true;
 }
 
@@ -957,16 +963,14 @@ SweepArgs base_args(ising_s* g)
 
 int32_t choose_launch(ising_s* g)
 {
-    if (packed_eligible(g)) {
+    if (packed_eligible(g) && choose_packed(g)) {
         // the packed kernel sizes its own blocks (one replica per block)
-        g->G = 1;
+        g->use_lean = g->lean_small = g->lean_long = g->use_track = false;
         g->tables_smem = 1;
         g->thr_smem = 1;
         g->stage_words = 0;
         g->cmax = 1;
-        choose_fast(g);
-        if (g->use_packed)
-            return ISING_OK;
+        return ISING_OK;
     }
     const int sms = g_num_sms > 0 ? g_num_sms : 148;
     const size_t kMaxSmem = sweep_max_dynamic_smem() ? sweep_max_dynamic_smem() : 200 * 1024;
@@ -2780,9 +2784,11 @@ extern "C" int32_t ising_batch_autotune(ising_batch_t b, uint32_t flags)
         ising_t t = nullptr;
         int32_t rc = ising_create(src->n, src->row_ptr.data(), src->col.data(), src->J.data(),
                                   src->h.data(), src->M, 0u, &t);
-        if (!rc)
+        if (!rc) {
+            t->packed_off = true;  // the shapes of the batch's own instances (no packed kernel)
             rc = replicas_init_impl(t, src->R, src->betas.data(), src->seed, src->rng, src->field_bits,
                                     src->inst);
+        }
         if (rc) {
             if (t)
                 ising_destroy(t);
