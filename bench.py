@@ -274,6 +274,10 @@ def workload_line(name, rng, steps, warmup, flush, stream, dev_index, sweeps=0):
            "kernel_variant": info["fast_kernel"], "levels": info["levels"],
            "roofline": roofline(c, rng, per_step * steps, t["kernel_ms"], t["sweep_launches"], t["clocks"],
                                 info["fast_kernel"], name)}
+    if out["roofline"] and t["sweep_launches"] > 0:
+        out["roofline"]["latency_floor"] = latency_floor(
+            info["levels"], c["sweeps"] * steps / t["sweep_launches"], t["kernel_ms"] / t["sweep_launches"],
+            t["clocks"])
     if t["first_clocks"] is not None:
         out["remeasured"] = {"first_clocks": t["first_clocks"]}
     return out
@@ -375,6 +379,9 @@ def run_ours(args):
         line["remeasured"] = {"first_clocks": first_clocks, "why": "slowdown or locked clock in the first timed pass"}
     line["roofline"] = roofline(c, args.rng, per_step * args.steps, kernel_ms, sweep_launches, clocks,
                                 info["fast_kernel"], args.workload)
+    if line["roofline"] and sweep_launches > 0:
+        line["roofline"]["latency_floor"] = latency_floor(
+            info["levels"], sweeps * args.steps / sweep_launches, kernel_ms / sweep_launches, clocks)
     if e2e is not None:
         line["e2e"] = e2e
     if args.workload == "paper" and c["sweeps"] == 30000:
@@ -514,6 +521,33 @@ def roofline(c, rng, attempts, kernel_ms, launches, clocks, kernel, name="cfg1")
             "peak_basis": f"152 SM x 128 lanes x {mhz:.0f} MHz sampled SM clock (derived, not measured)",
             "kernel_ms_per_launch": kernel_ms / launches, "launches": int(launches),
             "ops_per_attempt": ops_per_attempt(g, rng)}
+
+
+# one sweep level's dependent chain: the neighbour's column word (a shared
+# load), ten dependent integer operations (the spin bit, its 2J, three adds of
+# the field tree, the Trotter term, the sign, the threshold index, the compare,
+# the flip), the threshold shuffle and the level barrier
+LEVEL_CHAIN_INT_OPS = 10
+_LATENCIES = None
+
+
+def latency_floor(levels, sweeps_per_launch, kernel_ms_per_launch, clocks):
+    """Latency floor of a sweep launch: levels x sweeps x the cycles of one
+    level's dependent chain, with the latencies measured on this GPU
+    (ising_measure_latencies), at the sampled SM clock; frac = floor /
+    measured kernel time."""
+    global _LATENCIES
+    from paper_1004_0024_gb300 import ising
+    if _LATENCIES is None:
+        _LATENCIES = ising.ising_measure_latencies()
+    lat = _LATENCIES
+    cyc = lat["shared_load"] + LEVEL_CHAIN_INT_OPS * lat["int_mad"] + lat["shuffle"] + lat["barrier_8_warps"]
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    floor_ms = levels * sweeps_per_launch * cyc / (mhz * 1e3)
+    return {"cycles_per_level": cyc, "levels_per_sweep": int(levels), "sweeps_per_launch": sweeps_per_launch,
+            "ms_per_launch": floor_ms, "frac": floor_ms / kernel_ms_per_launch if kernel_ms_per_launch else None,
+            "latencies_cycles": lat, "chain": f"shared load + {LEVEL_CHAIN_INT_OPS} dependent int ops + shuffle + "
+                                              "8-warp barrier, per level (measured latencies)"}
 
 
 # ------------------------------------------------------------- CPU oracle

@@ -583,6 +583,20 @@ int32_t ising_mlp_destroy(ising_mlp_t m);
 int32_t ising_set_alloc_cap(uint64_t bytes);
 int32_t ising_selftest_wait(int32_t kind, void* stream);
 
+/*
+ * ising_measure_latencies -- the latencies, in SM clock cycles per
+ * operation, of the operations on the critical path of one sweep level,
+ * measured on the current device: cycles[0] a shared-memory load whose
+ * address depends on the previous one, cycles[1] a dependent 32-bit integer
+ * multiply-add, cycles[2] a dependent warp shuffle, cycles[3] a barrier of
+ * one block's 8 warps (chains of 4096 operations in one 256-thread block,
+ * clock64).  Not in the paper: it gives the latency floor of a sweep (levels
+ * x the dependent chain of one level) that bench.py reports next to the
+ * issue-rate roofline.  Synchronises the device.  Errors: INVALID_ARG (NULL
+ * cycles), OOM, CUDA.
+ */
+int32_t ising_measure_latencies(double* cycles);
+
 /* Release all device memory of the handle (NULL is ignored).  MT19937 word
  * buffers of 256 MB or more are not returned to the driver: up to two of
  * them are kept (after a device synchronisation) for the next handle whose

@@ -142,6 +142,7 @@ _SIGS = {
     "ising_split_swap_threshold": ([ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64],
                                    ctypes.c_uint32),
     "ising_selftest_wait": ([ctypes.c_int32, _vp], ctypes.c_int32),
+    "ising_measure_latencies": ([_f64p], ctypes.c_int32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -335,6 +336,14 @@ ACCEPT_MODES = {"exact": 0, "fast": 1, "accurate": 2}  # ISING_ACCEPT_*
 def ising_release_cached_memory():
     """Free the MT19937 word buffers that destroyed handles left for reuse."""
     _check(_lib.ising_release_cached_memory())
+
+
+def ising_measure_latencies() -> dict:
+    """Cycles per dependent operation on the current GPU (shared load,
+    integer multiply-add, warp shuffle, 8-warp block barrier)."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(_lib.ising_measure_latencies(_p(out, _f64p)))
+    return dict(zip(("shared_load", "int_mad", "shuffle", "barrier_8_warps"), (float(x) for x in out)))
 
 
 def ising_selftest_wait(kind, stream=None):

@@ -107,3 +107,16 @@ def test_clock_samples_and_the_remeasure_rule(tmp_path):
     assert bench.clocks_rejected({"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": ["sw_thermal_slowdown"]})
     assert bench.clocks_rejected({"sm_mhz": 1200.0, "sm_max_mhz": 2070.0, "reasons": []})
     assert not bench.clocks_rejected({"sm_mhz": 1200.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]})
+
+
+def test_latency_floor_is_levels_times_the_level_chain():
+    import bench
+    bench._LATENCIES = {"shared_load": 30.0, "int_mad": 4.0, "shuffle": 36.0, "barrier_8_warps": 24.0}
+    try:
+        f = bench.latency_floor(400, 200, 26.0, {"sm_mhz": 2000.0})
+    finally:
+        bench._LATENCIES = None
+    cyc = 30.0 + bench.LEVEL_CHAIN_INT_OPS * 4.0 + 36.0 + 24.0
+    assert f["cycles_per_level"] == cyc
+    assert abs(f["ms_per_launch"] - 400 * 200 * cyc / 2.0e6) < 1e-9
+    assert abs(f["frac"] - f["ms_per_launch"] / 26.0) < 1e-12

@@ -53,3 +53,11 @@ def test_allocation_cap_reports_oom_and_lifts(ising):
 
 def test_selftest_rejects_unknown_kind(ising):
     assert ising.ERRORS[ising.ising_selftest_wait(7)] == "INVALID_ARG"
+
+
+def test_measured_latencies_are_plausible(ising):
+    lat = ising.ising_measure_latencies()
+    assert 5.0 < lat["shared_load"] < 300.0, lat
+    assert 1.0 < lat["int_mad"] < 40.0, lat
+    assert 5.0 < lat["shuffle"] < 300.0, lat
+    assert 2.0 < lat["barrier_8_warps"] < 1000.0, lat
