@@ -406,9 +406,19 @@ typedef struct {
     uint32_t seed;          /* base seed (see ising_replicas_init)        */
 } ising_instance_t;
 
+/* flags of ising_batch_create */
+#define ISING_BATCH_PER_SWEEP 1 /* run with per-sweep batched launches, not persistent waves */
+
 /* Create and initialise n_inst instances with one RNG mode and field width.
- * flags reserved (0).  Errors: as ising_create / ising_replicas_init for the
- * first failing instance (its index is in ising_last_error()). */
+ * When every instance's model is one the packed kernel takes (layered, M in
+ * {8, 16, 32}, spatial degree <= 6, |J| <= 127, at most 384 slots) and each
+ * instance's ladder fits on the GPU at once, the batch runs as persistent
+ * waves: whole instances grouped by block shape and level count, one
+ * cooperative launch per wave and call that runs all the call's sweeps,
+ * every instance's PT passes fused behind its own bounded barrier (flags:
+ * ISING_BATCH_PER_SWEEP keeps the per-sweep launches).  Errors: as
+ * ising_create / ising_replicas_init for the first failing instance (its
+ * index is in ising_last_error()), INVALID_ARG (unknown flags). */
 int32_t ising_batch_create(int32_t n_inst, const ising_instance_t* inst, int32_t rng_mode,
                            int32_t field_bits, uint32_t flags, ising_batch_t* out);
 int32_t ising_batch_set_stream(ising_batch_t b, void* cuda_stream);
@@ -417,7 +427,8 @@ int32_t ising_batch_set_stream(ising_batch_t b, void* cuda_stream);
  * candidate launch shapes (resident vs streamed, replicas and threads per
  * block) on a representative instance and keep the cheapest in SM-time per
  * sweep.  flags reserved (0).  Results never change, only speed.  Runs
- * sweeps on scratch copies of the representatives, never on the batch. */
+ * sweeps on scratch copies of the representatives, never on the batch.  A
+ * batch of persistent waves has nothing to tune (returns OK). */
 int32_t ising_batch_autotune(ising_batch_t b, uint32_t flags);
 
 /* n sweeps of every instance with a PT pass after every swap_every-th sweep
@@ -429,7 +440,9 @@ int32_t ising_batch_read_state(ising_batch_t b, int32_t inst, int8_t* spins, int
                                int64_t* energy, int32_t* temp_of_slot, uint64_t* counters);
 int32_t ising_batch_read_swap_stats(ising_batch_t b, int32_t inst, uint64_t* accepted);
 
-/* Launch facts of instance `inst`; resident = 1 if it runs as one block. */
+/* Launch facts of instance `inst`; resident = 1 if its whole ladder stays on
+ * the GPU for a whole ising_batch_run call (one block per ladder, or the
+ * persistent waves of a packed batch, fast_kernel 4). */
 int32_t ising_batch_get_info(ising_batch_t b, int32_t inst, ising_info_t* out, int32_t* resident);
 int32_t ising_batch_destroy(ising_batch_t b);
 

@@ -10,8 +10,8 @@ namespace {
 
 void* pick(int field_bits, int rng, int cmax, int variant = 0, bool batch = false, bool split = false)
 {
-    if (variant == 5)  // packed: single-instance, plain couplings; cmax = slot rounds per thread
-        return (batch || split) ? nullptr : packed_kernel_ptr(rng, cmax);
+    if (variant == 5)  // packed: plain couplings; cmax = slot rounds per thread
+        return split ? nullptr : packed_kernel_ptr(rng, cmax, batch);
     if (split)  // lean variants only, single-instance launches only
         return (batch || !(variant == 1 || variant == 3 || variant == 4))
                    ? nullptr
@@ -52,7 +52,7 @@ cudaError_t fast_set_smem_limits()
         for (int fb : {16, 32})
             for (int rng : {0, 1})
                 for (int cm : {1, 2, 3, 4, 5, 8}) {
-                    if ((variant == 2 && cm != 1) || (variant == 5 && (batch != 0 || fb != 16)) ||
+                    if ((variant == 2 && cm != 1) || (variant == 5 && (batch == 2 || fb != 16)) ||
                         (variant != 5 && (cm == 3 || cm == 5)))
                         continue;
                     void* fn = pick(fb, rng, cm, variant, batch == 1, batch == 2);
@@ -94,6 +94,24 @@ cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int thread
     if (cooperative)
         return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, st);
     return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+cudaError_t fast_max_blocks_per_sm_batch(int rng, int cmax, int threads, size_t smem, int* out)
+{
+    void* fn = pick(16, rng, cmax, 5, true, false);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, threads, smem);
+}
+
+cudaError_t launch_packed_batch(const SweepArgs* args, const BatchItem* items, int n_items, int rng, int rmax,
+                                int threads, size_t smem, cudaStream_t st)
+{
+    void* fn = pick(16, rng, rmax, 5, true, false);
+    if (!fn)
+        return cudaErrorInvalidValue;
+    void* params[] = {&args, &items};
+    return cudaLaunchCooperativeKernel(fn, dim3(n_items), dim3(threads), params, smem, st);
 }
 
 cudaError_t launch_fast_batch(const SweepArgs* args, const BatchItem* items, int n_items,

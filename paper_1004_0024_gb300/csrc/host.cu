@@ -2318,6 +2318,14 @@ int32_t ising_destroy(ising_t g)
 // threads per block); every planned op of a group becomes ONE batched launch
 // whose blocks are (instance, block) items, and the groups run as parallel
 // branches of one recorded CUDA graph.
+struct PackedWave {
+    int T = 0;               // sweep threads per block (every instance of the wave)
+    int rmax = 1;            // slot rounds per thread
+    size_t smem = 0;         // dynamic shared memory: the largest instance's
+    std::vector<int> ids;    // instances, longest level count first
+    long long blocks = 0;    // replicas of the wave (one block each)
+};
+
 struct ising_batch_s {
     std::vector<ising_s*> inst;
     std::vector<int> resident;  // 1: the whole ladder runs as one block
@@ -2329,8 +2337,23 @@ struct ising_batch_s {
     struct Run {
         cudaGraphExec_t exec = nullptr;
         std::vector<void*> bufs;  // device argument records of the graph
+        // persistent (packed) batches: the launches of a call, each one wave
+        // for `sweeps` sweeps with PT every `every` (0: none)
+        struct Launch {
+            int wave, sweeps, every, n_items;
+            const SweepArgs* args;
+            const BatchItem* items;
+            const MtGenArgs* gen;  // MT19937: the wave's swap-stream words (or null)
+            const BatchItem* gen_items;
+            int n_gen;
+        };
+        std::vector<Launch> launches;
     };
     std::map<std::pair<long long, int>, Run> runs;
+    // persistent batches of the packed kernel (waves of whole, co-resident instances)
+    bool packed = false;
+    std::vector<PackedWave> waves;
+    unsigned* d_bar = nullptr;  // [instances] grid-barrier counters of the persistent launches
 
     void drop_runs()
     {
@@ -2453,6 +2476,194 @@ struct BatchGroup {
     size_t smem_plain = 0, smem_fused = 0;
     int max_S = 0, max_R = 0;
 };
+
+// ---------------------------------------------- persistent packed batches
+// Instances whose models the packed kernel takes run as waves: whole
+// instances whose replicas (one block each) are resident together, grouped
+// by block shape and ordered by level count, one cooperative launch per wave
+// for all sweeps of a call with every instance's PT passes fused behind its
+// own bounded barrier.  Returns whether the batch runs this way.
+bool packed_batch_setup(ising_batch_s* b)
+{
+    if (!g_coop)
+        return false;
+    const int gen = b->inst.empty() || b->inst[0]->rng != ISING_RNG_MT19937 ? 0 : kPackedGenWarps;
+    std::map<std::pair<int, int>, std::vector<int>> by_T;  // (sweep threads, rounds)
+    std::vector<size_t> smem(b->inst.size(), 0);
+    for (int i = 0; i < int(b->inst.size()); ++i) {
+        ising_s* g = b->inst[i];
+        const bool ok = (g->M == 8 || g->M == 16 || g->M == 32) && g->max_sp_deg <= 6 && g->max_sp_J <= 127 &&
+                        g->S < 65536 && g->D0 < 65536 && g->nslots >= 1 && g->nslots <= 384 && !g->split &&
+                        g->R <= 16384;
+        if (!ok)
+            return false;
+        if (!g->d_pk) {
+            const std::vector<uint32_t> pk = packed_tables(g);
+            if (upload(&g->d_pk, pk) != ISING_OK)
+                return false;
+            g->pk_bytes = uint32_t(pk.size() * 4);
+        }
+        // one slot per thread up to 256 slots, else 128 threads of three rounds
+        const int T = g->nslots <= 256 ? ((g->nslots + 31) / 32) * 32 : 128;
+        const int rmax = g->nslots <= 256 ? 1 : 3;
+        SweepArgs a = base_args(g);
+        a.G = 1;
+        a.gen = gen;
+        a.swap_every = 1;
+        smem[i] = packed_smem_bytes(a, T);
+        by_T[std::make_pair(T, rmax)].push_back(i);
+    }
+    const size_t lim = sweep_max_dynamic_smem() ? sweep_max_dynamic_smem() : 200 * 1024;
+    std::vector<PackedWave> waves;
+    for (auto& kv : by_T) {
+        const int T = kv.first.first, rmax = kv.first.second;
+        std::vector<int>& ids = kv.second;
+        std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return b->inst[x]->D > b->inst[y]->D; });
+        PackedWave w;
+        w.T = T;
+        w.rmax = rmax;
+        long long cap = 0;
+        for (int i : ids) {
+            const size_t sm = std::max(w.smem, smem[i]);
+            int per_sm = 0;
+            if (sm > lim || fast_max_blocks_per_sm_batch(b->inst[i]->rng, rmax, T + 32 * gen, sm, &per_sm) != cudaSuccess)
+                return false;
+            cap = (long long)per_sm * g_num_sms;
+            if (!w.ids.empty() && w.blocks + b->inst[i]->R > cap) {
+                waves.push_back(w);
+                w = PackedWave{};
+                w.T = T;
+                w.rmax = rmax;
+                if (fast_max_blocks_per_sm_batch(b->inst[i]->rng, rmax, T + 32 * gen, smem[i], &per_sm) != cudaSuccess)
+                    return false;
+                cap = (long long)per_sm * g_num_sms;
+            }
+            if (b->inst[i]->R > cap)
+                return false;  // one instance alone is not resident
+            w.ids.push_back(i);
+            w.smem = std::max(w.smem, smem[i]);
+            w.blocks += b->inst[i]->R;
+        }
+        if (!w.ids.empty())
+            waves.push_back(w);
+    }
+    if (dalloc(&b->d_bar, std::max<size_t>(b->inst.size(), 1)) != ISING_OK)
+        return false;
+    b->waves = waves;
+    return true;
+}
+
+// The launches of ising_batch_run(n, swap_every) on a persistent batch:
+// every wave for its fused part (whole groups of swap_every sweeps, PT after
+// each) and its remainder (no PT), as plan() splits a single instance's run.
+int32_t packed_batch_build(ising_batch_s* b, long long n, int swap_every, ising_batch_s::Run* run)
+{
+    const long long every = swap_every > 0 ? swap_every : 0;
+    const long long fused = (every > 0 && n >= every) ? (n / every) * every : 0;
+    const long long rest = n - fused;
+    const bool mt = b->inst[0]->rng == ISING_RNG_MT19937;
+    if (fused > (1LL << 30) || rest > (1LL << 30))
+        return fail(ISING_ERR_INVALID_ARG, "a persistent batch run takes at most 2^30 sweeps per call");
+    for (int wi = 0; wi < int(b->waves.size()); ++wi) {
+        const PackedWave& w = b->waves[wi];
+        for (int part = 0; part < 2; ++part) {
+            const long long m = part == 0 ? fused : rest;
+            if (m == 0)
+                continue;
+            const int passes = part == 0 ? int(m / every) : 0;
+            std::vector<SweepArgs> args;
+            std::vector<BatchItem> items;
+            std::vector<MtGenArgs> gargs;
+            std::vector<BatchItem> gitems;
+            int max_S = 0;
+            for (int j = 0; j < int(w.ids.size()); ++j) {
+                ising_s* g = b->inst[w.ids[j]];
+                if (mt) {
+                    // the sweep kernel's two-sweep word buffer; the swap stream's words
+                    if (g->wbuf_cap < 2) {
+                        big_free(g->d_wbuf);
+                        int32_t rc = big_alloc(&g->d_wbuf, size_t(2) * g->R * g->S * g->Mp);
+                        if (rc)
+                            return rc;
+                        g->wbuf_cap = 2;
+                    }
+                    if (passes > g->swbuf_cap) {
+                        dfree(g->d_swbuf);
+                        int32_t rc = dalloc(&g->d_swbuf, size_t(passes) * std::max(g->maxpairs, 1));
+                        if (rc)
+                            return rc;
+                        g->swbuf_cap = passes;
+                    }
+                    if (passes > 0) {
+                        int blocks = 0;
+                        gargs.push_back(gen_args(g, Op{Op::GEN, 0, passes, 0}, &blocks));
+                        gitems.push_back({int(gargs.size()) - 1, g->R});
+                        max_S = std::max(max_S, g->S);
+                    }
+                }
+                SweepArgs a = base_args(g);
+                a.G = 1;
+                a.nsweeps = int(m);
+                a.swap_every = part == 0 ? int(every) : 0;
+                a.inst_blocks = g->R;
+                a.sweep_threads = w.T;
+                a.gen = mt ? kPackedGenWarps : 0;
+                a.wbuf = g->d_wbuf;
+                a.swbuf = g->d_swbuf;
+                a.gridbar = b->d_bar + w.ids[j];
+                args.push_back(a);
+                for (int k = 0; k < g->R; ++k)
+                    items.push_back({j, k});
+            }
+            ising_batch_s::Run::Launch L{};
+            L.wave = wi;
+            L.sweeps = int(m);
+            L.every = part == 0 ? int(every) : 0;
+            L.n_items = int(items.size());
+            int32_t rc = upload_raw(run->bufs, args, &L.args);
+            if (!rc)
+                rc = upload_raw(run->bufs, items, &L.items);
+            if (!rc && !gargs.empty()) {
+                rc = upload_raw(run->bufs, gargs, &L.gen);
+                if (!rc)
+                    rc = upload_raw(run->bufs, gitems, &L.gen_items);
+                L.n_gen = int(gitems.size());
+            }
+            if (rc)
+                return rc;
+            (void)max_S;
+            run->launches.push_back(L);
+        }
+    }
+    return ISING_OK;
+}
+
+int32_t packed_batch_launch(ising_batch_s* b, const ising_batch_s::Run& run)
+{
+    const bool mt = b->inst[0]->rng == ISING_RNG_MT19937;
+    for (const auto& L : run.launches) {
+        const PackedWave& w = b->waves[L.wave];
+        cudaError_t e = cudaSuccess;
+        if (L.n_gen > 0) {
+            int max_S = 0;
+            for (int i : w.ids)
+                max_S = std::max(max_S, b->inst[i]->S);
+            e = launch_mt_gen_batch(L.gen, L.gen_items, L.n_gen, max_S, b->stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * b->inst.size(), b->stream);
+        if (e == cudaSuccess)
+            e = launch_packed_batch(L.args, L.items, L.n_items, mt ? 0 : 1, w.rmax,
+                                    w.T + (mt ? 32 * kPackedGenWarps : 0), w.smem, b->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "persistent batch launch");
+        for (int i : w.ids) {
+            b->inst[i]->n_launches += 1 + (L.n_gen > 0 ? 1 : 0);
+            b->inst[i]->n_sweep_launches += 1;
+        }
+    }
+    return ISING_OK;
+}
 
 int32_t batch_record(ising_batch_s* b, long long n, int swap_every, ising_batch_s::Run* run)
 {
@@ -2611,8 +2822,8 @@ int32_t ising_batch_create(int32_t n_inst, const ising_instance_t* in, int32_t r
     if (!out || !in || n_inst < 1)
         return fail(ISING_ERR_INVALID_ARG, "need n_inst >= 1 instances and an output pointer");
     *out = nullptr;
-    if (flags != 0)
-        return fail(ISING_ERR_INVALID_ARG, "flags must be 0");
+    if (flags & ~uint32_t(ISING_BATCH_PER_SWEEP))
+        return fail(ISING_ERR_INVALID_ARG, "unknown batch flags");
     ising_batch_s* b = new ising_batch_s();
     long long words_per_sweep = 0;
     for (int i = 0; i < n_inst; ++i) {
@@ -2642,6 +2853,7 @@ int32_t ising_batch_create(int32_t n_inst, const ising_instance_t* in, int32_t r
     b->resident.resize(n_inst);
     for (int i = 0; i < n_inst; ++i)
         b->resident[i] = configure_instance(b->inst[i], true, 0) ? 1 : 0;
+    b->packed = !(flags & ISING_BATCH_PER_SWEEP) && packed_batch_setup(b);
     *out = b;
     return ISING_OK;
 }
@@ -2667,6 +2879,19 @@ int32_t ising_batch_run(ising_batch_t b, int64_t n, int32_t swap_every)
         return ISING_OK;
     const auto key = std::make_pair((long long)n, swap_every > 0 ? int(swap_every) : 0);
     auto it = b->runs.find(key);
+    if (b->packed) {
+        if (it == b->runs.end()) {
+            ising_batch_s::Run run;
+            const int32_t rc = packed_batch_build(b, n, key.second, &run);
+            if (rc) {
+                for (void* p : run.bufs)
+                    cudaFree(p);
+                return rc;
+            }
+            it = b->runs.emplace(key, run).first;
+        }
+        return packed_batch_launch(b, it->second);
+    }
     if (it == b->runs.end()) {
         ising_batch_s::Run run;
         const int32_t rc = batch_record(b, n, key.second, &run);
@@ -2703,8 +2928,20 @@ int32_t ising_batch_get_info(ising_batch_t b, int32_t inst, ising_info_t* out, i
     if (!b || inst < 0 || inst >= int(b->inst.size()))
         return fail(ISING_ERR_INVALID_ARG, "no such instance");
     if (resident)
-        *resident = b->resident[inst];
-    return ising_get_info(b->inst[inst], out);
+        *resident = b->packed ? 1 : b->resident[inst];
+    const int32_t rc = ising_get_info(b->inst[inst], out);
+    if (rc || !b->packed || !out)
+        return rc;
+    for (const PackedWave& w : b->waves)  // the persistent packed launch of this instance
+        if (std::find(w.ids.begin(), w.ids.end(), int(inst)) != w.ids.end()) {
+            out->fast_kernel = 4;
+            out->replicas_per_block = 1;
+            out->threads_per_block = w.T;
+            out->blocks = b->inst[inst]->R;
+            out->smem_bytes = int(w.smem);
+            out->persistent_ok = 1;
+        }
+    return ISING_OK;
 }
 
 int32_t ising_batch_destroy(ising_batch_t b)
@@ -2712,6 +2949,7 @@ int32_t ising_batch_destroy(ising_batch_t b)
     if (!b)
         return ISING_OK;
     b->drop_runs();
+    dfree(b->d_bar);
     for (ising_s* g : b->inst)
         ising_destroy(g);
     for (cudaStream_t s : b->side)
@@ -2774,6 +3012,8 @@ extern "C" int32_t ising_batch_autotune(ising_batch_t b, uint32_t flags)
         return fail(ISING_ERR_INVALID_ARG, "NULL batch");
     if (flags != 0)
         return fail(ISING_ERR_INVALID_ARG, "flags must be 0");
+    if (b->packed)
+        return ISING_OK;  // persistent waves: the block shape follows from the slot counts
     std::map<std::tuple<int, int, int>, std::vector<int>> classes;
     for (int i = 0; i < int(b->inst.size()); ++i) {
         ising_s* g = b->inst[i];

@@ -331,6 +331,11 @@ cudaError_t launch_fast_batch(const SweepArgs* args, const BatchItem* items, int
                               int field_bits, int rng, int cmax, int threads, size_t smem, int variant,
                               cudaStream_t st);
 cudaError_t launch_pt_batch(const PtArgs* args, int n_inst, int max_R, cudaStream_t st);
+// Packed kernel over ragged batches (one cooperative launch of whole
+// instances, block b = items[b]; rmax: 1 or 2 slot rounds per thread).
+cudaError_t fast_max_blocks_per_sm_batch(int rng, int rmax, int threads, size_t smem, int* out);
+cudaError_t launch_packed_batch(const SweepArgs* args, const BatchItem* items, int n_items, int rng, int rmax,
+                                int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_mt_gen_batch(const MtGenArgs* args, const BatchItem* items, int n_items,
                                 int max_S, cudaStream_t st);
 // split: the split-coupling instantiation of the lean kernel (variants 1, 3, 4

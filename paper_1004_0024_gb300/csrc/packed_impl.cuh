@@ -667,6 +667,34 @@ __global__ void __launch_bounds__(RMAX == 1 ? 256 + 64 : 128 + 64, 2) packed_ker
     packed_body<RNG, RMAX>(a, int(blockIdx.x), int(gridDim.x));
 }
 
+// Ragged batches: block b runs replica items[b].block of instance
+// items[b].inst with that instance's arguments (copied to shared memory), all
+// sweeps of the launch with the instance's PT passes fused; a launch holds
+// whole instances, all of its blocks resident (cooperative launch), and the
+// instances' grid-barrier counters start at zero.
+template <int RNG, int RMAX>
+__global__ void __launch_bounds__(RMAX == 1 ? 256 + 64 : 128 + 64, 2)
+    packed_batch_kernel(const SweepArgs* __restrict__ args, const BatchItem* __restrict__ items)
+{
+    __shared__ SweepArgs sa;
+    const BatchItem it = items[blockIdx.x];
+    if (threadIdx.x == 0)
+        sa = args[it.inst];
+    __syncthreads();
+    packed_body<RNG, RMAX>(sa, it.block, sa.inst_blocks);
+}
+
+template <int RNG>
+void* pick_packed_batch(int rmax)
+{
+    switch (rmax) {
+    case 1: return reinterpret_cast<void*>(&packed_batch_kernel<RNG, 1>);
+    case 2: return reinterpret_cast<void*>(&packed_batch_kernel<RNG, 2>);
+    case 3: return reinterpret_cast<void*>(&packed_batch_kernel<RNG, 3>);
+    default: return nullptr;
+    }
+}
+
 template <int RNG>
 void* pick_packed(int rmax)
 {
@@ -686,11 +714,11 @@ void* pick_packed(int rmax)
 // packed_philox.cu)
 constexpr int kPackedRounds[5] = {1, 2, 3, 5, 8};
 constexpr int kPackedGenWarps = packed_detail::kGenWarps;
-void* packed_kernel_mt(int rmax);
-void* packed_kernel_philox(int rmax);
-inline void* packed_kernel_ptr(int rng, int rmax)
+void* packed_kernel_mt(int rmax, bool batch = false);
+void* packed_kernel_philox(int rmax, bool batch = false);
+inline void* packed_kernel_ptr(int rng, int rmax, bool batch = false)
 {
-    return rng == 0 ? packed_kernel_mt(rmax) : packed_kernel_philox(rmax);
+    return rng == 0 ? packed_kernel_mt(rmax, batch) : packed_kernel_philox(rmax, batch);
 }
 size_t packed_smem_bytes(const SweepArgs& a, int threads);
 

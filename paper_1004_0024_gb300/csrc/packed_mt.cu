@@ -2,7 +2,10 @@
 #include "packed_impl.cuh"
 
 namespace isg {
-void* packed_kernel_mt(int rmax) { return packed_detail::pick_packed<0>(rmax); }
+void* packed_kernel_mt(int rmax, bool batch)
+{
+    return batch ? packed_detail::pick_packed_batch<0>(rmax) : packed_detail::pick_packed<0>(rmax);
+}
 
 size_t packed_smem_bytes(const SweepArgs& a, int threads)
 {

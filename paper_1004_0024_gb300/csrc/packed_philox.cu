@@ -2,5 +2,8 @@
 #include "packed_impl.cuh"
 
 namespace isg {
-void* packed_kernel_philox(int rmax) { return packed_detail::pick_packed<1>(rmax); }
+void* packed_kernel_philox(int rmax, bool batch)
+{
+    return batch ? packed_detail::pick_packed_batch<1>(rmax) : packed_detail::pick_packed<1>(rmax);
+}
 }  // namespace isg

@@ -308,6 +308,7 @@ LAUNCH_GENERIC = 2
 LAUNCH_NO_LEAN = 4
 LAUNCH_TRACK = 8
 LAUNCH_NO_PACKED = 16
+BATCH_PER_SWEEP = 1
 
 
 def ising_set_launch(h, replicas_per_block=0, threads_per_block=0, launch_flags=LAUNCH_PERSISTENT):
@@ -473,7 +474,7 @@ class Batch:
     except that its Philox counters use instance = b.
     """
 
-    def __init__(self, instances, rng="mt19937", field_bits=16, stream=None):
+    def __init__(self, instances, rng="mt19937", field_bits=16, stream=None, per_sweep=False):
         self._keep = []
         arr = (IsingInstance * len(instances))()
         self.sizes = []
@@ -491,7 +492,7 @@ class Batch:
             self.sizes.append((int(g.n), int(b.size)))
         out = _vp()
         _check(_lib.ising_batch_create(len(instances), arr, RNG[rng] if isinstance(rng, str) else rng,
-                                       int(field_bits), 0, ctypes.byref(out)))
+                                       int(field_bits), BATCH_PER_SWEEP if per_sweep else 0, ctypes.byref(out)))
         self.h = out
         self._keep = []  # inputs are copied by the library
         if stream is not None:

@@ -65,6 +65,37 @@ def test_mixed_batch_bit_exact(ising, rng):
     b.close()
 
 
+def _packed_instances():
+    """Layered models the packed kernel takes (M in {8, 16, 32}), several
+    lattices and ragged ladders: a batch of them runs as persistent waves."""
+    specs = [(8, 16, 8), (8, 32, 13), (9, 16, 32), (10, 16, 20), (12, 8, 5), (16, 16, 9), (6, 8, 3),
+             (11, 32, 24), (8, 16, 1), (6, 16, 40), (14, 32, 7)]
+    return [(W.layered_graph(L, M, graph_seed=800 + k), W.geometric_betas(R, 0.1, 3.0), 7000 + 13 * k)
+            for k, (L, M, R) in enumerate(specs)]
+
+
+@pytest.mark.parametrize("rng", ["philox", "mt19937"])
+@pytest.mark.parametrize("per_sweep", [False, True])
+def test_packed_batch_bit_exact(ising, rng, per_sweep):
+    """Persistent waves (one cooperative launch per wave and call, PT fused per
+    instance) and the per-sweep launches of the same batch: every instance
+    bit-exact against its oracle run, over calls with PT after every sweep,
+    every second sweep (with a remainder) and none."""
+    inst = _packed_instances()
+    b = ising.Batch(inst, rng=rng, field_bits=16, per_sweep=per_sweep)
+    kinds = {(b.info(k)["resident"], b.info(k)["fast_kernel"]) for k in range(len(inst))}
+    if not per_sweep:
+        assert kinds == {(1, 4)}, kinds
+    else:
+        assert all(kind != 4 for _, kind in kinds), kinds
+    schedule = [(7, 1), (5, 2), (3, 0), (7, 1)]
+    for n, every in schedule:
+        b.run(n, every)
+    for k in range(len(inst)):
+        _check_instance(b, k, inst[k], rng, schedule)
+    b.close()
+
+
 def test_autotune_changes_speed_not_results(ising):
     inst = _mixed_instances()[:8]
     b = ising.Batch(inst, rng="philox", field_bits=16)
@@ -78,14 +109,16 @@ def test_autotune_changes_speed_not_results(ising):
 
 def test_full_ragged_workload_sampled_parity(ising):
     """4096 instances (spin counts log-uniform in 2^11..2^15, 8..64 replicas),
-    100 sweeps + PT in one recorded graph; bit-exact on 64 sampled instances
-    plus the smallest and the largest, fields/energies consistent elsewhere."""
+    100 sweeps + PT per instance, in persistent waves; bit-exact on 64
+    sampled instances plus the smallest and the largest, fields/energies
+    consistent elsewhere."""
     descs = W.ragged_instances(4096)
     built = [W.build_instance(d) for d in descs]
     inst = [(x["graph"], x["betas"], x["seed"]) for x in built]
     b = ising.Batch(inst, rng="philox", field_bits=16)
     b.autotune()
     b.run(100, 1)
+    assert all(b.info(k)["fast_kernel"] == 4 for k in range(0, len(inst), 97))  # persistent waves
     sizes = [x["graph"].n for x in built]
     rng = np.random.default_rng(11)
     sample = set(rng.choice(len(inst), 64, replace=False).tolist())
