@@ -2348,6 +2348,7 @@ struct ising_batch_s {
             int n_gen;
         };
         std::vector<Launch> launches;
+        bool no_graph = false;  // recording was refused: launched directly
     };
     std::map<std::pair<long long, int>, Run> runs;
     // persistent batches of the packed kernel (waves of whole, co-resident instances)
@@ -2638,7 +2639,7 @@ int32_t packed_batch_build(ising_batch_s* b, long long n, int swap_every, ising_
     return ISING_OK;
 }
 
-int32_t packed_batch_launch(ising_batch_s* b, const ising_batch_s::Run& run)
+int32_t packed_batch_enqueue(ising_batch_s* b, const ising_batch_s::Run& run, cudaStream_t st)
 {
     const bool mt = b->inst[0]->rng == ISING_RNG_MT19937;
     for (const auto& L : run.launches) {
@@ -2648,20 +2649,48 @@ int32_t packed_batch_launch(ising_batch_s* b, const ising_batch_s::Run& run)
             int max_S = 0;
             for (int i : w.ids)
                 max_S = std::max(max_S, b->inst[i]->S);
-            e = launch_mt_gen_batch(L.gen, L.gen_items, L.n_gen, max_S, b->stream);
+            e = launch_mt_gen_batch(L.gen, L.gen_items, L.n_gen, max_S, st);
         }
         if (e == cudaSuccess)
-            e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * b->inst.size(), b->stream);
+            e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * b->inst.size(), st);
         if (e == cudaSuccess)
             e = launch_packed_batch(L.args, L.items, L.n_items, mt ? 0 : 1, w.rmax,
-                                    w.T + (mt ? 32 * kPackedGenWarps : 0), w.smem, b->stream);
+                                    w.T + (mt ? 32 * kPackedGenWarps : 0), w.smem, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "persistent batch launch");
-        for (int i : w.ids) {
+    }
+    return ISING_OK;
+}
+
+// A call's launches, waves one after another, recorded once into a CUDA
+// graph (on the batch's private capture stream) and replayed; if recording
+// is refused the launches are enqueued directly.
+int32_t packed_batch_launch(ising_batch_s* b, ising_batch_s::Run& run)
+{
+    if (!run.exec && !run.no_graph) {
+        if (!b->cap)
+            CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        int32_t rc = e == cudaSuccess ? packed_batch_enqueue(b, run, b->cap) : ISING_OK;
+        const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(b->cap, &graph) : e;
+        if (!rc && e2 == cudaSuccess && graph && cudaGraphInstantiate(&run.exec, graph, 0) != cudaSuccess)
+            run.exec = nullptr;
+        if (graph)
+            cudaGraphDestroy(graph);
+        cudaGetLastError();  // a refused capture leaves no sticky state
+        if (!run.exec)
+            run.no_graph = true;
+    }
+    if (run.exec)
+        CK(cudaGraphLaunch(run.exec, b->stream));
+    else if (int32_t rc = packed_batch_enqueue(b, run, b->stream))
+        return rc;
+    for (const auto& L : run.launches)
+        for (int i : b->waves[L.wave].ids) {
             b->inst[i]->n_launches += 1 + (L.n_gen > 0 ? 1 : 0);
             b->inst[i]->n_sweep_launches += 1;
         }
-    }
     return ISING_OK;
 }
 
