@@ -88,7 +88,7 @@ cudaError_t launch_fast(const SweepArgs& a, int field_bits, int cmax, int thread
     if (!fn)
         return cudaErrorInvalidValue;
     if (variant == 5)  // the packed kernel's blocks: its sweep threads and the generator warps
-        threads = a.sweep_threads + (a.rng == 0 ? 32 * a.gen : 0);
+        threads = a.sweep_threads + 32 * a.gen;
     SweepArgs copy = a;
     void* args[] = {&copy};
     if (cooperative)

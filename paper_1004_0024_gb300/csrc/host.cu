@@ -711,10 +711,10 @@ SweepArgs base_args(ising_s* g);
 
 // The register-resident kernel keeps up to 8 columns per thread; it needs
 // M <= 32, the slice tables in shared memory and spatial degree <= 255.
-// The packed kernel generates its MT19937 sweep words itself (an extra warp
-// per block, two-sweep word buffer); the separate generator then only makes
-// the swap stream's words.
-bool packed_gen(const ising_s* g) { return g->use_packed && g->rng == ISING_RNG_MT19937; }
+// The packed kernel generates its sweep words itself (two extra warps per
+// block, two-sweep word buffer: MT19937 streams or Philox blocks); the
+// separate generator then only makes MT19937's swap-stream words.
+bool packed_gen(const ising_s* g) { return g->use_packed; }
 
 int kernel_variant(const ising_s* g)
 {
@@ -763,7 +763,7 @@ bool choose_packed(ising_s* g)
     }
     SweepArgs a = base_args(g);
     a.G = 1;
-    a.gen = g->rng == ISING_RNG_MT19937 ? kPackedGenWarps : 0;
+    a.gen = kPackedGenWarps;
     const size_t plain = packed_smem_bytes(a, T);
     a.swap_every = 1;
     const size_t fused = packed_smem_bytes(a, T);
@@ -1118,10 +1118,10 @@ long long words_cap(ising_s* g, long long n)
 
 int32_t ensure_buffers(ising_s* g, long long cap_sweeps, long long cap_passes)
 {
-    if (g->rng != ISING_RNG_MT19937)
-        return ISING_OK;
     if (packed_gen(g))
-        cap_sweeps = 2;  // the sweep kernel's two-sweep word buffer
+        cap_sweeps = 2;  // the sweep kernel's two-sweep word buffer (both generators)
+    else if (g->rng != ISING_RNG_MT19937)
+        return ISING_OK;
     if (cap_sweeps > g->wbuf_cap) {
         big_free(g->d_wbuf);
         // fully written by the generator before any sweep reads it: no zero fill
@@ -1130,7 +1130,7 @@ int32_t ensure_buffers(ising_s* g, long long cap_sweeps, long long cap_passes)
             return rc;
         g->wbuf_cap = cap_sweeps;
     }
-    if (cap_passes > g->swbuf_cap) {
+    if (g->rng == ISING_RNG_MT19937 && cap_passes > g->swbuf_cap) {
         dfree(g->d_swbuf);
         int32_t rc = dalloc(&g->d_swbuf, size_t(cap_passes) * std::max(g->maxpairs, 1));
         if (rc)
@@ -2488,7 +2488,7 @@ bool packed_batch_setup(ising_batch_s* b)
 {
     if (!g_coop)
         return false;
-    const int gen = b->inst.empty() || b->inst[0]->rng != ISING_RNG_MT19937 ? 0 : kPackedGenWarps;
+    const int gen = kPackedGenWarps;  // the generator warps (both generators)
     std::map<std::pair<int, int>, std::vector<int>> by_T;  // (sweep threads, rounds)
     std::vector<size_t> smem(b->inst.size(), 0);
     for (int i = 0; i < int(b->inst.size()); ++i) {
@@ -2579,15 +2579,14 @@ int32_t packed_batch_build(ising_batch_s* b, long long n, int swap_every, ising_
             int max_S = 0;
             for (int j = 0; j < int(w.ids.size()); ++j) {
                 ising_s* g = b->inst[w.ids[j]];
-                if (mt) {
-                    // the sweep kernel's two-sweep word buffer; the swap stream's words
-                    if (g->wbuf_cap < 2) {
-                        big_free(g->d_wbuf);
-                        int32_t rc = big_alloc(&g->d_wbuf, size_t(2) * g->R * g->S * g->Mp);
-                        if (rc)
-                            return rc;
-                        g->wbuf_cap = 2;
-                    }
+                if (g->wbuf_cap < 2) {  // the sweep kernel's two-sweep word buffer
+                    big_free(g->d_wbuf);
+                    int32_t rc = big_alloc(&g->d_wbuf, size_t(2) * g->R * g->S * g->Mp);
+                    if (rc)
+                        return rc;
+                    g->wbuf_cap = 2;
+                }
+                if (mt) {  // the swap stream's words
                     if (passes > g->swbuf_cap) {
                         dfree(g->d_swbuf);
                         int32_t rc = dalloc(&g->d_swbuf, size_t(passes) * std::max(g->maxpairs, 1));
@@ -2608,7 +2607,7 @@ int32_t packed_batch_build(ising_batch_s* b, long long n, int swap_every, ising_
                 a.swap_every = part == 0 ? int(every) : 0;
                 a.inst_blocks = g->R;
                 a.sweep_threads = w.T;
-                a.gen = mt ? kPackedGenWarps : 0;
+                a.gen = kPackedGenWarps;
                 a.wbuf = g->d_wbuf;
                 a.swbuf = g->d_swbuf;
                 a.gridbar = b->d_bar + w.ids[j];
@@ -2654,8 +2653,8 @@ int32_t packed_batch_enqueue(ising_batch_s* b, const ising_batch_s::Run& run, cu
         if (e == cudaSuccess)
             e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * b->inst.size(), st);
         if (e == cudaSuccess)
-            e = launch_packed_batch(L.args, L.items, L.n_items, mt ? 0 : 1, w.rmax,
-                                    w.T + (mt ? 32 * kPackedGenWarps : 0), w.smem, st);
+            e = launch_packed_batch(L.args, L.items, L.n_items, mt ? 0 : 1, w.rmax, w.T + 32 * kPackedGenWarps,
+                                    w.smem, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "persistent batch launch");
     }

@@ -104,6 +104,7 @@ extern "C" int32_t ising_run_noalloc(ising_t h, int64_t n, int32_t swap_every)
     a.E_pub = reinterpret_cast<int*>(scratch + kScratchHeader);
     a.wbuf = nullptr;
     a.swbuf = nullptr;
+    a.gen = 0;  // no word buffer: the slots compute their Philox words themselves
     cudaStream_t st = fl.stream;
     const long long every = swap_every > 0 ? swap_every : 0;
     long long done = 0;

@@ -107,7 +107,7 @@ __host__ __device__ inline PackedLayout packed_layout(const SweepArgs& a, int th
         L.slot = o; o += r16(4u * uint32_t(a.R));
         L.temp = o; o += r16(4u * uint32_t(a.R));
     }
-    if (a.gen) {  // the generator warp's stream ring and four staged slices
+    if (a.gen && a.rng == 0) {  // the MT19937 generator's stream ring and four staged slices
         L.gring = o; o += 4u * kMtRing;
         L.gstg = o;  o += 16u * uint32_t(a.S);
     }
@@ -152,7 +152,11 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     // T sweep threads (threads 0 .. T-1), then with the MT19937 generator
     // a.gen more warps (glane numbers their threads)
     const int T = a.sweep_threads, NT = blockDim.x, tid = threadIdx.x;
-    const bool gen = RNG == 0 && a.gen != 0;
+    // the generator warps make the words of both generators (Philox: one call
+    // per column and 4-slice block); without them Philox words are made by
+    // the slots themselves
+    const bool gen = a.gen != 0;
+    const bool ring_words = RNG == 0 || gen;  // words come from the word buffer
     const bool is_gen = gen && tid >= T;
     const int st = tid;
     const int glane = tid - T, GL = NT - T;  // generator threads
@@ -407,15 +411,28 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             gw += uint32_t(group);
         }
     };
+    // Philox: the blocks of every column for sweep id `sid`, 16 bytes each
+    auto gen_sweep_philox = [&](uint32_t* wdst, uint32_t sid) {
+        for (int p = glane; p < S; p += GL) {
+            const int q = int(desc[p * kDescWords] >> 16);
+            uint4* dst = reinterpret_cast<uint4*>(wdst + (size_t(r) * S + p) * a.Mp);
+            for (int b = 0; b < nrb; ++b)
+                dst[b] = philox4x32_10(make_uint4(uint32_t(b * S + q), sid, a.inst, 0u), a.seed, uint32_t(r));
+        }
+    };
     // the half of the two-sweep buffer for sweep sw (the handle's own word buffer)
     auto gen_buf = [&](int sw) { return const_cast<uint32_t*>(a.wbuf) + size_t(sw & 1) * a.wbuf_sweep_stride; };
     if (is_gen) {
-        for (int i = glane; i < kMtRing; i += GL)
-            gring[i] = a.mtring[size_t(r) * kMtRing + i];
-        gw = uint32_t(a.mtpos[r]);
-        gen_sync();
-        if (a.nsweeps > 0)
-            gen_sweep(gen_buf(0));
+        if (RNG == 0) {
+            for (int i = glane; i < kMtRing; i += GL)
+                gring[i] = a.mtring[size_t(r) * kMtRing + i];
+            gw = uint32_t(a.mtpos[r]);
+            gen_sync();
+            if (a.nsweeps > 0)
+                gen_sweep(gen_buf(0));
+        } else if (a.nsweeps > 0) {
+            gen_sweep_philox(gen_buf(0), uint32_t(sweep0));
+        }
     }
 
     if (!is_gen)
@@ -423,18 +440,21 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     __syncthreads();  // the first sweep's words are ready
     for (int sw = 0; sw < a.nsweeps; ++sw) {
         const uint32_t sid = uint32_t(sweep0 + sw);
-        const uint32_t* wsw = (RNG == 0) ? (gen ? gen_buf(sw) : a.wbuf + size_t(sw) * a.wbuf_sweep_stride)
-                                         : nullptr;
+        const uint32_t* wsw = gen ? gen_buf(sw) : (RNG == 0 ? a.wbuf + size_t(sw) * a.wbuf_sweep_stride : nullptr);
         if (is_gen) {
             // the generator: the next sweep's words while this one runs, handed over
             // at the sweep's end barrier
             __syncthreads();
-            if (sw + 1 < a.nsweeps)
-                gen_sweep(gen_buf(sw + 1));
+            if (sw + 1 < a.nsweeps) {
+                if (RNG == 0)
+                    gen_sweep(gen_buf(sw + 1));
+                else
+                    gen_sweep_philox(gen_buf(sw + 1), uint32_t(sweep0 + sw + 1));
+            }
             __syncthreads();
         } else {
         // the blocks that start in levels [0, 8)
-        if (RNG == 0) {
+        if (ring_words) {
             if (sw == 0) {  // later sweeps: requested at the end of the previous one
                 request_words(wsw, -8);
                 request_words(wsw, -4);
@@ -450,7 +470,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         for (int l = 0; l < a.D; ++l) {
             const int phase = l & 3;
             if (phase == 0) {
-                if (RNG == 0)
+                if (ring_words)
                     cp_async_wait_group<1>();  // the copies requested 8 levels ago have landed
                 // a slot takes up its next column at the last multiple of 4 before
                 // the column's start (the previous one has ended by then: the host
@@ -516,7 +536,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             }
             }  // any
             // the word stream
-            if (RNG == 0) {
+            if (ring_words) {
                 if (phase == 0) {
                     request_words(wsw, l);
                     cp_async_commit();
@@ -552,7 +572,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         // slots back at their first column; MT19937: the next sweep's first
         // blocks requested, in flight during PT
         restart(true);
-        if (RNG == 0 && sw + 1 < a.nsweeps) {
+        if (ring_words && sw + 1 < a.nsweeps) {
             const uint32_t* wn = gen ? gen_buf(sw + 1) : wsw + a.wbuf_sweep_stride;
             request_words(wn, -8);
             request_words(wn, -4);
@@ -609,9 +629,9 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             ++npass;
         }
     }
-    if (RNG == 0)
+    if (ring_words)
         asm volatile("cp.async.wait_all;" ::: "memory");
-    if (is_gen) {  // the stream as it now stands
+    if (RNG == 0 && is_gen) {  // the stream as it now stands
         gen_sync();
         for (int i = glane; i < kMtRing; i += GL)
             a.mtring[size_t(r) * kMtRing + i] = gring[i];
