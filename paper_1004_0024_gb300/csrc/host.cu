@@ -658,34 +658,40 @@ int32_t extract_slices(ising_s* g)
     return ISING_OK;
 }
 
-// The packed kernel's table buffer: column descriptors [S][8] (lev0 | site <<
-// 16, jtau, six neighbour entries pos << 16 | (uint16) J, missing ones
-// padded with the column itself and J = 0), positions [S], slot offsets
-// [nslots + 1], slot columns [S], and per position the constant part of the
-// spatial field h_q - sum_j J_qj [S], each part padded to 16 bytes.  A
-// neighbour entry is pos << 16 | (uint8) J << 8 | (uint8) dlev with dlev =
-// lev0(p) - lev0(neighbour) clamped to [-128, 127].
+// The packed kernel's table buffer: column descriptors [S][16] (lev0 | site
+// << 16, byte offset 4 p of the column's own word, 2 Jtau, the field constant
+// h_q - sum_j J_qj - 2 Jtau, six byte offsets of the spatial neighbours'
+// words, their six 2 J; missing neighbours padded with the column itself and
+// J = 0), positions [S], slot offsets [nslots + 1], slot columns [S], each
+// part padded to 16 bytes.
 std::vector<uint32_t> packed_tables(const ising_s* g)
 {
     using isg::packed_detail::kDescWords;
+    using isg::packed_detail::kMaxDeg;
     const int S = g->S;
     auto pad4 = [](size_t n) { return (n + 3) & ~size_t(3); };
     std::vector<uint32_t> pk(isg::packed_detail::packed_table_bytes(S, g->nslots) / 4, 0u);
     for (int p = 0; p < S; ++p) {
         uint32_t* d = pk.data() + size_t(p) * kDescWords;
+        const int jt2 = 2 * g->jtau[p];
+        long long c = g->h[g->site[p]] - jt2;
         d[0] = uint32_t(g->lev0p[p]) | (uint32_t(g->site[p]) << 16);
-        d[1] = uint32_t(g->jtau[p]);
+        d[1] = 4u * uint32_t(p);
+        d[2] = uint32_t(jt2);
         const int e0 = g->nbr_off[p], deg = g->nbr_off[p + 1] - e0;
-        for (int e = 0; e < isg::packed_detail::kMaxDeg; ++e) {
+        for (int e = 0; e < kMaxDeg; ++e) {
             if (e >= deg) {
-                d[2 + e] = uint32_t(p) << 16;
+                d[4 + e] = 4u * uint32_t(p);
+                d[10 + e] = 0u;
                 continue;
             }
             const uint32_t en = g->nbr[e0 + e];
             const int pj = int(en >> 16), J = int(int16_t(en & 0xFFFFu));
-            const int dlev = std::max(-128, std::min(127, g->lev0p[p] - g->lev0p[pj]));
-            d[2 + e] = (uint32_t(pj) << 16) | ((uint32_t(J) & 0xFFu) << 8) | (uint32_t(dlev) & 0xFFu);
+            c -= J;
+            d[4 + e] = 4u * uint32_t(pj);
+            d[10 + e] = uint32_t(2 * J);
         }
+        d[3] = uint32_t(int32_t(c));
     }
     size_t o = size_t(S) * kDescWords;
     for (int q = 0; q < S; ++q)
@@ -696,13 +702,6 @@ std::vector<uint32_t> packed_tables(const ising_s* g)
     o += pad4(size_t(g->nslots) + 1);
     for (int i = 0; i < S; ++i)
         pk[o + i] = uint32_t(g->slot_col_v[i]);
-    o += pad4(S);
-    for (int p = 0; p < S; ++p) {
-        long long c = g->h[g->site[p]];
-        for (int e = g->nbr_off[p]; e < g->nbr_off[p + 1]; ++e)
-            c -= int16_t(g->nbr[e] & 0xFFFFu);
-        pk[o + p] = uint32_t(int32_t(c));
-    }
     return pk;
 }
 

@@ -41,16 +41,17 @@
 // The Trotter part of the field, Jtau (s_{t-1} + s_{t+1}), comes from the
 // owner's register bits.
 //
-// Random words go through a ring of four 4-word blocks per slot in shared
-// memory, word w of ring entry j of slot sl at (4 j + w) NSP + sl (a lane's
-// word reads are conflict-free).  MT19937 words come from the pre-generated
-// word buffer by 4-byte cp.async copies (not waited for by the level
-// barrier), one commit group every fourth level; at a level divisible by 4
-// the thread waits until at most one group is pending, i.e. for the copies
-// requested 8 levels earlier.  Philox blocks are computed by the slot, the
+// Random words go through a ring of 16 levels per slot in shared memory: the
+// word of the slot's item at level l sits at (l mod 16) NSP + sl, so a
+// level's reads are conflict-free and their address is the same offset for
+// every slot.  Words come from the word buffer by 4-byte cp.async copies (not
+// waited for by the level barrier), one commit group every fourth level; at
+// a level divisible by 4 the thread waits until at most one group is
+// pending, i.e. for the copies requested 8 levels earlier (the ring then
+// holds levels l .. l + 15: the four being read and up to 11 in flight).
+// Without the generator warps, Philox blocks are computed by the slot, the
 // ten rounds spread over four levels (3, 3, 3, 1), and stored after the
-// fourth.  A block is written after the last item that reads the ring entry
-// it replaces.
+// fourth.  An entry is written after the last item that reads it.
 //
 // MT19937 words are generated inside the kernel: after its T sweep threads a
 // block has `gen` more warps (two), which advance the replica's stream (its
@@ -66,6 +67,7 @@
 // barrier, every block runs the same PT pass on its own copy of the labels).
 #pragma once
 #include <climits>
+#include <type_traits>
 
 #include "fast_impl.cuh"
 
@@ -76,14 +78,16 @@ using fast_detail::grid_sync;
 
 constexpr int kMaxDeg = 6;
 constexpr int kGenWarps = 2;  // MT19937 generator warps per block
-// descriptor words: [0] lev0 | site << 16, [1] jtau, [2..7] one per spatial
-// neighbour: pos << 16 | (uint8) J << 8 | (uint8) dlev, dlev = lev0(q) -
-// lev0(neighbour) clamped to [-128, 127] (missing neighbours: the column
-// itself with J = 0)
-constexpr int kDescWords = 8;
+// descriptor words of the column at position p: [0] lev0 | site << 16,
+// [1] byte offset of its column word (4 p), [2] 2 Jtau, [3] the field constant
+// h_q - sum_j J_qj - 2 Jtau, [4..9] byte offsets of the spatial neighbours'
+// column words, [10..15] their 2 J (missing neighbours: the column itself
+// with J = 0).  The kernel turns the byte offsets into shared-memory
+// addresses once per launch.
+constexpr int kDescWords = 16;
 
 struct PackedLayout {
-    uint32_t bar, desc, pos, soff, scol, cq, colw, stage, thr, eacc, slot, temp, gring, gstg, total;
+    uint32_t bar, desc, pos, soff, scol, colw, stage, thr, eacc, slot, temp, gring, gstg, total;
 };
 
 // Shared-memory layout; the table part (desc .. scol) is one bulk copy of the
@@ -97,9 +101,8 @@ __host__ __device__ inline PackedLayout packed_layout(const SweepArgs& a, int th
     L.pos = o;   o += r16(4u * uint32_t(a.S));
     L.soff = o;  o += r16(4u * uint32_t(a.nslots + 1));
     L.scol = o;  o += r16(4u * uint32_t(a.S));
-    L.cq = o;    o += r16(4u * uint32_t(a.S));
     L.colw = o;  o += r16(4u * uint32_t(a.S));
-    L.stage = o;  // the word ring: 4 entries x 4 words x slots rounded up to whole rounds
+    L.stage = o;  // the word ring: 16 levels x slots rounded up to whole rounds
     o += 64u * uint32_t((a.nslots + threads - 1) / threads) * uint32_t(threads);
     L.thr = o;   o += r16(4u * uint32_t(a.K));
     L.eacc = o;  o += 16;
@@ -115,12 +118,11 @@ __host__ __device__ inline PackedLayout packed_layout(const SweepArgs& a, int th
     return L;
 }
 
-// bytes of the table part (desc, pos, slot offsets, slot columns, the
-// constant c_p = h_q - sum_j J_qj of the column at each position)
+// bytes of the table part (desc, pos, slot offsets, slot columns)
 __host__ __device__ inline uint32_t packed_table_bytes(int S, int nslots)
 {
     return 4u * kDescWords * uint32_t(S) + r16(4u * uint32_t(S)) + r16(4u * uint32_t(nslots + 1)) +
-           2u * r16(4u * uint32_t(S));
+           r16(4u * uint32_t(S));
 }
 
 // 16-byte asynchronous copy without its own commit group.
@@ -164,11 +166,10 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     const int S = a.S, M = a.M, N = a.N, K = a.K, R = a.R;
     const int r = blk;  // one replica per block
-    const uint32_t* desc = reinterpret_cast<const uint32_t*>(smem + L.desc);
+    uint32_t* desc = reinterpret_cast<uint32_t*>(smem + L.desc);
     const int* pos = reinterpret_cast<const int*>(smem + L.pos);
     const int* soff = reinterpret_cast<const int*>(smem + L.soff);
     const int* scol = reinterpret_cast<const int*>(smem + L.scol);
-    const int* cqt = reinterpret_cast<const int*>(smem + L.cq);
     uint32_t* colw = reinterpret_cast<uint32_t*>(smem + L.colw);
     uint32_t* stage = reinterpret_cast<uint32_t*>(smem + L.stage);
     uint32_t* thr_s = reinterpret_cast<uint32_t*>(smem + L.thr);
@@ -202,10 +203,17 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     }
     mbar_wait(bar, 0, kWaitPolls);
 
-    // ---- column bits from the spins (the fields follow from them)
+    // ---- column bits from the spins (the fields follow from them); the
+    // descriptors' byte offsets become shared-memory addresses
+    const uint32_t colw_s = smem_u32(colw), stage_s = smem_u32(stage);
     const int8_t* spg = a.spins + size_t(r) * N;
     for (int p = tid; p < S; p += NT) {
-        const int q = int(desc[p * kDescWords] >> 16);
+        uint32_t* d = desc + p * kDescWords;
+        d[1] += colw_s;
+#pragma unroll
+        for (int e = 0; e < kMaxDeg; ++e)
+            d[4 + e] += colw_s;
+        const int q = int(d[0] >> 16);
         uint32_t b = 0u;
         for (int t = 0; t < M; ++t)
             b |= (spg[size_t(t) * S + q] > 0 ? 1u : 0u) << t;
@@ -227,45 +235,53 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     const unsigned long long sweep0 = a.counters[0];
     const unsigned long long pass0 = a.counters[1];
     const int NSP = ((a.nslots + T - 1) / T) * T;  // slots rounded up to whole rounds
-    const uint32_t colw_s = smem_u32(colw), stage_s = smem_u32(stage);
+    const uint32_t sbase = stage_s + 4u * uint32_t(st);  // the slot's ring column (round 0)
+    const uint32_t lstride = 4u * uint32_t(NSP);          // bytes per ring level
+    // ring column of each round; rounds past the last slot (always idle)
+    // read round 0's
+    uint32_t sbc[RMAX];
+#pragma unroll
+    for (int c = 0; c < RMAX; ++c)
+        sbc[c] = sbase + (c * T < NSP ? 4u * uint32_t(c * T) : 0u);
     constexpr int kNone = INT_MAX / 2;
     int npass = 0;
-    int dE = 0;
+    int dk = 0;  // sum of s_t f over the flips: the energy change is 2 dk
 
     // per slot (round c): the current column (busy, or the next to become
     // busy) and its successor in the slot's list
-    int lv[RMAX] = {}, kk[RMAX] = {}, ke[RMAX] = {}, pp[RMAX] = {}, qq[RMAX] = {}, jt2[RMAX] = {},
-        rs[RMAX] = {};
+    int lv[RMAX] = {}, kk[RMAX] = {}, ke[RMAX] = {}, pp[RMAX] = {}, qq[RMAX] = {}, jt2[RMAX] = {};
     int pn[RMAX] = {}, qn[RMAX] = {}, ln[RMAX] = {};
-    int cq[RMAX];
+    int cq[RMAX];       // h_q - sum_j J_qj - 2 Jtau
+    uint32_t sa[RMAX];  // shared address of the column's own word
+    // slice mask of the level: bit t of the column (t = level - lev0, with
+    // the word's copies for M < 32), rotated by one each level
+    uint32_t mrot[RMAX] = {};
     uint32_t bits[RMAX], nw[RMAX][kMaxDeg];  // nw: shared address of each neighbour's column word
     int nj[RMAX][kMaxDeg];                    // 2 J of each neighbour
-    int rq[RMAX];  // 4 * (ring entry of the column's block 0)
-    // Philox block in progress: counter, keys, ring entry, whether any
-    uint4 pc[RMAX];
+    // request cursor: the slot's next block to fetch (block xb of the column
+    // at position xcol, site xsite, xk in the slot's list), its first level xx
+    int xx[RMAX], xb[RMAX] = {}, xcol[RMAX] = {}, xsite[RMAX] = {}, xk[RMAX] = {};
+    // Philox block in progress: counter, keys, first level, whether any
+    uint4 pc[RMAX] = {};
     uint32_t pk0[RMAX], pk1[RMAX];
-    int pring[RMAX];
+    int px[RMAX];
     bool pgo[RMAX];
 
-    // take up column p at level s (a multiple of 4, before the level's items)
-    auto load_col = [&](int c, int p, int s) {
-        const uint4 d0 = *reinterpret_cast<const uint4*>(desc + p * kDescWords);
-        const uint4 d1 = *reinterpret_cast<const uint4*>(desc + p * kDescWords + 4);
+    // take up column p at level l (before the first of its items)
+    auto load_col = [&](int c, int p, int l) {
+        const uint4* d = reinterpret_cast<const uint4*>(desc + p * kDescWords);
+        const uint4 d0 = d[0], d1 = d[1], d2 = d[2], d3 = d[3];
         lv[c] = int(d0.x & 0xFFFFu);
         qq[c] = int(d0.x >> 16);
-        jt2[c] = 2 * int(d0.y);
-        const uint32_t e6[kMaxDeg] = {d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-        (void)s;
-#pragma unroll
-        for (int e = 0; e < kMaxDeg; ++e) {
-            nw[c][e] = colw_s + 4u * (e6[e] >> 16);
-            nj[c][e] = 2 * int(int8_t((e6[e] >> 8) & 0xFFu));
-        }
+        sa[c] = d0.y;
+        jt2[c] = int(d0.z);
+        cq[c] = int(d0.w);
+        nw[c][0] = d1.x; nw[c][1] = d1.y; nw[c][2] = d1.z; nw[c][3] = d1.w; nw[c][4] = d2.x; nw[c][5] = d2.y;
+        nj[c][0] = int(d2.z); nj[c][1] = int(d2.w); nj[c][2] = int(d3.x);
+        nj[c][3] = int(d3.y); nj[c][4] = int(d3.z); nj[c][5] = int(d3.w);
         pp[c] = p;
-        cq[c] = cqt[p];
         bits[c] = colw[p] * rep;
-        rs[c] = (kk[c] * nrb) & 3;
-        rq[c] = 4 * rs[c];
+        mrot[c] = __funnelshift_r(rep, rep, uint32_t(lv[c] - l));
     };
     auto set_next = [&](int c) {
         pn[c] = kk[c] + 1 < ke[c] ? scol[kk[c] + 1] : -1;
@@ -276,94 +292,107 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     // slots restart at their first column (every column word is current:
     // owners store theirs at each flip; after a sweep's last level barrier
     // every thread sees them)
-    auto restart = [&](bool) {
+    auto restart = [&]() {
 #pragma unroll
         for (int c = 0; c < RMAX; ++c) {
             const int sl = st + c * T;
             lv[c] = kNone;
             kk[c] = ke[c] = 0;
-            pp[c] = qq[c] = jt2[c] = rs[c] = 0;
+            pp[c] = qq[c] = jt2[c] = 0;
             pn[c] = -1;
             qn[c] = 0;
             ln[c] = kNone;
             cq[c] = 0;
+            sa[c] = colw_s;
             bits[c] = 0u;
-            rq[c] = 0;
 #pragma unroll
             for (int e = 0; e < kMaxDeg; ++e) {
                 nw[c][e] = colw_s;
                 nj[c][e] = 0;
             }
             pgo[c] = false;
-            pring[c] = 0;
+            px[c] = 0;
+            xx[c] = kNone;
+            xb[c] = xcol[c] = xsite[c] = xk[c] = 0;
             if (sl < a.nslots) {
                 kk[c] = soff[sl];
                 ke[c] = soff[sl + 1];
                 if (kk[c] < ke[c]) {
-                    load_col(c, scol[kk[c]], 0);  // at a sweep's start no window has closed
+                    load_col(c, scol[kk[c]], 0);
                     set_next(c);
+                    xx[c] = lv[c];
+                    xcol[c] = pp[c];
+                    xsite[c] = qq[c];
+                    xk[c] = kk[c];
                 }
             }
         }
     };
-    // The block of round c's stream that starts in levels [l + 8, l + 12):
-    // of the current column, else of the next one (at most one of them).
-    auto candidate = [&](int c, int l, int& col, int& b, int& ring, int& site) -> bool {
-        const int b1 = (l + 8 - lv[c] + 3) >> 2;
-        if (lv[c] < kNone && b1 >= 0 && b1 < nrb) {
-            col = pp[c];
-            b = b1;
-            ring = (rs[c] + b1) & 3;
-            site = qq[c];
-            return true;
+    // Round c's next block if it starts in levels [l + 8, l + 12) (blocks are
+    // fetched in order, one at most per window: a column's blocks start 4
+    // levels apart and the slot's next column at least 4 after its last one),
+    // and the cursor moved past it.
+    auto next_block = [&](int c, int l, int& col, int& b, int& x, int& site) -> bool {
+        if (xx[c] >= l + 12)
+            return false;
+        col = xcol[c];
+        b = xb[c];
+        x = xx[c];
+        site = xsite[c];
+        if (++xb[c] < nrb) {
+            xx[c] += 4;
+        } else if (++xk[c] < ke[c]) {
+            xcol[c] = scol[xk[c]];
+            const uint32_t d0 = desc[xcol[c] * kDescWords];
+            xx[c] = int(d0 & 0xFFFFu);
+            xsite[c] = int(d0 >> 16);
+            xb[c] = 0;
+        } else {
+            xx[c] = kNone;
         }
-        const int b2 = (l + 8 - ln[c] + 3) >> 2;
-        if (ln[c] < kNone && b2 >= 0 && b2 < nrb) {
-            col = pn[c];
-            b = b2;
-            ring = (rs[c] + nrb + b2) & 3;
-            site = qn[c];
-            return true;
-        }
-        return false;
+        return true;
     };
-    // MT19937: 4-byte copies of the candidate block of every round into its ring entry
+    // ring address of round c's word for level x
+    auto ring_addr = [&](int c, int x) {
+        return sbase + 4u * uint32_t(c * T) + uint32_t(x & 15) * lstride;
+    };
+    // 4-byte copies of the next block of every round into its ring levels
     auto request_words = [&](const uint32_t* wsw, int l) {
 #pragma unroll
         for (int c = 0; c < RMAX; ++c) {
-            int col = 0, b = 0, ring = 0, site = 0;
-            if (candidate(c, l, col, b, ring, site)) {
+            int col = 0, b = 0, x = 0, site = 0;
+            if (next_block(c, l, col, b, x, site)) {
                 const uint32_t* src = wsw + (size_t(r) * S + col) * a.Mp + 4 * b;
-                const uint32_t dst = stage_s + 4u * uint32_t((4 * ring) * NSP + st + c * T);
 #pragma unroll
                 for (int w = 0; w < 4; ++w)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * uint32_t(w * NSP)),
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(ring_addr(c, x + w)),
                                  "l"(src + w)
                                  : "memory");
             }
         }
     };
-    // Philox: start (and with `full`, finish and store) the candidate blocks
+    auto philox_store = [&](int c) {
+        const uint32_t v[4] = {pc[c].x, pc[c].y, pc[c].z, pc[c].w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            asm volatile("st.shared.u32 [%0], %1;" ::"r"(ring_addr(c, px[c] + w)), "r"(v[w]) : "memory");
+        pgo[c] = false;
+    };
+    // Philox: start (and with `full`, finish and store) the next blocks
     auto philox_start = [&](uint32_t sid, int l, bool full) {
 #pragma unroll
         for (int c = 0; c < RMAX; ++c) {
-            int col = 0, b = 0, ring = 0, site = 0;
-            pgo[c] = candidate(c, l, col, b, ring, site);
+            int col = 0, b = 0, x = 0, site = 0;
+            pgo[c] = next_block(c, l, col, b, x, site);
             if (pgo[c]) {
                 pc[c] = make_uint4(uint32_t(b * S + site), sid, a.inst, 0u);
                 pk0[c] = a.seed;
                 pk1[c] = uint32_t(r);
-                pring[c] = ring;
+                px[c] = x;
                 for (int i = 0; i < (full ? 10 : 3); ++i)
                     philox_round(pc[c], pk0[c], pk1[c]);
-                if (full) {
-                    uint32_t* sp = stage + (4 * ring) * NSP + st + c * T;
-                    sp[0] = pc[c].x;
-                    sp[NSP] = pc[c].y;
-                    sp[2 * NSP] = pc[c].z;
-                    sp[3 * NSP] = pc[c].w;
-                    pgo[c] = false;
-                }
+                if (full)
+                    philox_store(c);
             }
         }
     };
@@ -436,7 +465,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     }
 
     if (!is_gen)
-        restart(false);
+        restart();
     __syncthreads();  // the first sweep's words are ready
     for (int sw = 0; sw < a.nsweeps; ++sw) {
         const uint32_t sid = uint32_t(sweep0 + sw);
@@ -467,9 +496,13 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         }
         __syncthreads();  // sweep start (block-wide)
 
-        for (int l = 0; l < a.D; ++l) {
-            const int phase = l & 3;
-            if (phase == 0) {
+        // One level: the items first (the rounds are independent: a neighbour
+        // of a busy spin is at another level, so all loads go first, then the
+        // fields and decisions, then the stores of the flipped columns), then
+        // the word stream, then the level barrier.  PH = l mod 4.
+        auto level = [&](const int l, auto ph_c) {
+            constexpr int PH = decltype(ph_c)::value;
+            if (PH == 0) {
                 if (ring_words)
                     cp_async_wait_group<1>();  // the copies requested 8 levels ago have landed
                 // a slot takes up its next column at the last multiple of 4 before
@@ -485,64 +518,68 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                     }
                 }
             }
-            // the items of the level: the rounds are independent (a neighbour of a
-            // busy spin is at another level), so all loads go first, then the
-            // fields and decisions, then the stores of the flipped columns
-            int tt[RMAX];
-            uint32_t uu[RMAX], wn[RMAX][kMaxDeg];
+            const uint32_t lofs = uint32_t(l & 15) * lstride;
+            uint32_t mnext[RMAX];  // the next level's slice masks
+#pragma unroll
+            for (int c = 0; c < RMAX; ++c)
+                mnext[c] = __funnelshift_l(mrot[c], mrot[c], 1);
             bool any = true;
             if (RMAX == 1)  // one round: a warp without a busy slot skips the level's items
                 any = __any_sync(FULL, unsigned(l - lv[0]) < unsigned(M));
             if (any) {
+                uint32_t uu[RMAX], wn[RMAX][kMaxDeg];
 #pragma unroll
-            for (int c = 0; c < RMAX; ++c) {
-                const int t0 = l - lv[c];
-                const bool act = unsigned(t0) < unsigned(M);
-                tt[c] = act ? t0 : -1;
-                const int t = act ? t0 : 0;
-                // lanes without a busy slot all read word 0 (one broadcast, no conflicts)
+                for (int c = 0; c < RMAX; ++c) {
+                    // idle slots read their last column's words (valid addresses)
 #pragma unroll
-                for (int e = 0; e < kMaxDeg; ++e)
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(wn[c][e]) : "r"(act ? nw[c][e] : colw_s) : "memory");
-                // ring word (4 entry + w) for slice t: entry (rs + t / 4) & 3, word t & 3
-                uu[c] = stage[act ? ((rq[c] + t) & 15) * NSP + st + c * T : 0];
-            }
+                    for (int e = 0; e < kMaxDeg; ++e)
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(wn[c][e]) : "r"(nw[c][e]) : "memory");
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(uu[c]) : "r"(sbc[c] + lofs) : "memory");
+                }
 #pragma unroll
-            for (int c = 0; c < RMAX; ++c) {
-                const bool act = tt[c] >= 0;
-                const int t = act ? tt[c] : 0;
-                int g6[kMaxDeg];
+                for (int c = 0; c < RMAX; ++c) {
+                    const bool act = unsigned(l - lv[c]) < unsigned(M);
+                    // bit t of every column word (neighbours store M bits), bits
+                    // t -/+ 1 of the own word (M-periodic, so the rotation wraps)
+                    const uint32_t m = mrot[c];
+                    const uint32_t mp = __funnelshift_r(m, m, 1), mn = mnext[c];
+                    int fa = cq[c], fb = 0;
 #pragma unroll
-                for (int e = 0; e < kMaxDeg; ++e)
-                    g6[e] = int((wn[c][e] >> t) & 1u) * nj[c][e];
-                const int f = cq[c] + ((g6[0] + g6[1]) + (g6[2] + g6[3])) + (g6[4] + g6[5]);  // a tree
-                // bits 0, 1, 2 = s_{t-1}, s_t, s_{t+1} (ring wrap included)
-                const uint32_t w3 = __funnelshift_r(bits[c], bits[c], (t - 1) & 31);
-                const int h = f + jt2[c] * (__popc(w3 & 5u) - 1);  // the local field
-                const int k = (w3 & 2u) ? h : -h;                  // s_t f
-                // T(k) by lane k for 0 < k < K, else T(0) = 0: flip iff k <= 0 or u < T(k)
-                uint32_t th;
-                if (shfl_thr)
-                    th = __shfl_sync(FULL, thr_lane, unsigned(k - 1) < unsigned(K - 1) ? k : 0);
-                else
-                    th = unsigned(k - 1) < unsigned(K - 1) ? thr_s[k] : 0u;
-                const bool take = act && (k <= 0 || uu[c] < th);
-                bits[c] ^= take ? (rep << t) : 0u;
-                dE += take ? 2 * k : 0;
-                asm volatile("{ .reg .pred p; setp.ne.b32 p, %2, 0; @p st.shared.u32 [%0], %1; }" ::"r"(
-                                 colw_s + 4u * uint32_t(pp[c])),
-                             "r"(bits[c] & cmask), "r"(take ? 1u : 0u)
-                             : "memory");
-            }
+                    for (int e = 0; e < kMaxDeg; e += 2) {
+                        fa += (wn[c][e] & m) ? nj[c][e] : 0;
+                        fb += (wn[c][e + 1] & m) ? nj[c][e + 1] : 0;
+                    }
+                    fa += (bits[c] & mp) ? jt2[c] : 0;
+                    fb += (bits[c] & mn) ? jt2[c] : 0;
+                    const int h = fa + fb;                 // the local field
+                    const int k = (bits[c] & m) ? h : -h;  // s_t f
+                    // T(k) for 0 < k < K (lane k), else T(0) = 0: flip iff k <= 0
+                    // or u < T(k).  Lane index min(k, 32) as unsigned: lanes K ..
+                    // 31 hold 0, and 32 (k < 0 or k >= 32) wraps to lane 0.
+                    uint32_t th;
+                    if (shfl_thr)
+                        th = __shfl_sync(FULL, thr_lane, min(unsigned(k), 32u));
+                    else
+                        th = unsigned(k - 1) < unsigned(K - 1) ? thr_s[k] : 0u;
+                    const bool take = act && (k <= 0 || uu[c] < th);
+                    bits[c] ^= take ? m : 0u;
+                    dk += take ? k : 0;
+                    asm volatile("{ .reg .pred p; setp.ne.b32 p, %2, 0; @p st.shared.u32 [%0], %1; }" ::"r"(sa[c]),
+                                 "r"(bits[c] & cmask), "r"(take ? 1u : 0u)
+                                 : "memory");
+                }
             }  // any
+#pragma unroll
+            for (int c = 0; c < RMAX; ++c)
+                mrot[c] = mnext[c];
             // the word stream
             if (ring_words) {
-                if (phase == 0) {
+                if (PH == 0) {
                     request_words(wsw, l);
                     cp_async_commit();
                 }
             } else {
-                if (phase == 0) {
+                if (PH == 0) {
                     philox_start(sid, l, false);
                 } else {
 #pragma unroll
@@ -550,28 +587,31 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                         if (pgo[c]) {
 #pragma unroll
                             for (int i = 0; i < 3; ++i)
-                                if (phase < 3 || i == 0)
+                                if (PH < 3 || i == 0)
                                     philox_round(pc[c], pk0[c], pk1[c]);
-                            if (phase == 3) {
-                                uint32_t* sp = stage + (4 * pring[c]) * NSP + st + c * T;
-                                sp[0] = pc[c].x;
-                                sp[NSP] = pc[c].y;
-                                sp[2 * NSP] = pc[c].z;
-                                sp[3 * NSP] = pc[c].w;
-                                pgo[c] = false;
-                            }
+                            if (PH == 3)
+                                philox_store(c);
                         }
                     }
                 }
             }
             // the level barrier of the sweep threads
             asm volatile("bar.sync 1, %0;" ::"r"(T) : "memory");
+        };
+        for (int l = 0; l < a.D; l += 4) {
+            level(l, std::integral_constant<int, 0>{});
+            if (l + 1 < a.D)
+                level(l + 1, std::integral_constant<int, 1>{});
+            if (l + 2 < a.D)
+                level(l + 2, std::integral_constant<int, 2>{});
+            if (l + 3 < a.D)
+                level(l + 3, std::integral_constant<int, 3>{});
         }
         __syncthreads();  // sweep end (block-wide): the generator has the next sweep's words
 
-        // slots back at their first column; MT19937: the next sweep's first
-        // blocks requested, in flight during PT
-        restart(true);
+        // slots back at their first column; the next sweep's first blocks
+        // requested, in flight during PT
+        restart();
         if (ring_words && sw + 1 < a.nsweeps) {
             const uint32_t* wn = gen ? gen_buf(sw + 1) : wsw + a.wbuf_sweep_stride;
             request_words(wn, -8);
@@ -580,9 +620,9 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         }  // sweep threads
 
         if (fused && (sw + 1) % a.swap_every == 0) {
-            if (dE != 0)
-                atomicAdd(&eacc[0], dE);
-            dE = 0;
+            if (dk != 0)
+                atomicAdd(&eacc[0], 2 * dk);
+            dk = 0;
             __syncthreads();
             int* Ep = a.E_pub + size_t(npass & 1) * R;
             if (tid == 0) {
@@ -640,8 +680,8 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     }
 
     // ---- energies and write-back (coalesced over the spin index)
-    if (dE != 0)
-        atomicAdd(&eacc[0], dE);
+    if (dk != 0)
+        atomicAdd(&eacc[0], 2 * dk);
     __syncthreads();
     if (tid == 0)
         a.E[r] += eacc[0];
@@ -651,9 +691,9 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         const int tm = (t == 0) ? M - 1 : t - 1, tp = (t == M - 1) ? 0 : t + 1;
         const uint32_t cb = colw[p];
         const uint32_t* d = desc + p * kDescWords;
-        int f = cqt[p] + int(d[1]) * (2 * int(((cb >> tm) & 1u) + ((cb >> tp) & 1u)) - 2);
+        int f = int(d[3]) + int(d[2]) * int(((cb >> tm) & 1u) + ((cb >> tp) & 1u));
         for (int e = 0; e < kMaxDeg; ++e)
-            f += 2 * int(int8_t((d[2 + e] >> 8) & 0xFFu)) * int((colw[d[2 + e] >> 16] >> t) & 1u);
+            f += int(d[10 + e]) * int((colw[(d[4 + e] - colw_s) >> 2] >> t) & 1u);
         spo[i] = ((cb >> t) & 1u) ? int8_t(1) : int8_t(-1);
         if (f16)
             static_cast<int16_t*>(a.fields)[size_t(r) * N + i] = int16_t(f);
