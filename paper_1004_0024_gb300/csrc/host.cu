@@ -661,8 +661,8 @@ int32_t extract_slices(ising_s* g)
 // The packed kernel's table buffer: column descriptors [S][16] (lev0 | site
 // << 16, byte offset 4 p of the column's own word, 2 Jtau, the field constant
 // h_q - sum_j J_qj - 2 Jtau, six byte offsets of the spatial neighbours'
-// words, their six 2 J; missing neighbours padded with the column itself and
-// J = 0), positions [S], slot offsets [nslots + 1], slot columns [S], each
+// words, their six 2 J; missing neighbours padded with word 0 and J = 0),
+// positions [S], slot offsets [nslots + 1], slot columns [S], each
 // part padded to 16 bytes.
 std::vector<uint32_t> packed_tables(const ising_s* g)
 {
@@ -680,8 +680,8 @@ std::vector<uint32_t> packed_tables(const ising_s* g)
         d[2] = uint32_t(jt2);
         const int e0 = g->nbr_off[p], deg = g->nbr_off[p + 1] - e0;
         for (int e = 0; e < kMaxDeg; ++e) {
-            if (e >= deg) {
-                d[4 + e] = 4u * uint32_t(p);
+            if (e >= deg) {  // word 0 with J = 0: one word for all such loads of a warp
+                d[4 + e] = 0u;
                 d[10 + e] = 0u;
                 continue;
             }

@@ -44,11 +44,13 @@
 // Random words go through a ring of 16 levels per slot in shared memory: the
 // word of the slot's item at level l sits at (l mod 16) NSP + sl, so a
 // level's reads are conflict-free and their address is the same offset for
-// every slot.  Words come from the word buffer by 4-byte cp.async copies (not
-// waited for by the level barrier), one commit group every fourth level; at
-// a level divisible by 4 the thread waits until at most one group is
-// pending, i.e. for the copies requested 8 levels earlier (the ring then
-// holds levels l .. l + 15: the four being read and up to 11 in flight).
+// every slot.  Words come from the word buffer: at a level l divisible by 4
+// a slot loads the 4-word block that starts in levels [l + 8, l + 12) with
+// one 16-byte load into registers and stores it into the ring at level l + 4
+// (four plain stores to four ring levels; 4-byte asynchronous copies of
+// scattered blocks cost several shared-memory wavefronts each); the ring
+// then holds levels l .. l + 14.  The blocks of a sweep's first 8 levels are
+// asynchronous copies requested before the sweep (during the PT pass).
 // Without the generator warps, Philox blocks are computed by the slot, the
 // ten rounds spread over four levels (3, 3, 3, 1), and stored after the
 // fourth.  An entry is written after the last item that reads it.
@@ -261,6 +263,10 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     // request cursor: the slot's next block to fetch (block xb of the column
     // at position xcol, site xsite, xk in the slot's list), its first level xx
     int xx[RMAX], xb[RMAX] = {}, xcol[RMAX] = {}, xsite[RMAX] = {}, xk[RMAX] = {};
+    // block fetched at the last level divisible by 4 (16-byte load into
+    // registers), stored into the ring at the next one; wx = its first level
+    uint4 wq[RMAX];
+    int wx[RMAX];
     // Philox block in progress: counter, keys, first level, whether any
     uint4 pc[RMAX] = {};
     uint32_t pk0[RMAX], pk1[RMAX];
@@ -314,6 +320,8 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             px[c] = 0;
             xx[c] = kNone;
             xb[c] = xcol[c] = xsite[c] = xk[c] = 0;
+            wx[c] = kNone;
+            wq[c] = make_uint4(0u, 0u, 0u, 0u);
             if (sl < a.nslots) {
                 kk[c] = soff[sl];
                 ke[c] = soff[sl + 1];
@@ -356,7 +364,30 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     auto ring_addr = [&](int c, int x) {
         return sbase + 4u * uint32_t(c * T) + uint32_t(x & 15) * lstride;
     };
-    // 4-byte copies of the next block of every round into its ring levels
+    // the block fetched four levels ago into its ring levels
+    auto store_fetched = [&](int c) {
+        if (wx[c] < kNone) {
+            const uint32_t v[4] = {wq[c].x, wq[c].y, wq[c].z, wq[c].w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(ring_addr(c, wx[c] + w)), "r"(v[w]) : "memory");
+            wx[c] = kNone;
+        }
+    };
+    // in a sweep: the next block of every round, one 16-byte load into
+    // registers (through L2: the generator warps write the buffer)
+    auto fetch_words = [&](const uint32_t* wsw, int l) {
+#pragma unroll
+        for (int c = 0; c < RMAX; ++c) {
+            int col = 0, b = 0, x = 0, site = 0;
+            if (next_block(c, l, col, b, x, site)) {
+                wq[c] = __ldcg(reinterpret_cast<const uint4*>(wsw + (size_t(r) * S + col) * a.Mp + 4 * b));
+                wx[c] = x;
+            }
+        }
+    };
+    // at a sweep's start: 4-byte copies of the next block of every round into
+    // its ring levels
     auto request_words = [&](const uint32_t* wsw, int l) {
 #pragma unroll
         for (int c = 0; c < RMAX; ++c) {
@@ -503,8 +534,11 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         auto level = [&](const int l, auto ph_c) {
             constexpr int PH = decltype(ph_c)::value;
             if (PH == 0) {
-                if (ring_words)
-                    cp_async_wait_group<1>();  // the copies requested 8 levels ago have landed
+                if (ring_words) {
+#pragma unroll
+                    for (int c = 0; c < RMAX; ++c)
+                        store_fetched(c);
+                }
                 // a slot takes up its next column at the last multiple of 4 before
                 // the column's start (the previous one has ended by then: the host
                 // packs a slot's next column at or after the first multiple of 4
@@ -574,10 +608,8 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 mrot[c] = mnext[c];
             // the word stream
             if (ring_words) {
-                if (PH == 0) {
-                    request_words(wsw, l);
-                    cp_async_commit();
-                }
+                if (PH == 0)
+                    fetch_words(wsw, l);
             } else {
                 if (PH == 0) {
                     philox_start(sid, l, false);
