@@ -658,17 +658,155 @@ int32_t extract_slices(ising_s* g)
     return ISING_OK;
 }
 
+// Word slots of the packed kernel's column words (a permutation of the
+// positions; bank = slot mod 32).  A level's neighbour loads of a warp (one
+// instruction per neighbour entry, one address per lane) take as many
+// shared-memory wavefronts as the most-used bank has distinct words, so the
+// slots are chosen by a greedy search over swaps that lowers the sum of those
+// counts over one sweep's load instructions, simulated with the kernel's own
+// slot schedule (a lane holds its slot's current column: the first one from
+// the sweep's start, the next one from the last level divisible by 4 before
+// its start; warps without a busy lane skip the level when a thread has one
+// slot).  Deterministic; about 40 tries per column.  Batch instances keep
+// the identity (thousands of small models: the search would dominate their
+// setup).
+std::vector<int> packed_word_slots(const ising_s* g, int T)
+{
+    const int S = g->S, M = g->M, D = g->D, ns = g->nslots;
+    std::vector<int> slot(S);
+    for (int p = 0; p < S; ++p)
+        slot[p] = p;
+    if (S < 64 || T <= 0 || g->packed_off)  // packed_off: a batch instance
+        return slot;
+    const int rounds = (ns + T - 1) / T;
+    const int NSP = rounds * T;
+    // the load instructions of a sweep: distinct positions per (level, warp,
+    // round, entry); -1 stands for word 0 (padding, idle rounds)
+    std::vector<int> cur(NSP, -1), idx(NSP, 0);
+    for (int sl = 0; sl < ns; ++sl)
+        if (g->slot_off_v[sl] < g->slot_off_v[sl + 1])
+            cur[sl] = g->slot_col_v[g->slot_off_v[sl]];
+    std::vector<int> ioff(1, 0), iword;  // instruction i: iword[ioff[i] .. ioff[i + 1])
+    std::vector<char> iw0;               // instruction reads word 0
+    std::vector<int> tmp;
+    for (int l = 0; l < D; ++l) {
+        if ((l & 3) == 0)
+            for (int sl = 0; sl < ns; ++sl) {
+                const int k = g->slot_off_v[sl] + idx[sl] + 1;
+                if (k < g->slot_off_v[sl + 1] && (g->lev0p[g->slot_col_v[k]] & ~3) <= l) {
+                    ++idx[sl];
+                    cur[sl] = g->slot_col_v[k];
+                }
+            }
+        for (int c = 0; c < rounds; ++c)
+            for (int w0 = 0; w0 < T; w0 += 32) {
+                bool busy = rounds > 1;
+                for (int i = 0; i < 32 && !busy; ++i) {
+                    const int p = cur[c * T + w0 + i];
+                    busy = p >= 0 && unsigned(l - g->lev0p[p]) < unsigned(M);
+                }
+                if (!busy)
+                    continue;
+                for (int e = 0; e < isg::packed_detail::kMaxDeg; ++e) {
+                    tmp.clear();
+                    char w0flag = 0;
+                    for (int i = 0; i < 32; ++i) {
+                        const int p = cur[c * T + w0 + i];
+                        if (p < 0 || e >= g->nbr_off[p + 1] - g->nbr_off[p]) {
+                            w0flag = 1;
+                            continue;
+                        }
+                        tmp.push_back(int(g->nbr[g->nbr_off[p] + e] >> 16));
+                    }
+                    std::sort(tmp.begin(), tmp.end());
+                    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+                    iword.insert(iword.end(), tmp.begin(), tmp.end());
+                    ioff.push_back(int(iword.size()));
+                    iw0.push_back(w0flag);
+                }
+            }
+    }
+    const int ni = int(iw0.size());
+    if (ni == 0)
+        return slot;
+    std::vector<std::vector<int>> occ(S);
+    std::vector<int16_t> cnt(size_t(ni) * 32, 0);
+    std::vector<int16_t> mx(ni, 0);
+    for (int i = 0; i < ni; ++i) {
+        int16_t* ci = cnt.data() + size_t(i) * 32;
+        if (iw0[i])
+            ci[0] += 1;
+        for (int k = ioff[i]; k < ioff[i + 1]; ++k) {
+            occ[iword[k]].push_back(i);
+            ci[iword[k] & 31] += 1;
+        }
+        mx[i] = *std::max_element(ci, ci + 32);
+    }
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {
+        st ^= st << 13;
+        st ^= st >> 7;
+        st ^= st << 17;
+        return st;
+    };
+    std::vector<int> aff;
+    std::vector<int16_t> nmx;
+    const long long iters = 40LL * S;
+    for (long long it = 0; it < iters; ++it) {
+        const int a = int(next() % uint64_t(S)), b = int(next() % uint64_t(S));
+        const int A = slot[a] & 31, B = slot[b] & 31;
+        if (A == B)
+            continue;
+        aff.clear();
+        aff.insert(aff.end(), occ[a].begin(), occ[a].end());
+        aff.insert(aff.end(), occ[b].begin(), occ[b].end());
+        std::sort(aff.begin(), aff.end());
+        aff.erase(std::unique(aff.begin(), aff.end()), aff.end());
+        for (int i : occ[a]) {
+            cnt[size_t(i) * 32 + A] -= 1;
+            cnt[size_t(i) * 32 + B] += 1;
+        }
+        for (int i : occ[b]) {
+            cnt[size_t(i) * 32 + B] -= 1;
+            cnt[size_t(i) * 32 + A] += 1;
+        }
+        int d = 0;
+        nmx.resize(aff.size());
+        for (size_t k = 0; k < aff.size(); ++k) {
+            const int16_t* ci = cnt.data() + size_t(aff[k]) * 32;
+            nmx[k] = *std::max_element(ci, ci + 32);
+            d += nmx[k] - mx[aff[k]];
+        }
+        if (d <= 0) {
+            std::swap(slot[a], slot[b]);
+            for (size_t k = 0; k < aff.size(); ++k)
+                mx[aff[k]] = nmx[k];
+        } else {
+            for (int i : occ[a]) {
+                cnt[size_t(i) * 32 + A] += 1;
+                cnt[size_t(i) * 32 + B] -= 1;
+            }
+            for (int i : occ[b]) {
+                cnt[size_t(i) * 32 + B] += 1;
+                cnt[size_t(i) * 32 + A] -= 1;
+            }
+        }
+    }
+    return slot;
+}
+
 // The packed kernel's table buffer: column descriptors [S][16] (lev0 | site
-// << 16, byte offset 4 p of the column's own word, 2 Jtau, the field constant
+// << 16, byte offset of the column's own word (4 x its word slot), 2 Jtau, the field constant
 // h_q - sum_j J_qj - 2 Jtau, six byte offsets of the spatial neighbours'
 // words, their six 2 J; missing neighbours padded with word 0 and J = 0),
 // positions [S], slot offsets [nslots + 1], slot columns [S], each
 // part padded to 16 bytes.
-std::vector<uint32_t> packed_tables(const ising_s* g)
+std::vector<uint32_t> packed_tables(const ising_s* g, int T)
 {
     using isg::packed_detail::kDescWords;
     using isg::packed_detail::kMaxDeg;
     const int S = g->S;
+    const std::vector<int> ws = packed_word_slots(g, T);
     auto pad4 = [](size_t n) { return (n + 3) & ~size_t(3); };
     std::vector<uint32_t> pk(isg::packed_detail::packed_table_bytes(S, g->nslots) / 4, 0u);
     for (int p = 0; p < S; ++p) {
@@ -676,7 +814,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g)
         const int jt2 = 2 * g->jtau[p];
         long long c = g->h[g->site[p]] - jt2;
         d[0] = uint32_t(g->lev0p[p]) | (uint32_t(g->site[p]) << 16);
-        d[1] = 4u * uint32_t(p);
+        d[1] = 4u * uint32_t(ws[p]);
         d[2] = uint32_t(jt2);
         const int e0 = g->nbr_off[p], deg = g->nbr_off[p + 1] - e0;
         for (int e = 0; e < kMaxDeg; ++e) {
@@ -688,7 +826,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g)
             const uint32_t en = g->nbr[e0 + e];
             const int pj = int(en >> 16), J = int(int16_t(en & 0xFFFFu));
             c -= J;
-            d[4 + e] = 4u * uint32_t(pj);
+            d[4 + e] = 4u * uint32_t(ws[pj]);
             d[10 + e] = uint32_t(2 * J);
         }
         d[3] = uint32_t(int32_t(c));
@@ -755,7 +893,7 @@ bool choose_packed(ising_s* g)
     if (rmax == 0)
         return false;
     if (!g->d_pk) {
-        const std::vector<uint32_t> pk = packed_tables(g);
+        const std::vector<uint32_t> pk = packed_tables(g, T);
         if (upload(&g->d_pk, pk) != ISING_OK)
             return false;
         g->pk_bytes = uint32_t(pk.size() * 4);
@@ -2497,14 +2635,14 @@ bool packed_batch_setup(ising_batch_s* b)
                         g->R <= 16384;
         if (!ok)
             return false;
+        // one slot per thread up to 256 slots, else 128 threads of three rounds
+        const int T = g->nslots <= 256 ? ((g->nslots + 31) / 32) * 32 : 128;
         if (!g->d_pk) {
-            const std::vector<uint32_t> pk = packed_tables(g);
+            const std::vector<uint32_t> pk = packed_tables(g, T);
             if (upload(&g->d_pk, pk) != ISING_OK)
                 return false;
             g->pk_bytes = uint32_t(pk.size() * 4);
         }
-        // one slot per thread up to 256 slots, else 128 threads of three rounds
-        const int T = g->nslots <= 256 ? ((g->nslots + 31) / 32) * 32 : 128;
         const int rmax = g->nslots <= 256 ? 1 : 3;
         SweepArgs a = base_args(g);
         a.G = 1;

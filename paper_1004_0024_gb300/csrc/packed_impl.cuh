@@ -81,7 +81,8 @@ using fast_detail::grid_sync;
 constexpr int kMaxDeg = 6;
 constexpr int kGenWarps = 2;  // MT19937 generator warps per block
 // descriptor words of the column at position p: [0] lev0 | site << 16,
-// [1] byte offset of its column word (4 p), [2] 2 Jtau, [3] the field constant
+// [1] byte offset of its column word (the host places the words so that the
+// neighbour loads of a warp spread over the banks), [2] 2 Jtau, [3] the field constant
 // h_q - sum_j J_qj - 2 Jtau, [4..9] byte offsets of the spatial neighbours'
 // column words, [10..15] their 2 J (missing neighbours: the column itself
 // with J = 0).  The kernel turns the byte offsets into shared-memory
@@ -219,7 +220,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         uint32_t b = 0u;
         for (int t = 0; t < M; ++t)
             b |= (spg[size_t(t) * S + q] > 0 ? 1u : 0u) << t;
-        colw[p] = b;
+        colw[(d[1] - colw_s) >> 2] = b;
     }
     {
         const int temp = fused ? temp_s[r] : a.temp_of_slot[r];
@@ -286,7 +287,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         nj[c][0] = int(d2.z); nj[c][1] = int(d2.w); nj[c][2] = int(d3.x);
         nj[c][3] = int(d3.y); nj[c][4] = int(d3.z); nj[c][5] = int(d3.w);
         pp[c] = p;
-        bits[c] = colw[p] * rep;
+        bits[c] = colw[(d0.y - colw_s) >> 2] * rep;
         mrot[c] = __funnelshift_r(rep, rep, uint32_t(lv[c] - l));
     };
     auto set_next = [&](int c) {
@@ -721,8 +722,8 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     for (int i = tid; i < N; i += NT) {
         const int t = i / S, q = i - t * S, p = pos[q];
         const int tm = (t == 0) ? M - 1 : t - 1, tp = (t == M - 1) ? 0 : t + 1;
-        const uint32_t cb = colw[p];
         const uint32_t* d = desc + p * kDescWords;
+        const uint32_t cb = colw[(d[1] - colw_s) >> 2];
         int f = int(d[3]) + int(d[2]) * int(((cb >> tm) & 1u) + ((cb >> tp) & 1u));
         for (int e = 0; e < kMaxDeg; ++e)
             f += int(d[10 + e]) * int((colw[(d[4 + e] - colw_s) >> 2] >> t) & 1u);
