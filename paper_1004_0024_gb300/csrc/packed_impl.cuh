@@ -668,11 +668,11 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 __syncthreads();
             else if (!grid_sync(a.gridbar, unsigned(npass + 1) * unsigned(nblk), a.err, &s_flag))
                 return;
-            if (tid < 32) {
+            {  // the pairs of a pass are disjoint: one per thread
                 const unsigned long long p = pass0 + npass;
                 const int par = int(p & 1ull);
                 const int npairs = par ? (R - 1) / 2 : R / 2;
-                for (int j = tid; j < npairs; j += 32) {
+                for (int j = tid; j < npairs; j += NT) {
                     const int k = 2 * j + par;
                     const int sa = slot_s[k], sb = slot_s[k + 1];
                     const long long d = (long long)__ldcg(Ep + sa) - (long long)__ldcg(Ep + sb);
