@@ -729,9 +729,9 @@ std::vector<int> packed_word_slots(const ising_s* g, int T)
     const int ni = int(iw0.size());
     if (ni == 0)
         return slot;
+    // per instruction: words per bank, how many banks hold each count, max
     std::vector<std::vector<int>> occ(S);
-    std::vector<int16_t> cnt(size_t(ni) * 32, 0);
-    std::vector<int16_t> mx(ni, 0);
+    std::vector<int16_t> cnt(size_t(ni) * 32, 0), hist(size_t(ni) * 33, 0), mx(ni, 0);
     for (int i = 0; i < ni; ++i) {
         int16_t* ci = cnt.data() + size_t(i) * 32;
         if (iw0[i])
@@ -740,8 +740,24 @@ std::vector<int> packed_word_slots(const ising_s* g, int T)
             occ[iword[k]].push_back(i);
             ci[iword[k] & 31] += 1;
         }
+        for (int b = 0; b < 32; ++b)
+            hist[size_t(i) * 33 + ci[b]] += 1;
         mx[i] = *std::max_element(ci, ci + 32);
     }
+    auto move = [&](int i, int from, int to) {  // one word of instruction i from bank `from` to `to`
+        int16_t* ci = cnt.data() + size_t(i) * 32;
+        int16_t* hi = hist.data() + size_t(i) * 33;
+        hi[ci[from]] -= 1;
+        ci[from] -= 1;
+        hi[ci[from]] += 1;
+        if (hi[mx[i]] == 0)
+            mx[i] -= 1;
+        hi[ci[to]] -= 1;
+        ci[to] += 1;
+        hi[ci[to]] += 1;
+        if (ci[to] > mx[i])
+            mx[i] = ci[to];
+    };
     uint64_t st = 0x9E3779B97F4A7C15ull;
     auto next = [&]() {
         st ^= st << 13;
@@ -749,50 +765,66 @@ std::vector<int> packed_word_slots(const ising_s* g, int T)
         st ^= st << 17;
         return st;
     };
-    std::vector<int> aff;
-    std::vector<int16_t> nmx;
-    const long long iters = 40LL * S;
-    for (long long it = 0; it < iters; ++it) {
+    std::vector<int> stamp(ni, -1), aff;
+    std::vector<int16_t> old_mx(ni, 0);
+    const int iters = 40 * S;
+    for (int it = 0; it < iters; ++it) {
         const int a = int(next() % uint64_t(S)), b = int(next() % uint64_t(S));
         const int A = slot[a] & 31, B = slot[b] & 31;
         if (A == B)
             continue;
         aff.clear();
-        aff.insert(aff.end(), occ[a].begin(), occ[a].end());
-        aff.insert(aff.end(), occ[b].begin(), occ[b].end());
-        std::sort(aff.begin(), aff.end());
-        aff.erase(std::unique(aff.begin(), aff.end()), aff.end());
-        for (int i : occ[a]) {
-            cnt[size_t(i) * 32 + A] -= 1;
-            cnt[size_t(i) * 32 + B] += 1;
-        }
-        for (int i : occ[b]) {
-            cnt[size_t(i) * 32 + B] -= 1;
-            cnt[size_t(i) * 32 + A] += 1;
-        }
+        for (const std::vector<int>* o : {&occ[a], &occ[b]})
+            for (int i : *o)
+                if (stamp[i] != it) {
+                    stamp[i] = it;
+                    old_mx[i] = mx[i];
+                    aff.push_back(i);
+                }
+        for (int i : occ[a])
+            move(i, A, B);
+        for (int i : occ[b])
+            move(i, B, A);
         int d = 0;
-        nmx.resize(aff.size());
-        for (size_t k = 0; k < aff.size(); ++k) {
-            const int16_t* ci = cnt.data() + size_t(aff[k]) * 32;
-            nmx[k] = *std::max_element(ci, ci + 32);
-            d += nmx[k] - mx[aff[k]];
-        }
+        for (int i : aff)
+            d += mx[i] - old_mx[i];
         if (d <= 0) {
             std::swap(slot[a], slot[b]);
-            for (size_t k = 0; k < aff.size(); ++k)
-                mx[aff[k]] = nmx[k];
         } else {
-            for (int i : occ[a]) {
-                cnt[size_t(i) * 32 + A] += 1;
-                cnt[size_t(i) * 32 + B] -= 1;
-            }
-            for (int i : occ[b]) {
-                cnt[size_t(i) * 32 + B] += 1;
-                cnt[size_t(i) * 32 + A] -= 1;
-            }
+            for (int i : occ[b])
+                move(i, A, B);
+            for (int i : occ[a])
+                move(i, B, A);
         }
     }
     return slot;
+}
+
+// The search's result per model and block shape (the last few, compared in
+// full): handles of the same model made one after another skip the search.
+std::vector<int> packed_word_slots_cached(const ising_s* g, int T)
+{
+    std::vector<int> key = {g->S, g->M, g->D, g->nslots, T};
+    key.insert(key.end(), g->lev0p.begin(), g->lev0p.end());
+    key.insert(key.end(), g->nbr_off.begin(), g->nbr_off.end());
+    for (uint32_t e : g->nbr)
+        key.push_back(int(e >> 16));
+    key.insert(key.end(), g->slot_off_v.begin(), g->slot_off_v.end());
+    key.insert(key.end(), g->slot_col_v.begin(), g->slot_col_v.end());
+    static std::mutex mu;
+    static std::vector<std::pair<std::vector<int>, std::vector<int>>> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto& e : cache)
+            if (e.first == key)
+                return e.second;
+    }
+    std::vector<int> ws = packed_word_slots(g, T);
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() >= 4)
+        cache.erase(cache.begin());
+    cache.emplace_back(std::move(key), ws);
+    return ws;
 }
 
 // The packed kernel's table buffer: column descriptors [S][16] (lev0 | site
@@ -806,7 +838,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g, int T)
     using isg::packed_detail::kDescWords;
     using isg::packed_detail::kMaxDeg;
     const int S = g->S;
-    const std::vector<int> ws = packed_word_slots(g, T);
+    const std::vector<int> ws = packed_word_slots_cached(g, T);
     auto pad4 = [](size_t n) { return (n + 3) & ~size_t(3); };
     std::vector<uint32_t> pk(isg::packed_detail::packed_table_bytes(S, g->nslots) / 4, 0u);
     for (int p = 0; p < S; ++p) {

@@ -653,9 +653,24 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         }  // sweep threads
 
         if (fused && (sw + 1) % a.swap_every == 0) {
-            if (dk != 0)
-                atomicAdd(&eacc[0], 2 * dk);
+            {  // one shared atomic per warp
+                const int wsum = __reduce_add_sync(FULL, dk);
+                if ((tid & 31) == 0 && wsum != 0)
+                    atomicAdd(&eacc[0], 2 * wsum);
+            }
             dk = 0;
+            const unsigned long long p = pass0 + npass;
+            const int par = int(p & 1ull);
+            // the pass moves this replica's temperature t at most to its pair
+            // partner: both threshold rows are loaded before the barrier
+            const int t_old = temp_s[r];
+            const int t_alt = ((t_old - par) & 1) == 0 ? t_old + 1 : t_old - 1;
+            uint32_t th_old = 0u, th_alt = 0u;
+            if (shfl_thr && (tid & 31) < K) {
+                th_old = __ldg(a.thr + size_t(t_old) * K + (tid & 31));
+                if (t_alt >= 0 && t_alt < R)
+                    th_alt = __ldg(a.thr + size_t(t_alt) * K + (tid & 31));
+            }
             __syncthreads();
             int* Ep = a.E_pub + size_t(npass & 1) * R;
             if (tid == 0) {
@@ -669,8 +684,6 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             else if (!grid_sync(a.gridbar, unsigned(npass + 1) * unsigned(nblk), a.err, &s_flag))
                 return;
             {  // the pairs of a pass are disjoint: one per thread
-                const unsigned long long p = pass0 + npass;
-                const int par = int(p & 1ull);
                 const int npairs = par ? (R - 1) / 2 : R / 2;
                 for (int j = tid; j < npairs; j += NT) {
                     const int k = 2 * j + par;
@@ -695,10 +708,13 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 }
             }
             __syncthreads();
-            for (int k = tid; k < K; k += NT)
-                thr_s[k] = a.thr[size_t(temp_s[r]) * K + k];
-            __syncthreads();
-            thr_lane = (shfl_thr && (tid & 31) < K) ? thr_s[tid & 31] : 0u;
+            if (shfl_thr) {
+                thr_lane = temp_s[r] == t_old ? th_old : th_alt;
+            } else {
+                for (int k = tid; k < K; k += NT)
+                    thr_s[k] = a.thr[size_t(temp_s[r]) * K + k];
+                __syncthreads();
+            }
             ++npass;
         }
     }
@@ -713,8 +729,11 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     }
 
     // ---- energies and write-back (coalesced over the spin index)
-    if (dk != 0)
-        atomicAdd(&eacc[0], 2 * dk);
+    {
+        const int wsum = __reduce_add_sync(FULL, dk);
+        if ((tid & 31) == 0 && wsum != 0)
+            atomicAdd(&eacc[0], 2 * wsum);
+    }
     __syncthreads();
     if (tid == 0)
         a.E[r] += eacc[0];
