@@ -284,6 +284,10 @@ def _bind_mlp(lib):
     lib.orc_log_q.restype = ctypes.c_double
     lib.orc_column_log_accept.argtypes = [d, d, _i32p, _i8p, _i8p, _f64p, ctypes.c_double, _i64p]
     lib.orc_column_log_accept.restype = ctypes.c_double
+    lib.orc_column_log_accept_mix.argtypes = [d, d, _i32p, _i8p, _i8p, _f64p, ctypes.c_double, _i64p]
+    lib.orc_column_log_accept_mix.restype = ctypes.c_double
+    lib.orc_log_q_mix.argtypes = [d, _f64p, _i8p]
+    lib.orc_log_q_mix.restype = ctypes.c_double
 
 
 # --------------------------------------------------- learned column proposal
@@ -328,12 +332,21 @@ def log_q(logits, s):
     return float(lib.orc_log_q(lg.size, _ptr(lg, _f64p), _ptr(s, _i8p)))
 
 
-def column_log_accept(M, jtau, phi, s, s2, logits, beta):
-    """(log A, dE) of the column move s -> s2 under the given logits."""
+def log_q_mix(logits, s):
+    """log of the flip-symmetric mixture (q(s) + q(-s)) / 2."""
+    lib = _load()
+    lg = _c(logits, np.float64); s = _c(s, np.int8)
+    return float(lib.orc_log_q_mix(lg.size, _ptr(lg, _f64p), _ptr(s, _i8p)))
+
+
+def column_log_accept(M, jtau, phi, s, s2, logits, beta, mixture=False):
+    """(log A, dE) of the column move s -> s2 under the given logits (with
+    mixture: the flip-symmetric mixture proposal)."""
     lib = _load()
     phi = _c(phi, np.int32); s = _c(s, np.int8); s2 = _c(s2, np.int8)
     lg = _c(logits, np.float64)
     dE = ctypes.c_int64(0)
-    la = lib.orc_column_log_accept(M, jtau, _ptr(phi, _i32p), _ptr(s, _i8p), _ptr(s2, _i8p),
-                                   _ptr(lg, _f64p), float(beta), ctypes.byref(dE))
+    fn = lib.orc_column_log_accept_mix if mixture else lib.orc_column_log_accept
+    la = fn(M, jtau, _ptr(phi, _i32p), _ptr(s, _i8p), _ptr(s2, _i8p), _ptr(lg, _f64p), float(beta),
+            ctypes.byref(dE))
     return float(la), int(dE.value)

@@ -19,6 +19,12 @@
  * batch.  The proposal q(s') = prod_t sigma(s'_t l_t) is independent of the
  * current column, so the Metropolis-Hastings log ratio of s -> s' is
  *     log A = -beta (E_col(s') - E_col(s)) + log q(s) - log q(s').
+ *
+ * Flip-symmetric mixture: q_mix(s') = (q(s') + q(-s')) / 2, drawn by taking
+ * q's draw or its complement with probability 1/2 each.  It is again
+ * independent of the current column, so the same ratio holds with q_mix in
+ * place of q.  (A column aligned along the Trotter ring then has its whole
+ * reversal as a likely proposal.)
  */
 #include <math.h>
 #include <stdint.h>
@@ -138,6 +144,28 @@ double orc_log_q(int M, const double* logits, const int8_t* s)
     for (int t = 0; t < M; t++)
         a -= softplus(-(double)s[t] * logits[t]);
     return a;
+}
+
+/* log q_mix(s) = log((q(s) + q(-s)) / 2), formed as the log of a sum of two
+ * exponentials. */
+double orc_log_q_mix(int M, const double* logits, const int8_t* s)
+{
+    int8_t neg[64];
+    for (int t = 0; t < M; t++)
+        neg[t] = (int8_t)-s[t];
+    const double a = orc_log_q(M, logits, s), b = orc_log_q(M, logits, neg);
+    const double m = a > b ? a : b;
+    return m + log(0.5 * exp(a - m) + 0.5 * exp(b - m));
+}
+
+/* MH log ratio of the move s -> s2 under the mixture proposal; dE as below. */
+double orc_column_log_accept_mix(int M, int jtau, const int32_t* phi, const int8_t* s,
+                                 const int8_t* s2, const double* logits, double beta, int64_t* dE)
+{
+    const int64_t d = orc_column_energy(M, jtau, phi, s2) - orc_column_energy(M, jtau, phi, s);
+    if (dE)
+        *dE = d;
+    return -beta * (double)d + orc_log_q_mix(M, logits, s) - orc_log_q_mix(M, logits, s2);
 }
 
 /* MH log ratio of the move s -> s2 (see the file header); dE receives

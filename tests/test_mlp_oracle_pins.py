@@ -144,3 +144,54 @@ def test_fp32_ceiling_of_proposal_thresholds_is_exact():
     assert top.any() and np.all(word_below(np.full(top.sum(), 0xFFFFFFFF, np.uint32), cf[top]))
     zero = ci == 0                                                        # p = 0: never
     assert zero.any() and not np.any(word_below(np.zeros(zero.sum(), np.uint32), cf[zero]))
+
+
+def test_mixture_proposal_is_normalised_and_flip_symmetric():
+    lg = np.array([0.3, -1.2, 2.0, 0.0, 4.5])
+    cols = [np.array(c, np.int8) for c in itertools.product([-1, 1], repeat=lg.size)]
+    tot = sum(math.exp(oracle.log_q_mix(lg, c)) for c in cols)
+    assert abs(tot - 1.0) < 1e-12
+    for c in cols:
+        assert abs(oracle.log_q_mix(lg, c) - oracle.log_q_mix(lg, -c)) < 1e-12
+        # half of q(c) plus half of q(-c), each from the independent law
+        direct = 0.5 * math.exp(oracle.log_q(lg, c)) + 0.5 * math.exp(oracle.log_q(lg, -c))
+        assert abs(math.exp(oracle.log_q_mix(lg, c)) - direct) < 1e-15
+
+
+def test_mixture_of_uniform_proposal_is_uniform():
+    lg = np.zeros(6)
+    for c in itertools.product([-1, 1], repeat=6):
+        assert abs(oracle.log_q_mix(lg, np.array(c, np.int8)) + 6 * math.log(2.0)) < 1e-12
+
+
+def test_mixture_column_move_leaves_conditional_boltzmann_stationary():
+    """Exact 2^M x 2^M matrix of one MH column move with the mixture of an
+    arbitrary fixed proposal: exp(-beta E_col) is invariant and the flow is
+    balanced term by term; a strongly one-sided q makes whole-column
+    reversals likely proposals."""
+    M, jtau, beta = 4, 3, 0.9
+    phi = np.array([2, -1, 1, 3], np.int32)
+    lg = np.array([2.4, 3.1, 1.7, 2.9])
+    cols = [np.array(c, np.int8) for c in itertools.product([-1, 1], repeat=M)]
+    n = len(cols)
+    P = np.zeros((n, n))
+    for a, s in enumerate(cols):
+        for b, s2 in enumerate(cols):
+            if a == b:
+                continue
+            la, dE = oracle.column_log_accept(M, jtau, phi, s, s2, lg, beta, mixture=True)
+            assert dE == oracle.column_energy(M, jtau, phi, s2) - oracle.column_energy(M, jtau, phi, s)
+            P[a, b] = math.exp(oracle.log_q_mix(lg, s2)) * min(1.0, math.exp(la))
+        P[a, a] = 1.0 - P[a].sum()
+    E = np.array([oracle.column_energy(M, jtau, phi, c) for c in cols], float)
+    pi = np.exp(-beta * (E - E.min()))
+    pi /= pi.sum()
+    assert np.abs(pi @ P - pi).max() < 1e-12
+    F = pi[:, None] * P
+    assert np.abs(F - F.T).max() < 1e-12
+    # all -1 (the reversal of the column q favours) is proposed a third of
+    # the time: half of q(all +1) = prod_t sigma(l_t) = 0.70
+    assert cols[0].tolist() == [-1] * M
+    assert abs(math.exp(oracle.log_q_mix(lg, cols[0])) - 0.5 * math.exp(oracle.log_q(lg, -cols[0]))
+               - 0.5 * math.exp(oracle.log_q(lg, cols[0]))) < 1e-15
+    assert math.exp(oracle.log_q_mix(lg, cols[0])) > 0.35
