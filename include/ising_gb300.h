@@ -514,8 +514,20 @@ int32_t ising_mlp_grad(ising_mlp_t m, int32_t B, const float* X, const uint32_t*
  * network's M.  Errors: INVALID_ARG (capacity exceeded, slices differ),
  * NOT_INITIALISED. */
 int32_t ising_mlp_collect(ising_mlp_t m, ising_t h);
+/* As ising_mlp_collect; flags ISING_COLLECT_ORIENTED records each column in
+ * the orientation its spatial field prefers: Y is the column if
+ * sum_t s_t phi_t >= 0, else its complement (the training set of a network
+ * meant for the flip-symmetric mixture proposal, which adds the other
+ * orientation itself).  Errors as ising_mlp_collect, INVALID_ARG for
+ * unknown flags. */
+#define ISING_COLLECT_ORIENTED 1
+int32_t ising_mlp_collect_flags(ising_mlp_t m, ising_t h, uint32_t flags);
 int64_t ising_mlp_n_records(ising_mlp_t m);
 int32_t ising_mlp_clear_records(ising_mlp_t m);
+/* Copy records start .. start + n - 1 to the host: X [n][M + 1] (phi_t / 8 and
+ * beta as stored, bf16 values widened to float), Y [n] (column bits).
+ * Synchronous.  Errors: INVALID_ARG (NULL, range beyond the records). */
+int32_t ising_mlp_get_records(ising_mlp_t m, int64_t start, int64_t n, float* X, uint32_t* Y);
 
 /* `epochs` passes of Adam over the recorded columns in batches of `batch`
  * (a multiple of 128; records shuffled each epoch by std::mt19937_64(seed +
@@ -546,6 +558,14 @@ typedef struct {
 } ising_learned_stats_t;
 
 #define ISING_LEARNED_FP64_ONLY 1 /* decide every move by the FP64 product */
+/* Flip-symmetric mixture proposal q_mix(s') = (q(s') + q(-s')) / 2: the sign
+ * bit of word 33 (the second word of counter 2 + 4 * 8) takes q's draw or its
+ * complement, and the Hastings ratio becomes q_mix(s) / q_mix(s') = q(s) /
+ * q(s') * (1 + exp(-K(s))) / (1 + exp(-K(s'))), K(x) = sum_t x_t kappa_t,
+ * kappa_t = log(c_t / (2^32 - c_t)) (FP32 screen with an error bound, FP64
+ * otherwise, as for the plain ratio).  A column aligned along its Trotter
+ * ring then has its reversal as a likely proposal. */
+#define ISING_LEARNED_MIXTURE 2
 
 /* One learned pass over handle h: every column of every replica once, the
  * colour classes of the slice graph (greedy colouring in site order; no two

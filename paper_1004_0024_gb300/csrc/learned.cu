@@ -203,6 +203,7 @@ struct LearnedArgs {
     unsigned long long* n_exact;  // decisions taken by the FP64 product
     unsigned long long* n_changed;  // accepted moves with s' != s
     int fp64_only;                // decide every move by the FP64 product
+    int mixture;                  // flip-symmetric mixture (q(s') + q(-s')) / 2
     void* fields;                 // [R][N] local fields, int16 or int32
     int field_bits;
 };
@@ -415,6 +416,15 @@ __device__ __forceinline__ bool word_below(uint32_t u, float c)
 // with exact exponents, so it is the ratio of the probabilities of the draws
 // actually made.  An FP32 estimate of its logarithm, with a bound on its
 // error, decides whenever the bound allows.
+//
+// Mixture (flip-symmetric) proposal q_mix(s') = (q(s') + q(-s')) / 2: the
+// sign bit of word 33 (Philox block 34's second word) chooses q's draw or its
+// complement.  With kappa_t = log(c_t / (2^32 - c_t)) and K(x) = sum_t x_t
+// kappa_t (x_t = +-1), log q(-x) - log q(x) = -K(x), so
+//     log q_mix(s) - log q_mix(s') = log q(s) - log q(s')
+//                                    + softplus(-K(s)) - softplus(-K(s')),
+// the first part the ratio above, the rest summed over all M slices (FP32
+// with its error bound, FP64 when the bound cannot decide).
 constexpr int kMhLanes = 8;
 constexpr int kMhThreads = 256;
 constexpr int kMhRows = kMhThreads / kMhLanes;  // rows per block
@@ -441,6 +451,14 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
         const bool live = 4 * g < M;
         uint32_t prop = 0u;
         float lq = 0.f, mag = 0.f;
+        float ks = 0.f, ks2 = 0.f, magk = 0.f;  // mixture: K(s), K(s'), sum |kappa|
+        bool flip = false;                       // mixture: the complement of q's draw
+        if (a.mixture) {
+            uint32_t bw = 0u;
+            if (g == 0)
+                bw = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 34u), a.seed, uint32_t(r)).y;
+            flip = (__shfl_sync(gmask, bw, threadIdx.x & 24) >> 31) != 0u;
+        }
         if (live) {
             const uint4 w = philox4x32_10(make_uint4(uint32_t(q), a.pass, a.inst, 2u + 4u * uint32_t(g)), a.seed,
                                           uint32_t(r));
@@ -454,13 +472,20 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
                 const int t = 4 * g + u;
                 if (t < M) {
                     const float c1 = proposal_c(lv[u]);
-                    const bool up = word_below(wv[u], c1);
+                    const bool up = word_below(wv[u], c1) != flip;
+                    const bool ob = (old >> t) & 1u;
                     prop |= uint32_t(up) << t;
-                    if (up != bool((old >> t) & 1u)) {  // FP32 log of this bit's ratio
+                    if (up != ob) {  // FP32 log of this bit's ratio
                         const float cp = c1, cm = 4294967296.f - c1;  // cm: 2^32 - c rounded once
                         const float term = logf(up ? cm / cp : cp / cm);
                         lq += term;
                         mag += fabsf(term);
+                    }
+                    if (a.mixture) {
+                        const float kap = logf(c1 / (4294967296.f - c1));
+                        ks += ob ? kap : -kap;
+                        ks2 += up ? kap : -kap;
+                        magk += fabsf(kap);
                     }
                 }
             }
@@ -470,6 +495,9 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
             prop |= __shfl_xor_sync(gmask, prop, o);
             lq += __shfl_xor_sync(gmask, lq, o);
             mag += __shfl_xor_sync(gmask, mag, o);
+            ks += __shfl_xor_sync(gmask, ks, o);
+            ks2 += __shfl_xor_sync(gmask, ks2, o);
+            magk += __shfl_xor_sync(gmask, magk, o);
         }
         int dE = 0;
         if (live) {
@@ -488,14 +516,19 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
         if (g == 0) {
             const uint32_t ua = a.acc_word[row];
             const float bdE = a.betas32[a.temp_of_slot[r]] * float(dE);
-            const float la = -bdE + lq;
+            auto softplus32 = [](float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); };
+            const float lmix = a.mixture ? softplus32(-ks) - softplus32(-ks2) : 0.f;
+            const float la = -bdE + lq + lmix;
             const float lu = logf((float(ua) + 0.5f) * 2.3283064365386963e-10f);
             // Bound on |la - logA| + |lu - log u'|: each term's ratio carries 3
             // roundings (1.8e-7 in the log, 5.8e-6 over 32 terms) and logf 1
             // ulp (1.2e-7 |term|); the sums at most 31 roundings (1.9e-6 mag);
             // beta, the product and the sum 1.8e-7 |bdE|; lu 2.9e-6.  Below
-            // 8.7e-6 + 1.8e-7 |bdE| + 2.1e-6 mag.
-            const float eps = 1e-5f * (1.f + fabsf(bdE) + mag);
+            // 8.7e-6 + 1.8e-7 |bdE| + 2.1e-6 mag.  Mixture: each kappa carries
+            // 2 roundings and logf 1 ulp (1.2e-7 + 1.2e-7 |kappa|), each K sum
+            // 31 roundings (1.9e-6 magk), softplus (slope <= 1) its own 3e-7
+            // (1 + |K|): both terms below 8.5e-6 + 4.6e-6 magk.
+            const float eps = 1e-5f * (1.f + fabsf(bdE) + mag) + (a.mixture ? 1e-5f * (1.f + magk) : 0.f);
             bool decided = !a.fp64_only;
             if (decided) {
                 if (la >= eps || lu < la - eps)
@@ -522,8 +555,19 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
                         ed += k;
                     }
                 }
-                const double logA = -a.betas[a.temp_of_slot[r]] * double(dE) + log(num / den) +
-                                    double(en - ed) * 0.6931471805599453;
+                double logA = -a.betas[a.temp_of_slot[r]] * double(dE) + log(num / den) +
+                              double(en - ed) * 0.6931471805599453;
+                if (a.mixture) {  // + softplus(-K(s)) - softplus(-K(s')) in FP64
+                    double k1 = 0.0, k2 = 0.0;
+                    for (int t = 0; t < M; ++t) {
+                        const double cp = double(proposal_c(Lr[size_t(t) * 128]));
+                        const double kap = log(cp / (4294967296.0 - cp));
+                        k1 += ((old >> t) & 1u) ? kap : -kap;
+                        k2 += ((prop >> t) & 1u) ? kap : -kap;
+                    }
+                    auto softplus64 = [](double z) { return fmax(z, 0.0) + log1p(exp(-fabs(z))); };
+                    logA += softplus64(-k1) - softplus64(-k2);
+                }
                 acc = (logA >= 0.0) || (log((double(ua) + 0.5) * 2.3283064365386963e-10) < logA);
                 atomicAdd(a.n_exact, 1ull);
             }
@@ -568,8 +612,11 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
             atomicAdd(&a.E[r0 + k], s_dE[k]);
 }
 
-// Training records of every (replica, column): X = (phi/8, beta), Y = spins
-__global__ void collect_kernel(const LearnedArgs a, bf16* __restrict__ Xd, uint32_t* __restrict__ Yd)
+// Training records of every (replica, column): X = (phi/8, beta), Y = spins;
+// with `oriented`, Y is the column or its complement, whichever has
+// sum_t s_t phi_t >= 0 (the orientation its spatial field prefers)
+__global__ void collect_kernel(const LearnedArgs a, bf16* __restrict__ Xd, uint32_t* __restrict__ Yd,
+                               int oriented)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;  // k = r * S + q
     if (k >= a.R * a.S)
@@ -578,10 +625,15 @@ __global__ void collect_kernel(const LearnedArgs a, bf16* __restrict__ Xd, uint3
     const int8_t* sp = a.spins + size_t(r) * a.N;
     bf16* x = Xd + size_t(k) * kIn;
     uint32_t y = 0u;
+    long long dot = 0;
     for (int t = 0; t < a.M; ++t) {
-        x[t] = __float2bfloat16(float(spatial_field(a, sp, t, q)) * 0.125f);
+        const int f = spatial_field(a, sp, t, q);
+        x[t] = __float2bfloat16(float(f) * 0.125f);
         y |= (sp[t * a.S + q] > 0 ? 1u : 0u) << t;
+        dot += (long long)f * sp[t * a.S + q];
     }
+    if (oriented && dot < 0)
+        y = ~y & (a.M == 32 ? 0xFFFFFFFFu : ((1u << a.M) - 1u));
     x[a.M] = __float2bfloat16(a.betas32[a.temp_of_slot[r]]);
     for (int c = a.M + 1; c < kIn; ++c)
         x[c] = __float2bfloat16(0.f);
@@ -1289,8 +1341,12 @@ int32_t ising_mlp_grad(ising_mlp_t m, int32_t B, const float* X, const uint32_t*
     return ISING_OK;
 }
 
-int32_t ising_mlp_collect(ising_mlp_t m, ising_t h)
+int32_t ising_mlp_collect(ising_mlp_t m, ising_t h) { return ising_mlp_collect_flags(m, h, 0u); }
+
+int32_t ising_mlp_collect_flags(ising_mlp_t m, ising_t h, uint32_t flags)
 {
+    if (flags & ~uint32_t(ISING_COLLECT_ORIENTED))
+        return isg_fail(ISING_ERR_INVALID_ARG, "unknown collect flags");
     if (!m || !h)
         return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument");
     if (!h->inited)
@@ -1303,7 +1359,8 @@ int32_t ising_mlp_collect(ising_mlp_t m, ising_t h)
     if (m->n_rec + rows > m->cap)
         return isg_fail(ISING_ERR_INVALID_ARG, "record capacity exceeded");
     LearnedArgs a = learned_args(h, m);
-    collect_kernel<<<cdiv(rows, 256), 256, 0, h->stream>>>(a, m->Xd + size_t(m->n_rec) * kIn, m->Yd + m->n_rec);
+    collect_kernel<<<cdiv(rows, 256), 256, 0, h->stream>>>(a, m->Xd + size_t(m->n_rec) * kIn, m->Yd + m->n_rec,
+                                                           (flags & ISING_COLLECT_ORIENTED) ? 1 : 0);
     LCK(cudaGetLastError());
     LCK(cudaStreamSynchronize(h->stream));
     m->n_rec += rows;
@@ -1317,6 +1374,23 @@ int32_t ising_mlp_clear_records(ising_mlp_t m)
     if (!m)
         return isg_fail(ISING_ERR_INVALID_ARG, "network is NULL");
     m->n_rec = 0;
+    return ISING_OK;
+}
+
+int32_t ising_mlp_get_records(ising_mlp_t m, int64_t start, int64_t n, float* X, uint32_t* Y)
+{
+    if (!m || n < 0 || start < 0 || (n > 0 && (!X || !Y)))
+        return isg_fail(ISING_ERR_INVALID_ARG, "NULL argument or negative range");
+    if (start + n > m->n_rec)
+        return isg_fail(ISING_ERR_INVALID_ARG, "range beyond the recorded rows");
+    if (n == 0)
+        return ISING_OK;
+    std::vector<bf16> xb(size_t(n) * kIn);
+    LCK(cudaMemcpy(xb.data(), m->Xd + size_t(start) * kIn, xb.size() * sizeof(bf16), cudaMemcpyDeviceToHost));
+    LCK(cudaMemcpy(Y, m->Yd + start, size_t(n) * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c <= m->M; ++c)
+            X[i * (m->M + 1) + c] = __bfloat162float(xb[size_t(i) * kIn + c]);
     return ISING_OK;
 }
 
@@ -1410,6 +1484,7 @@ int32_t ising_learned_pass(ising_t h, ising_mlp_t m, uint32_t flags, ising_learn
         a.rows = rows;
         a.sites = h->d_colour_sites + h->colour_off[c];
         a.fp64_only = (flags & ISING_LEARNED_FP64_ONLY) ? 1 : 0;
+        a.mixture = (flags & ISING_LEARNED_MIXTURE) ? 1 : 0;
         learned_gather_kernel<<<cdiv(rows_pad, 128), 128, 0, st>>>(a, rows_pad);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (m->profiling) {

@@ -76,6 +76,8 @@ class LearnedStats(ctypes.Structure):
 _f32p = ctypes.POINTER(ctypes.c_float)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 LEARNED_FP64_ONLY = 1
+LEARNED_MIXTURE = 2
+COLLECT_ORIENTED = 1
 
 _SIGS = {
     "ising_last_error": ([], ctypes.c_char_p),
@@ -121,6 +123,8 @@ _SIGS = {
     "ising_mlp_forward": ([_vp, ctypes.c_int32, _f32p, _f32p], ctypes.c_int32),
     "ising_mlp_grad": ([_vp, ctypes.c_int32, _f32p, _u32p, _f32p, _f32p], ctypes.c_int32),
     "ising_mlp_collect": ([_vp, _vp], ctypes.c_int32),
+    "ising_mlp_collect_flags": ([_vp, _vp, ctypes.c_uint32], ctypes.c_int32),
+    "ising_mlp_get_records": ([_vp, ctypes.c_int64, ctypes.c_int64, _f32p, _u32p], ctypes.c_int32),
     "ising_mlp_n_records": ([_vp], ctypes.c_int64),
     "ising_mlp_clear_records": ([_vp], ctypes.c_int32),
     "ising_mlp_train": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _f32p], ctypes.c_int32),
@@ -611,8 +615,10 @@ class Mlp:
                                    ctypes.byref(loss)))
         return g, float(loss.value)
 
-    def collect(self, sim: "Ising"):
-        _check(_lib.ising_mlp_collect(self.m, sim.h))
+    def collect(self, sim: "Ising", oriented=False):
+        """Record sim's columns; oriented=True stores each in the orientation
+        its spatial field prefers (training set for the mixture proposal)."""
+        _check(_lib.ising_mlp_collect_flags(self.m, sim.h, COLLECT_ORIENTED if oriented else 0))
 
     @property
     def n_records(self) -> int:
@@ -621,18 +627,28 @@ class Mlp:
     def clear_records(self):
         _check(_lib.ising_mlp_clear_records(self.m))
 
+    def records(self, start=0, n=None):
+        """(X [n][M + 1] float32, Y [n] uint32) of recorded rows."""
+        n = self.n_records - start if n is None else n
+        X = np.empty((n, self.M + 1), np.float32)
+        Y = np.empty(n, np.uint32)
+        _check(_lib.ising_mlp_get_records(self.m, start, n, _p(X, _f32p), _p(Y, _u32p)))
+        return X, Y
+
     def train(self, epochs=1, batch=4096, lr=1e-3) -> float:
         loss = ctypes.c_float()
         _check(_lib.ising_mlp_train(self.m, int(epochs), int(batch), ctypes.c_float(lr), ctypes.byref(loss)))
         return float(loss.value)
 
-    def learned_pass(self, sim: "Ising", trace=False, fp64_only=False, sync=True):
+    def learned_pass(self, sim: "Ising", trace=False, fp64_only=False, sync=True, mixture=False):
         """One learned pass over ``sim``.  Returns a dict of its counts
         (proposed, accepted, changed, exact_decisions) and, with trace=True,
         the per-row record as a second value.  sync=False only enqueues the
-        pass and returns None."""
+        pass and returns None.  mixture=True proposes from the flip-symmetric
+        mixture (q(s') + q(-s')) / 2."""
+        flags = (LEARNED_FP64_ONLY if fp64_only else 0) | (LEARNED_MIXTURE if mixture else 0)
         if not sync and not trace:
-            _check(_lib.ising_learned_pass(sim.h, self.m, LEARNED_FP64_ONLY if fp64_only else 0, None, None))
+            _check(_lib.ising_learned_pass(sim.h, self.m, flags, None, None))
             return None
         st = LearnedStats()
         tr = None
@@ -645,7 +661,7 @@ class Mlp:
             tr = LearnedTrace(rows, _p(t["replica"], _i32p), _p(t["site"], _i32p), _p(t["phi"], _i32p),
                               _p(t["logits"], _f32p), _p(t["old_bits"], _u32p), _p(t["prop_bits"], _u32p),
                               _p(t["accepted"], ctypes.POINTER(ctypes.c_uint8)))
-        _check(_lib.ising_learned_pass(sim.h, self.m, LEARNED_FP64_ONLY if fp64_only else 0, ctypes.byref(st),
+        _check(_lib.ising_learned_pass(sim.h, self.m, flags, ctypes.byref(st),
                                        ctypes.byref(tr) if tr is not None else None))
         stats = {k: int(getattr(st, k)) for k in ("proposed", "accepted", "changed", "exact_decisions")}
         return (stats, t) if trace else stats

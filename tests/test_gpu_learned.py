@@ -151,9 +151,11 @@ def _sigmoid32(l):
     return float(np.float32(1.0) / (np.float32(1.0) + np.exp(-l, dtype=np.float32)))
 
 
-def replay(g, betas, seed, inst, pass_idx, before, trace):
+def replay(g, betas, seed, inst, pass_idx, before, trace, mixture=False):
     """Re-derive a learned pass row by row from the oracle; returns the spins
-    and energies it leads to and the number of near-ties skipped."""
+    and energies it leads to and the number of near-ties skipped.  With
+    mixture, the sign bit of word 33 takes the complement of the draw and the
+    ratio is the mixture's."""
     M = g.n_slices
     S = g.n // M
     spins = before["spins"].copy()
@@ -189,10 +191,12 @@ def replay(g, betas, seed, inst, pass_idx, before, trace):
                 prop |= int(trace["prop_bits"][row]) & (1 << t)
             elif float(words[t]) < thr:
                 prop |= 1 << t
+        if mixture and int(words[33]) >> 31:
+            prop ^= (1 << M) - 1
         assert int(trace["prop_bits"][row]) == prop, f"proposal of row {row}"
         s2 = np.array([1 if (prop >> t) & 1 else -1 for t in range(M)], dtype=np.int8)
         logA, dE = oracle.column_log_accept(M, jtau.get(q, 0), phi, col, s2, logits.astype(np.float64),
-                                            float(beta_of[r]))
+                                            float(beta_of[r]), mixture=mixture)
         lu = np.log((float(words[32]) + 0.5) * 2.0 ** -32)
         acc_ref = logA >= 0 or lu < logA
         # the kernel's log A uses the exact probabilities of its discrete
@@ -214,11 +218,12 @@ def _with_output_bias(net, bias):
     net.set_params(np.concatenate([u[k].ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")]))
 
 
-@pytest.mark.parametrize("model,rng_mode,bias", [("L4_M8", "philox", 0.0), ("L3_M2", "mt19937", 0.0),
-                                                 ("L4_M3", "philox", 0.0), ("L3_M1", "mt19937", 0.0),
-                                                 ("ring_S5_M4", "philox", 1.5), ("L5_M32", "philox", -0.7),
-                                                 ("ring_S5_M4_J30", "mt19937", 0.0)])
-def test_learned_pass_replays_on_the_oracle(ising, model, rng_mode, bias):
+@pytest.mark.parametrize("model,rng_mode,bias,mixture", [
+    ("L4_M8", "philox", 0.0, False), ("L3_M2", "mt19937", 0.0, False), ("L4_M3", "philox", 0.0, False),
+    ("L3_M1", "mt19937", 0.0, False), ("ring_S5_M4", "philox", 1.5, False), ("L5_M32", "philox", -0.7, False),
+    ("ring_S5_M4_J30", "mt19937", 0.0, False), ("L4_M8", "philox", 2.0, True), ("L5_M32", "mt19937", 1.2, True),
+    ("ring_S5_M4", "philox", -1.5, True), ("L3_M1", "philox", 0.5, True)])
+def test_learned_pass_replays_on_the_oracle(ising, model, rng_mode, bias, mixture):
     # ring_S5_M4_J30: couplings up to 90, beyond the byte-lane bound
     # (sum_j 2 |J| <= 127 per site) of the neighbour sums: the slice-by-slice path
     if model.startswith("ring"):
@@ -236,7 +241,7 @@ def test_learned_pass_replays_on_the_oracle(ising, model, rng_mode, bias):
     sim.run(12, 1)
     for pass_idx in range(2):
         before = sim.read_state()
-        stats, tr = net.learned_pass(sim, trace=True)
+        stats, tr = net.learned_pass(sim, trace=True, mixture=mixture)
         after = sim.read_state()
         S = g.n // M
         assert stats["proposed"] == R * S
@@ -244,7 +249,7 @@ def test_learned_pass_replays_on_the_oracle(ising, model, rng_mode, bias):
         assert stats["accepted"] == int(tr["accepted"].sum())
         moved = (tr["accepted"] > 0) & (tr["old_bits"] != tr["prop_bits"])
         assert stats["changed"] == int(moved.sum())
-        spins, E, ties = replay(g, betas, seed, 0, pass_idx, before, tr)
+        spins, E, ties = replay(g, betas, seed, 0, pass_idx, before, tr, mixture=mixture)
         assert ties <= 2
         assert np.array_equal(after["spins"], spins)
         assert np.array_equal(after["energy"], E)
@@ -336,8 +341,9 @@ def _exact_energy_law(g):
     return E
 
 
-@pytest.mark.parametrize("model", ["layered_L3_M2", "ring_S5_M4"])
-def test_learned_chain_samples_the_boltzmann_law(ising, model):
+@pytest.mark.parametrize("model,mixture", [("layered_L3_M2", False), ("ring_S5_M4", False),
+                                           ("layered_L3_M2", True), ("ring_S5_M4", True)])
+def test_learned_chain_samples_the_boltzmann_law(ising, model, mixture):
     """A chain of learned passes alone (no sweeps) at beta ~ 0.12 over 256
     independent replicas: every energy bin with expected mass >= 2% holds
     its exact Boltzmann probability within 3 standard errors (replicas as
@@ -361,7 +367,7 @@ def test_learned_chain_samples_the_boltzmann_law(ising, model):
         # is 12 SE off after 50 passes and within 2 SE after 1000)
         burn, passes = 1000, 1000
         for k in range(burn + passes):
-            net.learned_pass(sim)
+            net.learned_pass(sim, mixture=mixture)
             if k >= burn:
                 e = sim.read_state()["energy"]
                 assert np.isin(e, levels).all()
@@ -391,7 +397,8 @@ def test_observables_follow_the_temperature_labels(ising):
     sim.close()
 
 
-def test_fp32_screen_gives_the_fp64_decisions(ising):
+@pytest.mark.parametrize("mixture", [False, True])
+def test_fp32_screen_gives_the_fp64_decisions(ising, mixture):
     """Moves decided by the FP32 estimate with its error bound equal the moves
     decided by the FP64 product alone, pass after pass (identical Philox words,
     so any disagreement would show in the spins)."""
@@ -404,7 +411,7 @@ def test_fp32_screen_gives_the_fp64_decisions(ising):
         exact, acc = 0, []
         for _ in range(6):
             sim.run(2, 1)
-            stats, tr = net.learned_pass(sim, trace=True, fp64_only=fp64_only)
+            stats, tr = net.learned_pass(sim, trace=True, fp64_only=fp64_only, mixture=mixture)
             exact += stats["exact_decisions"]
             acc.append(tr["accepted"].copy())
         st = sim.read_state()
@@ -435,5 +442,48 @@ def test_learned_pass_after_reinit_with_more_replicas(ising):
     for r in range(16):
         assert st["energy"][r] == oracle.energy(g, st["spins"][r])
         assert np.array_equal(st["fields"][r], oracle.fields(g, st["spins"][r]))
+    net.close()
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_oriented_records_follow_the_spatial_field(ising):
+    """ising_mlp_collect_flags(ORIENTED): each record is the column, or its
+    complement when sum_t s_t phi_t < 0; plain records are the columns."""
+    c = W.config0()
+    g = c["graph"]
+    M = g.n_slices
+    S = g.n // M
+    sim = ising.Ising(g, c["betas"], seed=c["seed"], rng="philox")
+    sim.run(7, 1)
+    st = sim.read_state()
+    net = ising.Mlp(M, seed=3, capacity=2 * sim.R * S)
+    net.collect(sim)
+    net.collect(sim, oriented=True)
+    X, Y = net.records()
+    n = sim.R * S
+    mask = (1 << M) - 1
+    flipped = 0
+    for k in range(0, n, 7):
+        r, q = divmod(k, S)
+        s = st["spins"][r]
+        col = sum(1 << t for t in range(M) if s[t * S + q] > 0)
+        sp = []  # spatial fields phi_t of the column
+        for t in range(M):
+            i = t * S + q
+            f = int(g.h[i])
+            for e in range(g.row_ptr[i], g.row_ptr[i + 1]):
+                j = int(g.col[e])
+                if j // S == t:
+                    f += int(g.J[e]) * int(s[j])
+            sp.append(f)
+        assert int(Y[k]) == col
+        dot = sum(int(s[t * S + q]) * sp[t] for t in range(M))
+        want = col if dot >= 0 else (~col & mask)
+        flipped += dot < 0
+        assert int(Y[n + k]) == want, (k, dot)
+        assert np.array_equal(X[k], X[n + k])
+        assert np.allclose(X[k, :M], np.asarray(sp, np.float32) / 8, rtol=1e-2, atol=1e-2)
+    assert flipped > 0
     net.close()
     sim.close()
