@@ -563,8 +563,10 @@ typedef struct {
  * complement, and the Hastings ratio becomes q_mix(s) / q_mix(s') = q(s) /
  * q(s') * (1 + exp(-K(s))) / (1 + exp(-K(s'))), K(x) = sum_t x_t kappa_t,
  * kappa_t = log(c_t / (2^32 - c_t)) (FP32 screen with an error bound, FP64
- * otherwise, as for the plain ratio).  A column aligned along its Trotter
- * ring then has its reversal as a likely proposal. */
+ * otherwise, as for the plain ratio).  In this mode c_t is clamped to
+ * [1, 2^32 - 256], so that every column has a positive probability.  A
+ * column aligned along its Trotter ring then has its reversal as a likely
+ * proposal. */
 #define ISING_LEARNED_MIXTURE 2
 
 /* One learned pass over handle h: every column of every replica once, the

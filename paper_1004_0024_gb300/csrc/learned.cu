@@ -398,6 +398,15 @@ __device__ __forceinline__ float proposal_c(float l)
     return ceilf(1.f / (1.f + expf(-l)) * 4294967296.f);
 }
 
+// The mixture mode keeps every slice's probability strictly inside (0, 1):
+// c clamped to [1, 2^32 - 1] (integers, exact in FP32 up to 2^24 and, above,
+// 2^32 - 256 is the largest float below 2^32), so that log q is finite for
+// every column
+__device__ __forceinline__ float proposal_c_mix(float l)
+{
+    return fminf(fmaxf(proposal_c(l), 1.f), 4294967040.f);
+}
+
 // u < c for a 32-bit word u and an integer-valued c in [0, 2^32]
 __device__ __forceinline__ bool word_below(uint32_t u, float c)
 {
@@ -424,7 +433,8 @@ __device__ __forceinline__ bool word_below(uint32_t u, float c)
 //     log q_mix(s) - log q_mix(s') = log q(s) - log q(s')
 //                                    + softplus(-K(s)) - softplus(-K(s')),
 // the first part the ratio above, the rest summed over all M slices (FP32
-// with its error bound, FP64 when the bound cannot decide).
+// with its error bound, FP64 when the bound cannot decide).  In this mode c_t
+// is clamped to [1, 2^32 - 256] (proposal_c_mix), so every kappa is finite.
 constexpr int kMhLanes = 8;
 constexpr int kMhThreads = 256;
 constexpr int kMhRows = kMhThreads / kMhLanes;  // rows per block
@@ -471,7 +481,7 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
             for (int u = 0; u < 4; ++u) {
                 const int t = 4 * g + u;
                 if (t < M) {
-                    const float c1 = proposal_c(lv[u]);
+                    const float c1 = a.mixture ? proposal_c_mix(lv[u]) : proposal_c(lv[u]);
                     const bool up = word_below(wv[u], c1) != flip;
                     const bool ob = (old >> t) & 1u;
                     prop |= uint32_t(up) << t;
@@ -517,7 +527,8 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
             const uint32_t ua = a.acc_word[row];
             const float bdE = a.betas32[a.temp_of_slot[r]] * float(dE);
             auto softplus32 = [](float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); };
-            const float lmix = a.mixture ? softplus32(-ks) - softplus32(-ks2) : 0.f;
+            const float sp1 = a.mixture ? softplus32(-ks) : 0.f, sp2 = a.mixture ? softplus32(-ks2) : 0.f;
+            const float lmix = sp1 - sp2;
             const float la = -bdE + lq + lmix;
             const float lu = logf((float(ua) + 0.5f) * 2.3283064365386963e-10f);
             // Bound on |la - logA| + |lu - log u'|: each term's ratio carries 3
@@ -526,9 +537,17 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
             // beta, the product and the sum 1.8e-7 |bdE|; lu 2.9e-6.  Below
             // 8.7e-6 + 1.8e-7 |bdE| + 2.1e-6 mag.  Mixture: each kappa carries
             // 2 roundings and logf 1 ulp (1.2e-7 + 1.2e-7 |kappa|), each K sum
-            // 31 roundings (1.9e-6 magk), softplus (slope <= 1) its own 3e-7
-            // (1 + |K|): both terms below 8.5e-6 + 4.6e-6 magk.
-            const float eps = 1e-5f * (1.f + fabsf(bdE) + mag) + (a.mixture ? 1e-5f * (1.f + magk) : 0.f);
+            // at most 31 roundings, so |K - K_exact| <= eK = 3.9e-6 + 2e-6 magk;
+            // softplus(-K) moves by at most eK sigma(-(K - eK)) (its slope is
+            // sigma(-K), decreasing in K), taken 1% high, plus its own FP32
+            // rounding (expf, log1pf, the add) below 1e-6 (1 + its value); the
+            // difference and the last sum 2e-7 |lmix| + 1e-7.
+            float eps = 1e-5f * (1.f + fabsf(bdE) + mag);
+            if (a.mixture) {
+                const float eK = 3.9e-6f + 2e-6f * magk;
+                const float sg = 1.f / (1.f + expf(ks - eK)) + 1.f / (1.f + expf(ks2 - eK));
+                eps += 1.01f * eK * sg + 1e-6f * (2.f + sp1 + sp2) + 2e-7f * fabsf(lmix) + 1e-7f;
+            }
             bool decided = !a.fp64_only;
             if (decided) {
                 if (la >= eps || lu < la - eps)
@@ -543,7 +562,8 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
                 int en = 0, ed = 0, n = 0;
                 for (uint32_t ch = old ^ prop; ch; ch &= ch - 1u) {
                     const int b = __ffs(ch) - 1;
-                    const double cp = double(proposal_c(Lr[size_t(b) * 128])), cm = 4294967296.0 - cp;
+                    const float cb = a.mixture ? proposal_c_mix(Lr[size_t(b) * 128]) : proposal_c(Lr[size_t(b) * 128]);
+                    const double cp = double(cb), cm = 4294967296.0 - cp;
                     const bool ob = (old >> b) & 1u;
                     num *= ob ? cp : cm;
                     den *= ob ? cm : cp;
@@ -560,7 +580,7 @@ __global__ void __launch_bounds__(kMhThreads) learned_mh_kernel(const LearnedArg
                 if (a.mixture) {  // + softplus(-K(s)) - softplus(-K(s')) in FP64
                     double k1 = 0.0, k2 = 0.0;
                     for (int t = 0; t < M; ++t) {
-                        const double cp = double(proposal_c(Lr[size_t(t) * 128]));
+                        const double cp = double(proposal_c_mix(Lr[size_t(t) * 128]));
                         const double kap = log(cp / (4294967296.0 - cp));
                         k1 += ((old >> t) & 1u) ? kap : -kap;
                         k2 += ((prop >> t) & 1u) ? kap : -kap;

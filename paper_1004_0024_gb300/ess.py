@@ -141,16 +141,17 @@ def _seconds_per_step(sim, step, n_steps):
 
 
 def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time: int = 200, ctrl=None,
-            ctrl_seed: int | None = None):
+            ctrl_seed: int | None = None, mix_net=None):
     """Plain chain (one sweep + PT per step) against the 1:1 chain (one sweep
     + PT, then one learned pass per step), both from the handle's current
     state.  With ``ctrl`` (a second handle of the same configuration, Philox
     streams) a second plain chain runs from the same state with other random
     numbers: after loading the shared state its seed is set to ``ctrl_seed``
     (the loaded checkpoint carries the first chain's key), so the spread
-    between two correct chains calibrates the comparison.  Returns
-    per-temperature series, ESS and ESS/s of E and m, and the learned
-    acceptance and change rates."""
+    between two correct chains calibrates the comparison.  With ``mix_net``
+    a "mixture" chain interleaves learned passes of that network with the
+    flip-symmetric mixture proposal.  Returns per-temperature series, ESS and
+    ESS/s of E and m, and the learned acceptance and change rates."""
     blob = sim.save()
     if ctrl is not None and ctrl_seed is None:
         raise ValueError("a control chain needs its own seed")
@@ -165,7 +166,13 @@ def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time:
     def plain_ctrl():
         ctrl.run(1, swap_every)
 
+    def mixture():
+        sim.run(1, swap_every)
+        mix_net.learned_pass(sim, sync=False, mixture=True)
+
     chains = [("plain", sim, plain), ("learned", sim, learned)]
+    if mix_net is not None:
+        chains.append(("mixture", sim, mixture))
     if ctrl is not None:
         chains.append(("plain_ctrl", ctrl, plain_ctrl))
     out = {}
@@ -213,6 +220,56 @@ def compare(sim, net, n_steps: int, swap_every: int = 1, warm: int = 20, n_time:
     sim.load(blob)
     out["accept_rate"] = acc[0] / max(1, acc[1])
     out["change_rate"] = acc[2] / max(1, acc[1])
+    if mix_net is not None:
+        acc = [0, 0, 0]
+        for _ in range(min(50, n_steps)):
+            sim.run(1, swap_every)
+            st = mix_net.learned_pass(sim, mixture=True)
+            acc[0] += st["accepted"]
+            acc[1] += st["proposed"]
+            acc[2] += st["changed"]
+        sim.load(blob)
+        out["mixture_accept_rate"] = acc[0] / max(1, acc[1])
+        out["mixture_change_rate"] = acc[2] / max(1, acc[1])
+    return out
+
+
+BANDS = ((0.05, 0.3), (0.3, 1.0), (1.0, 5.0 + 1e-9))
+
+
+def band_summary(res: dict, betas, chain: str, bands=BANDS, max_tau_frac: float = 1.0 / 50) -> list:
+    """ESS/s of ``chain`` against the plain chain per inverse-temperature band:
+    per temperature of the band, E and m count where both chains pass the
+    split-half check and have tau_int below max_tau_frac of the run (so that
+    tau is estimated from at least 50 autocorrelation times); the band reports
+    how many temperatures qualified, the median ESS/s ratio over them and
+    the median tau_int of each chain."""
+    P, L = res["plain"], res[chain]
+    n = P["E"].shape[0]
+    betas = np.asarray(betas)
+    out = []
+    for lo, hi in bands:
+        ks = np.nonzero((betas >= lo) & (betas < hi))[0]
+        row = {"betas": [float(lo), float(min(hi, betas.max()))], "temps": int(ks.size)}
+        for o in ("E", "m"):
+            good, ratio, tp, tl = [], [], [], []
+            for k in ks:
+                xp, xl = P[o][:, k], L[o][:, k]
+                if not (equilibrated(xp) and equilibrated(xl)):
+                    continue
+                a, b = tau_int(xp), tau_int(xl)
+                if max(a, b) >= max_tau_frac * n:
+                    continue
+                good.append(int(k))
+                ratio.append(L[f"ess_{o}_per_s"][k] / P[f"ess_{o}_per_s"][k])
+                tp.append(a)
+                tl.append(b)
+            row[o] = {"qualified": len(good),
+                      "ess_per_s_ratio_median": float(np.median(ratio)) if ratio else None,
+                      "ess_per_s_ratio_min_max": [float(np.min(ratio)), float(np.max(ratio))] if ratio else None,
+                      "tau_int_median_plain": float(np.median(tp)) if tp else None,
+                      f"tau_int_median_{chain}": float(np.median(tl)) if tl else None}
+        out.append(row)
     return out
 
 
