@@ -322,7 +322,7 @@ def summarize(res: dict, betas) -> dict:
     moves on this time scale, is reported by the energies reached."""
     P, L = res["plain"], res["learned"]
     R = P["E"].shape[1]
-    names = ["plain", "learned"] + (["plain_ctrl"] if "plain_ctrl" in res else [])
+    names = ["plain", "learned"] + [k for k in ("plain_ctrl", "mixture") if k in res]
     fm = fast_mixing(res, names)
     out = {"accept_rate": res["accept_rate"], "change_rate": res["change_rate"],
            "ms_per_step": {"plain": 1e3 * P["seconds_per_step"], "learned": 1e3 * L["seconds_per_step"]},
@@ -336,6 +336,16 @@ def summarize(res: dict, betas) -> dict:
                   "ess_per_s_plain_median": float(np.median(P[f"ess_{o}_per_s"][fm])) if fm.any() else None,
                   "ess_per_s_learned_median": float(np.median(L[f"ess_{o}_per_s"][fm])) if fm.any() else None}
     out["histograms_learned_vs_plain"] = _hist_stats(res, "learned", "plain", fm)
+    out["bands_learned"] = band_summary(res, betas, "learned")
+    if "mixture" in res:
+        X = res["mixture"]
+        out["mixture"] = {"accept_rate": res.get("mixture_accept_rate"), "change_rate": res.get("mixture_change_rate"),
+                          "ms_per_step": 1e3 * X["seconds_per_step"],
+                          "histograms_vs_plain": _hist_stats(res, "mixture", "plain", fm),
+                          "bands": band_summary(res, betas, "mixture")}
+        for o in ("E", "m"):
+            ratio = X[f"ess_{o}_per_s"] / P[f"ess_{o}_per_s"]
+            out["mixture"][o] = {"ess_per_s_ratio_median": float(np.median(ratio[fm])) if fm.any() else None}
     if "plain_ctrl" in res:
         out["histograms_plain_vs_plain"] = _hist_stats(res, "plain_ctrl", "plain", fm)
     cold = slice(3 * R // 4, R)
@@ -366,14 +376,20 @@ def study(ising, W, burn: int, n_steps: int, epochs: int, records: int = 1 << 20
         sim.run(k, 1)
         done += k
     S = c["graph"].n // c["graph"].n_slices
+    # two networks on the same snapshots: the independent proposal on the
+    # columns as sampled, the mixture proposal on the columns in the
+    # orientation their spatial field prefers
     net = ising.Mlp(c["graph"].n_slices, seed=seed_net, capacity=records)
+    mix = ising.Mlp(c["graph"].n_slices, seed=seed_net + 1, capacity=records)
     while net.n_records + c["R"] * S <= records:
         sim.run(10, 1)
         net.collect(sim)
+        mix.collect(sim, oriented=True)
     t0 = time.perf_counter()
     losses = [net.train(1, 4096, 1e-3) for _ in range(epochs)]
+    losses_mix = [mix.train(1, 4096, 1e-3) for _ in range(epochs)]
     train_s = time.perf_counter() - t0
-    res = compare(sim, net, n_steps, ctrl=ctrl, ctrl_seed=c["seed"] + 7919)
+    res = compare(sim, net, n_steps, ctrl=ctrl, ctrl_seed=c["seed"] + 7919, mix_net=mix)
     out = summarize(res, c["betas"])
     # the fused network kernel alone, timed with CUDA events around each launch
     net.set_profiling(True)
@@ -388,8 +404,10 @@ def study(ising, W, burn: int, n_steps: int, epochs: int, records: int = 1 << 20
                       "tflops": prof["network_rows"] * flop / (prof["network_ms"] * 1e-3) / 1e12
                       if prof["network_ms"] > 0 else None}
     out.update({"burn_in_sweeps": burn, "records": int(net.n_records), "epochs": epochs,
-                "loss_first_last": [losses[0], losses[-1]] if losses else None, "train_seconds": train_s,
-                "rng": "philox"})
+                "loss_first_last": [losses[0], losses[-1]] if losses else None,
+                "mixture_loss_first_last": [losses_mix[0], losses_mix[-1]] if losses_mix else None,
+                "train_seconds": train_s, "rng": "philox"})
+    mix.close()
     net.close()
     ctrl.close()
     sim.close()
