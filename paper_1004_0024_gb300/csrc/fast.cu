@@ -51,9 +51,9 @@ cudaError_t fast_set_smem_limits()
     for (int variant : {0, 1, 2, 3, 4, 5})
         for (int fb : {16, 32})
             for (int rng : {0, 1})
-                for (int cm : {1, 2, 3, 4, 5, 8}) {
+                for (int cm : {1, 2, 3, 4, 5, 8, 101, 102}) {
                     if ((variant == 2 && cm != 1) || (variant == 5 && (batch == 2 || fb != 16)) ||
-                        (variant != 5 && (cm == 3 || cm == 5)))
+                        (variant != 5 && (cm == 3 || cm == 5 || cm > 100)) || (cm > 100 && batch != 0))
                         continue;
                     void* fn = pick(fb, rng, cm, variant, batch == 1, batch == 2);
                     if (!fn)

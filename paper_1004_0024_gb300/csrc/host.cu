@@ -676,7 +676,7 @@ std::vector<int> packed_word_slots(const ising_s* g, int T)
     std::vector<int> slot(S);
     for (int p = 0; p < S; ++p)
         slot[p] = p;
-    if (S < 64 || T <= 0 || g->packed_off)  // packed_off: a batch instance
+    if (S < 64 || T <= 0 || g->packed_off || M > 32)  // packed_off: a batch instance
         return slot;
     const int rounds = (ns + T - 1) / T;
     const int NSP = rounds * T;
@@ -839,6 +839,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g, int T)
     using isg::packed_detail::kMaxDeg;
     const int S = g->S;
     const std::vector<int> ws = packed_word_slots_cached(g, T);
+    const uint32_t W = g->M > 32 ? uint32_t(g->M / 32) : 1u;  // words per column
     auto pad4 = [](size_t n) { return (n + 3) & ~size_t(3); };
     std::vector<uint32_t> pk(isg::packed_detail::packed_table_bytes(S, g->nslots) / 4, 0u);
     for (int p = 0; p < S; ++p) {
@@ -846,7 +847,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g, int T)
         const int jt2 = 2 * g->jtau[p];
         long long c = g->h[g->site[p]] - jt2;
         d[0] = uint32_t(g->lev0p[p]) | (uint32_t(g->site[p]) << 16);
-        d[1] = 4u * uint32_t(ws[p]);
+        d[1] = 4u * W * uint32_t(ws[p]);
         d[2] = uint32_t(jt2);
         const int e0 = g->nbr_off[p], deg = g->nbr_off[p + 1] - e0;
         for (int e = 0; e < kMaxDeg; ++e) {
@@ -858,7 +859,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g, int T)
             const uint32_t en = g->nbr[e0 + e];
             const int pj = int(en >> 16), J = int(int16_t(en & 0xFFFFu));
             c -= J;
-            d[4 + e] = 4u * uint32_t(ws[pj]);
+            d[4 + e] = 4u * W * uint32_t(ws[pj]);
             d[10 + e] = uint32_t(2 * J);
         }
         d[3] = uint32_t(int32_t(c));
@@ -893,13 +894,15 @@ int kernel_variant(const ising_s* g)
 }
 
 // The packed kernel's model limits: M in {8, 16, 32} (the column in one
-// register, whole 4-word blocks), spatial degree <= 6, |J| <= 127 (8 bits in
-// the descriptor), positions and levels in 16 bits, plain couplings, one
-// replica per block and no opt-out.
+// register, whole 4-word blocks) or a multiple of 32 up to 1024 (long columns:
+// M / 32 words, the busy one in a register), spatial degree <= 6,
+// |J| <= 127, positions and levels in 16 bits, plain couplings, one replica
+// per block and no opt-out.
 bool packed_eligible(const ising_s* g)
 {
-    return (g->M == 8 || g->M == 16 || g->M == 32) && g->max_sp_deg <= 6 && g->max_sp_J <= 127 &&
-           g->S < 65536 && g->D0 < 65536 && g->nslots >= 1 && !g->split &&
+    const bool long_cols = g->M > 32 && g->M % 32 == 0 && g->M <= 1024 && g->S * (g->M / 32) < (1 << 20);
+    return (g->M == 8 || g->M == 16 || g->M == 32 || long_cols) && g->max_sp_deg <= 6 && g->max_sp_J <= 127 &&
+           g->S < 65536 && g->D < 65536 && g->nslots >= 1 && !g->split &&
            g->G_req <= 1 && !g->packed_off && !g->lean_off && !g->fast_off && !g->track_on &&
            (g->T_req == 0 || g->T_req == 32 || g->T_req == 64 || g->T_req == 128 || g->T_req == 256);
 }
@@ -924,6 +927,11 @@ bool choose_packed(ising_s* g)
         }
     if (rmax == 0)
         return false;
+    if (g->M > 32) {  // long columns: instantiations of one and two rounds
+        if (rmax > 2)
+            return false;
+        rmax += isg::kPackedLong;
+    }
     if (!g->d_pk) {
         const std::vector<uint32_t> pk = packed_tables(g, T);
         if (upload(&g->d_pk, pk) != ISING_OK)

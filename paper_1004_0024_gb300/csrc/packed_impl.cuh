@@ -104,7 +104,7 @@ __host__ __device__ inline PackedLayout packed_layout(const SweepArgs& a, int th
     L.pos = o;   o += r16(4u * uint32_t(a.S));
     L.soff = o;  o += r16(4u * uint32_t(a.nslots + 1));
     L.scol = o;  o += r16(4u * uint32_t(a.S));
-    L.colw = o;  o += r16(4u * uint32_t(a.S));
+    L.colw = o;  o += r16(4u * uint32_t(a.S) * uint32_t(a.M > 32 ? a.M / 32 : 1));  // M / 32 words per long column
     L.stage = o;  // the word ring: 16 levels x slots rounded up to whole rounds
     o += 64u * uint32_t((a.nslots + threads - 1) / threads) * uint32_t(threads);
     L.thr = o;   o += r16(4u * uint32_t(a.K));
@@ -149,7 +149,9 @@ __device__ __forceinline__ void philox_round(uint4& c, uint32_t& k0, uint32_t& k
     k1 += 0xBB67AE85u;
 }
 
-template <int RNG, int RMAX>
+// LONG: columns of M = 32 W slices (W >= 2), W consecutive words per column;
+// a slot keeps the busy word and its two neighbours in registers.
+template <int RNG, int RMAX, bool LONG = false>
 __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, const int nblk)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -217,10 +219,19 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         for (int e = 0; e < kMaxDeg; ++e)
             d[4 + e] += colw_s;
         const int q = int(d[0] >> 16);
-        uint32_t b = 0u;
-        for (int t = 0; t < M; ++t)
-            b |= (spg[size_t(t) * S + q] > 0 ? 1u : 0u) << t;
-        colw[(d[1] - colw_s) >> 2] = b;
+        if constexpr (LONG) {
+            for (int w = 0; w < M / 32; ++w) {
+                uint32_t b = 0u;
+                for (int t = 0; t < 32; ++t)
+                    b |= (spg[size_t(32 * w + t) * S + q] > 0 ? 1u : 0u) << t;
+                colw[((d[1] - colw_s) >> 2) + w] = b;
+            }
+        } else {
+            uint32_t b = 0u;
+            for (int t = 0; t < M; ++t)
+                b |= (spg[size_t(t) * S + q] > 0 ? 1u : 0u) << t;
+            colw[(d[1] - colw_s) >> 2] = b;
+        }
     }
     {
         const int temp = fused ? temp_s[r] : a.temp_of_slot[r];
@@ -229,8 +240,8 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     }
     __syncthreads();
 
-    const uint32_t rep = (M == 32) ? 1u : (M == 16 ? 0x00010001u : 0x01010101u);
-    const uint32_t cmask = (M == 32) ? 0xFFFFFFFFu : ((1u << M) - 1u);
+    const uint32_t rep = (LONG || M == 32) ? 1u : (M == 16 ? 0x00010001u : 0x01010101u);
+    const uint32_t cmask = (LONG || M == 32) ? 0xFFFFFFFFu : ((1u << M) - 1u);
     const int nrb = M >> 2;  // word blocks per column
     const unsigned FULL = 0xFFFFFFFFu;
     const bool shfl_thr = K <= 32;
@@ -260,6 +271,9 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     // the word's copies for M < 32), rotated by one each level
     uint32_t mrot[RMAX] = {};
     uint32_t bits[RMAX], nw[RMAX][kMaxDeg];  // nw: shared address of each neighbour's column word
+    // LONG: the words before and after the busy one (for the Trotter bits at
+    // a word's edges) and the address of the column's first word
+    uint32_t wprev[RMAX] = {}, wnext[RMAX] = {}, sa0[RMAX] = {};
     int nj[RMAX][kMaxDeg];                    // 2 J of each neighbour
     // request cursor: the slot's next block to fetch (block xb of the column
     // at position xcol, site xsite, xk in the slot's list), its first level xx
@@ -287,7 +301,15 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         nj[c][0] = int(d2.z); nj[c][1] = int(d2.w); nj[c][2] = int(d3.x);
         nj[c][3] = int(d3.y); nj[c][4] = int(d3.z); nj[c][5] = int(d3.w);
         pp[c] = p;
-        bits[c] = colw[(d0.y - colw_s) >> 2] * rep;
+        if constexpr (LONG) {
+            const int w0 = int((d0.y - colw_s) >> 2), W = M / 32;
+            sa0[c] = d0.y;
+            bits[c] = colw[w0];
+            wprev[c] = colw[w0 + W - 1];  // slice M - 1, the ring neighbour of slice 0
+            wnext[c] = colw[w0 + 1];
+        } else {
+            bits[c] = colw[(d0.y - colw_s) >> 2] * rep;
+        }
         mrot[c] = __funnelshift_r(rep, rep, uint32_t(lv[c] - l));
     };
     auto set_next = [&](int c) {
@@ -584,8 +606,13 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                         fa += (wn[c][e] & m) ? nj[c][e] : 0;
                         fb += (wn[c][e + 1] & m) ? nj[c][e + 1] : 0;
                     }
-                    fa += (bits[c] & mp) ? jt2[c] : 0;
-                    fb += (bits[c] & mn) ? jt2[c] : 0;
+                    if constexpr (LONG) {  // at a word's edges the Trotter bit is in the next word
+                        fa += ((m == 1u ? wprev[c] : bits[c]) & mp) ? jt2[c] : 0;
+                        fb += ((m == 0x80000000u ? wnext[c] : bits[c]) & mn) ? jt2[c] : 0;
+                    } else {
+                        fa += (bits[c] & mp) ? jt2[c] : 0;
+                        fb += (bits[c] & mn) ? jt2[c] : 0;
+                    }
                     const int h = fa + fb;                 // the local field
                     const int k = (bits[c] & m) ? h : -h;  // s_t f
                     // T(k) for 0 < k < K (lane k), else T(0) = 0: flip iff k <= 0
@@ -604,6 +631,27 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                                  : "memory");
                 }
             }  // any
+            if constexpr (LONG) {
+                // a busy slot at the last slice of a word moves to the next word:
+                // its neighbours' words too; the next word is word 0 when
+                // entering the column's last word (slice M - 1's ring neighbour)
+#pragma unroll
+                for (int c = 0; c < RMAX; ++c) {
+                    const int t = l - lv[c];
+                    if (mrot[c] == 0x80000000u && t >= 0 && t < M - 1) {
+                        wprev[c] = bits[c];
+                        bits[c] = wnext[c];
+                        sa[c] += 4u;
+#pragma unroll
+                        for (int e = 0; e < kMaxDeg; ++e)
+                            nw[c][e] += 4u;
+                        asm volatile("ld.shared.u32 %0, [%1];"
+                                     : "=r"(wnext[c])
+                                     : "r"(t + 33 < M ? sa[c] + 4u : sa0[c])
+                                     : "memory");
+                    }
+                }
+            }
 #pragma unroll
             for (int c = 0; c < RMAX; ++c)
                 mrot[c] = mnext[c];
@@ -742,11 +790,16 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         const int t = i / S, q = i - t * S, p = pos[q];
         const int tm = (t == 0) ? M - 1 : t - 1, tp = (t == M - 1) ? 0 : t + 1;
         const uint32_t* d = desc + p * kDescWords;
-        const uint32_t cb = colw[(d[1] - colw_s) >> 2];
-        int f = int(d[3]) + int(d[2]) * int(((cb >> tm) & 1u) + ((cb >> tp) & 1u));
+        const int wo = LONG ? (t >> 5) : 0;  // the word of slice t (LONG)
+        const int bt = LONG ? (t & 31) : t;
+        const uint32_t* cw = colw + ((d[1] - colw_s) >> 2);
+        const uint32_t cb = cw[wo];
+        const uint32_t cbm = LONG ? cw[tm >> 5] : cb, cbp = LONG ? cw[tp >> 5] : cb;
+        int f = int(d[3]) + int(d[2]) * int(((cbm >> (LONG ? (tm & 31) : tm)) & 1u) +
+                                            ((cbp >> (LONG ? (tp & 31) : tp)) & 1u));
         for (int e = 0; e < kMaxDeg; ++e)
-            f += int(d[10 + e]) * int((colw[(d[4 + e] - colw_s) >> 2] >> t) & 1u);
-        spo[i] = ((cb >> t) & 1u) ? int8_t(1) : int8_t(-1);
+            f += int(d[10 + e]) * int((colw[((d[4 + e] - colw_s) >> 2) + wo] >> bt) & 1u);
+        spo[i] = ((cb >> bt) & 1u) ? int8_t(1) : int8_t(-1);
         if (f16)
             static_cast<int16_t*>(a.fields)[size_t(r) * N + i] = int16_t(f);
         else
@@ -773,10 +826,10 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
 // Register budget: about 30 registers per slot round; blocks of up to 256
 // sweep threads (one round) or 128 (more rounds), plus the generator warps,
 // two resident blocks per SM.
-template <int RNG, int RMAX>
+template <int RNG, int RMAX, bool LONG = false>
 __global__ void __launch_bounds__(RMAX == 1 ? 256 + 64 : 128 + 64, 2) packed_kernel(const SweepArgs a)
 {
-    packed_body<RNG, RMAX>(a, int(blockIdx.x), int(gridDim.x));
+    packed_body<RNG, RMAX, LONG>(a, int(blockIdx.x), int(gridDim.x));
 }
 
 // Ragged batches: block b runs replica items[b].block of instance
@@ -816,6 +869,9 @@ void* pick_packed(int rmax)
     case 3: return reinterpret_cast<void*>(&packed_kernel<RNG, 3>);
     case 5: return reinterpret_cast<void*>(&packed_kernel<RNG, 5>);
     case 8: return reinterpret_cast<void*>(&packed_kernel<RNG, 8>);
+    // long columns (M a multiple of 32 above 32): round count + kPackedLong
+    case 101: return reinterpret_cast<void*>(&packed_kernel<RNG, 1, true>);
+    case 102: return reinterpret_cast<void*>(&packed_kernel<RNG, 2, true>);
     default: return nullptr;
     }
 }
@@ -825,6 +881,7 @@ void* pick_packed(int rmax)
 // slot rounds per thread with an instantiation, and the kernels (packed_mt.cu,
 // packed_philox.cu)
 constexpr int kPackedRounds[5] = {1, 2, 3, 5, 8};
+constexpr int kPackedLong = 100;  // round codes of the long-column instantiations: 100 + rounds (1, 2)
 constexpr int kPackedGenWarps = packed_detail::kGenWarps;
 void* packed_kernel_mt(int rmax, bool batch = false);
 void* packed_kernel_philox(int rmax, bool batch = false);

@@ -296,17 +296,17 @@ def test_track_kernel_matches_lean_and_oracle(ising, L, M, R, rng, fb):
 
 
 @pytest.mark.parametrize("rng", ["mt19937", "philox"])
-@pytest.mark.parametrize("flags", [-1, 2])
+@pytest.mark.parametrize("flags", [-1, 16, 2])
 def test_paper_shape_sampled_replicas(ising, rng, flags):
     """The paper's workload shape (96-spin layers, 256 Trotter slices: the
-    lean kernel's long columns by default, the generic kernel with flag 2),
-    115 replicas without PT: the first 6 slots against an oracle run of those
-    replicas alone."""
+    packed kernel's long columns by default, the lean kernel's with flag 16
+    (no packed kernel), the generic kernel with flag 2), 115 replicas without
+    PT: the first 6 slots against an oracle run of those replicas alone."""
     c = W.config_paper()
     dev = ising.Ising(c["graph"], c["betas"], seed=c["seed"], rng=rng, field_bits=16)
     if flags >= 0:
         dev.set_launch(0, 0, flags)
-    assert dev.info()["fast_kernel"] == (2 if flags < 0 else 0)
+    assert dev.info()["fast_kernel"] == {-1: 4, 16: 2, 2: 0}[flags]
     dev.run(3, 0)
     dev.run(2, 0)
     st = dev.read_state()
@@ -318,19 +318,25 @@ def test_paper_shape_sampled_replicas(ising, rng, flags):
     dev.close()
 
 
-@pytest.mark.parametrize("L,M,fb", [(3, 64, 32), (3, 96, 16), (3, 128, 16), (4, 160, 32), (3, 64, 16)])
+@pytest.mark.parametrize("L,M,fb", [(3, 64, 32), (3, 96, 16), (3, 128, 16), (4, 160, 32), (3, 64, 16),
+                                    (5, 256, 16)])
 @pytest.mark.parametrize("rng", ["mt19937", "philox"])
-def test_long_columns(ising, L, M, fb, rng):
-    """M a multiple of 32 above 32: the lean kernel keeps the column as M/32
-    words and walks them in registers (ring wrap at both ends); with PT after
-    every sweep, bit-exact against the oracle."""
+@pytest.mark.parametrize("path", ["packed", "lean"])
+def test_long_columns(ising, L, M, fb, rng, path):
+    """M a multiple of 32 above 32: the packed kernel (by default) and the
+    lean kernel (flag 16) keep the column as M/32 words and walk them in
+    registers (ring wrap at both ends, Trotter bits across word edges); with
+    PT after every sweep, bit-exact against the oracle."""
     g = W.layered_graph(L, M, graph_seed=L * 100 + M, j_tau=3)
     betas = W.geometric_betas(9, 0.1, 2.0)
-    dev, ref = pair(ising, g, betas, 4242 + M, rng, fb)
-    assert dev.info()["fast_kernel"] == 2
+    dev, ref = pair(ising, g, betas, 4242 + M, rng, fb, None if path == "packed" else (0, 0, 16))
+    assert dev.info()["fast_kernel"] == (4 if path == "packed" else 2)
     dev.run(7, 1)
     ref.run(7, 1)
     assert_same(dev, ref)
+    dev.run(5, 2)
+    ref.run(5, 2)
+    assert_same(dev, ref, "after 5 more sweeps, PT every second")
 
 
 @pytest.mark.parametrize("accept", ["fast", "accurate"])
