@@ -277,7 +277,7 @@ def workload_line(name, rng, steps, warmup, flush, stream, dev_index, sweeps=0):
     if out["roofline"] and t["sweep_launches"] > 0:
         out["roofline"]["latency_floor"] = latency_floor(
             info["levels"], c["sweeps"] * steps / t["sweep_launches"], t["kernel_ms"] / t["sweep_launches"],
-            t["clocks"])
+            t["clocks"], info.get("persistent_ok", 1))
     if t["first_clocks"] is not None:
         out["remeasured"] = {"first_clocks": t["first_clocks"]}
     return out
@@ -381,7 +381,8 @@ def run_ours(args):
                                 info["fast_kernel"], args.workload)
     if line["roofline"] and sweep_launches > 0:
         line["roofline"]["latency_floor"] = latency_floor(
-            info["levels"], sweeps * args.steps / sweep_launches, kernel_ms / sweep_launches, clocks)
+            info["levels"], sweeps * args.steps / sweep_launches, kernel_ms / sweep_launches, clocks,
+            info.get("persistent_ok", 1))
     if e2e is not None:
         line["e2e"] = e2e
     if args.workload == "paper" and c["sweeps"] == 30000:
@@ -549,11 +550,16 @@ LEVEL_CHAIN_INT_OPS = 10
 _LATENCIES = None
 
 
-def latency_floor(levels, sweeps_per_launch, kernel_ms_per_launch, clocks):
+def latency_floor(levels, sweeps_per_launch, kernel_ms_per_launch, clocks, resident=1):
     """Latency floor of a sweep launch: levels x sweeps x the cycles of one
     level's dependent chain, with the latencies measured on this GPU
     (ising_measure_latencies), at the sampled SM clock; frac = floor /
-    measured kernel time."""
+    measured kernel time.  Only for ladders whose replicas are all resident
+    at once (a persistent launch); a larger ladder runs in waves of resident
+    blocks and is bound by throughput, not by one replica's chain."""
+    if not resident:
+        return {"frac": None, "why": "replicas not all resident at once: the launch runs waves of blocks and is "
+                                     "throughput-bound, so one replica's chain of levels does not bound it"}
     global _LATENCIES
     from paper_1004_0024_gb300 import ising
     if _LATENCIES is None:
