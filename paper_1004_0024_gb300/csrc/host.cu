@@ -839,7 +839,6 @@ std::vector<uint32_t> packed_tables(const ising_s* g, int T)
     using isg::packed_detail::kMaxDeg;
     const int S = g->S;
     const std::vector<int> ws = packed_word_slots_cached(g, T);
-    const uint32_t W = g->M > 32 ? uint32_t(g->M / 32) : 1u;  // words per column
     auto pad4 = [](size_t n) { return (n + 3) & ~size_t(3); };
     std::vector<uint32_t> pk(isg::packed_detail::packed_table_bytes(S, g->nslots) / 4, 0u);
     for (int p = 0; p < S; ++p) {
@@ -847,7 +846,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g, int T)
         const int jt2 = 2 * g->jtau[p];
         long long c = g->h[g->site[p]] - jt2;
         d[0] = uint32_t(g->lev0p[p]) | (uint32_t(g->site[p]) << 16);
-        d[1] = 4u * W * uint32_t(ws[p]);
+        d[1] = 4u * uint32_t(ws[p]);  // long columns: their first word (word w is S words further on per w)
         d[2] = uint32_t(jt2);
         const int e0 = g->nbr_off[p], deg = g->nbr_off[p + 1] - e0;
         for (int e = 0; e < kMaxDeg; ++e) {
@@ -859,7 +858,7 @@ std::vector<uint32_t> packed_tables(const ising_s* g, int T)
             const uint32_t en = g->nbr[e0 + e];
             const int pj = int(en >> 16), J = int(int16_t(en & 0xFFFFu));
             c -= J;
-            d[4 + e] = 4u * W * uint32_t(ws[pj]);
+            d[4 + e] = 4u * uint32_t(ws[pj]);
             d[10 + e] = uint32_t(2 * J);
         }
         d[3] = uint32_t(int32_t(c));

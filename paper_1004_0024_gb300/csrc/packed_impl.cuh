@@ -149,8 +149,10 @@ __device__ __forceinline__ void philox_round(uint4& c, uint32_t& k0, uint32_t& k
     k1 += 0xBB67AE85u;
 }
 
-// LONG: columns of M = 32 W slices (W >= 2), W consecutive words per column;
-// a slot keeps the busy word and its two neighbours in registers.
+// LONG: columns of M = 32 W slices (W >= 2), stored word-major (word w of
+// the column at slot c is colw[w S + c], so a warp's loads of different
+// columns spread over the banks); a slot keeps the busy word and its two
+// neighbours in registers.
 template <int RNG, int RMAX, bool LONG = false>
 __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, const int nblk)
 {
@@ -224,7 +226,7 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 uint32_t b = 0u;
                 for (int t = 0; t < 32; ++t)
                     b |= (spg[size_t(32 * w + t) * S + q] > 0 ? 1u : 0u) << t;
-                colw[((d[1] - colw_s) >> 2) + w] = b;
+                colw[((d[1] - colw_s) >> 2) + w * S] = b;
             }
         } else {
             uint32_t b = 0u;
@@ -305,8 +307,8 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             const int w0 = int((d0.y - colw_s) >> 2), W = M / 32;
             sa0[c] = d0.y;
             bits[c] = colw[w0];
-            wprev[c] = colw[w0 + W - 1];  // slice M - 1, the ring neighbour of slice 0
-            wnext[c] = colw[w0 + 1];
+            wprev[c] = colw[w0 + (W - 1) * S];  // slice M - 1, the ring neighbour of slice 0
+            wnext[c] = colw[w0 + S];
         } else {
             bits[c] = colw[(d0.y - colw_s) >> 2] * rep;
         }
@@ -632,22 +634,24 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 }
             }  // any
             if constexpr (LONG) {
-                // a busy slot at the last slice of a word moves to the next word:
+                // a busy slot at the last slice of a word moves to the next word (S
+                // words further on):
                 // its neighbours' words too; the next word is word 0 when
                 // entering the column's last word (slice M - 1's ring neighbour)
 #pragma unroll
                 for (int c = 0; c < RMAX; ++c) {
                     const int t = l - lv[c];
                     if (mrot[c] == 0x80000000u && t >= 0 && t < M - 1) {
+                        const uint32_t wstride = 4u * uint32_t(S);  // bytes between a column's words
                         wprev[c] = bits[c];
                         bits[c] = wnext[c];
-                        sa[c] += 4u;
+                        sa[c] += wstride;
 #pragma unroll
                         for (int e = 0; e < kMaxDeg; ++e)
-                            nw[c][e] += 4u;
+                            nw[c][e] += wstride;
                         asm volatile("ld.shared.u32 %0, [%1];"
                                      : "=r"(wnext[c])
-                                     : "r"(t + 33 < M ? sa[c] + 4u : sa0[c])
+                                     : "r"(t + 33 < M ? sa[c] + wstride : sa0[c])
                                      : "memory");
                     }
                 }
@@ -793,12 +797,12 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
         const int wo = LONG ? (t >> 5) : 0;  // the word of slice t (LONG)
         const int bt = LONG ? (t & 31) : t;
         const uint32_t* cw = colw + ((d[1] - colw_s) >> 2);
-        const uint32_t cb = cw[wo];
-        const uint32_t cbm = LONG ? cw[tm >> 5] : cb, cbp = LONG ? cw[tp >> 5] : cb;
+        const uint32_t cb = cw[wo * S];
+        const uint32_t cbm = LONG ? cw[(tm >> 5) * S] : cb, cbp = LONG ? cw[(tp >> 5) * S] : cb;
         int f = int(d[3]) + int(d[2]) * int(((cbm >> (LONG ? (tm & 31) : tm)) & 1u) +
                                             ((cbp >> (LONG ? (tp & 31) : tp)) & 1u));
         for (int e = 0; e < kMaxDeg; ++e)
-            f += int(d[10 + e]) * int((colw[((d[4 + e] - colw_s) >> 2) + wo] >> bt) & 1u);
+            f += int(d[10 + e]) * int((colw[((d[4 + e] - colw_s) >> 2) + wo * S] >> bt) & 1u);
         spo[i] = ((cb >> bt) & 1u) ? int8_t(1) : int8_t(-1);
         if (f16)
             static_cast<int16_t*>(a.fields)[size_t(r) * N + i] = int16_t(f);
