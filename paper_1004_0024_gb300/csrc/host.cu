@@ -667,16 +667,19 @@ int32_t extract_slices(ising_s* g)
 // slot schedule (a lane holds its slot's current column: the first one from
 // the sweep's start, the next one from the last level divisible by 4 before
 // its start; warps without a busy lane skip the level when a thread has one
-// slot).  Deterministic; about 40 tries per column.  Batch instances keep
-// the identity (thousands of small models: the search would dominate their
-// setup).
+// slot; long columns: the busy word of each column, all at one bank offset
+// when S is a multiple of 32).  Deterministic; about 40 tries per column.
+// Batch instances keep the identity (thousands of small models: the search
+// would dominate their setup).
 std::vector<int> packed_word_slots(const ising_s* g, int T)
 {
     const int S = g->S, M = g->M, D = g->D, ns = g->nslots;
     std::vector<int> slot(S);
     for (int p = 0; p < S; ++p)
         slot[p] = p;
-    if (S < 64 || T <= 0 || g->packed_off || M > 32)  // packed_off: a batch instance
+    // packed_off: a batch instance; long columns are stored word-major, so a
+    // word's bank is its slot's only when S is a multiple of 32
+    if (S < 64 || T <= 0 || g->packed_off || (M > 32 && S % 32 != 0))
         return slot;
     const int rounds = (ns + T - 1) / T;
     const int NSP = rounds * T;
