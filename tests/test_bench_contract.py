@@ -21,8 +21,23 @@ def test_alu_roofline_counts_algorithmic_ops_over_the_issue_peak():
     assert r["achieved"] == pytest.approx(attempts * ops / 0.036 / 1e12)
     assert r["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] is None  # no DRAM capture of the current kernel build
+    assert r["traffic"] is None  # lean kernel (variant 2): no DRAM capture of its current build
     assert bench.ops_per_attempt(g, "philox") == pytest.approx(ops + 3)
+
+
+def test_measured_traffic_of_the_packed_kernel_scales_with_the_sweeps():
+    """The packed kernel's DRAM bytes come from its 1-pass ncu captures: the
+    200-sweep launch as captured, other launch lengths on the line through the
+    10- and 200-sweep captures; other kernels and generators report none."""
+    c = W.config1()
+    g = c["graph"]
+    per_sweep = g.n * c["R"]
+    r = bench.roofline(c, "mt19937", per_sweep * 200, 19.2, 1, {"sm_mhz": 2070.0}, 4)
+    assert r["traffic"] == pytest.approx(3311.4e6)
+    r10 = bench.roofline(c, "mt19937", per_sweep * 20, 2.3, 2, {"sm_mhz": 2070.0}, 4)
+    assert r10["traffic"] == pytest.approx(234.3e6)
+    assert "ncu" in r["traffic_basis"]
+    assert bench.roofline(c, "philox", per_sweep * 200, 19.6, 1, {"sm_mhz": 2070.0}, 4)["traffic"] is None
 
 
 def test_hbm_roofline_of_streamed_words():
@@ -120,3 +135,9 @@ def test_latency_floor_is_levels_times_the_level_chain():
     assert f["cycles_per_level"] == cyc
     assert abs(f["ms_per_launch"] - 400 * 200 * cyc / 2.0e6) < 1e-9
     assert abs(f["frac"] - f["ms_per_launch"] / 26.0) < 1e-12
+
+
+
+def test_latency_floor_only_for_resident_ladders():
+    f = bench.latency_floor(83, 500, 1086.0, {"sm_mhz": 2070.0}, resident=0)
+    assert f["frac"] is None and "resident" in f["why"]
