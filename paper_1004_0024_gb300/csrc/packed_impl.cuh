@@ -723,6 +723,17 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 if (t_alt >= 0 && t_alt < R)
                     th_alt = __ldg(a.thr + size_t(t_alt) * K + (tid & 31));
             }
+            // this thread's first pair: its table row and (MT19937) swap word do
+            // not depend on the energies, so they are loaded before the barrier
+            const int npairs = par ? (R - 1) / 2 : R / 2;
+            int pre_len = 0, pre_off = 0;
+            uint32_t pre_u = 0u;
+            if (tid < npairs) {
+                pre_len = a.swlen[2 * tid + par];
+                pre_off = a.swoff[2 * tid + par];
+                if (RNG == 0)
+                    pre_u = a.swbuf[size_t(npass) * a.maxpairs + tid];
+            }
             __syncthreads();
             int* Ep = a.E_pub + size_t(npass & 1) * R;
             if (tid == 0) {
@@ -736,19 +747,20 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
             else if (!grid_sync(a.gridbar, unsigned(npass + 1) * unsigned(nblk), a.err, &s_flag))
                 return;
             {  // the pairs of a pass are disjoint: one per thread
-                const int npairs = par ? (R - 1) / 2 : R / 2;
                 for (int j = tid; j < npairs; j += NT) {
                     const int k = 2 * j + par;
+                    const bool first = j == tid;
                     const int sa = slot_s[k], sb = slot_s[k + 1];
                     const long long d = (long long)__ldcg(Ep + sa) - (long long)__ldcg(Ep + sb);
                     uint32_t u;
                     if (RNG == 0)
-                        u = a.swbuf[size_t(npass) * a.maxpairs + j];
+                        u = first ? pre_u : a.swbuf[size_t(npass) * a.maxpairs + j];
                     else
                         u = pick4(philox4x32_10(make_uint4(uint32_t(j) >> 2, uint32_t(p), a.inst, 1u), a.seed,
                                                 0xFFFFFFFFu),
                                   j & 3);
-                    const bool take = (d <= 0) || (d < a.swlen[k] && u < a.swthr[a.swoff[k] + d]);
+                    const int len = first ? pre_len : a.swlen[k], off = first ? pre_off : a.swoff[k];
+                    const bool take = (d <= 0) || (d < len && u < a.swthr[off + d]);
                     if (take) {
                         slot_s[k] = sb;
                         slot_s[k + 1] = sa;
