@@ -668,18 +668,17 @@ int32_t extract_slices(ising_s* g)
 // the sweep's start, the next one from the last level divisible by 4 before
 // its start; warps without a busy lane skip the level when a thread has one
 // slot; long columns: the busy word of each column, all at one bank offset
-// when S is a multiple of 32).  Deterministic; about 40 tries per column.
-// Batch instances keep the identity (thousands of small models: the search
-// would dominate their setup).
+// when S is a multiple of 32).  Deterministic; about 40 tries per column
+// (a batch runs its instances' searches on the host threads).
 std::vector<int> packed_word_slots(const ising_s* g, int T)
 {
     const int S = g->S, M = g->M, D = g->D, ns = g->nslots;
     std::vector<int> slot(S);
     for (int p = 0; p < S; ++p)
         slot[p] = p;
-    // packed_off: a batch instance; long columns are stored word-major, so a
-    // word's bank is its slot's only when S is a multiple of 32
-    if (S < 64 || T <= 0 || g->packed_off || (M > 32 && S % 32 != 0))
+    // long columns are stored word-major, so a word's bank is its slot's only
+    // when S is a multiple of 32
+    if (S < 64 || T <= 0 || (M > 32 && S % 32 != 0))
         return slot;
     const int rounds = (ns + T - 1) / T;
     const int NSP = rounds * T;
@@ -2669,21 +2668,36 @@ bool packed_batch_setup(ising_batch_s* b)
         return false;
     const int gen = kPackedGenWarps;  // the generator warps (both generators)
     std::map<std::pair<int, int>, std::vector<int>> by_T;  // (sweep threads, rounds)
-    std::vector<size_t> smem(b->inst.size(), 0);
-    for (int i = 0; i < int(b->inst.size()); ++i) {
-        ising_s* g = b->inst[i];
+    const int n_inst = int(b->inst.size());
+    std::vector<size_t> smem(n_inst, 0);
+    // one slot per thread up to 256 slots, else 128 threads of three rounds
+    auto threads_of = [](const ising_s* g) { return g->nslots <= 256 ? ((g->nslots + 31) / 32) * 32 : 128; };
+    for (const ising_s* g : b->inst) {
         const bool ok = (g->M == 8 || g->M == 16 || g->M == 32) && g->max_sp_deg <= 6 && g->max_sp_J <= 127 &&
                         g->S < 65536 && g->D0 < 65536 && g->nslots >= 1 && g->nslots <= 384 && !g->split &&
                         g->R <= 16384;
         if (!ok)
             return false;
-        // one slot per thread up to 256 slots, else 128 threads of three rounds
-        const int T = g->nslots <= 256 ? ((g->nslots + 31) / 32) * 32 : 128;
+    }
+    // the instances' tables (with their word placement searches) on the host
+    // threads, then uploaded in order
+    std::vector<std::vector<uint32_t>> pks(n_inst);
+    {
+        const int nthr = std::max(1, std::min(isg::host_threads(), n_inst));
+        isg::host_parallel(nthr, [&](int p) {
+            for (int i = p; i < n_inst; i += nthr)
+                if (!b->inst[i]->d_pk)
+                    pks[i] = packed_tables(b->inst[i], threads_of(b->inst[i]));
+        });
+    }
+    for (int i = 0; i < n_inst; ++i) {
+        ising_s* g = b->inst[i];
+        const int T = threads_of(g);
         if (!g->d_pk) {
-            const std::vector<uint32_t> pk = packed_tables(g, T);
-            if (upload(&g->d_pk, pk) != ISING_OK)
+            if (upload(&g->d_pk, pks[i]) != ISING_OK)
                 return false;
-            g->pk_bytes = uint32_t(pk.size() * 4);
+            g->pk_bytes = uint32_t(pks[i].size() * 4);
+            std::vector<uint32_t>().swap(pks[i]);
         }
         const int rmax = g->nslots <= 256 ? 1 : 3;
         SweepArgs a = base_args(g);
