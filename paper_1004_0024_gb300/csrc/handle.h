@@ -87,6 +87,7 @@ struct ising_s {
     uint32_t* d_pk = nullptr;
     uint32_t pk_bytes = 0;
     bool use_packed = false, packed_off = false;
+    int gen_slices = 4;  // the packed kernel's MT19937 staging: 4 slices, or 2 where 4 would not fit
     int fast_cmax = 1;
     size_t fast_smem = 0, smem_fused = 0;
     int G_req = 0, T_req = 0, allow_persistent = 1;

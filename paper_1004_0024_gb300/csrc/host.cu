@@ -942,10 +942,28 @@ bool choose_packed(ising_s* g)
     SweepArgs a = base_args(g);
     a.G = 1;
     a.gen = kPackedGenWarps;
-    const size_t plain = packed_smem_bytes(a, T);
+    // MT19937: stage 4 slices per generator store, or 2 where the blocks of
+    // a ladder would otherwise not all be resident (16 S bytes -> 8 S)
+    int gsl = 4;
+    a.gen_slices = 4;
+    const int sw0 = a.swap_every;
+    size_t plain = packed_smem_bytes(a, T);
     a.swap_every = 1;
-    const size_t fused = packed_smem_bytes(a, T);
+    size_t fused = packed_smem_bytes(a, T);
     const size_t lim = sweep_max_dynamic_smem() ? sweep_max_dynamic_smem() : 200 * 1024;
+    if (g->rng == ISING_RNG_MT19937) {
+        int per4 = 0;
+        const bool ok4 = fused <= lim && fast_max_blocks_per_sm(g->field_bits, rmax, g->rng, T + 32 * a.gen, fused,
+                                                               &per4, 5) == cudaSuccess;
+        if (!(ok4 && (long long)per4 * g_num_sms >= g->R)) {
+            gsl = 2;
+            a.gen_slices = 2;
+            a.swap_every = sw0;
+            plain = packed_smem_bytes(a, T);
+            a.swap_every = 1;
+            fused = packed_smem_bytes(a, T);
+        }
+    }
     if (plain > lim)
         return false;
     // A ladder that cannot be resident at once is throughput-bound rather than
@@ -962,6 +980,7 @@ bool choose_packed(ising_s* g)
         return false;
     g->use_packed = true;
     g->use_fast = true;
+    g->gen_slices = gsl;
     g->G = 1;
     g->T = T;
     g->blocks = g->R;
@@ -1133,6 +1152,7 @@ SweepArgs base_args(ising_s* g)
     a.nslots = g->nslots;
     a.field_bits = g->field_bits;
     a.gen = packed_gen(g) ? kPackedGenWarps : 0;
+    a.gen_slices = g->gen_slices;
     a.mtring = g->d_mtring;
     a.mtpos = g->d_mtpos;
     a.sweep_threads = g->T;

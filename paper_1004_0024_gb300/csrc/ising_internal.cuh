@@ -106,6 +106,7 @@ struct SweepArgs {
     // write the next sweep's words into a two-sweep buffer (wbuf, parity of
     // the sweep) while the block's sweep_threads threads run the current one
     int gen;
+    int gen_slices;  // MT19937: slices the generator stages per column store (4, or 2 to save shared memory; 0 = 4)
     uint32_t* mtring;
     unsigned long long* mtpos;
     int sweep_threads;

@@ -115,7 +115,7 @@ __host__ __device__ inline PackedLayout packed_layout(const SweepArgs& a, int th
     }
     if (a.gen && a.rng == 0) {  // the MT19937 generator's stream ring and four staged slices
         L.gring = o; o += 4u * kMtRing;
-        L.gstg = o;  o += 16u * uint32_t(a.S);
+        L.gstg = o;  o += 4u * (a.gen_slices == 2 ? 2u : 4u) * uint32_t(a.S);
     }
     L.total = o;
     return L;
@@ -461,8 +461,9 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
     auto gen_sync = [&]() { asm volatile("bar.sync 2, %0;" ::"r"(GL) : "memory"); };
     auto gen_sweep = [&](uint32_t* wdst) {
         const int lane = glane;
-        for (int t0 = 0; t0 < M; t0 += 4) {
-            const int group = 4 * S;
+        const int G = a.gen_slices == 2 ? 2 : 4;  // slices staged per column store
+        for (int t0 = 0; t0 < M; t0 += G) {
+            const int group = G * S;
             for (int base = 0; base < group; base += kMtStep) {
                 const int cnt = min(kMtStep, group - base);
                 // the thread's (up to) 4 words of the step: their inputs first (all
@@ -488,10 +489,17 @@ __device__ __forceinline__ void packed_body(const SweepArgs& a, const int blk, c
                 }
                 gen_sync();
             }
-            // column q gets the words of slices t0 .. t0 + 3 as one 16-byte store
-            for (int q = lane; q < S; q += GL)
-                *reinterpret_cast<uint4*>(wdst + (size_t(r) * S + pos[q]) * a.Mp + t0) =
-                    make_uint4(gstg[q], gstg[S + q], gstg[2 * S + q], gstg[3 * S + q]);
+            // column q gets the words of slices t0 .. t0 + G - 1 as one 16-byte
+            // (or 8-byte) store
+            if (G == 4) {
+                for (int q = lane; q < S; q += GL)
+                    *reinterpret_cast<uint4*>(wdst + (size_t(r) * S + pos[q]) * a.Mp + t0) =
+                        make_uint4(gstg[q], gstg[S + q], gstg[2 * S + q], gstg[3 * S + q]);
+            } else {
+                for (int q = lane; q < S; q += GL)
+                    *reinterpret_cast<uint2*>(wdst + (size_t(r) * S + pos[q]) * a.Mp + t0) =
+                        make_uint2(gstg[q], gstg[S + q]);
+            }
             gen_sync();
             gw += uint32_t(group);
         }
