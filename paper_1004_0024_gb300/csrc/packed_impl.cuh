@@ -16,12 +16,13 @@
 //
 // Per level a thread only does the items of its busy slots: six neighbour
 // words, the random word, the decision, and on a flip one store of the
-// column word.  Everything else
-// happens every fourth level, at the same level for every thread (no
-// divergence): at a level l divisible by 4, before its items, a slot whose
-// column has ended moves on to its next column (descriptor from shared
-// memory); after the items, the word block of the slot that starts in levels
-// [l + 8, l + 12) is requested.
+// column word (the level loop is unrolled by four).  Everything else happens
+// every fourth level, at the same level for every thread (no divergence): at
+// a level l divisible by 4, before its items, a slot whose next column starts
+// in [l, l + 4) takes it up (one 64-byte descriptor from shared memory) and
+// the word block fetched four levels earlier goes into the ring; after the
+// items, the slot fetches its next word block.  The column words are placed
+// in banks by the host so that a level's neighbour loads spread over them.
 //
 // Fields by gathering.  A visit computes the spatial field from the
 // neighbours' column bits, f_space = (h_q - sum_j J_qj) + sum_j 2 J_qj b_j(t),
@@ -39,7 +40,8 @@
 // it sees the value of the sequential sweep: updated for a lower-indexed
 // neighbour (visited at an earlier level), not yet for a higher-indexed one.
 // The Trotter part of the field, Jtau (s_{t-1} + s_{t+1}), comes from the
-// owner's register bits.
+// owner's register bits: the bits of a slice mask rotated by one each level
+// and by one either way for the ring neighbours.
 //
 // Random words go through a ring of 16 levels per slot in shared memory: the
 // word of the slot's item at level l sits at (l mod 16) NSP + sl, so a
@@ -55,13 +57,14 @@
 // ten rounds spread over four levels (3, 3, 3, 1), and stored after the
 // fourth.  An entry is written after the last item that reads it.
 //
-// MT19937 words are generated inside the kernel: after its T sweep threads a
-// block has `gen` more warps (two), which advance the replica's stream (its
-// ring of 1024 words in shared memory; 227 consecutive words of the stream
-// depend only on earlier ones and are computed in parallel) and write the
-// next sweep's words into a two-sweep buffer in global memory (in L2 for a
-// resident ladder), four slices at a time staged in shared memory and then
-// one 16-byte store per column.  The sweep threads synchronise levels with a
+// The words are generated inside the kernel: after its T sweep threads a
+// block has `gen` more warps (two), which write the next sweep's words into a
+// two-sweep buffer in global memory (in L2 for a resident ladder).  MT19937:
+// they advance the replica's stream (its ring of 1024 words in shared memory;
+// 227 consecutive words of the stream depend only on earlier ones and are
+// computed in parallel), four slices at a time (two where shared memory is
+// short) staged in shared memory and then one 16-byte (8-byte) store per
+// column.  Philox: one call per column and 4-slice block.  The sweep threads synchronise levels with a
 // barrier of their own; block-wide barriers at the start and end of a sweep
 // hand a buffer half from the generator to the sweep threads and back.
 //
